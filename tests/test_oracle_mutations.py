@@ -1,0 +1,89 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case below plants one mistake (a dropped term, a wrong sign or index, a
+swapped operand) in a temporary copy of the oracle, rebuilds it, and runs
+the oracle pin tests against that copy.  The test passes when the pins fail.
+Mistakes are planted only in the CPU oracle, never in GPU code.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (file, original text, planted text, what it breaks, pin files expected to catch it)
+MUTATIONS = [
+    ("mc_history.inc", "if (r1 <= (RC(1) + ta) / (RC(9) + ta)) {", "if (r1 <= (RC(1) + ta) / (RC(8) + ta)) {",
+     "Kahn branch probability", "test_oracle_sampling.py"),
+    ("mc_history.inc", "if (r3 <= RC(0.5) * (ct * ct + RC(1) / x)) break;", "if (r3 <= RC(0.5) * (ct * ct + x)) break;",
+     "Kahn second-branch acceptance", "test_oracle_sampling.py"),
+    ("mc_history.inc", "nw_ = w * ct - st * t * cp;", "nw_ = w * ct + st * t * cp;",
+     "rotation sign", "test_oracle_sampling.py"),
+    ("mc_history.inc", "*sp = RC(2) * a * b / r2;", "*sp = RC(2) * a * a / r2;",
+     "azimuth sine", "test_oracle_sampling.py"),
+    ("mc_history.inc", "if (RC(2) * b <= RC(1) + mu * mu) return mu;", "if (b <= RC(1) + mu * mu) return mu;",
+     "Thomson acceptance", "test_oracle_sampling.py"),
+    ("mc_history.inc", "w0[a] = RC(1) - t; w1[a] = t;", "w0[a] = t; w1[a] = RC(1) - t;",
+     "trilinear weights swapped", "test_oracle_transport.py"),
+    ("mc_history.inc", "REAL c1 = muR, c2 = c1 + muC, c3 = c2 + muP;", "REAL c1 = muR, c2 = c1 + muP, c3 = c2 + muC;",
+     "interaction channels swapped", "test_oracle_transport.py"),
+    ("mc_history.inc", "REAL s = -LOGR(xi_s) / mumax;", "REAL s = -LOGR(xi_s) / (RC(0.9) * mumax);",
+     "free path scale", "test_oracle_transport.py"),
+    ("mc_history.inc", "rho_m[p->material[v]] += w * (REAL)p->density[v];", "rho_m[p->material[v]] = w * (REAL)p->density[v];",
+     "dropped corner terms", "test_oracle_transport.py"),
+    ("mc_history.inc", "int64_t iy = cy ? i1[1] : i0[1];", "int64_t iy = cy ? i1[0] : i0[0];",
+     "wrong corner index", "test_oracle_transport.py"),
+    ("mc_history.inc", "REAL fu = au * GEO(idu) + GEO(hu);", "REAL fu = -au * GEO(idu) + GEO(hu);",
+     "detector u axis flipped", "test_oracle_transport.py"),
+    ("mc_history.inc", "scattered = 1;\n                r.n_rayleigh++;", "r.n_rayleigh++;",
+     "Rayleigh not marked as scatter", "test_oracle_transport.py"),
+    ("mc_history.inc", "r.e_deposited += (double)e - (double)e2;", "r.e_deposited += (double)e;",
+     "energy ledger", "test_oracle_transport.py"),
+    ("gdrr_oracle.c", "if (xi <= cdf[mid]) hi = mid; else lo = mid + 1;", "if (xi < cdf[mid]) hi = mid; else lo = mid + 1;",
+     "inverse-CDF boundary (harmless for continuous xi, must NOT be required)", None),
+    ("gdrr_oracle.c", "uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;", "uint32_t n2 = (uint32_t)(p0 >> 32) ^ c1 ^ k1;",
+     "Philox round word", "test_oracle_rng.py"),
+    ("gdrr_oracle.c", "k1 += 0xBB67AE85u;", "k1 += 0x9E3779B9u;",
+     "Philox key schedule", "test_oracle_rng.py"),
+    ("gdrr_oracle.c", "float poly = (float)(1.0 / 3.0) + s2 * ((float)(1.0 / 5.0)", "float poly = (float)(1.0 / 3.0) + s2 * ((float)(1.0 / 6.0)",
+     "log series term", "test_oracle_rng.py"),
+    ("gdrr_oracle.c", "major[e] = (float)(mx * (1.0 + 1e-5));", "major[e] = (float)(mx * 0.8);",
+     "majorant below mu", "test_oracle_transport.py"),
+    ("gdrr_oracle.c", "rad += dl * orc_mu_at(&c, x, &mu_e[(size_t)b * p->n_mat]);", "rad += 0.5 * orc_mu_at(&c, x, &mu_e[(size_t)b * p->n_mat]);",
+     "ray-tracing interval length", "test_oracle_rt.py"),
+    ("gdrr_oracle.c", "double tt = tmin + (s + 0.5) * dl, x[3];", "double tt = tmin + s * dl, x[3];",
+     "interval end point instead of midpoint", "test_oracle_rt.py"),
+    ("oracle.py", "sigma - (1.0 / beta) * (1.0 - s_hat / s)", "sigma - (1.0 / beta) * (1.0 - s / s_hat)",
+     "denoiser fidelity term", "test_oracle_image.py"),
+    ("oracle.py", "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[:-2, 1:-1]\n        s = ",
+     "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[1:-1, 1:-1]\n        s = ",
+     "denoiser stencil", "test_oracle_image.py"),
+    ("oracle.py", "return n_hat * np.sqrt(float(n_sim) / (zeta * mas))", "return n_hat * np.sqrt(float(n_sim) * (zeta * mas))",
+     "noise scaling", "test_oracle_image.py"),
+]
+
+
+def _run_pins(tmp, pin_file):
+    env = dict(os.environ)
+    env["PYTHONPATH"] = ROOT
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", os.path.join("tests", pin_file)]
+    return subprocess.run(cmd, cwd=tmp, env=env, capture_output=True, text=True, timeout=600)
+
+
+@pytest.mark.parametrize("case", [m for m in MUTATIONS if m[4]], ids=lambda m: m[3])
+def test_pins_catch_planted_mistake(case, tmp_path):
+    fname, old, new, _, pin_file = case
+    tmp = str(tmp_path)
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(tmp, "oracle"),
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(tmp, "tests"),
+                    ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
+    path = os.path.join(tmp, "oracle", fname)
+    src = open(path).read()
+    assert src.count(old) == 1, f"mutation anchor not unique in {fname}: {old!r}"
+    open(path, "w").write(src.replace(old, new))
+    res = _run_pins(tmp, pin_file)
+    assert res.returncode != 0, f"pins in {pin_file} did not catch: {case[3]}\n{res.stdout[-2000:]}"
