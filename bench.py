@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the gDRR projection path on GB300.
+
+Workload: the 2 mm ellipsoid torso (256x256x128 voxels, uint8 material +
+FP32 density), 120 kVp Kramers spectrum with 2.5 mm Al, aluminium bowtie
+0-30 mm, 512x384 detector of 0.776 mm pixels, CsI-like response, 1e8 photon
+histories per projection.  One step = one whole projection, Steps 1-4:
+ray-traced primary, Monte Carlo primary + scatter, tally finalisation,
+4x4 scatter binning, Poisson denoising (Eq. 5), upsampling, noise scaling.
+
+Metric: photon histories per second (and seconds per projection).
+Multi-GPU (torchrun): each rank simulates its own projection angle of a scan
+(independent work, no data-path collective): weak scaling.
+
+--impl reference runs the CPU oracle on the host cores instead (bounded
+samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MC photon histories/s and s/projection, 2 mm torso 120 kVp; batched vs plain"
+UNIT = "histories/s"
+WORKLOAD = "torso-256x256x128-2mm, 120kVp Kramers+2.5mmAl, Al bowtie 0-30mm, 512x384 det 0.776mm, CsI response, 1e8 histories"
+BYTES_PER_STEP_ALGO = 8 * 5          # 8 corner voxels x (1 B material + 4 B density) per Woodcock step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--histories", type=float, default=1e8)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(prob, target_s, threads, seed=1):
+    """Histories/s of the CPU oracle (FP32 transport, the parity reference) on
+    a bounded sample of the same workload: first history ids of the stream."""
+    import oracle
+    oracle.build()
+    n = 20000
+    t0 = time.perf_counter()
+    oracle.mc_run(prob, n, seed=seed, threads=threads)
+    dt = time.perf_counter() - t0
+    n2 = int(max(n, min(5e7, n * target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.mc_run(prob, n2, seed=seed, threads=threads)
+    dt2 = time.perf_counter() - t0
+    return n2 / dt2, n2, dt2
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1204_6367_gb300 import inputs
+    import oracle
+    oracle.build()
+    prob = inputs.torso_problem()
+    threads = os.cpu_count() or 1
+    # each step: a bounded sample of the projection's histories, sized so the
+    # whole --steps/--warmup run stays within a few minutes
+    probe = 20000
+    t0 = time.perf_counter()
+    oracle.mc_run(prob, probe, seed=1, threads=threads)
+    rate0 = probe / (time.perf_counter() - t0)
+    per_step = int(max(probe, min(2e7, rate0 * 150.0 / max(1, args.steps + args.warmup))))
+    for w in range(args.warmup):
+        oracle.mc_run(prob, per_step, seed=1, history_offset=w * per_step, threads=threads)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.mc_run(prob, per_step, seed=1, history_offset=(args.warmup + k) * per_step, threads=threads)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = per_step * args.steps / tot
+    sample = f"{per_step} histories per step of the 1e8-history projection (history ids in order), FP32 oracle"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "s_per_projection": args.histories / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "histories_per_projection": int(args.histories),
+                   "l2": "oracle runs on host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_1204_6367_gb300 import gdrr, inputs
+    gdrr.lib()
+    prob = inputs.torso_problem()
+    n_hist = int(args.histories)
+    angle = 2.0 * math.pi * rank / max(world, 1)     # one projection angle per rank
+    seed = 1
+    stream = torch.cuda.current_stream()
+    ctx = gdrr.Context(prob, stream)
+    npix = prob.nu * prob.nv
+    iters = 300
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+    stats = torch.zeros(gdrr.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+
+    def step(stats_buf):
+        return gdrr.project(ctx, n_hist, seed, angle, bin_factor=4, beta=0.02, iters=iters, stats=stats_buf)
+
+    # count scale needs one host read of the scatter photon count; take it from
+    # a warm-up projection so the timed step stays asynchronous
+    for _ in range(max(args.warmup, 3)):
+        stats.zero_()
+        out = step(stats)
+    torch.cuda.synchronize()
+    st = gdrr.stats_dict(stats)
+    steps_per_proj = st["steps"]
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev_mc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def timed_step(k):
+        # the whole hot path, Steps 1-4, with the MC launch bracketed separately
+        P = gdrr.gdrr_raytrace_primary(ctx, angle)
+        ev_mc[k][0].record(stream)
+        prim, scat = gdrr.gdrr_mc_project(ctx, n_hist, seed, angle, stats=stats)
+        ev_mc[k][1].record(stream)
+        P_hat = gdrr.gdrr_finalize(ctx, prim, n_hist)
+        S_hat = gdrr.gdrr_finalize(ctx, scat, n_hist)
+        S_hat_c = gdrr.gdrr_finalize(ctx, gdrr.gdrr_bin_tally(ctx, scat, 4), n_hist)
+        S_c = gdrr.gdrr_denoise_scatter(ctx, S_hat_c, count_scale, 0.02, 0.8, iters)
+        S = gdrr.gdrr_upsample(ctx, S_c, 4)
+        return gdrr.gdrr_noise_calibrate(ctx, P_hat, P, S_hat, S, n_hist, 0.4, 5.2913e9)
+
+    count_scale = float(out["S_hat"].sum().item()) / max(1, st["tally_scatter"])
+    launches_per_step = 1 + 1 + 3 + 1 + (iters + 2) + 1 + 1
+
+    clocks = ClockSampler(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                     # evict L2 between timed iterations
+        ev[k][0].record(stream)
+        timed_step(k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    mc_ms = [a.elapsed_time(b) for a, b in ev_mc]
+    tot_ms = sum(step_ms)
+    t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot_ms = float(t.item())
+
+    # end to end through the public API: inputs from pinned host memory
+    # (gdrr_create stages phantom and tables), one projection, results read
+    # back to host (P, P^, S^, S, N)
+    e2e = None
+    if not args.no_e2e:
+        pinned = {}
+        for name in ("material", "density", "mu_hat", "spec_e", "spec_w", "fluence", "response"):
+            a = np.ascontiguousarray(getattr(prob, name))
+            t_pin = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            t_pin.numpy()[...] = a
+            pinned[name] = t_pin
+        import copy
+        hp = copy.copy(prob)
+        for name, t_pin in pinned.items():
+            setattr(hp, name, t_pin.numpy())
+        h2d = sum(t_pin.numel() * t_pin.element_size() for t_pin in pinned.values())
+        host_out = [torch.empty((prob.nv, prob.nu), dtype=torch.float64, pin_memory=True) for _ in range(5)]
+        d2h = sum(h.numel() * h.element_size() for h in host_out)
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            with gdrr.Context(hp, stream) as c2:
+                o = gdrr.project(c2, n_hist, seed, angle, beta=0.02, iters=iters)
+                for h, key in zip(host_out, ("P", "P_hat", "S_hat", "S", "N")):
+                    h.copy_(o[key], non_blocking=True)
+                torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": n_hist * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "s_per_projection": e2e_s}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    mc_avg_s = statistics.mean(mc_ms) / 1e3
+    algo_bytes = steps_per_proj * BYTES_PER_STEP_ALGO
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = algo_bytes / mc_avg_s / 1e9
+    value = n_hist * world * args.steps / (tot_ms / 1e3)
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "mc_transport_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, n_s, dt = cpu_oracle_rate(prob, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {n_s} histories of the 1e8-history projection, FP32 oracle, {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "s_per_projection": tot_ms / args.steps / 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "histories_per_projection": n_hist, "angle_rad": angle,
+                   "woodcock_steps_per_projection": steps_per_proj, "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"one projection angle per GPU x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "mc_kernel",
+                     "mc_ms": statistics.mean(mc_ms),
+                     "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} steps"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,256 @@
+/*
+ * gdrr.h -- C ABI of the GB300 gDRR projection library (libgdrr.so).
+ *
+ * gDRR (Jia et al., arXiv:1204.6367) computes a cone-beam CT projection as
+ * primary P(u), scatter S(u) and noise N(u) (Section 2.2, Fig. 3):
+ *   Step 1  ray-traced primary                      gdrr_raytrace_primary
+ *   Step 2  Monte Carlo primary and scatter tallies  gdrr_mc_project[_batched]
+ *           and their conversion to signal           gdrr_finalize
+ *   Step 3  Poisson denoising of the scatter         gdrr_denoise_scatter
+ *   Step 4  noise N = alpha (N_P + N_S), zeta fit    gdrr_noise_calibrate, gdrr_fit_zeta
+ *
+ * Conventions for every call:
+ *  - Units: lengths mm, energies keV, density g/cm^3, mass attenuation cm^2/g.
+ *  - Host input structs and arrays are borrowed for the duration of the call
+ *    and deep-copied by gdrr_create; the caller may free them afterwards.
+ *  - Pointers named *_dev are device pointers owned by the caller (for example
+ *    torch tensors); every kernel runs on the context's stream and the call
+ *    returns without synchronising unless stated.  Results are valid after the
+ *    stream is synchronised (gdrr_sync does that and reports kernel errors).
+ *  - Images are row-major [nv][nu] (u fastest).  The phantom is x-fastest:
+ *    index = x + nx * (y + ny * z), box centred on the isocentre.
+ *  - Return value: GDRR_OK (0) or a negative GDRR_ERR_* code; no call throws.
+ *    A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GDRR_H
+#define GDRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GDRR_API __attribute__((visibility("default")))
+#else
+#define GDRR_API
+#endif
+
+enum {
+    GDRR_OK = 0,
+    GDRR_ERR_INVALID_ARG = -1,   /* a size, pointer or value is out of range      */
+    GDRR_ERR_CUDA = -2,          /* a CUDA runtime call failed                     */
+    GDRR_ERR_OOM = -3,           /* device allocation failed                       */
+    GDRR_ERR_TALLY_OVERFLOW = -4,/* an int64 tally would exceed its headroom       */
+    GDRR_ERR_STEP_LIMIT = -5,    /* histories hit the free-flight limit            */
+    GDRR_ERR_UNSUPPORTED = -6    /* valid input this build does not handle         */
+};
+
+/* Maximum number of materials the transport kernels handle. */
+#define GDRR_MAX_MATERIALS 8
+/* Fixed-point tally unit: 2^-GDRR_TALLY_BITS keV per count. */
+#define GDRR_TALLY_BITS 24
+
+typedef struct gdrr_ctx gdrr_ctx;
+
+/* Scanner geometry, Section 2.1 / Fig. 1: the source rotates in the xOy plane
+ * at distance sad_mm from the isocentre O, at angle phi between SO and +x; the
+ * imager is perpendicular to xOy and to OP, at AID = sdd_mm - sad_mm from O,
+ * with theta_rad the angle between SO and OP (0: opposite the source).  The
+ * detector frame (u, v) has its origin at P, v parallel to z, u = OP x z
+ * normalised; nu x nv pixels of du_mm x dv_mm centred on P. */
+typedef struct {
+    double sad_mm, sdd_mm, theta_rad;
+    int32_t nu, nv;
+    double du_mm, dv_mm;
+} gdrr_geometry;
+
+/* Voxel phantom, Section 2.1: a material index i(x) and a density rho(x) per
+ * voxel.  Densities must be finite and >= 0; indices < n_materials. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx_mm, dy_mm, dz_mm;
+    const uint8_t* material;   /* host, nx*ny*nz */
+    const float* density;      /* host, nx*ny*nz, g/cm^3 */
+} gdrr_phantom;
+
+/* Mass attenuation mu_hat_k(i, E) of each material, Section 2.1, for
+ * k = 0 Rayleigh, 1 Compton, 2 photoelectric, tabulated on the energy grid
+ * e0_kev + j * de_kev, j < n_energies (linear interpolation between nodes).
+ * Layout [n_materials][3][n_energies], cm^2/g, host. */
+typedef struct {
+    int32_t n_materials, n_energies;
+    double e0_kev, de_kev;
+    const float* mu_hat;
+} gdrr_materials;
+
+/* Source spectrum phi(E) after the bowtie, Section 2.1: n_bins energy
+ * channels (keV) and non-negative weights (normalised by the library). */
+typedef struct {
+    int32_t n_bins;
+    const double* energy_kev;
+    const double* weight;
+} gdrr_spectrum;
+
+/* Photon fluence map w(u) after the bowtie, Section 2.1: the probability of
+ * a source photon heading for each detector pixel, [nv][nu], non-negative,
+ * normalised by the library. */
+typedef struct {
+    const double* fluence;
+} gdrr_bowtie;
+
+/* Detector response r(E), Section 2.1: energy (keV) recorded for an incoming
+ * photon of energy E, tabulated on r0_kev + j * dr_kev (linear interpolation). */
+typedef struct {
+    int32_t n_energies;
+    double e0_kev, de_kev;
+    const float* response;
+} gdrr_detector;
+
+/* Transport options (defaults in brackets).  Zero means "default". */
+typedef struct {
+    double e_cut_kev;          /* absorb photons below this energy [1.0]           */
+    int32_t max_steps;         /* free flights per history before giving up [1e5]  */
+    int32_t block_size;        /* threads per block, multiple of 32 [256]           */
+    int32_t blocks_per_sm;     /* resident blocks per SM for the persistent grid [by occupancy] */
+    int32_t hist_per_thread;   /* histories a warp claims per lane at a time [8]    */
+    int32_t refill_interval;   /* steps between refills of finished lanes [1]       */
+} gdrr_mc_options;
+
+/* Transport counters, accumulated by every gdrr_mc_project* call (device
+ * array of GDRR_NSTATS uint64 in this order). */
+enum {
+    GDRR_ST_HISTORIES = 0, GDRR_ST_STEPS, GDRR_ST_VIRTUAL, GDRR_ST_RAYLEIGH, GDRR_ST_COMPTON,
+    GDRR_ST_PHOTO, GDRR_ST_TALLY_PRIMARY, GDRR_ST_TALLY_SCATTER, GDRR_ST_MISS, GDRR_ST_CUTOFF,
+    GDRR_ST_STEP_LIMIT, GDRR_NSTATS
+};
+
+/* Per-history event record (tiny parity runs only). outcome: 0 primary tally,
+ * 1 scatter tally, 2 photoelectric absorption, 3 energy cut-off, 4 missed the
+ * detector, 5 step limit.  first_interaction: 0 none, 1 Rayleigh, 2 Compton,
+ * 3 photoelectric.  rng_blocks: Philox blocks the history consumed. */
+typedef struct {
+    uint32_t n_steps, n_virtual, n_rayleigh, n_compton;
+    uint32_t n_photo, outcome, rng_blocks, first_interaction;
+    int32_t pixel;
+    float e_source, e_final;
+    uint32_t pad;
+    double e_deposited;
+} gdrr_history_record;
+
+/* Create a context: validates and deep-copies the inputs, stages the phantom
+ * and tables on the current CUDA device, and binds cuda_stream (a
+ * cudaStream_t; NULL = the legacy default stream) to every later call.
+ * Fails with GDRR_ERR_INVALID_ARG when an input is inconsistent (sizes,
+ * negative weights, material index out of range, imager plane cutting the
+ * phantom box), GDRR_ERR_UNSUPPORTED for more than GDRR_MAX_MATERIALS
+ * materials.  *out is set only on success.  Follows Section 2.1 (inputs) and
+ * Section 4 (the package takes phantom, geometry, source and detector). */
+GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phantom,
+                         const gdrr_materials* materials, const gdrr_spectrum* spectrum,
+                         const gdrr_bowtie* bowtie, const gdrr_detector* detector,
+                         void* cuda_stream, gdrr_ctx** out);
+
+/* Release every device buffer of the context (synchronises its stream). */
+GDRR_API void gdrr_destroy(gdrr_ctx* ctx);
+
+/* Static description of an error code. */
+GDRR_API const char* gdrr_error_string(int code);
+
+/* Set / read transport options; invalid values give GDRR_ERR_INVALID_ARG. */
+GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* options);
+GDRR_API int gdrr_get_options(const gdrr_ctx* ctx, gdrr_mc_options* options);
+
+/* Synchronise the context stream; returns GDRR_ERR_CUDA on a kernel fault. */
+GDRR_API int gdrr_sync(gdrr_ctx* ctx);
+
+/* Step 1, Section 2.3, Eq. 1: P(u) = w(u) sum_E phi(E) r(E) exp(-int mu dl)
+ * for the ray from the source to each pixel centre at gantry angle
+ * angle_rad.  The ray inside the phantom box is cut into equal intervals no
+ * longer than half the smallest voxel size, mu taken at interval midpoints
+ * with the trilinear field.  P_dev: caller-owned device double[nv*nu],
+ * overwritten, per source photon (keV). */
+GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_dev);
+
+/* Step 2, Section 2.4: transport n_photons source photons with Woodcock
+ * tracking, photoelectric / Compton (Klein-Nishina) / Rayleigh (Thomson)
+ * interactions, and tally r(E) at the detector pixel each escaping photon
+ * hits, into the primary counter when it never scattered, else the scatter
+ * counter.  History h (h = history_offset .. history_offset + n_photons - 1)
+ * draws from Philox4x32-10 with key = seed, counter = (block, angle_index,
+ * h lo, h hi), so any split of the history range sums to the same tallies.
+ * prim_dev / scat_dev: caller-owned device int64[nv*nu], ACCUMULATED (not
+ * cleared) in units of 2^-24 keV.  stats_dev: NULL or device
+ * uint64[GDRR_NSTATS], accumulated.  records_dev: NULL or device
+ * gdrr_history_record[n_photons], written (debug / parity use; slower). */
+GDRR_API int gdrr_mc_project(gdrr_ctx* ctx, double angle_rad, uint32_t angle_index,
+                             uint64_t n_photons, uint64_t seed, uint64_t history_offset,
+                             int64_t* prim_dev, int64_t* scat_dev, uint64_t* stats_dev,
+                             gdrr_history_record* records_dev);
+
+/* Step 2 for a multi-angle scan in one persistent launch: angle a
+ * (a < n_angles) at angles_rad[a] (host) transports budgets[a] (host)
+ * histories with angle_index = a and history ids 0 .. budgets[a]-1, so each
+ * angle's tallies equal gdrr_mc_project(angle_index = a, history_offset = 0).
+ * prim_dev / scat_dev: device int64[n_angles][nv*nu], accumulated.
+ * stats_dev: NULL or device uint64[GDRR_NSTATS], accumulated over angles. */
+GDRR_API int gdrr_mc_project_batched(gdrr_ctx* ctx, int32_t n_angles, const double* angles_rad,
+                                     const uint64_t* budgets, uint64_t seed, int64_t* prim_dev,
+                                     int64_t* scat_dev, uint64_t* stats_dev);
+
+/* Tally -> signal per source photon in FP64 (Section 2.6: MC results are
+ * normalised by the number of source photons): out = tally * 2^-24 / n_photons.
+ * n elements; tally_dev int64, signal_dev double, both caller-owned device.
+ * Fails with GDRR_ERR_TALLY_OVERFLOW (after a stream sync) if any tally is
+ * negative, which only an int64 wrap-around can produce. */
+GDRR_API int gdrr_finalize(gdrr_ctx* ctx, const int64_t* tally_dev, int64_t n,
+                           uint64_t n_photons, double* signal_dev);
+
+/* Exact integer factor x factor binning of a [nv][nu] int64 tally to
+ * [nv/factor][nu/factor] (the coarse scatter grid); nu, nv multiples of factor. */
+GDRR_API int gdrr_bin_tally(gdrr_ctx* ctx, const int64_t* tally_dev, int32_t nu, int32_t nv,
+                            int32_t factor, int64_t* out_dev);
+
+/* Bilinear interpolation of a coarse [cv][cu] image (a factor x factor binned
+ * sum) to the fine [cv*factor][cu*factor] grid, divided by factor^2.  Coarse
+ * pixel centres sit at fine coordinate (I + 1/2) factor - 1/2; edges clamp. */
+GDRR_API int gdrr_upsample(gdrr_ctx* ctx, const double* coarse_dev, int32_t cu, int32_t cv,
+                           int32_t factor, double* fine_dev);
+
+/* Step 3, Section 2.5, Eq. 2-5: denoise a Poisson-noisy scatter image by
+ *   S <- (1 - omega) S + omega/4 [Sigma S - (1/beta)(1 - S^/S)]
+ * for iters iterations from S = max(S^, eps), every term using the previous
+ * iterate, replicate edges, S kept >= eps = 1e-3 counts.  The iteration runs
+ * on the count scale: S^ / count_scale (count_scale > 0 is the signal of one
+ * detected photon); the result is returned on the input scale.  The paper uses
+ * omega = 0.8.  It is stable while beta * S > omega / (4 (2 - omega)) in
+ * counts.  S_hat_dev, S_dev: caller-owned device double[nv*nu]. */
+GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double* S_dev,
+                                  int32_t nu, int32_t nv, double count_scale, double beta,
+                                  double omega, int32_t iters);
+
+/* Step 4, Section 2.6, Eq. 4 and the scaling equation that follows it:
+ * N = ((P^ - P) + (S^ - S)) sqrt(n_sim / (zeta * mAs)), element-wise over n
+ * pixels; all arrays caller-owned device double. */
+GDRR_API int gdrr_noise_calibrate(gdrr_ctx* ctx, const double* P_hat_dev, const double* P_dev,
+                                  const double* S_hat_dev, const double* S_dev, int64_t n,
+                                  uint64_t n_sim, double mAs, double zeta, double* N_dev);
+
+/* Step 4 calibration, Section 2.6: fit sigma_X / sigma_N^ = k / sqrt(I)
+ * (least squares through the origin) over n host points, zeta = n_sim / k^2.
+ * Host-only; zeta_out and k_out are host pointers (k_out may be NULL). */
+GDRR_API int gdrr_fit_zeta(const double* inv_sqrt_mAs, const double* ratio, int32_t n,
+                           uint64_t n_sim, double* zeta_out, double* k_out);
+
+/* Parity hook: the Philox words of n_hist history streams (ids hid0 ..),
+ * n_blocks blocks each, exactly as the transport draws them.  out_dev:
+ * device uint32[n_hist][4 * n_blocks].  Runs on cuda_stream. */
+GDRR_API int gdrr_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid0, int32_t n_hist,
+                               int32_t n_blocks, uint32_t* out_dev, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDRR_H */

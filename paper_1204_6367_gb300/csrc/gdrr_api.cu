@@ -1,0 +1,550 @@
+// Host side of libgdrr: the C ABI declared in include/gdrr.h.
+//
+// gdrr_create validates and deep-copies the inputs of Section 2.1, builds the
+// derived tables on the host in FP64 (material coefficients in mm^-1, the
+// Woodcock majorant, inverse-CDF tables of the fluence map and spectrum, the
+// ray-tracing channel tables) and stages them in device memory.  Every other
+// call only enqueues kernels on the context stream.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "gdrr_internal.cuh"
+
+using namespace gdrr;
+
+struct gdrr_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int n_sm = 0;
+    // inputs (host copies of the scalars)
+    gdrr_geometry geo{};
+    int nx = 0, ny = 0, nz = 0;
+    double vox[3] = {0, 0, 0};
+    int n_mat = 0, n_e = 0, n_r = 0, n_bins = 0;
+    double e0 = 0, de = 0, r0 = 0, dr = 0;
+    // staged device data
+    uint8_t* d_mat = nullptr;
+    float* d_dens = nullptr;
+    float* d_tab = nullptr;
+    float* d_major = nullptr;
+    float* d_resp = nullptr;
+    float* d_bin_e = nullptr;
+    double* d_cdf_pix = nullptr;
+    int* d_guide_pix = nullptr;
+    double* d_cdf_e = nullptr;
+    int* d_guide_e = nullptr;
+    double* d_wnorm = nullptr;
+    float* d_mu_rt = nullptr;
+    float* d_wr = nullptr;
+    int n_guide_pix = 0, n_guide_e = 0;
+    // scratch owned by the context
+    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_stats = nullptr;   // used when the caller passes none
+    int* d_flag = nullptr;
+    Job* d_jobs = nullptr;
+    int jobs_cap = 0;
+    double* d_denoise = nullptr;
+    size_t denoise_cap = 0;
+    gdrr_mc_options opt{};
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return GDRR_OK;
+    return e == cudaErrorMemoryAllocation ? GDRR_ERR_OOM : GDRR_ERR_CUDA;
+}
+
+#define TRY_CUDA(x)                               \
+    do {                                          \
+        cudaError_t _e = (x);                     \
+        if (_e != cudaSuccess) return cuda_err(_e); \
+    } while (0)
+
+template <typename T>
+int upload(T** dst, const T* src, size_t n, cudaStream_t s) {
+    TRY_CUDA(cudaMalloc((void**)dst, std::max<size_t>(n, 1) * sizeof(T)));
+    if (n) TRY_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return GDRR_OK;
+}
+
+// Inverse-CDF table of non-negative weights: running FP64 sum, divided by the
+// total (last entry exactly 1).  Empty vector on invalid weights.
+std::vector<double> build_cdf(const double* w, int n) {
+    std::vector<double> c(n);
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(w[i] >= 0.0) || !std::isfinite(w[i])) return {};
+        s += w[i];
+        c[i] = s;
+    }
+    if (!(s > 0.0)) return {};
+    for (int i = 0; i < n; ++i) c[i] = c[i] / s;
+    return c;
+}
+
+// Guide table: g[i] = first j with cdf[j] >= i / G (a starting point only;
+// the device search corrects it in both directions).
+std::vector<int> build_guide(const std::vector<double>& cdf, int G) {
+    std::vector<int> g(G);
+    int j = 0;
+    const int n = (int)cdf.size();
+    for (int i = 0; i < G; ++i) {
+        const double t = (double)i / (double)G;
+        while (j < n - 1 && cdf[j] < t) ++j;
+        g[i] = j;
+    }
+    return g;
+}
+
+// The imager frame at gantry angle phi (Fig. 1), computed in FP64, stored FP32.
+Frame make_frame(const gdrr_geometry& g, double phi) {
+    const double ang = phi + g.theta_rad, aid = g.sdd_mm - g.sad_mm;
+    const double S[3] = {-g.sad_mm * cos(phi), -g.sad_mm * sin(phi), 0.0};
+    const double n[3] = {cos(ang), sin(ang), 0.0};
+    const double P[3] = {aid * cos(ang), aid * sin(ang), 0.0};
+    const double eu[3] = {sin(ang), -cos(ang), 0.0};
+    const double ev[3] = {0.0, 0.0, 1.0};
+    Frame f;
+    for (int k = 0; k < 3; ++k) {
+        f.S[k] = (float)S[k]; f.n[k] = (float)n[k]; f.P[k] = (float)P[k];
+        f.eu[k] = (float)eu[k]; f.ev[k] = (float)ev[k];
+    }
+    return f;
+}
+
+// The source must be outside the voxel box and the whole box (and source)
+// strictly on the source side of the imager plane.
+bool geometry_ok(const gdrr_ctx* c, double phi) {
+    const double ang = phi + c->geo.theta_rad, aid = c->geo.sdd_mm - c->geo.sad_mm;
+    const double S[3] = {-c->geo.sad_mm * cos(phi), -c->geo.sad_mm * sin(phi), 0.0};
+    const double n[3] = {cos(ang), sin(ang), 0.0};
+    const double P[3] = {aid * cos(ang), aid * sin(ang), 0.0};
+    const int dims[3] = {c->nx, c->ny, c->nz};
+    double lo[3], hi[3];
+    bool src_in = true;
+    for (int k = 0; k < 3; ++k) {
+        hi[k] = 0.5 * dims[k] * c->vox[k];
+        lo[k] = -hi[k];
+        if (!(S[k] > lo[k] && S[k] < hi[k])) src_in = false;
+    }
+    if (src_in) return false;
+    for (int corner = 0; corner < 8; ++corner) {
+        double side = 0.0;
+        for (int k = 0; k < 3; ++k) side += (((corner >> k) & 1 ? hi[k] : lo[k]) - P[k]) * n[k];
+        if (!(side < 0.0)) return false;
+    }
+    double s_side = 0.0;
+    for (int k = 0; k < 3; ++k) s_side += (S[k] - P[k]) * n[k];
+    return s_side < 0.0;
+}
+
+void fill_box(const gdrr_ctx* c, float lo[3], float hi[3], float ivox[3]) {
+    const int dims[3] = {c->nx, c->ny, c->nz};
+    for (int k = 0; k < 3; ++k) {
+        const double half = 0.5 * dims[k] * c->vox[k];
+        lo[k] = (float)(-half);
+        hi[k] = (float)half;
+        ivox[k] = (float)(1.0 / c->vox[k]);
+    }
+}
+
+double interp_d(const std::vector<double>& t, double e0, double de, double e) {
+    const int n = (int)t.size();
+    double fi = (e - e0) / de;
+    fi = std::min(std::max(fi, 0.0), (double)(n - 1));
+    int i = std::min((int)fi, n - 2);
+    const double f = fi - i;
+    return t[i] + f * (t[i + 1] - t[i]);
+}
+
+void set_defaults(gdrr_mc_options* o) {
+    if (o->e_cut_kev <= 0.0) o->e_cut_kev = 1.0;
+    if (o->max_steps <= 0) o->max_steps = 100000;
+    if (o->block_size <= 0) o->block_size = 256;
+    if (o->hist_per_thread <= 0) o->hist_per_thread = 8;
+    if (o->refill_interval <= 0) o->refill_interval = 1;
+}
+
+int free_ctx(gdrr_ctx* c) {
+    if (!c) return GDRR_OK;
+    cudaStreamSynchronize(c->stream);
+    void* bufs[] = {c->d_mat, c->d_dens, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_cdf_pix,
+                    c->d_guide_pix, c->d_cdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr,
+                    c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete c;
+    return GDRR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+GDRR_API const char* gdrr_error_string(int code) {
+    switch (code) {
+        case GDRR_OK: return "ok";
+        case GDRR_ERR_INVALID_ARG: return "invalid argument";
+        case GDRR_ERR_CUDA: return "CUDA runtime error";
+        case GDRR_ERR_OOM: return "device out of memory";
+        case GDRR_ERR_TALLY_OVERFLOW: return "int64 tally overflow";
+        case GDRR_ERR_STEP_LIMIT: return "histories hit the free-flight limit";
+        case GDRR_ERR_UNSUPPORTED: return "unsupported input";
+        default: return "unknown error";
+    }
+}
+
+GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phantom,
+                         const gdrr_materials* materials, const gdrr_spectrum* spectrum,
+                         const gdrr_bowtie* bowtie, const gdrr_detector* detector, void* cuda_stream,
+                         gdrr_ctx** out) {
+    if (!geometry || !phantom || !materials || !spectrum || !bowtie || !detector || !out)
+        return GDRR_ERR_INVALID_ARG;
+    const gdrr_geometry& g = *geometry;
+    if (!(g.sad_mm > 0 && g.sdd_mm > g.sad_mm && g.nu > 0 && g.nv > 0 && g.du_mm > 0 && g.dv_mm > 0)
+        || !std::isfinite(g.theta_rad))
+        return GDRR_ERR_INVALID_ARG;
+    if ((int64_t)g.nu * g.nv > (1 << 28)) return GDRR_ERR_INVALID_ARG;
+    const gdrr_phantom& ph = *phantom;
+    if (ph.nx <= 0 || ph.ny <= 0 || ph.nz <= 0 || !(ph.dx_mm > 0 && ph.dy_mm > 0 && ph.dz_mm > 0)
+        || !ph.material || !ph.density)
+        return GDRR_ERR_INVALID_ARG;
+    const int64_t nvox = (int64_t)ph.nx * ph.ny * ph.nz;
+    if (nvox >= ((int64_t)1 << 31)) return GDRR_ERR_UNSUPPORTED;
+    const gdrr_materials& mt = *materials;
+    if (mt.n_materials <= 0 || mt.n_energies < 2 || !(mt.de_kev > 0) || !mt.mu_hat) return GDRR_ERR_INVALID_ARG;
+    if (mt.n_materials > GDRR_MAX_MATERIALS) return GDRR_ERR_UNSUPPORTED;
+    const gdrr_spectrum& sp = *spectrum;
+    if (sp.n_bins <= 0 || !sp.energy_kev || !sp.weight) return GDRR_ERR_INVALID_ARG;
+    if (sp.n_bins > 512) return GDRR_ERR_UNSUPPORTED;
+    const gdrr_detector& dt = *detector;
+    if (dt.n_energies < 2 || !(dt.de_kev > 0) || !dt.response || !bowtie->fluence) return GDRR_ERR_INVALID_ARG;
+
+    for (int64_t v = 0; v < nvox; ++v)
+        if (ph.material[v] >= mt.n_materials || !(ph.density[v] >= 0.0f) || !std::isfinite(ph.density[v]))
+            return GDRR_ERR_INVALID_ARG;
+    const int64_t nt = (int64_t)mt.n_materials * 3 * mt.n_energies;
+    for (int64_t i = 0; i < nt; ++i)
+        if (!(mt.mu_hat[i] >= 0.0f) || !std::isfinite(mt.mu_hat[i])) return GDRR_ERR_INVALID_ARG;
+    for (int i = 0; i < dt.n_energies; ++i)
+        if (!std::isfinite(dt.response[i])) return GDRR_ERR_INVALID_ARG;
+    for (int i = 0; i < sp.n_bins; ++i)
+        if (!(sp.energy_kev[i] > 0.0) || !std::isfinite(sp.energy_kev[i])) return GDRR_ERR_INVALID_ARG;
+
+    const int npix = g.nu * g.nv;
+    std::vector<double> cdf_pix = build_cdf(bowtie->fluence, npix);
+    std::vector<double> cdf_e = build_cdf(sp.weight, sp.n_bins);
+    if (cdf_pix.empty() || cdf_e.empty()) return GDRR_ERR_INVALID_ARG;
+
+    gdrr_ctx* c = new (std::nothrow) gdrr_ctx();
+    if (!c) return GDRR_ERR_OOM;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->geo = g;
+    c->nx = ph.nx; c->ny = ph.ny; c->nz = ph.nz;
+    c->vox[0] = ph.dx_mm; c->vox[1] = ph.dy_mm; c->vox[2] = ph.dz_mm;
+    c->n_mat = mt.n_materials; c->n_e = mt.n_energies; c->e0 = mt.e0_kev; c->de = mt.de_kev;
+    c->n_r = dt.n_energies; c->r0 = dt.e0_kev; c->dr = dt.de_kev;
+    c->n_bins = sp.n_bins;
+    set_defaults(&c->opt);
+    if (!geometry_ok(c, 0.0)) { delete c; return GDRR_ERR_INVALID_ARG; }
+
+    int rc = GDRR_OK;
+    do {
+        if (cudaGetDevice(&c->device) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
+        if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+            rc = GDRR_ERR_CUDA;
+            break;
+        }
+        // material coefficients in mm^-1 per g/cm^3 (mu_hat cm^2/g * 0.1)
+        std::vector<float> tab(nt);
+        for (int64_t i = 0; i < nt; ++i) tab[i] = (float)((double)mt.mu_hat[i] * 0.1);
+        // Woodcock majorant nodes: max over materials of the largest density of
+        // that material times its total coefficient, with a 1e-5 margin.
+        std::vector<double> rho_max(mt.n_materials, 0.0);
+        for (int64_t v = 0; v < nvox; ++v)
+            rho_max[ph.material[v]] = std::max(rho_max[ph.material[v]], (double)ph.density[v]);
+        std::vector<float> major(mt.n_energies);
+        for (int e = 0; e < mt.n_energies; ++e) {
+            double mx = 0.0;
+            for (int m = 0; m < mt.n_materials; ++m) {
+                const float* t = tab.data() + (size_t)m * 3 * mt.n_energies;
+                const double tot = ((double)t[e] + (double)t[mt.n_energies + e]) + (double)t[2 * mt.n_energies + e];
+                mx = std::max(mx, rho_max[m] * tot);
+            }
+            major[e] = (float)(mx * (1.0 + 1e-5));
+        }
+        std::vector<float> bin_e(sp.n_bins);
+        for (int b = 0; b < sp.n_bins; ++b) bin_e[b] = (float)sp.energy_kev[b];
+        c->n_guide_pix = npix;
+        c->n_guide_e = std::max(sp.n_bins, 16);
+        std::vector<int> guide_pix = build_guide(cdf_pix, c->n_guide_pix);
+        std::vector<int> guide_e = build_guide(cdf_e, c->n_guide_e);
+        // ray-tracing channel tables: total mu_hat per material at each
+        // channel energy (FP64 interpolation), and phi_b r(E_b)
+        std::vector<float> mu_rt((size_t)sp.n_bins * mt.n_materials);
+        std::vector<float> wr(sp.n_bins);
+        double wsum = 0.0;
+        for (int b = 0; b < sp.n_bins; ++b) wsum += sp.weight[b];
+        std::vector<double> tot(mt.n_energies), rsp(dt.n_energies);
+        for (int i = 0; i < dt.n_energies; ++i) rsp[i] = dt.response[i];
+        for (int m = 0; m < mt.n_materials; ++m) {
+            const float* t = mt.mu_hat + (size_t)m * 3 * mt.n_energies;
+            for (int e = 0; e < mt.n_energies; ++e)
+                tot[e] = 0.1 * ((double)t[e] + (double)t[mt.n_energies + e] + (double)t[2 * mt.n_energies + e]);
+            for (int b = 0; b < sp.n_bins; ++b)
+                mu_rt[(size_t)b * mt.n_materials + m] = (float)interp_d(tot, mt.e0_kev, mt.de_kev, sp.energy_kev[b]);
+        }
+        for (int b = 0; b < sp.n_bins; ++b)
+            wr[b] = (float)((sp.weight[b] / wsum) * interp_d(rsp, dt.e0_kev, dt.de_kev, sp.energy_kev[b]));
+        double fsum = 0.0;
+        for (int i = 0; i < npix; ++i) fsum += bowtie->fluence[i];
+        std::vector<double> wnorm(npix);
+        for (int i = 0; i < npix; ++i) wnorm[i] = bowtie->fluence[i] / fsum;
+
+        cudaStream_t s = c->stream;
+        if ((rc = upload(&c->d_mat, ph.material, (size_t)nvox, s))) break;
+        if ((rc = upload(&c->d_dens, ph.density, (size_t)nvox, s))) break;
+        if ((rc = upload(&c->d_tab, tab.data(), tab.size(), s))) break;
+        if ((rc = upload(&c->d_major, major.data(), major.size(), s))) break;
+        if ((rc = upload(&c->d_resp, dt.response, (size_t)dt.n_energies, s))) break;
+        if ((rc = upload(&c->d_bin_e, bin_e.data(), bin_e.size(), s))) break;
+        if ((rc = upload(&c->d_cdf_pix, cdf_pix.data(), cdf_pix.size(), s))) break;
+        if ((rc = upload(&c->d_guide_pix, guide_pix.data(), guide_pix.size(), s))) break;
+        if ((rc = upload(&c->d_cdf_e, cdf_e.data(), cdf_e.size(), s))) break;
+        if ((rc = upload(&c->d_guide_e, guide_e.data(), guide_e.size(), s))) break;
+        if ((rc = upload(&c->d_wnorm, wnorm.data(), wnorm.size(), s))) break;
+        if ((rc = upload(&c->d_mu_rt, mu_rt.data(), mu_rt.size(), s))) break;
+        if ((rc = upload(&c->d_wr, wr.data(), wr.size(), s))) break;
+        if ((rc = cuda_err(cudaMalloc((void**)&c->d_counter, sizeof(unsigned long long))))) break;
+        if ((rc = cuda_err(cudaMalloc((void**)&c->d_stats, GDRR_NSTATS * sizeof(unsigned long long))))) break;
+        if ((rc = cuda_err(cudaMalloc((void**)&c->d_flag, sizeof(int))))) break;
+        // the host vectors above die at return: finish the copies first
+        if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
+    } while (0);
+    if (rc) { free_ctx(c); return rc; }
+    *out = c;
+    return GDRR_OK;
+}
+
+GDRR_API void gdrr_destroy(gdrr_ctx* ctx) { free_ctx(ctx); }
+
+GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
+    if (!ctx || !o) return GDRR_ERR_INVALID_ARG;
+    gdrr_mc_options n = *o;
+    set_defaults(&n);
+    if (n.block_size % 32 || n.block_size > 256 || n.block_size < 32) return GDRR_ERR_INVALID_ARG;
+    if (n.hist_per_thread > 4096 || n.refill_interval > 1024 || n.blocks_per_sm < 0 || n.blocks_per_sm > 64)
+        return GDRR_ERR_INVALID_ARG;
+    if (!(n.e_cut_kev < 1e6)) return GDRR_ERR_INVALID_ARG;
+    ctx->opt = n;
+    return GDRR_OK;
+}
+
+GDRR_API int gdrr_get_options(const gdrr_ctx* ctx, gdrr_mc_options* o) {
+    if (!ctx || !o) return GDRR_ERR_INVALID_ARG;
+    *o = ctx->opt;
+    return GDRR_OK;
+}
+
+GDRR_API int gdrr_sync(gdrr_ctx* ctx) {
+    if (!ctx) return GDRR_ERR_INVALID_ARG;
+    return cuda_err(cudaStreamSynchronize(ctx->stream));
+}
+
+GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_dev) {
+    if (!ctx || !P_dev || !std::isfinite(angle_rad)) return GDRR_ERR_INVALID_ARG;
+    if (!geometry_ok(ctx, angle_rad)) return GDRR_ERR_INVALID_ARG;
+    RtParams p;
+    p.nx = ctx->nx; p.ny = ctx->ny; p.nz = ctx->nz;
+    fill_box(ctx, p.lo, p.hi, p.ivox);
+    p.mat = ctx->d_mat; p.dens = ctx->d_dens;
+    p.n_mat = ctx->n_mat; p.n_bins = ctx->n_bins;
+    p.mu_rt = ctx->d_mu_rt; p.wr = ctx->d_wr; p.wnorm = ctx->d_wnorm;
+    p.nu = ctx->geo.nu; p.nv = ctx->geo.nv;
+    p.hu = (float)(0.5 * ctx->geo.nu); p.hv = (float)(0.5 * ctx->geo.nv);
+    p.du = (float)ctx->geo.du_mm; p.dv = (float)ctx->geo.dv_mm;
+    p.half_step = (float)(0.5 * std::min(ctx->vox[0], std::min(ctx->vox[1], ctx->vox[2])));
+    p.f = make_frame(ctx->geo, angle_rad);
+    return cuda_err(launch_rt(p, P_dev, ctx->stream));
+}
+
+static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total, uint64_t seed,
+                     uint64_t* stats_dev, gdrr_history_record* records_dev) {
+    if (total == 0) return GDRR_OK;
+    const int nj = (int)jobs.size();
+    if (nj > ctx->jobs_cap) {
+        if (ctx->d_jobs) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->d_jobs); ctx->d_jobs = nullptr; }
+        TRY_CUDA(cudaMalloc((void**)&ctx->d_jobs, sizeof(Job) * nj));
+        ctx->jobs_cap = nj;
+    }
+    // pageable source: staged before the call returns, so the vector may die
+    TRY_CUDA(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(Job) * nj, cudaMemcpyHostToDevice, ctx->stream));
+    TRY_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
+    McParams p;
+    p.nx = ctx->nx; p.ny = ctx->ny; p.nz = ctx->nz;
+    fill_box(ctx, p.lo, p.hi, p.ivox);
+    p.mat = ctx->d_mat; p.dens = ctx->d_dens;
+    p.n_mat = ctx->n_mat; p.n_e = ctx->n_e;
+    p.e0 = (float)ctx->e0; p.inv_de = (float)(1.0 / ctx->de);
+    p.tab = ctx->d_tab; p.major = ctx->d_major;
+    p.n_r = ctx->n_r; p.r0 = (float)ctx->r0; p.inv_dr = (float)(1.0 / ctx->dr); p.resp = ctx->d_resp;
+    p.npix = ctx->geo.nu * ctx->geo.nv; p.n_guide_pix = ctx->n_guide_pix;
+    p.cdf_pix = ctx->d_cdf_pix; p.guide_pix = ctx->d_guide_pix;
+    p.n_bins = ctx->n_bins; p.n_guide_e = ctx->n_guide_e;
+    p.cdf_e = ctx->d_cdf_e; p.guide_e = ctx->d_guide_e; p.bin_e = ctx->d_bin_e;
+    p.nu = ctx->geo.nu; p.nv = ctx->geo.nv;
+    p.hu = (float)(0.5 * ctx->geo.nu); p.hv = (float)(0.5 * ctx->geo.nv);
+    p.du = (float)ctx->geo.du_mm; p.dv = (float)ctx->geo.dv_mm;
+    p.idu = (float)(1.0 / ctx->geo.du_mm); p.idv = (float)(1.0 / ctx->geo.dv_mm);
+    p.e_cut = (float)ctx->opt.e_cut_kev;
+    p.max_steps = ctx->opt.max_steps;
+    p.seed = seed;
+    p.jobs = ctx->d_jobs; p.n_jobs = nj; p.total = total;
+    p.counter = ctx->d_counter;
+    if (stats_dev) {
+        p.stats = reinterpret_cast<unsigned long long*>(stats_dev);
+    } else {
+        TRY_CUDA(cudaMemsetAsync(ctx->d_stats, 0, GDRR_NSTATS * sizeof(unsigned long long), ctx->stream));
+        p.stats = ctx->d_stats;
+    }
+    p.records = records_dev;
+    p.chunk = 32 * ctx->opt.hist_per_thread;
+    p.refill_interval = ctx->opt.refill_interval;
+    const bool rec = records_dev != nullptr;
+    const int block = ctx->opt.block_size;
+    int per_sm = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : mc_occupancy_blocks(ctx->n_mat, block, rec);
+    int64_t grid = (int64_t)per_sm * ctx->n_sm;
+    const int64_t useful = (int64_t)((total + 31) / 32 * 32 + block - 1) / block;
+    if (grid > useful) grid = useful;
+    if (grid < 1) grid = 1;
+    return cuda_err(launch_mc(p, block, (int)grid, rec, ctx->stream));
+}
+
+GDRR_API int gdrr_mc_project(gdrr_ctx* ctx, double angle_rad, uint32_t angle_index, uint64_t n_photons,
+                             uint64_t seed, uint64_t history_offset, int64_t* prim_dev, int64_t* scat_dev,
+                             uint64_t* stats_dev, gdrr_history_record* records_dev) {
+    if (!ctx || !prim_dev || !scat_dev || !std::isfinite(angle_rad)) return GDRR_ERR_INVALID_ARG;
+    if (!geometry_ok(ctx, angle_rad)) return GDRR_ERR_INVALID_ARG;
+    if (history_offset + n_photons < history_offset) return GDRR_ERR_INVALID_ARG;
+    Job j;
+    memset(&j, 0, sizeof j);
+    j.f = make_frame(ctx->geo, angle_rad);
+    j.angle_index = angle_index;
+    j.first = 0;
+    j.count = n_photons;
+    j.hid_offset = history_offset;
+    j.tally_p = prim_dev;
+    j.tally_s = scat_dev;
+    return mc_launch(ctx, std::vector<Job>(1, j), n_photons, seed, stats_dev, records_dev);
+}
+
+GDRR_API int gdrr_mc_project_batched(gdrr_ctx* ctx, int32_t n_angles, const double* angles_rad,
+                                     const uint64_t* budgets, uint64_t seed, int64_t* prim_dev, int64_t* scat_dev,
+                                     uint64_t* stats_dev) {
+    if (!ctx || n_angles <= 0 || !angles_rad || !budgets || !prim_dev || !scat_dev) return GDRR_ERR_INVALID_ARG;
+    std::vector<Job> jobs;
+    jobs.reserve(n_angles);
+    const size_t npix = (size_t)ctx->geo.nu * ctx->geo.nv;
+    uint64_t total = 0;
+    for (int a = 0; a < n_angles; ++a) {
+        if (!std::isfinite(angles_rad[a]) || !geometry_ok(ctx, angles_rad[a])) return GDRR_ERR_INVALID_ARG;
+        if (budgets[a] == 0) continue;
+        Job j;
+        memset(&j, 0, sizeof j);
+        j.f = make_frame(ctx->geo, angles_rad[a]);
+        j.angle_index = (uint32_t)a;
+        j.first = total;
+        j.count = budgets[a];
+        j.hid_offset = 0;
+        j.tally_p = prim_dev + (size_t)a * npix;
+        j.tally_s = scat_dev + (size_t)a * npix;
+        if (total + budgets[a] < total) return GDRR_ERR_INVALID_ARG;
+        total += budgets[a];
+        jobs.push_back(j);
+    }
+    if (jobs.empty()) return GDRR_OK;
+    return mc_launch(ctx, jobs, total, seed, stats_dev, nullptr);
+}
+
+GDRR_API int gdrr_finalize(gdrr_ctx* ctx, const int64_t* tally_dev, int64_t n, uint64_t n_photons,
+                           double* signal_dev) {
+    if (!ctx || !tally_dev || !signal_dev || n < 0 || n_photons == 0) return GDRR_ERR_INVALID_ARG;
+    TRY_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    const double scale = ldexp(1.0, -GDRR_TALLY_BITS) / (double)n_photons;
+    TRY_CUDA(launch_finalize(tally_dev, n, scale, signal_dev, ctx->d_flag, ctx->stream));
+    int bad = 0;
+    TRY_CUDA(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    return bad ? GDRR_ERR_TALLY_OVERFLOW : GDRR_OK;
+}
+
+GDRR_API int gdrr_bin_tally(gdrr_ctx* ctx, const int64_t* tally_dev, int32_t nu, int32_t nv, int32_t factor,
+                            int64_t* out_dev) {
+    if (!ctx || !tally_dev || !out_dev || nu <= 0 || nv <= 0 || factor <= 0 || nu % factor || nv % factor)
+        return GDRR_ERR_INVALID_ARG;
+    return cuda_err(launch_bin(tally_dev, nu, nv, factor, out_dev, ctx->stream));
+}
+
+GDRR_API int gdrr_upsample(gdrr_ctx* ctx, const double* coarse_dev, int32_t cu, int32_t cv, int32_t factor,
+                           double* fine_dev) {
+    if (!ctx || !coarse_dev || !fine_dev || cu <= 0 || cv <= 0 || factor <= 0) return GDRR_ERR_INVALID_ARG;
+    if ((int64_t)cu * factor * cv * factor > (1 << 28)) return GDRR_ERR_INVALID_ARG;
+    return cuda_err(launch_upsample(coarse_dev, cu, cv, factor, fine_dev, ctx->stream));
+}
+
+GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double* S_dev, int32_t nu, int32_t nv,
+                                  double count_scale, double beta, double omega, int32_t iters) {
+    if (!ctx || !S_hat_dev || !S_dev || nu <= 0 || nv <= 0 || iters < 0) return GDRR_ERR_INVALID_ARG;
+    if (!(count_scale > 0) || !(beta > 0) || !(omega > 0 && omega < 2) || !std::isfinite(count_scale)
+        || !std::isfinite(beta))
+        return GDRR_ERR_INVALID_ARG;
+    if ((int64_t)nu * nv > (1 << 28)) return GDRR_ERR_INVALID_ARG;
+    const size_t need = denoise_scratch_doubles(nu, nv);
+    if (need > ctx->denoise_cap) {
+        if (ctx->d_denoise) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->d_denoise); ctx->d_denoise = nullptr; }
+        TRY_CUDA(cudaMalloc((void**)&ctx->d_denoise, need * sizeof(double)));
+        ctx->denoise_cap = need;
+    }
+    return cuda_err(launch_denoise(S_hat_dev, S_dev, nu, nv, count_scale, beta, omega, iters, ctx->d_denoise,
+                                   ctx->stream));
+}
+
+GDRR_API int gdrr_noise_calibrate(gdrr_ctx* ctx, const double* P_hat_dev, const double* P_dev,
+                                  const double* S_hat_dev, const double* S_dev, int64_t n, uint64_t n_sim,
+                                  double mAs, double zeta, double* N_dev) {
+    if (!ctx || !P_hat_dev || !P_dev || !S_hat_dev || !S_dev || !N_dev || n < 0 || n_sim == 0) return GDRR_ERR_INVALID_ARG;
+    if (!(mAs > 0) || !(zeta > 0) || !std::isfinite(mAs) || !std::isfinite(zeta)) return GDRR_ERR_INVALID_ARG;
+    const double alpha = sqrt((double)n_sim / (zeta * mAs));
+    return cuda_err(launch_noise(P_hat_dev, P_dev, S_hat_dev, S_dev, n, alpha, N_dev, ctx->stream));
+}
+
+GDRR_API int gdrr_fit_zeta(const double* inv_sqrt_mAs, const double* ratio, int32_t n, uint64_t n_sim,
+                           double* zeta_out, double* k_out) {
+    if (!inv_sqrt_mAs || !ratio || n <= 0 || n_sim == 0 || !zeta_out) return GDRR_ERR_INVALID_ARG;
+    double sxy = 0.0, sxx = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(inv_sqrt_mAs[i]) || !std::isfinite(ratio[i])) return GDRR_ERR_INVALID_ARG;
+        sxy += inv_sqrt_mAs[i] * ratio[i];
+        sxx += inv_sqrt_mAs[i] * inv_sqrt_mAs[i];
+    }
+    if (!(sxx > 0.0)) return GDRR_ERR_INVALID_ARG;
+    const double k = sxy / sxx;
+    if (!(k != 0.0)) return GDRR_ERR_INVALID_ARG;
+    *zeta_out = (double)n_sim / (k * k);
+    if (k_out) *k_out = k;
+    return GDRR_OK;
+}
+
+GDRR_API int gdrr_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid0, int32_t n_hist, int32_t n_blocks,
+                               uint32_t* out_dev, void* cuda_stream) {
+    if (n_hist < 0 || n_blocks <= 0 || n_blocks > (1 << 20) || (n_hist > 0 && !out_dev)) return GDRR_ERR_INVALID_ARG;
+    return cuda_err(launch_stream_words(seed, angle_index, hid0, n_hist, n_blocks, out_dev, (cudaStream_t)cuda_stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gdrr.h"
+
+namespace gdrr {
+
+// Per-angle imager frame in FP32 (Section 2.1, Fig. 1).
+struct Frame {
+    float S[3];    // source position
+    float n[3];    // imager normal, direction OP
+    float P[3];    // imager centre
+    float eu[3];   // detector u axis
+    float ev[3];   // detector v axis (z)
+};
+
+// One angle of a (possibly batched) transport launch.
+struct Job {
+    Frame f;
+    uint32_t angle_index;
+    uint32_t pad;
+    uint64_t first;        // first flattened history of this job
+    uint64_t count;        // histories of this job
+    uint64_t hid_offset;   // history id of the job's first history
+    int64_t* tally_p;      // [nv*nu]
+    int64_t* tally_s;      // [nv*nu]
+};
+
+// Everything the transport kernel reads, by value.
+struct McParams {
+    // phantom box and voxel data
+    int nx, ny, nz;
+    float lo[3], hi[3], ivox[3];
+    const uint8_t* mat;
+    const float* dens;
+    // material tables, mm^-1 per g/cm^3, [m][k][e]; majorant nodes [e]
+    int n_mat, n_e;
+    float e0, inv_de;
+    const float* tab;
+    const float* major;
+    // detector response
+    int n_r;
+    float r0, inv_dr;
+    const float* resp;
+    // source: pixel and energy inverse CDFs with guide tables
+    int npix, n_guide_pix;
+    const double* cdf_pix;
+    const int* guide_pix;
+    int n_bins, n_guide_e;
+    const double* cdf_e;
+    const int* guide_e;
+    const float* bin_e;
+    // detector grid
+    int nu, nv;
+    float hu, hv, du, dv, idu, idv;
+    // options
+    float e_cut;
+    int max_steps;
+    uint64_t seed;
+    // jobs
+    const Job* jobs;
+    int n_jobs;
+    uint64_t total;                // sum of job counts
+    unsigned long long* counter;   // work counter (flattened histories claimed)
+    unsigned long long* stats;     // GDRR_NSTATS
+    gdrr_history_record* records;  // NULL or [total]
+    int chunk;                     // histories a warp claims at a time
+    int refill_interval;
+};
+
+// Ray-tracing parameters.
+struct RtParams {
+    int nx, ny, nz;
+    float lo[3], hi[3], ivox[3];
+    const uint8_t* mat;
+    const float* dens;
+    int n_mat, n_bins;
+    const float* mu_rt;     // [n_bins][n_mat] total mu_hat at the channel energy, mm^-1 per g/cm^3
+    const float* wr;        // [n_bins] phi_b r(E_b), phi normalised
+    const double* wnorm;    // [npix] normalised fluence
+    int nu, nv;
+    float hu, hv, du, dv;
+    float half_step;        // half the smallest voxel size
+    Frame f;
+};
+
+cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s);
+int mc_occupancy_blocks(int n_mat, int block, bool records);
+cudaError_t launch_rt(const RtParams& p, double* out, cudaStream_t s);
+cudaError_t launch_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist,
+                                int n_blocks, uint32_t* out, cudaStream_t s);
+
+cudaError_t launch_finalize(const int64_t* t, int64_t n, double scale, double* out, int* bad, cudaStream_t s);
+cudaError_t launch_bin(const int64_t* t, int nu, int nv, int f, int64_t* out, cudaStream_t s);
+cudaError_t launch_upsample(const double* c, int cu, int cv, int f, double* out, cudaStream_t s);
+cudaError_t launch_noise(const double* ph, const double* p, const double* sh, const double* sc, int64_t n,
+                         double alpha, double* out, cudaStream_t s);
+cudaError_t launch_denoise(const double* s_hat, double* s, int nu, int nv, double count_scale, double beta,
+                           double omega, int iters, double* scratch, cudaStream_t stream);
+size_t denoise_scratch_doubles(int nu, int nv);
+
+}  // namespace gdrr

@@ -1,0 +1,395 @@
+"""Python binding of libgdrr (include/gdrr.h): argument marshalling only.
+
+Every step of the projection runs in the library's CUDA kernels; this module
+turns torch tensors into device pointers and CUDA streams into handles, and
+raises GdrrError on a non-zero return code.  It never falls back to another
+implementation: if libgdrr.so is missing or cannot load, the first call
+raises.  Function names are those of the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgdrr.so")
+
+GDRR_NSTATS = 11
+STAT_NAMES = ("histories", "steps", "virtual", "rayleigh", "compton", "photo",
+              "tally_primary", "tally_scatter", "miss", "cutoff", "step_limit")
+TALLY_BITS = 24
+RECORD_DTYPE = np.dtype([
+    ("n_steps", "<u4"), ("n_virtual", "<u4"), ("n_rayleigh", "<u4"), ("n_compton", "<u4"),
+    ("n_photo", "<u4"), ("outcome", "<u4"), ("rng_blocks", "<u4"), ("first_interaction", "<u4"),
+    ("pixel", "<i4"), ("e_source", "<f4"), ("e_final", "<f4"), ("pad", "<u4"),
+    ("e_deposited", "<f8")])
+
+
+class GdrrError(RuntimeError):
+    def __init__(self, call, code):
+        msg = _lib_or_none().gdrr_error_string(code).decode() if _lib_or_none() else str(code)
+        super().__init__(f"{call} failed: {msg} ({code})")
+        self.code = code
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("sad_mm", ctypes.c_double), ("sdd_mm", ctypes.c_double), ("theta_rad", ctypes.c_double),
+                ("nu", ctypes.c_int32), ("nv", ctypes.c_int32), ("du_mm", ctypes.c_double), ("dv_mm", ctypes.c_double)]
+
+
+class Phantom(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx_mm", ctypes.c_double), ("dy_mm", ctypes.c_double), ("dz_mm", ctypes.c_double),
+                ("material", ctypes.c_void_p), ("density", ctypes.c_void_p)]
+
+
+class Materials(ctypes.Structure):
+    _fields_ = [("n_materials", ctypes.c_int32), ("n_energies", ctypes.c_int32),
+                ("e0_kev", ctypes.c_double), ("de_kev", ctypes.c_double), ("mu_hat", ctypes.c_void_p)]
+
+
+class Spectrum(ctypes.Structure):
+    _fields_ = [("n_bins", ctypes.c_int32), ("energy_kev", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+
+
+class Bowtie(ctypes.Structure):
+    _fields_ = [("fluence", ctypes.c_void_p)]
+
+
+class Detector(ctypes.Structure):
+    _fields_ = [("n_energies", ctypes.c_int32), ("e0_kev", ctypes.c_double), ("de_kev", ctypes.c_double),
+                ("response", ctypes.c_void_p)]
+
+
+class McOptions(ctypes.Structure):
+    _fields_ = [("e_cut_kev", ctypes.c_double), ("max_steps", ctypes.c_int32), ("block_size", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("hist_per_thread", ctypes.c_int32),
+                ("refill_interval", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def lib():
+    """Load libgdrr.so (built by __graft_entry__.build() or build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgdrr.so not found at {LIB_PATH}: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u32, u64, i64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_int64, ctypes.c_double)
+        sig = {
+            "gdrr_create": [vp, vp, vp, vp, vp, vp, vp, vp],
+            "gdrr_destroy": [vp],
+            "gdrr_set_options": [vp, vp],
+            "gdrr_get_options": [vp, vp],
+            "gdrr_sync": [vp],
+            "gdrr_raytrace_primary": [vp, dbl, vp],
+            "gdrr_mc_project": [vp, dbl, u32, u64, u64, u64, vp, vp, vp, vp],
+            "gdrr_mc_project_batched": [vp, i32, vp, vp, u64, vp, vp, vp],
+            "gdrr_finalize": [vp, vp, i64, u64, vp],
+            "gdrr_bin_tally": [vp, vp, i32, i32, i32, vp],
+            "gdrr_upsample": [vp, vp, i32, i32, i32, vp],
+            "gdrr_denoise_scatter": [vp, vp, vp, i32, i32, dbl, dbl, dbl, i32],
+            "gdrr_noise_calibrate": [vp, vp, vp, vp, vp, i64, u64, dbl, dbl, vp],
+            "gdrr_fit_zeta": [vp, vp, i32, u64, vp, vp],
+            "gdrr_stream_words": [u64, u32, u64, i32, i32, vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None if name == "gdrr_destroy" else ctypes.c_int
+        L.gdrr_error_string.argtypes = [ctypes.c_int]
+        L.gdrr_error_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(call, rc):
+    if rc != 0:
+        raise GdrrError(call, rc)
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t, dtype, numel=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream), stream
+
+
+class Context:
+    """Owns a gdrr_ctx: the staged phantom, tables and scratch of one problem."""
+
+    def __init__(self, prob, stream=None):
+        import torch
+        self._handle = None
+        self.prob = prob
+        self.nu, self.nv = int(prob.nu), int(prob.nv)
+        h, self.stream = _stream_handle(stream)
+        keep = dict(
+            material=np.ascontiguousarray(prob.material, np.uint8),
+            density=np.ascontiguousarray(prob.density, np.float32),
+            mu_hat=np.ascontiguousarray(prob.mu_hat, np.float32),
+            spec_e=np.ascontiguousarray(prob.spec_e, np.float64),
+            spec_w=np.ascontiguousarray(prob.spec_w, np.float64),
+            fluence=np.ascontiguousarray(prob.fluence, np.float64),
+            response=np.ascontiguousarray(prob.response, np.float32))
+        nz, ny, nx = keep["material"].shape
+        geo = Geometry(prob.sad, prob.sdd, prob.theta, self.nu, self.nv, prob.du, prob.dv)
+        ph = Phantom(nx, ny, nz, prob.voxel[0], prob.voxel[1], prob.voxel[2],
+                     _np_ptr(keep["material"]), _np_ptr(keep["density"]))
+        mt = Materials(keep["mu_hat"].shape[0], keep["mu_hat"].shape[2], prob.e0, prob.de, _np_ptr(keep["mu_hat"]))
+        sp = Spectrum(keep["spec_e"].size, _np_ptr(keep["spec_e"]), _np_ptr(keep["spec_w"]))
+        bt = Bowtie(_np_ptr(keep["fluence"]))
+        dt = Detector(keep["response"].size, prob.r0, prob.dr, _np_ptr(keep["response"]))
+        handle = ctypes.c_void_p()
+        torch.cuda.current_device()   # make sure torch has set up the primary context
+        _check("gdrr_create", lib().gdrr_create(ctypes.byref(geo), ctypes.byref(ph), ctypes.byref(mt),
+                                                ctypes.byref(sp), ctypes.byref(bt), ctypes.byref(dt), h,
+                                                ctypes.byref(handle)))
+        self._handle = handle
+
+    @property
+    def handle(self):
+        if self._handle is None:
+            raise RuntimeError("context is closed")
+        return self._handle
+
+    def close(self):
+        if self._handle is not None:
+            lib().gdrr_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---- the C ABI, one wrapper per call -------------------------------------
+
+def gdrr_create(prob, stream=None) -> Context:
+    return Context(prob, stream)
+
+
+def gdrr_destroy(ctx: Context):
+    ctx.close()
+
+
+def gdrr_set_options(ctx: Context, **kw):
+    o = McOptions()
+    _check("gdrr_get_options", lib().gdrr_get_options(ctx.handle, ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    _check("gdrr_set_options", lib().gdrr_set_options(ctx.handle, ctypes.byref(o)))
+
+
+def gdrr_get_options(ctx: Context) -> dict:
+    o = McOptions()
+    _check("gdrr_get_options", lib().gdrr_get_options(ctx.handle, ctypes.byref(o)))
+    return {k: getattr(o, k) for k, _ in McOptions._fields_}
+
+
+def gdrr_sync(ctx: Context):
+    _check("gdrr_sync", lib().gdrr_sync(ctx.handle))
+
+
+def gdrr_raytrace_primary(ctx: Context, angle_rad: float, out=None):
+    import torch
+    if out is None:
+        out = torch.empty((ctx.nv, ctx.nu), dtype=torch.float64, device="cuda")
+    _check("gdrr_raytrace_primary",
+           lib().gdrr_raytrace_primary(ctx.handle, float(angle_rad), _dev_ptr(out, torch.float64, ctx.nu * ctx.nv, "P")))
+    return out
+
+
+def new_tallies(ctx: Context, n_angles: int | None = None):
+    import torch
+    shape = (ctx.nv, ctx.nu) if n_angles is None else (n_angles, ctx.nv, ctx.nu)
+    return (torch.zeros(shape, dtype=torch.int64, device="cuda"),
+            torch.zeros(shape, dtype=torch.int64, device="cuda"))
+
+
+def gdrr_mc_project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, angle_index: int = 0,
+                    history_offset: int = 0, prim=None, scat=None, stats=None, records=None):
+    """Accumulates into prim / scat (int64 [nv, nu], created zeroed if None)."""
+    import torch
+    if prim is None or scat is None:
+        prim, scat = new_tallies(ctx)
+    npix = ctx.nu * ctx.nv
+    sp = _dev_ptr(stats, torch.int64, GDRR_NSTATS, "stats") if stats is not None else None
+    rp = None
+    if records is not None:
+        if records.dtype != torch.uint8 or records.numel() != n_photons * RECORD_DTYPE.itemsize:
+            raise ValueError("records must be a uint8 CUDA tensor of n_photons * record size bytes")
+        rp = _dev_ptr(records, torch.uint8, None, "records")
+    _check("gdrr_mc_project",
+           lib().gdrr_mc_project(ctx.handle, float(angle_rad), int(angle_index), int(n_photons), int(seed),
+                                 int(history_offset), _dev_ptr(prim, torch.int64, npix, "prim"),
+                                 _dev_ptr(scat, torch.int64, npix, "scat"), sp, rp))
+    return prim, scat
+
+
+def gdrr_mc_project_batched(ctx: Context, angles_rad, budgets, seed: int, prim=None, scat=None, stats=None):
+    import torch
+    angles = np.ascontiguousarray(angles_rad, np.float64)
+    bud = np.ascontiguousarray(budgets, np.uint64)
+    if angles.size != bud.size:
+        raise ValueError("angles and budgets differ in length")
+    if prim is None or scat is None:
+        prim, scat = new_tallies(ctx, angles.size)
+    n = angles.size * ctx.nu * ctx.nv
+    sp = _dev_ptr(stats, torch.int64, GDRR_NSTATS, "stats") if stats is not None else None
+    _check("gdrr_mc_project_batched",
+           lib().gdrr_mc_project_batched(ctx.handle, angles.size, _np_ptr(angles), _np_ptr(bud), int(seed),
+                                         _dev_ptr(prim, torch.int64, n, "prim"), _dev_ptr(scat, torch.int64, n, "scat"),
+                                         sp))
+    return prim, scat
+
+
+def gdrr_finalize(ctx: Context, tally, n_photons: int, out=None):
+    import torch
+    if out is None:
+        out = torch.empty(tally.shape, dtype=torch.float64, device="cuda")
+    _check("gdrr_finalize", lib().gdrr_finalize(ctx.handle, _dev_ptr(tally, torch.int64, None, "tally"), tally.numel(),
+                                                int(n_photons), _dev_ptr(out, torch.float64, tally.numel(), "out")))
+    return out
+
+
+def gdrr_bin_tally(ctx: Context, tally, factor: int, out=None):
+    import torch
+    nv, nu = tally.shape[-2:]
+    if out is None:
+        out = torch.empty((nv // factor, nu // factor), dtype=torch.int64, device="cuda")
+    _check("gdrr_bin_tally", lib().gdrr_bin_tally(ctx.handle, _dev_ptr(tally, torch.int64, nu * nv, "tally"), nu, nv,
+                                                  int(factor), _dev_ptr(out, torch.int64, (nu // factor) * (nv // factor), "out")))
+    return out
+
+
+def gdrr_upsample(ctx: Context, coarse, factor: int, out=None):
+    import torch
+    cv, cu = coarse.shape
+    if out is None:
+        out = torch.empty((cv * factor, cu * factor), dtype=torch.float64, device="cuda")
+    _check("gdrr_upsample", lib().gdrr_upsample(ctx.handle, _dev_ptr(coarse, torch.float64, cu * cv, "coarse"), cu, cv,
+                                                int(factor), _dev_ptr(out, torch.float64, cu * cv * factor * factor, "out")))
+    return out
+
+
+def gdrr_denoise_scatter(ctx: Context, s_hat, count_scale: float, beta: float, omega: float = 0.8,
+                         iters: int = 500, out=None):
+    import torch
+    nv, nu = s_hat.shape
+    if out is None:
+        out = torch.empty_like(s_hat)
+    _check("gdrr_denoise_scatter",
+           lib().gdrr_denoise_scatter(ctx.handle, _dev_ptr(s_hat, torch.float64, nu * nv, "s_hat"),
+                                      _dev_ptr(out, torch.float64, nu * nv, "out"), nu, nv, float(count_scale),
+                                      float(beta), float(omega), int(iters)))
+    return out
+
+
+def gdrr_noise_calibrate(ctx: Context, p_hat, p, s_hat, s, n_sim: int, mas: float, zeta: float, out=None):
+    import torch
+    n = p_hat.numel()
+    if out is None:
+        out = torch.empty_like(p_hat)
+    ptrs = [_dev_ptr(t, torch.float64, n, nm) for t, nm in ((p_hat, "p_hat"), (p, "p"), (s_hat, "s_hat"), (s, "s"))]
+    _check("gdrr_noise_calibrate", lib().gdrr_noise_calibrate(ctx.handle, *ptrs, n, int(n_sim), float(mas), float(zeta),
+                                                              _dev_ptr(out, torch.float64, n, "out")))
+    return out
+
+
+def gdrr_fit_zeta(inv_sqrt_mas, ratio, n_sim: int):
+    x = np.ascontiguousarray(inv_sqrt_mas, np.float64)
+    y = np.ascontiguousarray(ratio, np.float64)
+    z, k = ctypes.c_double(), ctypes.c_double()
+    _check("gdrr_fit_zeta", lib().gdrr_fit_zeta(_np_ptr(x), _np_ptr(y), x.size, int(n_sim), ctypes.byref(z),
+                                                ctypes.byref(k)))
+    return z.value, k.value
+
+
+def gdrr_stream_words(seed: int, angle_index: int, hid0: int, n_hist: int, n_blocks: int, stream=None):
+    import torch
+    out = torch.empty((n_hist, 4 * n_blocks), dtype=torch.int32, device="cuda")
+    h, _ = _stream_handle(stream)
+    _check("gdrr_stream_words", lib().gdrr_stream_words(int(seed), int(angle_index), int(hid0), int(n_hist),
+                                                        int(n_blocks), _dev_ptr(out, torch.int32, None, "out"), h))
+    return out
+
+
+def stats_dict(stats) -> dict:
+    v = stats.cpu().numpy().view(np.uint64)
+    return dict(zip(STAT_NAMES, (int(x) for x in v)))
+
+
+def records_array(records) -> np.ndarray:
+    return records.cpu().numpy().view(RECORD_DTYPE)
+
+
+# ---- one full projection: Steps 1-4 of Section 2.2 ------------------------
+
+def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin_factor: int = 4,
+            beta: float = 0.02, omega: float = 0.8, iters: int = 300, mas: float = 0.4,
+            zeta: float = 5.2913e9, stats=None):
+    """P (ray traced), P^ and S^ (MC), S (denoised, coarse and full), N (scaled noise).
+
+    Every step is a libgdrr kernel.  The denoiser runs on the bin_factor x
+    bin_factor coarse scatter grid on the count scale: one detected scattered
+    photon deposits on average (scatter tally sum) / (scattered photons
+    tallied), the count_scale.
+    """
+    import torch
+    own_stats = stats is None
+    if own_stats:
+        stats = torch.zeros(GDRR_NSTATS, dtype=torch.int64, device="cuda")
+    P = gdrr_raytrace_primary(ctx, angle_rad)
+    prim, scat = gdrr_mc_project(ctx, n_photons, seed, angle_rad, stats=stats)
+    P_hat = gdrr_finalize(ctx, prim, n_photons)
+    S_hat = gdrr_finalize(ctx, scat, n_photons)
+    S_hat_c = gdrr_finalize(ctx, gdrr_bin_tally(ctx, scat, bin_factor), n_photons)
+    st = stats_dict(stats) if own_stats else None
+    n_det = max(1, (st or stats_dict(stats))["tally_scatter"])
+    count_scale = float(S_hat.sum().item()) / n_det if n_det else 1.0
+    if not count_scale > 0:
+        count_scale = 1.0 / n_photons
+    S_c = gdrr_denoise_scatter(ctx, S_hat_c, count_scale, beta, omega, iters)
+    S = gdrr_upsample(ctx, S_c, bin_factor)
+    N = gdrr_noise_calibrate(ctx, P_hat, P, S_hat, S, n_photons, mas, zeta)
+    return dict(P=P, P_hat=P_hat, S_hat=S_hat, S_hat_coarse=S_hat_c, S_coarse=S_c, S=S, N=N,
+                prim=prim, scat=scat, stats=stats)

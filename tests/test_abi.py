@@ -1,0 +1,108 @@
+"""The C ABI library loads without a GPU and exports every symbol declared in
+include/gdrr.h; host-side argument validation rejects bad inputs before any
+CUDA call (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "gdrr.h")).read()
+    return sorted(set(re.findall(r"GDRR_API\s+[^;(]*?\b(gdrr_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1204_6367_gb300 import build, gdrr
+    build.build()
+    return gdrr.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("gdrr_create", "gdrr_raytrace_primary", "gdrr_mc_project", "gdrr_denoise_scatter",
+                     "gdrr_noise_calibrate", "gdrr_finalize", "gdrr_destroy", "gdrr_error_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_library_exports_nothing_else(lib):
+    import subprocess
+    from paper_1204_6367_gb300 import gdrr
+    out = subprocess.run(["nm", "-D", "--defined-only", gdrr.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("gdrr_")}
+    assert exported == set(_declared())
+
+
+def test_error_strings(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert lib.gdrr_error_string(code)
+    assert lib.gdrr_error_string(-99) == b"unknown error"
+
+
+def test_fit_zeta_host_only(lib):
+    from paper_1204_6367_gb300 import gdrr
+    from tests.golden.load import load
+    g = load("paper_noise_calibration.txt")
+    x = 1 / np.sqrt(np.array([0.1, 0.4, 1.6]))
+    z, k = gdrr.gdrr_fit_zeta(x, g["k"] * x, int(g["n_sim"]))
+    assert z == pytest.approx(g["zeta"], rel=g["rel_tol"]) and k == pytest.approx(g["k"])
+    with pytest.raises(gdrr.GdrrError):
+        gdrr.gdrr_fit_zeta(np.zeros(3), np.ones(3), 10)
+
+
+def _create_rc(prob, **override):
+    """gdrr_create on a problem with fields overridden; validation runs before
+    any CUDA call, so rejected inputs return without touching a device."""
+    from paper_1204_6367_gb300 import gdrr
+    L = gdrr.lib()
+    mat = np.ascontiguousarray(override.pop("material", prob.material), np.uint8)
+    den = np.ascontiguousarray(override.pop("density", prob.density), np.float32)
+    mu = np.ascontiguousarray(override.pop("mu_hat", prob.mu_hat), np.float32)
+    se = np.ascontiguousarray(prob.spec_e, np.float64)
+    sw = np.ascontiguousarray(override.pop("spec_w", prob.spec_w), np.float64)
+    fl = np.ascontiguousarray(override.pop("fluence", prob.fluence), np.float64)
+    rs = np.ascontiguousarray(prob.response, np.float32)
+    nz, ny, nx = mat.shape
+    geo = gdrr.Geometry(prob.sad, override.pop("sdd", prob.sdd), prob.theta, prob.nu, prob.nv, prob.du, prob.dv)
+    ph = gdrr.Phantom(nx, ny, nz, *prob.voxel, mat.ctypes.data, den.ctypes.data)
+    mt = gdrr.Materials(override.pop("n_materials", mu.shape[0]), mu.shape[2], prob.e0, prob.de, mu.ctypes.data)
+    sp = gdrr.Spectrum(se.size, se.ctypes.data, sw.ctypes.data)
+    bt = gdrr.Bowtie(fl.ctypes.data)
+    dt = gdrr.Detector(rs.size, prob.r0, prob.dr, rs.ctypes.data)
+    h = ctypes.c_void_p()
+    return L.gdrr_create(ctypes.byref(geo), ctypes.byref(ph), ctypes.byref(mt), ctypes.byref(sp), ctypes.byref(bt),
+                         ctypes.byref(dt), None, ctypes.byref(h))
+
+
+def test_create_rejects_bad_inputs(lib, small):
+    bad_mat = small.material.copy()
+    bad_mat[0, 0, 0] = 7
+    neg = small.density.copy()
+    neg[1, 2, 3] = -1.0
+    nan = small.density.copy()
+    nan[0, 0, 1] = np.nan
+    assert _create_rc(small, material=bad_mat) == -1
+    assert _create_rc(small, density=neg) == -1
+    assert _create_rc(small, density=nan) == -1
+    assert _create_rc(small, spec_w=-small.spec_w) == -1
+    assert _create_rc(small, fluence=np.zeros_like(small.fluence)) == -1
+    assert _create_rc(small, sdd=1030.0) == -1          # imager plane cuts the box
+    assert _create_rc(small, n_materials=9) in (-1, -6)
+
+
+def test_null_arguments(lib):
+    assert lib.gdrr_create(None, None, None, None, None, None, None, None) == -1
+    assert lib.gdrr_mc_project(None, 0.0, 0, 10, 1, 0, None, None, None, None) == -1
+    assert lib.gdrr_raytrace_primary(None, 0.0, None) == -1
+    assert lib.gdrr_denoise_scatter(None, None, None, 4, 4, 1.0, 1.0, 0.8, 1) == -1
+    assert lib.gdrr_stream_words(1, 0, 0, -1, 1, None, None) == -1

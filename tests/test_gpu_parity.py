@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer outputs (random words, int64 tallies, transport counters, per-history
+event records) must match the oracle's FP32 transport bit for bit: both sides
+perform the same IEEE operations in the same order.  The ray-traced primary
+is FP32 on the GPU against an FP64 oracle: tolerance 2e-4 relative, derived
+in the design notes from FP32 sampling-point positions and path sums.
+Image-domain steps are FP64 on both sides: 1e-12 relative.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1204_6367_gb300 import inputs  # noqa: E402
+
+NTH = os.cpu_count() or 1
+RT_RTOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def gd():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1204_6367_gb300 import build, gdrr
+    build.build()
+    gdrr.lib()
+    return gdrr
+
+
+def _run_gpu(gd, prob, n, seed, phi=0.0, angle_index=0, offset=0, records=False, **opts):
+    with gd.Context(prob) as ctx:
+        if opts:
+            gd.gdrr_set_options(ctx, **opts)
+        stats = torch.zeros(gd.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+        rec = torch.zeros(n * gd.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda") if records else None
+        prim, scat = gd.gdrr_mc_project(ctx, n, seed, phi, angle_index, offset, stats=stats, records=rec)
+        gd.gdrr_sync(ctx)
+        return (prim.cpu().numpy(), scat.cpu().numpy(), gd.stats_dict(stats),
+                gd.records_array(rec) if records else None)
+
+
+def test_stream_words_bit_exact(gd):
+    for seed, a, h0 in [(1, 0, 0), (0xFEDCBA9876543210, 63, (1 << 32) - 3), (12345, 7, 10**12)]:
+        w = gd.gdrr_stream_words(seed, a, h0, 64, 3).cpu().numpy().view(np.uint32)
+        torch.cuda.synchronize()
+        ref = np.stack([oracle.stream_words(seed, a, h0 + i, 3) for i in range(64)])
+        np.testing.assert_array_equal(w, ref)
+
+
+def test_tiny_run_event_by_event(gd, small):
+    n = 1000
+    tp, ts, st, rec = _run_gpu(gd, small, n, seed=1, records=True)
+    otp, ots, ost, orec = oracle.mc_run(small, n, seed=1, records=True)
+    for f in oracle.RECORD_DTYPE.names:
+        np.testing.assert_array_equal(rec[f], orec[f], err_msg=f)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
+
+
+@pytest.mark.parametrize("phi", [0.0, 1.1])
+def test_small_problem_1e6_bit_exact(gd, small, phi):
+    n = 1_000_000
+    tp, ts, st, _ = _run_gpu(gd, small, n, seed=3, phi=phi, angle_index=5)
+    otp, ots, ost, _ = oracle.mc_run(small, n, seed=3, phi=phi, angle_index=5, threads=NTH)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
+
+
+def test_torso_4mm_polyenergetic_bit_exact(gd):
+    prob = inputs.torso_problem(vox=4.0, nu=128, nv=96, det_px=0.776 * 4)
+    n = 300_000
+    tp, ts, st, _ = _run_gpu(gd, prob, n, seed=11, phi=0.4, angle_index=2)
+    otp, ots, ost, _ = oracle.mc_run(prob, n, seed=11, phi=0.4, angle_index=2, threads=NTH)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
+
+
+@pytest.mark.parametrize("opts", [dict(block_size=64, hist_per_thread=1, refill_interval=1),
+                                  dict(block_size=128, hist_per_thread=64, refill_interval=8),
+                                  dict(block_size=256, hist_per_thread=3, refill_interval=3, blocks_per_sm=1)])
+def test_launch_configuration_invariance(gd, small, opts):
+    n = 200_003
+    ref = _run_gpu(gd, small, n, seed=5)
+    got = _run_gpu(gd, small, n, seed=5, **opts)
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_array_equal(got[1], ref[1])
+    assert got[2] == ref[2]
+
+
+def test_split_and_accumulate(gd, small):
+    n, k = 300_000, 123_457
+    with gd.Context(small) as ctx:
+        full = gd.gdrr_mc_project(ctx, n, 9)
+        a_p, a_s = gd.gdrr_mc_project(ctx, k, 9)
+        gd.gdrr_mc_project(ctx, n - k, 9, history_offset=k, prim=a_p, scat=a_s)
+        gd.gdrr_sync(ctx)
+        assert torch.equal(full[0], a_p) and torch.equal(full[1], a_s)
+
+
+def test_zero_photons_is_a_noop(gd, small):
+    with gd.Context(small) as ctx:
+        p, s = gd.new_tallies(ctx)
+        p += 5
+        gd.gdrr_mc_project(ctx, 0, 1, prim=p, scat=s)
+        gd.gdrr_sync(ctx)
+        assert int(p.sum()) == 5 * p.numel() and int(s.abs().sum()) == 0
+
+
+def test_edge_phantoms(gd):
+    # one voxel; vacuum; eight materials; a single-pixel detector
+    one = inputs.uniform_slab_problem(nx=1, ny=1, nz=1, vox=30.0, nu=5, nv=3, det_px=4.0, pencil=False)
+    vac = inputs.uniform_slab_problem(mat_id=0, density=0.0, nu=7, nv=5, pencil=False)
+    mats = [inputs.AIR, inputs.WATER, inputs.BONE, inputs.LUNG, inputs.ALUMINIUM,
+            inputs.WATER, inputs.BONE, inputs.AIR]
+    eight = inputs.uniform_slab_problem(nx=9, ny=8, nz=7, nu=6, nv=6, det_px=3.0, materials=mats, pencil=False)
+    eight.material[:] = (np.arange(eight.material.size) % 8).reshape(eight.material.shape)
+    eight.density[:] = np.linspace(0.1, 2.5, eight.density.size).reshape(eight.density.shape)
+    single = inputs.uniform_slab_problem(nu=1, nv=1, det_px=2.0)
+    for prob in (one, vac, eight, single):
+        tp, ts, st, _ = _run_gpu(gd, prob, 20_000, seed=4, phi=0.3)
+        otp, ots, ost, _ = oracle.mc_run(prob, 20_000, seed=4, phi=0.3, threads=NTH)
+        assert st == ost
+        np.testing.assert_array_equal(tp, otp)
+        np.testing.assert_array_equal(ts, ots)
+
+
+def test_step_limit_counted(gd, small):
+    tp, ts, st, _ = _run_gpu(gd, small, 5000, seed=1, max_steps=2)
+    otp, ots, ost, _ = oracle.mc_run(small, 5000, seed=1, max_steps=2)
+    assert st == ost and st["step_limit"] > 0
+    np.testing.assert_array_equal(tp, otp)
+
+
+def test_batched_equals_per_angle(gd, small):
+    angles = np.linspace(0, 2 * math.pi, 6, endpoint=False)
+    budgets = np.array([3000, 0, 25_000, 1, 9_999, 40_000], np.uint64)
+    with gd.Context(small) as ctx:
+        bp, bs = gd.gdrr_mc_project_batched(ctx, angles, budgets, 17)
+        for a in range(angles.size):
+            p, s = gd.gdrr_mc_project(ctx, int(budgets[a]), 17, float(angles[a]), a)
+            assert torch.equal(bp[a], p) and torch.equal(bs[a], s), a
+    otp, ots, _, _ = oracle.mc_run(small, 9_999, seed=17, phi=float(angles[4]), angle_index=4, threads=NTH)
+    np.testing.assert_array_equal(bp[4].cpu().numpy(), otp)
+    np.testing.assert_array_equal(bs[4].cpu().numpy(), ots)
+
+
+def test_raytrace_small(gd, small):
+    with gd.Context(small) as ctx:
+        for phi in (0.0, 0.9):
+            P = gd.gdrr_raytrace_primary(ctx, phi).cpu().numpy()
+            ref = oracle.rt_primary(small, phi=phi)
+            np.testing.assert_allclose(P, ref, rtol=RT_RTOL, atol=1e-12 * ref.max())
+
+
+def test_raytrace_torso_sampled(gd):
+    # full-size 2 mm torso (512 x 384 detector): sampled pixels, the oracle's
+    # per-channel FP64 trace against the GPU's per-material FP32 trace
+    prob = inputs.torso_problem()
+    rng = np.random.default_rng(0)
+    pix = np.concatenate([rng.integers(0, prob.nu * prob.nv, 120), [0, prob.nu - 1, prob.nu * prob.nv - 1]])
+    with gd.Context(prob) as ctx:
+        for phi in (0.0, 1.3):
+            P = gd.gdrr_raytrace_primary(ctx, phi).cpu().numpy().ravel()[pix]
+            ref = oracle.rt_primary(prob, phi=phi, pixels=pix)
+            np.testing.assert_allclose(P, ref, rtol=RT_RTOL, atol=1e-12 * ref.max())
+
+
+def test_image_steps_match_oracle(gd, small):
+    rng = np.random.default_rng(3)
+    t = torch.from_numpy(rng.integers(0, 2**45, (64, 64), dtype=np.int64)).cuda()
+    with gd.Context(small) as ctx:
+        fin = gd.gdrr_finalize(ctx, t, 123456).cpu().numpy()
+        np.testing.assert_allclose(fin, oracle.finalize(t.cpu().numpy(), 123456), rtol=1e-15)
+        b = gd.gdrr_bin_tally(ctx, t, 4).cpu().numpy()
+        np.testing.assert_array_equal(b, oracle.bin_tally(t.cpu().numpy(), 4))
+        coarse = torch.from_numpy(rng.uniform(1, 100, (16, 16))).cuda()
+        up = gd.gdrr_upsample(ctx, coarse, 4).cpu().numpy()
+        np.testing.assert_allclose(up, oracle.upsample(coarse.cpu().numpy(), 4), rtol=1e-13)
+        s_hat = torch.from_numpy(rng.poisson(500.0, (24, 32)).astype(np.float64) * 0.37).cuda()
+        den = gd.gdrr_denoise_scatter(ctx, s_hat, 0.37, 0.02, 0.8, 400).cpu().numpy()
+        ref = oracle.denoise(s_hat.cpu().numpy() / 0.37, 0.02, 0.8, 400) * 0.37
+        np.testing.assert_allclose(den, ref, rtol=1e-11)
+        a, p, c, d = (torch.from_numpy(rng.normal(size=(8, 8))).cuda() for _ in range(4))
+        n = gd.gdrr_noise_calibrate(ctx, a, p, c, d, 10**8, 0.4, 5.2913e9).cpu().numpy()
+        np.testing.assert_allclose(n, oracle.noise_scale(*(x.cpu().numpy() for x in (a, p, c, d)), 10**8, 0.4, 5.2913e9),
+                                   rtol=1e-14)
+
+
+def test_finalize_flags_overflow(gd, small):
+    t = torch.tensor([1, -5, 3], dtype=torch.int64, device="cuda")
+    with gd.Context(small) as ctx:
+        with pytest.raises(gd.GdrrError) as e:
+            gd.gdrr_finalize(ctx, t, 10)
+        assert e.value.code == -4
+
+
+def test_full_size_torso_sampled_windows(gd):
+    # The 2 mm torso at 1e8 histories in the default launch configuration:
+    # the full run equals the sum of its split parts, and history windows of
+    # the same streams (start, middle, end) equal the oracle bit for bit.
+    prob = inputs.torso_problem()
+    n = 100_000_000
+    with gd.Context(prob) as ctx:
+        full_p, full_s = gd.gdrr_mc_project(ctx, n, 1)
+        parts_p, parts_s = gd.new_tallies(ctx)
+        for lo, hi in ((0, 37_000_000), (37_000_000, 81_234_567), (81_234_567, n)):
+            gd.gdrr_mc_project(ctx, hi - lo, 1, history_offset=lo, prim=parts_p, scat=parts_s)
+        gd.gdrr_sync(ctx)
+        assert torch.equal(full_p, parts_p) and torch.equal(full_s, parts_s)
+        for off in (0, 55_555_555, n - 40_000):
+            wp, ws = gd.gdrr_mc_project(ctx, 40_000, 1, history_offset=off)
+            otp, ots, _, _ = oracle.mc_run(prob, 40_000, seed=1, history_offset=off, threads=NTH)
+            np.testing.assert_array_equal(wp.cpu().numpy(), otp)
+            np.testing.assert_array_equal(ws.cpu().numpy(), ots)
+
+
+def _pooled(chunks):
+    """Per-pixel estimate and variance of a tally summed over k independent
+    chunks.  A tally is a compound-Poisson sum of deposits, Var = R * mean,
+    with one dispersion ratio R per image pooled over well-filled pixels."""
+    c = np.asarray(chunks, np.float64)
+    m, v = c.mean(0), c.var(0, ddof=1)
+    keep = m > np.percentile(m, 50)
+    R = v[keep].sum() / m[keep].sum()
+    tot = c.sum(0)
+    return tot, tot * R
+
+
+def test_statistical_agreement_with_fp64_oracle(gd, small):
+    # Large-run statistics against the independent FP64 transport: >= 99.7 %
+    # of pixels within 3 combined sigma, total scatter within 0.5 % (+3 sigma).
+    n_g, k_g = 100_000_000, 20
+    n_o, k_o = 40_000_000, 20
+    with gd.Context(small) as ctx:
+        cg_p, cg_s = [], []
+        for i in range(k_g):
+            p, s = gd.gdrr_mc_project(ctx, n_g // k_g, 1, history_offset=i * (n_g // k_g))
+            cg_p.append(p.cpu().numpy()); cg_s.append(s.cpu().numpy())
+    co_p, co_s = [], []
+    for i in range(k_o):
+        p, s, _, _ = oracle.mc_run(small, n_o // k_o, seed=77, history_offset=i * (n_o // k_o), precision=64,
+                                   threads=NTH)
+        co_p.append(p); co_s.append(s)
+    for cg, co in ((cg_p, co_p), (cg_s, co_s)):
+        tg, vg = _pooled(cg)
+        to, vo = _pooled(co)
+        g, o = tg / n_g, to / n_o
+        var = vg / n_g**2 + vo / n_o**2
+        keep = (tg > 0) | (to > 0)
+        z = np.abs(g - o)[keep] / np.sqrt(var[keep])
+        frac = float(np.mean(z < 3.0))
+        assert frac >= 0.997, frac
+    sg, so = np.sum(cg_s) / n_g, np.sum(co_s) / n_o
+    sig = math.sqrt(_pooled(cg_s)[1].sum() / n_g**2 + _pooled(co_s)[1].sum() / n_o**2)
+    assert abs(sg - so) <= 0.005 * so + 3 * sig, (sg, so, sig)
