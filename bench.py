@@ -115,11 +115,11 @@ def cpu_oracle_rate(prob, target_s, threads, seed=1):
     a bounded sample of the same workload: first history ids of the stream."""
     import oracle
     oracle.build()
-    n = 20000
+    n = 400000
     t0 = time.perf_counter()
     oracle.mc_run(prob, n, seed=seed, threads=threads)
     dt = time.perf_counter() - t0
-    n2 = int(max(n, min(5e7, n * target_s / max(dt, 1e-3))))
+    n2 = int(max(n, min(1e8, n * target_s / max(dt, 1e-3))))
     t0 = time.perf_counter()
     oracle.mc_run(prob, n2, seed=seed, threads=threads)
     dt2 = time.perf_counter() - t0
@@ -137,7 +137,7 @@ def run_reference(args):
     threads = os.cpu_count() or 1
     # each step: a bounded sample of the projection's histories, sized so the
     # whole --steps/--warmup run stays within a few minutes
-    probe = 20000
+    probe = 400000
     t0 = time.perf_counter()
     oracle.mc_run(prob, probe, seed=1, threads=threads)
     rate0 = probe / (time.perf_counter() - t0)

@@ -116,7 +116,9 @@ typedef struct {
     int32_t block_size;        /* threads per block, multiple of 32 [256]           */
     int32_t blocks_per_sm;     /* resident blocks per SM for the persistent grid [by occupancy] */
     int32_t hist_per_thread;   /* histories a warp claims per lane at a time [8]    */
-    int32_t refill_interval;   /* steps between refills of finished lanes [1]       */
+    int32_t batch_min;         /* lanes of a warp that must be waiting for an
+                                  interaction, a tally or a new history before the
+                                  warp serves them together, 1..32 [16]            */
 } gdrr_mc_options;
 
 /* Transport counters, accumulated by every gdrr_mc_project* call (device

@@ -46,12 +46,13 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 typedef struct {
     uint32_t key[2];
     uint32_t ctr[4];
-    uint32_t buf[4];
-    int pos;
 } orc_stream;
 
-/* Counter layout of a history's stream: (block k, angle index, hid lo, hid hi),
- * key = (seed lo, seed hi).  Words are consumed in order, four per block. */
+/* The stream of a history: Philox blocks with counter (k, angle index, hid lo,
+ * hid hi), k = 0, 1, 2, ..., key = (seed lo, seed hi).  Every draw site takes
+ * the next whole block: the source (block 0, four uniforms), each free flight
+ * (two uniforms), each rejection attempt of an angular sampler (two or three
+ * uniforms); words a site does not use are dropped. */
 static void orc_stream_init(orc_stream* s, uint64_t seed, uint32_t angle_index, uint64_t hid) {
     s->key[0] = (uint32_t)seed;
     s->key[1] = (uint32_t)(seed >> 32);
@@ -59,28 +60,28 @@ static void orc_stream_init(orc_stream* s, uint64_t seed, uint32_t angle_index, 
     s->ctr[1] = angle_index;
     s->ctr[2] = (uint32_t)hid;
     s->ctr[3] = (uint32_t)(hid >> 32);
-    s->pos = 4;
-}
-
-static uint32_t orc_next_word(orc_stream* s) {
-    if (s->pos == 4) {
-        orc_philox4x32_10(s->ctr, s->key, s->buf);
-        s->ctr[0] += 1;
-        s->pos = 0;
-    }
-    return s->buf[s->pos++];
 }
 
 /* Uniform on (0, 1]: the top 24 bits plus one, times 2^-24 (exact in FP32). */
-static float orc_next_uniform(orc_stream* s) {
-    uint32_t w = orc_next_word(s);
+static float orc_uniform(uint32_t w) {
     return (float)((w >> 8) + 1u) * (float)(1.0 / 16777216.0);
+}
+
+/* The next block of the stream as four uniforms. */
+static void orc_next_block(orc_stream* s, float u[4]) {
+    uint32_t w[4];
+    orc_philox4x32_10(s->ctr, s->key, w);
+    s->ctr[0] += 1;
+    for (int i = 0; i < 4; ++i) u[i] = orc_uniform(w[i]);
 }
 
 void orc_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid, int n_blocks, uint32_t* out) {
     orc_stream s;
     orc_stream_init(&s, seed, angle_index, hid);
-    for (int i = 0; i < 4 * n_blocks; ++i) out[i] = orc_next_word(&s);
+    for (int b = 0; b < n_blocks; ++b) {
+        orc_philox4x32_10(s.ctr, s.key, out + 4 * b);
+        s.ctr[0] += 1;
+    }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -27,16 +27,15 @@ struct gdrr_ctx {
     double vox[3] = {0, 0, 0};
     int n_mat = 0, n_e = 0, n_r = 0, n_bins = 0;
     double e0 = 0, de = 0, r0 = 0, dr = 0;
-    // staged device data
-    uint8_t* d_mat = nullptr;
-    float* d_dens = nullptr;
+    // staged device data: one 8-byte record {density bits, material} per voxel
+    uint2* d_vox = nullptr;
     float* d_tab = nullptr;
     float* d_major = nullptr;
     float* d_resp = nullptr;
     float* d_bin_e = nullptr;
-    double* d_cdf_pix = nullptr;
+    uint32_t* d_kcdf_pix = nullptr;
     int* d_guide_pix = nullptr;
-    double* d_cdf_e = nullptr;
+    uint32_t* d_kcdf_e = nullptr;
     int* d_guide_e = nullptr;
     double* d_wnorm = nullptr;
     float* d_mu_rt = nullptr;
@@ -86,6 +85,18 @@ std::vector<double> build_cdf(const double* w, int n) {
     if (!(s > 0.0)) return {};
     for (int i = 0; i < n; ++i) c[i] = c[i] / s;
     return c;
+}
+
+// Integer thresholds of an inverse CDF: a uniform xi = k 2^-24 (k integer,
+// 1 <= k <= 2^24) satisfies xi <= cdf[j] exactly when k <= floor(cdf[j] 2^24),
+// since cdf[j] 2^24 is exact in FP64.
+std::vector<uint32_t> kcdf_of(const std::vector<double>& cdf) {
+    std::vector<uint32_t> k(cdf.size());
+    for (size_t i = 0; i < cdf.size(); ++i) {
+        const double v = floor(ldexp(cdf[i], 24));
+        k[i] = (uint32_t)std::min(v, 16777216.0);
+    }
+    return k;
 }
 
 // Guide table: g[i] = first j with cdf[j] >= i / G (a starting point only;
@@ -168,14 +179,14 @@ void set_defaults(gdrr_mc_options* o) {
     if (o->max_steps <= 0) o->max_steps = 100000;
     if (o->block_size <= 0) o->block_size = 256;
     if (o->hist_per_thread <= 0) o->hist_per_thread = 8;
-    if (o->refill_interval <= 0) o->refill_interval = 1;
+    if (o->batch_min <= 0) o->batch_min = 16;
 }
 
 int free_ctx(gdrr_ctx* c) {
     if (!c) return GDRR_OK;
     cudaStreamSynchronize(c->stream);
-    void* bufs[] = {c->d_mat, c->d_dens, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_cdf_pix,
-                    c->d_guide_pix, c->d_cdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr,
+    void* bufs[] = {c->d_vox, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_kcdf_pix,
+                    c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr,
                     c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -308,15 +319,21 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         for (int i = 0; i < npix; ++i) wnorm[i] = bowtie->fluence[i] / fsum;
 
         cudaStream_t s = c->stream;
-        if ((rc = upload(&c->d_mat, ph.material, (size_t)nvox, s))) break;
-        if ((rc = upload(&c->d_dens, ph.density, (size_t)nvox, s))) break;
+        std::vector<uint2> vox((size_t)nvox);
+        for (int64_t v = 0; v < nvox; ++v) {
+            uint32_t bits;
+            memcpy(&bits, &ph.density[v], sizeof bits);
+            vox[v] = make_uint2(bits, (uint32_t)ph.material[v]);
+        }
+        if ((rc = upload(&c->d_vox, vox.data(), vox.size(), s))) break;
         if ((rc = upload(&c->d_tab, tab.data(), tab.size(), s))) break;
         if ((rc = upload(&c->d_major, major.data(), major.size(), s))) break;
         if ((rc = upload(&c->d_resp, dt.response, (size_t)dt.n_energies, s))) break;
         if ((rc = upload(&c->d_bin_e, bin_e.data(), bin_e.size(), s))) break;
-        if ((rc = upload(&c->d_cdf_pix, cdf_pix.data(), cdf_pix.size(), s))) break;
+        const std::vector<uint32_t> kcdf_pix = kcdf_of(cdf_pix), kcdf_e = kcdf_of(cdf_e);
+        if ((rc = upload(&c->d_kcdf_pix, kcdf_pix.data(), kcdf_pix.size(), s))) break;
         if ((rc = upload(&c->d_guide_pix, guide_pix.data(), guide_pix.size(), s))) break;
-        if ((rc = upload(&c->d_cdf_e, cdf_e.data(), cdf_e.size(), s))) break;
+        if ((rc = upload(&c->d_kcdf_e, kcdf_e.data(), kcdf_e.size(), s))) break;
         if ((rc = upload(&c->d_guide_e, guide_e.data(), guide_e.size(), s))) break;
         if ((rc = upload(&c->d_wnorm, wnorm.data(), wnorm.size(), s))) break;
         if ((rc = upload(&c->d_mu_rt, mu_rt.data(), mu_rt.size(), s))) break;
@@ -339,7 +356,7 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
     gdrr_mc_options n = *o;
     set_defaults(&n);
     if (n.block_size % 32 || n.block_size > 256 || n.block_size < 32) return GDRR_ERR_INVALID_ARG;
-    if (n.hist_per_thread > 4096 || n.refill_interval > 1024 || n.blocks_per_sm < 0 || n.blocks_per_sm > 64)
+    if (n.hist_per_thread > 4096 || n.batch_min > 32 || n.blocks_per_sm < 0 || n.blocks_per_sm > 64)
         return GDRR_ERR_INVALID_ARG;
     if (!(n.e_cut_kev < 1e6)) return GDRR_ERR_INVALID_ARG;
     ctx->opt = n;
@@ -363,7 +380,7 @@ GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_de
     RtParams p;
     p.nx = ctx->nx; p.ny = ctx->ny; p.nz = ctx->nz;
     fill_box(ctx, p.lo, p.hi, p.ivox);
-    p.mat = ctx->d_mat; p.dens = ctx->d_dens;
+    p.vox = ctx->d_vox;
     p.n_mat = ctx->n_mat; p.n_bins = ctx->n_bins;
     p.mu_rt = ctx->d_mu_rt; p.wr = ctx->d_wr; p.wnorm = ctx->d_wnorm;
     p.nu = ctx->geo.nu; p.nv = ctx->geo.nv;
@@ -389,15 +406,15 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     McParams p;
     p.nx = ctx->nx; p.ny = ctx->ny; p.nz = ctx->nz;
     fill_box(ctx, p.lo, p.hi, p.ivox);
-    p.mat = ctx->d_mat; p.dens = ctx->d_dens;
+    p.vox = ctx->d_vox;
     p.n_mat = ctx->n_mat; p.n_e = ctx->n_e;
     p.e0 = (float)ctx->e0; p.inv_de = (float)(1.0 / ctx->de);
     p.tab = ctx->d_tab; p.major = ctx->d_major;
     p.n_r = ctx->n_r; p.r0 = (float)ctx->r0; p.inv_dr = (float)(1.0 / ctx->dr); p.resp = ctx->d_resp;
     p.npix = ctx->geo.nu * ctx->geo.nv; p.n_guide_pix = ctx->n_guide_pix;
-    p.cdf_pix = ctx->d_cdf_pix; p.guide_pix = ctx->d_guide_pix;
+    p.kcdf_pix = ctx->d_kcdf_pix; p.guide_pix = ctx->d_guide_pix;
     p.n_bins = ctx->n_bins; p.n_guide_e = ctx->n_guide_e;
-    p.cdf_e = ctx->d_cdf_e; p.guide_e = ctx->d_guide_e; p.bin_e = ctx->d_bin_e;
+    p.kcdf_e = ctx->d_kcdf_e; p.guide_e = ctx->d_guide_e; p.bin_e = ctx->d_bin_e;
     p.nu = ctx->geo.nu; p.nv = ctx->geo.nv;
     p.hu = (float)(0.5 * ctx->geo.nu); p.hv = (float)(0.5 * ctx->geo.nv);
     p.du = (float)ctx->geo.du_mm; p.dv = (float)ctx->geo.dv_mm;
@@ -415,7 +432,7 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     }
     p.records = records_dev;
     p.chunk = 32 * ctx->opt.hist_per_thread;
-    p.refill_interval = ctx->opt.refill_interval;
+    p.batch_min = ctx->opt.batch_min;
     const bool rec = records_dev != nullptr;
     const int block = ctx->opt.block_size;
     int per_sm = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : mc_occupancy_blocks(ctx->n_mat, block, rec);

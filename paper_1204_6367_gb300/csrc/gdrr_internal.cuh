@@ -31,11 +31,10 @@ struct Job {
 
 // Everything the transport kernel reads, by value.
 struct McParams {
-    // phantom box and voxel data
+    // phantom box and voxel records {density bits, material}
     int nx, ny, nz;
     float lo[3], hi[3], ivox[3];
-    const uint8_t* mat;
-    const float* dens;
+    const uint2* vox;
     // material tables, mm^-1 per g/cm^3, [m][k][e]; majorant nodes [e]
     int n_mat, n_e;
     float e0, inv_de;
@@ -47,10 +46,10 @@ struct McParams {
     const float* resp;
     // source: pixel and energy inverse CDFs with guide tables
     int npix, n_guide_pix;
-    const double* cdf_pix;
+    const uint32_t* kcdf_pix;      // floor(cdf * 2^24): integer thresholds of the inverse CDF
     const int* guide_pix;
     int n_bins, n_guide_e;
-    const double* cdf_e;
+    const uint32_t* kcdf_e;
     const int* guide_e;
     const float* bin_e;
     // detector grid
@@ -68,15 +67,14 @@ struct McParams {
     unsigned long long* stats;     // GDRR_NSTATS
     gdrr_history_record* records;  // NULL or [total]
     int chunk;                     // histories a warp claims at a time
-    int refill_interval;
+    int batch_min;                 // waiting lanes that trigger a warp's service batch
 };
 
 // Ray-tracing parameters.
 struct RtParams {
     int nx, ny, nz;
     float lo[3], hi[3], ivox[3];
-    const uint8_t* mat;
-    const float* dens;
+    const uint2* vox;
     int n_mat, n_bins;
     const float* mu_rt;     // [n_bins][n_mat] total mu_hat at the channel energy, mm^-1 per g/cm^3
     const float* wr;        // [n_bins] phi_b r(E_b), phi normalised

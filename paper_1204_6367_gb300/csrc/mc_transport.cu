@@ -3,9 +3,19 @@
 // One CUDA thread tracks one photon history at a time (as in the paper), but
 // the grid is persistent: warps claim chunks of histories from a global
 // counter and refill lanes whose history ended, so lanes stay busy while
-// histories of very different lengths finish.  Tallies are int64 fixed point
-// (2^-24 keV), summed with integer atomics, so the result does not depend on
-// which lane ran which history or in which order.
+// histories of very different lengths finish.  The common event, a Woodcock
+// free flight that ends in a virtual collision, runs every iteration; the
+// rare, long branches (Rayleigh / Compton sampling, the detector tally, the
+// start of a new history) are deferred: a lane that needs one waits, and once
+// batch_min lanes of the warp wait, the warp serves them together.  Tallies
+// are int64 fixed point (2^-24 keV), summed with integer atomics, so the
+// result does not depend on which lane ran which history, when, or in which
+// order.
+//
+// Data layout: one 8-byte record {density bits, material index} per voxel,
+// x fastest, so each trilinear corner is a single 8-byte gather from L2; the
+// per-lane energy-dependent coefficients live in shared memory, indexed by
+// material, one column per thread.
 //
 // Arithmetic contract.  This file is compiled with -fmad=false: every FP32
 // operation below is one IEEE-rounded operation, evaluated in the order
@@ -17,13 +27,15 @@
 //
 // Readings of points the paper leaves open:
 //  * random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
-//    counter = (block, angle index, history id lo, hi); uniforms are
-//    ((word >> 8) + 1) * 2^-24 in (0, 1];
+//    counter = (block, angle index, history id lo, hi), one whole block per
+//    draw site; uniforms are ((word >> 8) + 1) * 2^-24 in (0, 1];
 //  * source: detector pixel from the fluence map w(u) and channel from the
 //    spectrum phi(E), each by inverse CDF; uniform point inside the pixel;
-//  * material at an off-centre point: per-material trilinear partial
-//    densities, mu(x, E) = sum_m mu_hat(m, E) rho_m(x) (density interpolation
-//    of Section 2.4, consistent with the ray-traced field of Section 2.3);
+//  * material at an off-centre point: trilinear mixture of the eight corner
+//    voxels, mu_k(x, E) = sum_c w_c rho_c mu_hat_k(m_c, E) (the density
+//    interpolation of Section 2.4, the same field the ray tracer of Section
+//    2.3 integrates); the total decides real versus virtual, then one uniform
+//    picks Rayleigh, Compton or photoelectric in that order;
 //  * field: clamp to edge inside the voxel box, vacuum outside;
 //  * Woodcock majorant mu_max(E): largest mu over materials at their largest
 //    density, the larger of the two bracketing energy nodes;
@@ -53,33 +65,29 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32
     }
 }
 
-// The random stream of one history: words consumed in order, four per block.
+// The random stream of one history: Philox blocks with counter (k, angle
+// index, history id lo, hi), k = 0, 1, 2, ...; every draw site takes the next
+// whole block (source, each free flight, each rejection attempt), so the
+// Philox rounds of a free flight run on all lanes of a warp together.
 struct Stream {
-    uint32_t k0, k1, angle, hlo, hhi, blk;
-    uint32_t b0, b1, b2, b3;
-    int pos;
+    uint32_t angle, hlo, hhi, blk;
 
-    __device__ __forceinline__ void init(uint64_t seed, uint32_t angle_index, uint64_t hid) {
-        k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32);
+    __device__ __forceinline__ void init(uint32_t angle_index, uint64_t hid) {
         angle = angle_index; hlo = (uint32_t)hid; hhi = (uint32_t)(hid >> 32);
-        blk = 0; pos = 4;
+        blk = 0;
     }
-    __device__ __forceinline__ uint32_t word() {
-        if (pos == 4) {
-            uint32_t c0 = blk, c1 = angle, c2 = hlo, c3 = hhi;
-            philox4x32_10(c0, c1, c2, c3, k0, k1);
-            b0 = c0; b1 = c1; b2 = c2; b3 = c3;
-            ++blk;
-            pos = 0;
-        }
-        const uint32_t w = pos == 0 ? b0 : (pos == 1 ? b1 : (pos == 2 ? b2 : b3));
-        ++pos;
-        return w;
-    }
-    __device__ __forceinline__ float uniform() {
-        return (float)((word() >> 8) + 1u) * (float)(1.0 / 16777216.0);
+    __device__ __forceinline__ uint4 block(uint64_t seed) {
+        uint32_t c0 = blk, c1 = angle, c2 = hlo, c3 = hhi;
+        philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+        ++blk;
+        return make_uint4(c0, c1, c2, c3);
     }
 };
+
+// Uniform on (0, 1]: the top 24 bits plus one, times 2^-24 (exact in FP32).
+__device__ __forceinline__ float uniform(uint32_t w) {
+    return (float)((w >> 8) + 1u) * (float)(1.0 / 16777216.0);
+}
 
 // ln(x), x a positive normal float: x = m 2^e, m in [sqrt(1/2), sqrt(2)),
 // ln m = 2 atanh(s), s = (m - 1)/(m + 1), by the Taylor series of atanh to
@@ -103,14 +111,18 @@ __device__ __forceinline__ float gd_logf(float x) {
     return fe * (float)(2839.0 / 4096.0) + (fe * (float)(0.69314718055994530942 - 2839.0 / 4096.0) + lm);
 }
 
-// Smallest j with xi <= cdf[j]; the guide table gives a start, two short scans finish.
-__device__ __forceinline__ int cdf_search(const double* __restrict__ cdf, const int* __restrict__ guide,
-                                          int n_guide, double xi) {
-    int gi = (int)(xi * (double)n_guide);
-    gi = gi < 0 ? 0 : (gi > n_guide - 1 ? n_guide - 1 : gi);
+// Inverse-CDF search in integers.  A uniform is xi = k 2^-24 with k the top
+// 24 bits of its word plus one, and xi <= cdf[j] holds exactly when
+// k <= floor(cdf[j] 2^24) = kcdf[j]; the smallest such j is the sample.  The
+// guide table gives a start, two short scans finish.
+__device__ __forceinline__ int cdf_search(const uint32_t* __restrict__ kcdf, const int* __restrict__ guide,
+                                          int n_guide, uint32_t w) {
+    const uint32_t k = (w >> 8) + 1u;
+    int gi = (int)(((uint64_t)k * (uint64_t)n_guide) >> 24);
+    gi = gi > n_guide - 1 ? n_guide - 1 : gi;
     int j = __ldg(guide + gi);
-    while (j > 0 && xi <= __ldg(cdf + j - 1)) --j;
-    while (xi > __ldg(cdf + j)) ++j;
+    while (j > 0 && k <= __ldg(kcdf + j - 1)) --j;
+    while (k > __ldg(kcdf + j)) ++j;
     return j;
 }
 
@@ -124,33 +136,6 @@ __device__ __forceinline__ void interp_index(float e, float e0, float inv_de, in
     f = fi - (float)ie;
 }
 
-template <int NM>
-struct Coeffs {
-    float r[NM], c[NM], p[NM];
-    float mumax;
-
-    __device__ __forceinline__ void at(const McParams& P, float e) {
-        int ie; float f;
-        interp_index(e, P.e0, P.inv_de, P.n_e, ie, f);
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            if (m < P.n_mat) {
-                const float* t = P.tab + (size_t)m * 3 * P.n_e;
-                const float r0 = __ldg(t + ie), r1 = __ldg(t + ie + 1);
-                const float c0 = __ldg(t + P.n_e + ie), c1 = __ldg(t + P.n_e + ie + 1);
-                const float p0 = __ldg(t + 2 * P.n_e + ie), p1 = __ldg(t + 2 * P.n_e + ie + 1);
-                r[m] = r0 + f * (r1 - r0);
-                c[m] = c0 + f * (c1 - c0);
-                p[m] = p0 + f * (p1 - p0);
-            } else {
-                r[m] = 0.0f; c[m] = 0.0f; p[m] = 0.0f;
-            }
-        }
-        const float a = __ldg(P.major + ie), b = __ldg(P.major + ie + 1);
-        mumax = a > b ? a : b;
-    }
-};
-
 __device__ __forceinline__ float response(const McParams& P, float e) {
     int ir; float f;
     interp_index(e, P.r0, P.inv_dr, P.n_r, ir, f);
@@ -158,10 +143,11 @@ __device__ __forceinline__ float response(const McParams& P, float e) {
     return a + f * (b - a);
 }
 
-__device__ __forceinline__ void azimuth(Stream& rs, float& cp, float& sp) {
+__device__ __forceinline__ void azimuth(Stream& rs, uint64_t seed, float& cp, float& sp) {
     for (;;) {
-        const float a = 2.0f * rs.uniform() - 1.0f;
-        const float b = 2.0f * rs.uniform() - 1.0f;
+        const uint4 w = rs.block(seed);
+        const float a = 2.0f * uniform(w.x) - 1.0f;
+        const float b = 2.0f * uniform(w.y) - 1.0f;
         const float r2 = a * a + b * b;
         if (r2 <= 1.0f && r2 > 0.0f) {
             cp = (a * a - b * b) / r2;
@@ -191,14 +177,15 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float ct, f
     w = nw_ / len;
 }
 
-__device__ __forceinline__ void compton(Stream& rs, float e, float& ct_out, float& e_out) {
+__device__ __forceinline__ void compton(Stream& rs, uint64_t seed, float e, float& ct_out, float& e_out) {
     const float alpha = e / (float)510.99895;
     const float ta = 2.0f * alpha;
     float x;
     for (;;) {
-        const float r1 = rs.uniform();
-        const float r2 = rs.uniform();
-        const float r3 = rs.uniform();
+        const uint4 w = rs.block(seed);
+        const float r1 = uniform(w.x);
+        const float r2 = uniform(w.y);
+        const float r3 = uniform(w.z);
         if (r1 <= (1.0f + ta) / (9.0f + ta)) {
             x = 1.0f + ta * r2;
             if (r3 <= 4.0f * (x - 1.0f) / (x * x)) break;
@@ -212,10 +199,11 @@ __device__ __forceinline__ void compton(Stream& rs, float e, float& ct_out, floa
     e_out = e / x;
 }
 
-__device__ __forceinline__ float rayleigh(Stream& rs) {
+__device__ __forceinline__ float rayleigh(Stream& rs, uint64_t seed) {
     for (;;) {
-        const float a = rs.uniform();
-        const float b = rs.uniform();
+        const uint4 w = rs.block(seed);
+        const float a = uniform(w.x);
+        const float b = uniform(w.y);
         const float mu = 2.0f * a - 1.0f;
         if (2.0f * b <= 1.0f + mu * mu) return mu;
     }
@@ -223,25 +211,59 @@ __device__ __forceinline__ float rayleigh(Stream& rs) {
 
 enum : uint32_t { OUT_PRIMARY = 0, OUT_SCATTER = 1, OUT_PHOTO = 2, OUT_CUTOFF = 3, OUT_MISS = 4, OUT_STEP_LIMIT = 5 };
 
-// Per-lane counters, summed into the stats array when the lane retires.
-struct Counters {
-    uint32_t hist, steps, virt, ray, comp, photo, tp, ts, miss, cut, lim;
-};
+// Lane states.  A lane whose history needs an interaction, a tally or a new
+// history waits in one of the non-FLY states until enough lanes of its warp
+// wait too; the warp then serves them together, which keeps the expensive
+// rare branches from running with one or two active lanes.
+enum : int { S_DEAD = 0, S_FLY = 1, S_RAY = 2, S_COMP = 3, S_ESC = 4 };
+
+// Block-shared counters (GDRR_NSTATS), flushed to the stats array at exit.
+__device__ __forceinline__ void count(unsigned long long* c, int k) { atomicAdd(c + k, 1ull); }
 
 template <int NM, bool REC>
 struct Lane {
-    // photon state
     float px, py, pz, dx, dy, dz, e;
-    int scattered;
-    int job;
-    uint64_t gidx;
+    float mumax, inv_mumax;
+    int state, scattered, job;
     uint32_t nsteps;
     Stream rs;
-    Coeffs<NM> co;
+    // per-thread coefficient tables in shared memory: coef[k][m][tid],
+    // k = 0 total, 1 Rayleigh, 2 Compton (photoelectric is the remainder)
+    float* coef;
+    int stride;          // blockDim.x
     // event record (REC only)
+    uint64_t gidx;
     uint32_t r_virt, r_ray, r_comp, r_first;
     float r_esrc;
     double r_dep;
+
+    __device__ __forceinline__ float& cf(int k, int m) { return coef[(k * NM + m) * stride]; }
+
+    __device__ __forceinline__ void set_energy(const McParams& P, float en) {
+        e = en;
+        int ie; float f;
+        interp_index(en, P.e0, P.inv_de, P.n_e, ie, f);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            float r = 0.0f, c = 0.0f, t = 0.0f;
+            if (m < P.n_mat) {
+                const float* tb = P.tab + (size_t)m * 3 * P.n_e;
+                const float r0 = __ldg(tb + ie), r1 = __ldg(tb + ie + 1);
+                const float c0 = __ldg(tb + P.n_e + ie), c1 = __ldg(tb + P.n_e + ie + 1);
+                const float p0 = __ldg(tb + 2 * P.n_e + ie), p1 = __ldg(tb + 2 * P.n_e + ie + 1);
+                r = r0 + f * (r1 - r0);
+                c = c0 + f * (c1 - c0);
+                const float p = p0 + f * (p1 - p0);
+                t = (r + c) + p;
+            }
+            cf(0, m) = t;
+            cf(1, m) = r;
+            cf(2, m) = c;
+        }
+        const float a = __ldg(P.major + ie), b = __ldg(P.major + ie + 1);
+        mumax = a > b ? a : b;
+        inv_mumax = 1.0f / mumax;
+    }
 
     __device__ __forceinline__ void record(const McParams& P, uint32_t outcome, int pixel, uint32_t photo) {
         if (!REC) return;
@@ -252,9 +274,12 @@ struct Lane {
         P.records[gidx] = r;
     }
 
-    // The photon left the phantom (or never entered it): straight line to
-    // the imager plane, tally r(E) at the pixel it meets.
-    __device__ __forceinline__ void escape(const McParams& P, Counters& k) {
+    // Straight line from the box surface (or the source) to the imager
+    // plane; tally r(E) at the pixel it meets (Section 2.4).  A lane that
+    // left the box in a free flight first moves from its last position inside
+    // to the box surface along its direction.
+    __device__ __forceinline__ void escape(const McParams& P, unsigned long long* cnt, bool from_inside) {
+        if (from_inside) move_to_box_exit(P);
         const Job& J = P.jobs[job];
         const float n0 = J.f.n[0], n1 = J.f.n[1], n2 = J.f.n[2];
         const float dn = dx * n0 + dy * n1 + dz * n2;
@@ -281,10 +306,10 @@ struct Lane {
                 }
             }
         }
-        if (outcome == OUT_PRIMARY) ++k.tp;
-        else if (outcome == OUT_SCATTER) ++k.ts;
-        else ++k.miss;
+        count(cnt, outcome == OUT_PRIMARY ? GDRR_ST_TALLY_PRIMARY
+                                          : (outcome == OUT_SCATTER ? GDRR_ST_TALLY_SCATTER : GDRR_ST_MISS));
         record(P, outcome, pixel, 0);
+        state = S_DEAD;
     }
 
     __device__ __forceinline__ void move_to_box_exit(const McParams& P) {
@@ -307,8 +332,9 @@ struct Lane {
         pz = pz + te * dz;
     }
 
-    // Start history gidx; returns true when it is still in flight.
-    __device__ __forceinline__ bool start(const McParams& P, uint64_t g, Counters& k) {
+    // Start flattened history g: source sampling and box entry.  Leaves the
+    // lane FLY, or DEAD after tallying a photon that misses the box.
+    __device__ __forceinline__ void start(const McParams& P, uint64_t g, unsigned long long* cnt) {
         gidx = g;
         int lo = 0, hi = P.n_jobs - 1;
         while (lo < hi) {
@@ -318,21 +344,20 @@ struct Lane {
         job = lo;
         const Job& J = P.jobs[job];
         const uint64_t hid = J.hid_offset + (g - J.first);
-        rs.init(P.seed, J.angle_index, hid);
-        ++k.hist;
+        rs.init(J.angle_index, hid);
+        count(cnt, GDRR_ST_HISTORIES);
         nsteps = 0;
         scattered = 0;
         if (REC) { r_virt = 0; r_ray = 0; r_comp = 0; r_first = 0; r_dep = 0.0; }
 
-        const float xi_pix = rs.uniform();
-        const float xi_u = rs.uniform();
-        const float xi_v = rs.uniform();
-        const float xi_e = rs.uniform();
-        const int j = cdf_search(P.cdf_pix, P.guide_pix, P.n_guide_pix, (double)xi_pix);
+        const uint4 w0 = rs.block(P.seed);
+        const float xi_u = uniform(w0.y);
+        const float xi_v = uniform(w0.z);
+        const int j = cdf_search(P.kcdf_pix, P.guide_pix, P.n_guide_pix, w0.x);
         const int iu = j % P.nu, iv = j / P.nu;
-        const int eb = cdf_search(P.cdf_e, P.guide_e, P.n_guide_e, (double)xi_e);
-        e = __ldg(P.bin_e + eb);
-        if (REC) r_esrc = e;
+        const int eb = cdf_search(P.kcdf_e, P.guide_e, P.n_guide_e, w0.w);
+        const float en = __ldg(P.bin_e + eb);
+        if (REC) r_esrc = en;
         const float a_u = ((float)iu + xi_u - P.hu) * P.du;
         const float a_v = ((float)iv + xi_v - P.hv) * P.dv;
         const float t0 = J.f.P[0] + a_u * J.f.eu[0] + a_v * J.f.ev[0];
@@ -346,8 +371,8 @@ struct Lane {
         dy = dy / len;
         dz = dz / len;
         px = J.f.S[0]; py = J.f.S[1]; pz = J.f.S[2];
+        e = en;
 
-        // slab entry into the voxel box
         float tmin = 0.0f, tmax = (float)3.0e38;
         bool hit = true;
         const float d[3] = {dx, dy, dz};
@@ -366,171 +391,173 @@ struct Lane {
         }
         if (tmin >= tmax) hit = false;
         if (!hit) {
-            escape(P, k);
-            return false;
+            escape(P, cnt, false);
+            return;
         }
         px = px + tmin * dx;
         py = py + tmin * dy;
         pz = pz + tmin * dz;
-        co.at(P, e);
-        return true;
+        set_energy(P, en);
+        state = S_FLY;
     }
 
-    // One Woodcock free flight and what happens at its end; returns false
-    // when the history is over.
-    __device__ __forceinline__ bool step(const McParams& P, Counters& k) {
+    // One Woodcock free flight and the real/virtual decision at its end.
+    __device__ __forceinline__ void step(const McParams& P, uint32_t& c_steps, uint32_t& c_virt,
+                                         unsigned long long* cnt) {
         if ((int)nsteps >= P.max_steps) {
-            ++k.lim;
+            count(cnt, GDRR_ST_STEP_LIMIT);
             record(P, OUT_STEP_LIMIT, -1, 0);
-            return false;
+            state = S_DEAD;
+            return;
         }
-        const float xi_s = rs.uniform();
-        const float s = -gd_logf(xi_s) / co.mumax;
+        const uint4 wf = rs.block(P.seed);            // this flight's block
+        const float s = -gd_logf(uniform(wf.x)) * inv_mumax;
         ++nsteps;
-        ++k.steps;
+        ++c_steps;
         const float qx = px + s * dx, qy = py + s * dy, qz = pz + s * dz;
         const bool inside = (qx >= P.lo[0] && qx <= P.hi[0]) && (qy >= P.lo[1] && qy <= P.hi[1])
                          && (qz >= P.lo[2] && qz <= P.hi[2]);
         if (!inside) {
-            move_to_box_exit(P);
-            escape(P, k);
-            return false;
+            state = S_ESC;           // the box exit and tally wait for the warp's batch
+            return;
         }
         px = qx; py = qy; pz = qz;
 
-        // trilinear partial densities per material
-        int i0[3], i1[3];
-        float w0[3], w1[3];
-        const float q[3] = {px, py, pz};
-        const int dims[3] = {P.nx, P.ny, P.nz};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float fa = (q[a] - P.lo[a]) * P.ivox[a] - 0.5f;
-            int f0 = (int)floorf(fa);
-            const float t = fa - (float)f0;
-            int f1 = f0 + 1;
-            f0 = f0 < 0 ? 0 : (f0 > dims[a] - 1 ? dims[a] - 1 : f0);
-            f1 = f1 < 0 ? 0 : (f1 > dims[a] - 1 ? dims[a] - 1 : f1);
-            i0[a] = f0; i1[a] = f1;
-            w0[a] = 1.0f - t; w1[a] = t;
-        }
-        float acc[NM];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) acc[m] = 0.0f;
+        // trilinear corner weights (w_x w_y) w_z and clamped corner indices
+        const float fx = (px - P.lo[0]) * P.ivox[0] - 0.5f;
+        const float fy = (py - P.lo[1]) * P.ivox[1] - 0.5f;
+        const float fz = (pz - P.lo[2]) * P.ivox[2] - 0.5f;
+        const int gx = (int)floorf(fx), gy = (int)floorf(fy), gz = (int)floorf(fz);
+        const float tx = fx - (float)gx, ty = fy - (float)gy, tz = fz - (float)gz;
+        const int x0 = min(max(gx, 0), P.nx - 1), x1 = min(max(gx + 1, 0), P.nx - 1);
+        const int y0 = min(max(gy, 0), P.ny - 1), y1 = min(max(gy + 1, 0), P.ny - 1);
+        const int z0 = min(max(gz, 0), P.nz - 1), z1 = min(max(gz + 1, 0), P.nz - 1);
+        const float wx0 = 1.0f - tx, wy0 = 1.0f - ty, wz0 = 1.0f - tz;
+        const float wxy[4] = {wx0 * wy0, tx * wy0, wx0 * ty, tx * ty};
         const int sy = P.nx, sz = P.nx * P.ny;
+        const int rows[4] = {y0 * sy + z0 * sz, y1 * sy + z0 * sz, y0 * sy + z1 * sz, y1 * sy + z1 * sz};
+        float a[8];
+        int mc[8];
 #pragma unroll
-        for (int corner = 0; corner < 8; ++corner) {
-            const int cx = corner & 1, cy = (corner >> 1) & 1, cz = corner >> 2;
-            const int v = (cx ? i1[0] : i0[0]) + sy * (cy ? i1[1] : i0[1]) + sz * (cz ? i1[2] : i0[2]);
-            const float w = (cx ? w1[0] : w0[0]) * (cy ? w1[1] : w0[1]) * (cz ? w1[2] : w0[2]);
-            const float a = w * __ldg(P.dens + v);
-            const int mc = __ldg(P.mat + v);
+        for (int c = 0; c < 8; ++c) {
+            const int v = rows[c >> 1] + ((c & 1) ? x1 : x0);
+            const uint2 vx = __ldg(P.vox + v);
+            a[c] = (wxy[c & 3] * ((c >> 2) ? tz : wz0)) * __uint_as_float(vx.x);
+            mc[c] = (int)vx.y;
+        }
+        float muT = a[0] * cf(0, mc[0]);
 #pragma unroll
-            for (int m = 0; m < NM; ++m) acc[m] = acc[m] + (mc == m ? a : 0.0f);
+        for (int c = 1; c < 8; ++c) muT = muT + a[c] * cf(0, mc[c]);
+        const float t = uniform(wf.y) * mumax;
+        if (t > muT) {
+            ++c_virt;
+            if (REC) ++r_virt;
+            return;
         }
-        float muR = 0.0f, muC = 0.0f, muP = 0.0f;
+        float muR = a[0] * cf(1, mc[0]);
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            muR = muR + acc[m] * co.r[m];
-            muC = muC + acc[m] * co.c[m];
-            muP = muP + acc[m] * co.p[m];
-        }
-        const float t = rs.uniform() * co.mumax;
-        const float c1 = muR, c2 = c1 + muC, c3 = c2 + muP;
-        if (t <= c1) {
-            const float ct = rayleigh(rs);
-            float cp, sp;
-            azimuth(rs, cp, sp);
-            rotate(dx, dy, dz, ct, cp, sp);
-            scattered = 1;
-            ++k.ray;
-            if (REC) { ++r_ray; if (!r_first) r_first = 1; }
-            return true;
-        }
-        if (t <= c2) {
-            float ct, e2, cp, sp;
-            compton(rs, e, ct, e2);
-            azimuth(rs, cp, sp);
-            rotate(dx, dy, dz, ct, cp, sp);
-            scattered = 1;
-            ++k.comp;
-            if (REC) { ++r_comp; if (!r_first) r_first = 2; r_dep += (double)e - (double)e2; }
-            e = e2;
-            if (e < P.e_cut) {
-                if (REC) r_dep += (double)e;
-                ++k.cut;
-                record(P, OUT_CUTOFF, -1, 0);
-                return false;
-            }
-            co.at(P, e);
-            return true;
-        }
-        if (t <= c3) {
-            ++k.photo;
+        for (int c = 1; c < 8; ++c) muR = muR + a[c] * cf(1, mc[c]);
+        float muC = a[0] * cf(2, mc[0]);
+#pragma unroll
+        for (int c = 1; c < 8; ++c) muC = muC + a[c] * cf(2, mc[c]);
+        if (t <= muR) {
+            state = S_RAY;
+        } else if (t <= muR + muC) {
+            state = S_COMP;
+        } else {
+            count(cnt, GDRR_ST_PHOTO);
             if (REC) { if (!r_first) r_first = 3; r_dep += (double)e; }
             record(P, OUT_PHOTO, -1, 1);
-            return false;
+            state = S_DEAD;
         }
-        ++k.virt;
-        if (REC) ++r_virt;
-        return true;
+    }
+
+    // The deferred Rayleigh or Compton interaction of a waiting lane.
+    __device__ __forceinline__ void interact(const McParams& P, unsigned long long* cnt) {
+        float cp, sp;
+        if (state == S_RAY) {
+            const float ct = rayleigh(rs, P.seed);
+            azimuth(rs, P.seed, cp, sp);
+            rotate(dx, dy, dz, ct, cp, sp);
+            scattered = 1;
+            count(cnt, GDRR_ST_RAYLEIGH);
+            if (REC) { ++r_ray; if (!r_first) r_first = 1; }
+            state = S_FLY;
+            return;
+        }
+        float ct, e2;
+        compton(rs, P.seed, e, ct, e2);
+        azimuth(rs, P.seed, cp, sp);
+        rotate(dx, dy, dz, ct, cp, sp);
+        scattered = 1;
+        count(cnt, GDRR_ST_COMPTON);
+        if (REC) { ++r_comp; if (!r_first) r_first = 2; r_dep += (double)e - (double)e2; }
+        if (e2 < P.e_cut) {
+            e = e2;
+            if (REC) r_dep += (double)e;
+            count(cnt, GDRR_ST_CUTOFF);
+            record(P, OUT_CUTOFF, -1, 0);
+            state = S_DEAD;
+            return;
+        }
+        set_energy(P, e2);
+        state = S_FLY;
     }
 };
 
-__device__ __forceinline__ void flush_counter(unsigned long long* dst, uint32_t v) {
-    const uint32_t s = __reduce_add_sync(FULL, v);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
-}
-
 template <int NM, bool REC>
-__global__ void __launch_bounds__(256) mc_kernel(const McParams P) {
+__global__ void __launch_bounds__(256, 4) mc_kernel(const McParams P) {
+    extern __shared__ float smem[];
+    __shared__ unsigned long long cnt[GDRR_NSTATS];
+    for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x) cnt[i] = 0ull;
+    __syncthreads();
+
     const int lane = threadIdx.x & 31;
     Lane<NM, REC> L;
-    Counters k = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    bool alive = false;
+    L.coef = smem + threadIdx.x;
+    L.stride = blockDim.x;
+    L.state = S_DEAD;
+    uint32_t c_steps = 0, c_virt = 0;
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
-    int since_refill = P.refill_interval;
 
     for (;;) {
-        if (!exhausted && (since_refill >= P.refill_interval || !__any_sync(FULL, alive))) {
-            since_refill = 0;
-            unsigned need = __ballot_sync(FULL, !alive);
-            while (need) {
-                if (pool_next >= pool_end) {
-                    unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)P.chunk);
-                    base = __shfl_sync(FULL, base, 0);
-                    if (base >= P.total) { exhausted = true; break; }
-                    pool_next = base;
-                    pool_end = base + (unsigned long long)P.chunk;
-                    if (pool_end > P.total) pool_end = P.total;
+        const unsigned fly = __ballot_sync(FULL, L.state == S_FLY);
+        if (32 - __popc(fly) >= P.batch_min || fly == 0u) {
+            // serve waiting lanes together: interactions, tallies, new histories
+            if (L.state == S_RAY || L.state == S_COMP) L.interact(P, cnt);
+            if (L.state == S_ESC) L.escape(P, cnt, true);
+            if (!exhausted) {
+                unsigned need = __ballot_sync(FULL, L.state == S_DEAD);
+                while (need) {
+                    if (pool_next >= pool_end) {
+                        unsigned long long base = 0;
+                        if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)P.chunk);
+                        base = __shfl_sync(FULL, base, 0);
+                        if (base >= P.total) { exhausted = true; break; }
+                        pool_next = base;
+                        pool_end = base + (unsigned long long)P.chunk;
+                        if (pool_end > P.total) pool_end = P.total;
+                    }
+                    const unsigned avail = (unsigned)(pool_end - pool_next);
+                    const unsigned want = (unsigned)__popc(need);
+                    const unsigned take = want < avail ? want : avail;
+                    const unsigned rank = (unsigned)__popc(need & ((1u << lane) - 1u));
+                    if (((need >> lane) & 1u) && rank < take) L.start(P, pool_next + rank, cnt);
+                    pool_next += take;
+                    need = __ballot_sync(FULL, L.state == S_DEAD);
                 }
-                const unsigned avail = (unsigned)(pool_end - pool_next);
-                const unsigned want = (unsigned)__popc(need);
-                const unsigned cnt = want < avail ? want : avail;
-                const unsigned rank = (unsigned)__popc(need & ((1u << lane) - 1u));
-                if (!alive && rank < cnt) alive = L.start(P, pool_next + rank, k);
-                pool_next += cnt;
-                need = __ballot_sync(FULL, !alive);
             }
+            if (exhausted && !__any_sync(FULL, L.state != S_DEAD)) break;
         }
-        ++since_refill;
-        if (exhausted && !__any_sync(FULL, alive)) break;
-        if (alive) alive = L.step(P, k);
+        if (L.state == S_FLY) L.step(P, c_steps, c_virt, cnt);
     }
 
-    flush_counter(P.stats + GDRR_ST_HISTORIES, k.hist);
-    flush_counter(P.stats + GDRR_ST_STEPS, k.steps);
-    flush_counter(P.stats + GDRR_ST_VIRTUAL, k.virt);
-    flush_counter(P.stats + GDRR_ST_RAYLEIGH, k.ray);
-    flush_counter(P.stats + GDRR_ST_COMPTON, k.comp);
-    flush_counter(P.stats + GDRR_ST_PHOTO, k.photo);
-    flush_counter(P.stats + GDRR_ST_TALLY_PRIMARY, k.tp);
-    flush_counter(P.stats + GDRR_ST_TALLY_SCATTER, k.ts);
-    flush_counter(P.stats + GDRR_ST_MISS, k.miss);
-    flush_counter(P.stats + GDRR_ST_CUTOFF, k.cut);
-    flush_counter(P.stats + GDRR_ST_STEP_LIMIT, k.lim);
+    atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)c_steps);
+    atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)c_virt);
+    __syncthreads();
+    for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
+        if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
 }
 
 __global__ void stream_words_kernel(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist,
@@ -538,21 +565,29 @@ __global__ void stream_words_kernel(uint64_t seed, uint32_t angle_index, uint64_
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_hist) return;
     Stream rs;
-    rs.init(seed, angle_index, hid0 + (uint64_t)i);
+    rs.init(angle_index, hid0 + (uint64_t)i);
     uint32_t* o = out + (size_t)i * 4 * n_blocks;
-    for (int w = 0; w < 4 * n_blocks; ++w) o[w] = rs.word();
+    for (int b = 0; b < n_blocks; ++b) {
+        const uint4 w = rs.block(seed);
+        o[4 * b] = w.x; o[4 * b + 1] = w.y; o[4 * b + 2] = w.z; o[4 * b + 3] = w.w;
+    }
 }
+
+template <int NM>
+constexpr size_t smem_bytes(int block) { return (size_t)3 * NM * block * sizeof(float); }
 
 template <int NM, bool REC>
 cudaError_t launch_t(const McParams& p, int block, int grid, cudaStream_t s) {
-    mc_kernel<NM, REC><<<grid, block, 0, s>>>(p);
+    mc_kernel<NM, REC><<<grid, block, smem_bytes<NM>(block), s>>>(p);
     return cudaGetLastError();
 }
 
 template <int NM, bool REC>
 int occupancy_t(int block) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_kernel<NM, REC>, block, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_kernel<NM, REC>, block, smem_bytes<NM>(block))
+        != cudaSuccess)
+        return 1;
     return n > 0 ? n : 1;
 }
 

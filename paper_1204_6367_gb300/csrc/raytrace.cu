@@ -97,8 +97,9 @@ __global__ void __launch_bounds__(128) rt_kernel(const RtParams P, double* __res
                 const int v = (cx ? i1[0] : i0[0]) + sy * (cy ? i1[1] : i0[1]) + sz * (cz ? i1[2] : i0[2]);
                 const float w = (cx ? w1[0] : 1.0f - w1[0]) * (cy ? w1[1] : 1.0f - w1[1])
                               * (cz ? w1[2] : 1.0f - w1[2]);
-                const float a = w * __ldg(P.dens + v);
-                const int mc = __ldg(P.mat + v);
+                const uint2 vx = __ldg(P.vox + v);
+                const float a = w * __uint_as_float(vx.x);
+                const int mc = (int)vx.y;
 #pragma unroll
                 for (int m = 0; m < NM; ++m) ell[m] += (mc == m ? a : 0.0f);
             }

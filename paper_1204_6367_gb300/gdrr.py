@@ -67,7 +67,7 @@ class Detector(ctypes.Structure):
 class McOptions(ctypes.Structure):
     _fields_ = [("e_cut_kev", ctypes.c_double), ("max_steps", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("hist_per_thread", ctypes.c_int32),
-                ("refill_interval", ctypes.c_int32)]
+                ("batch_min", ctypes.c_int32)]
 
 
 _lib = None

@@ -84,9 +84,9 @@ def test_torso_4mm_polyenergetic_bit_exact(gd):
     np.testing.assert_array_equal(ts, ots)
 
 
-@pytest.mark.parametrize("opts", [dict(block_size=64, hist_per_thread=1, refill_interval=1),
-                                  dict(block_size=128, hist_per_thread=64, refill_interval=8),
-                                  dict(block_size=256, hist_per_thread=3, refill_interval=3, blocks_per_sm=1)])
+@pytest.mark.parametrize("opts", [dict(block_size=64, hist_per_thread=1, batch_min=1),
+                                  dict(block_size=128, hist_per_thread=64, batch_min=32),
+                                  dict(block_size=256, hist_per_thread=3, batch_min=3, blocks_per_sm=1)])
 def test_launch_configuration_invariance(gd, small, opts):
     n = 200_003
     ref = _run_gpu(gd, small, n, seed=5)
@@ -256,9 +256,16 @@ def test_statistical_agreement_with_fp64_oracle(gd, small):
         g, o = tg / n_g, to / n_o
         var = vg / n_g**2 + vo / n_o**2
         keep = (tg > 0) | (to > 0)
-        z = np.abs(g - o)[keep] / np.sqrt(var[keep])
-        frac = float(np.mean(z < 3.0))
-        assert frac >= 0.997, frac
+        z = (g - o)[keep] / np.sqrt(var[keep])
+        n_pix = z.size
+        # 99.7 % within 3 sigma is the Gaussian expectation itself (99.73 %);
+        # over n_pix pixels the observed fraction scatters binomially around
+        # it, so allow its own 3-sigma band, and check the z distribution.
+        frac = float(np.mean(np.abs(z) < 3.0))
+        band = 3.0 * math.sqrt(0.0027 * 0.9973 / n_pix)
+        assert frac >= 0.997 - band, (frac, band)
+        assert abs(float(z.mean())) < 4.0 / math.sqrt(n_pix), float(z.mean())
+        assert abs(float(z.std()) - 1.0) < 0.05, float(z.std())
     sg, so = np.sum(cg_s) / n_g, np.sum(co_s) / n_o
     sig = math.sqrt(_pooled(cg_s)[1].sum() / n_g**2 + _pooled(co_s)[1].sum() / n_o**2)
     assert abs(sg - so) <= 0.005 * so + 3 * sig, (sg, so, sig)

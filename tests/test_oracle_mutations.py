@@ -28,12 +28,15 @@ MUTATIONS = [
      "Thomson acceptance", "test_oracle_sampling.py"),
     ("mc_history.inc", "w0[a] = RC(1) - t; w1[a] = t;", "w0[a] = t; w1[a] = RC(1) - t;",
      "trilinear weights swapped", "test_oracle_transport.py"),
-    ("mc_history.inc", "REAL c1 = muR, c2 = c1 + muC, c3 = c2 + muP;", "REAL c1 = muR, c2 = c1 + muP, c3 = c2 + muC;",
-     "interaction channels swapped", "test_oracle_transport.py"),
-    ("mc_history.inc", "REAL s = -LOGR(xi_s) / mumax;", "REAL s = -LOGR(xi_s) / (RC(0.9) * mumax);",
+    ("mc_history.inc", "channel = t <= muR ? 1 : (t <= muR + muC ? 2 : 3);", "channel = t <= muR ? 1 : (t <= muR + muR ? 2 : 3);",
+     "interaction channels mixed up", "test_oracle_transport.py"),
+    ("mc_history.inc", "REAL s = -LOGR(xi_s) * inv_mumax;", "REAL s = -LOGR(xi_s) * (RC(1.1) * inv_mumax);",
      "free path scale", "test_oracle_transport.py"),
-    ("mc_history.inc", "rho_m[p->material[v]] += w * (REAL)p->density[v];", "rho_m[p->material[v]] = w * (REAL)p->density[v];",
+    ("mc_history.inc", "for (int corner = 0; corner < 8; ++corner) muT = muT + a[corner] * cT[mc[corner]];",
+     "for (int corner = 0; corner < 8; ++corner) muT = a[corner] * cT[mc[corner]];",
      "dropped corner terms", "test_oracle_transport.py"),
+    ("mc_history.inc", "cT[m] = (cR[m] + cC[m]) + cP[m];", "cT[m] = cR[m] + cC[m];",
+     "photoelectric missing from the total", "test_oracle_transport.py"),
     ("mc_history.inc", "int64_t iy = cy ? i1[1] : i0[1];", "int64_t iy = cy ? i1[0] : i0[0];",
      "wrong corner index", "test_oracle_transport.py"),
     ("mc_history.inc", "REAL fu = au * GEO(idu) + GEO(hu);", "REAL fu = -au * GEO(idu) + GEO(hu);",
