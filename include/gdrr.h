@@ -233,6 +233,34 @@ GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double
                                   int32_t nu, int32_t nv, double count_scale, double beta,
                                   double omega, int32_t iters);
 
+/* Largest image, in pixels, that gdrr_denoise_scatter_static accepts. */
+#define GDRR_STATIC_DENOISE_MAX_PIXELS 65536
+
+/* The scatter denoiser of gdrr_denoise_scatter without a context and without
+ * allocating device memory, for callers that cannot allocate: a plug-in
+ * given a fixed device-memory budget by its host application, or code that
+ * must not call cudaMalloc / cudaFree because they can synchronise the
+ * device.  The paper has no counterpart; it computes exactly what
+ * gdrr_denoise_scatter computes, with the same arguments.
+ *  - Scratch: a file-scope device array of 2 * GDRR_STATIC_DENOISE_MAX_PIXELS
+ *    doubles (1 MiB) that every GPU loading the library holds until exit.
+ *    Images with nu * nv > GDRR_STATIC_DENOISE_MAX_PIXELS are rejected with
+ *    GDRR_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array, and the array keeps the
+ *    last call's contents (each call writes every element it reads before
+ *    reading it, so nothing needs clearing).  Calls that overlap on the GPU
+ *    (on different streams, or from different host threads) race on it and
+ *    must be ordered by the caller.
+ *  - Runs on cuda_stream (a cudaStream_t, NULL = legacy default stream) on the
+ *    current device; returns without synchronising.  S_hat_dev, S_dev:
+ *    caller-owned device double[nv * nu]. */
+GDRR_API int gdrr_denoise_scatter_static(const double* S_hat_dev, double* S_dev, int32_t nu, int32_t nv,
+                                         double count_scale, double beta, double omega, int32_t iters,
+                                         void* cuda_stream);
+
 /* Step 4, Section 2.6, Eq. 4 and the scaling equation that follows it:
  * N = ((P^ - P) + (S^ - S)) sqrt(n_sim / (zeta * mAs)), element-wise over n
  * pixels; all arrays caller-owned device double. */

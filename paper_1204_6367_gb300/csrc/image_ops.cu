@@ -6,6 +6,8 @@
 //  * Step 4, Section 2.6: N = ((P^ - P) + (S^ - S)) * alpha.
 // These are element-wise or 5-point-stencil passes over at most a detector
 // image (196,608 pixels): launch- and latency-bound, not bandwidth-bound.
+#include <mutex>
+
 #include "gdrr_internal.cuh"
 
 namespace gdrr {
@@ -139,3 +141,62 @@ cudaError_t launch_denoise(const double* s_hat, double* s_out, int nu, int nv, d
 }
 
 }  // namespace gdrr
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the scatter denoiser.
+//
+// Some callers cannot allocate device memory: host applications that hand a
+// plug-in a fixed device-memory budget and own the allocator, or code that
+// must not call cudaMalloc / cudaFree because those calls can synchronise the
+// device and stall other work.  gdrr_denoise_scatter_static serves them: it
+// takes no context and allocates nothing; its ping-pong scratch is the
+// file-scope device array below, which every GPU that loads this library
+// holds until the process exits.
+namespace gdrr {
+namespace {
+
+constexpr int STATIC_DENOISE_MAX_PIXELS = GDRR_STATIC_DENOISE_MAX_PIXELS;
+constexpr int MAX_DEVICES = 64;
+
+static __device__ __align__(256) double g_denoise_scratch[2 * (size_t)STATIC_DENOISE_MAX_PIXELS];
+
+std::mutex g_scratch_mutex;
+double* g_scratch_addr[MAX_DEVICES] = {nullptr};
+
+// The device address of g_denoise_scratch on the current device.  In host
+// code the array's name is only a host-side stand-in, so the address is
+// looked up with cudaGetSymbolAddress once per device, with that device
+// current, and cached.
+cudaError_t static_scratch(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_denoise_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace gdrr
+
+extern "C" GDRR_API int gdrr_denoise_scatter_static(const double* S_hat_dev, double* S_dev, int32_t nu, int32_t nv,
+                                                   double count_scale, double beta, double omega, int32_t iters,
+                                                   void* cuda_stream) {
+    if (!S_hat_dev || !S_dev || nu <= 0 || nv <= 0 || iters < 0) return GDRR_ERR_INVALID_ARG;
+    if (!(count_scale > 0) || !(beta > 0) || !(omega > 0 && omega < 2) || !isfinite(count_scale) || !isfinite(beta))
+        return GDRR_ERR_INVALID_ARG;
+    if ((int64_t)nu * nv > gdrr::STATIC_DENOISE_MAX_PIXELS) return GDRR_ERR_INVALID_ARG;
+    double* scratch = nullptr;
+    cudaError_t e = gdrr::static_scratch(&scratch);
+    if (e == cudaSuccess)
+        e = gdrr::launch_denoise(S_hat_dev, S_dev, nu, nv, count_scale, beta, omega, iters, scratch,
+                                 (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? GDRR_OK : GDRR_ERR_CUDA;
+}

@@ -100,6 +100,7 @@ def lib():
             "gdrr_bin_tally": [vp, vp, i32, i32, i32, vp],
             "gdrr_upsample": [vp, vp, i32, i32, i32, vp],
             "gdrr_denoise_scatter": [vp, vp, vp, i32, i32, dbl, dbl, dbl, i32],
+            "gdrr_denoise_scatter_static": [vp, vp, i32, i32, dbl, dbl, dbl, i32, vp],
             "gdrr_noise_calibrate": [vp, vp, vp, vp, vp, i64, u64, dbl, dbl, vp],
             "gdrr_fit_zeta": [vp, vp, i32, u64, vp, vp],
             "gdrr_stream_words": [u64, u32, u64, i32, i32, vp, vp],
@@ -321,6 +322,25 @@ def gdrr_denoise_scatter(ctx: Context, s_hat, count_scale: float, beta: float, o
            lib().gdrr_denoise_scatter(ctx.handle, _dev_ptr(s_hat, torch.float64, nu * nv, "s_hat"),
                                       _dev_ptr(out, torch.float64, nu * nv, "out"), nu, nv, float(count_scale),
                                       float(beta), float(omega), int(iters)))
+    return out
+
+
+STATIC_DENOISE_MAX_PIXELS = 65536
+
+
+def gdrr_denoise_scatter_static(s_hat, count_scale: float, beta: float, omega: float = 0.8, iters: int = 500,
+                                out=None, stream=None):
+    """The denoiser without a context and without device allocation inside the
+    library (its scratch is a static device array shared by all calls)."""
+    import torch
+    nv, nu = s_hat.shape
+    if out is None:
+        out = torch.empty_like(s_hat)
+    h, _ = _stream_handle(stream)
+    _check("gdrr_denoise_scatter_static",
+           lib().gdrr_denoise_scatter_static(_dev_ptr(s_hat, torch.float64, nu * nv, "s_hat"),
+                                             _dev_ptr(out, torch.float64, nu * nv, "out"), nu, nv,
+                                             float(count_scale), float(beta), float(omega), int(iters), h))
     return out
 
 
