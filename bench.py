@@ -219,6 +219,10 @@ def run_ours(args):
         return gdrr.gdrr_noise_calibrate(ctx, P_hat, P, S_hat, S, n_hist, 0.4, 5.2913e9)
 
     count_scale = float(out["S_hat"].sum().item()) / max(1, st["tally_scatter"])
+    # memory ceiling for the transport's access pattern: the same corner
+    # gathers at as many random cells as the projection has free flights
+    gdrr.gdrr_gather_roofline(ctx, min(steps_per_proj, 10**9))
+    probe_s = gdrr.gdrr_gather_roofline(ctx, steps_per_proj)
     launches_per_step = 1 + 1 + 3 + 1 + (iters + 2) + 1 + 1
 
     clocks = ClockSampler(dev)
@@ -316,8 +320,12 @@ def run_ours(args):
                    "parallelism": f"one projection angle per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "mc_kernel",
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
                      "mc_ms": statistics.mean(mc_ms),
-                     "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} steps"},
+                     "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} steps",
+                     "gather_roof": {"probe_gbs": algo_bytes / probe_s / 1e9, "probe_ms": 1e3 * probe_s,
+                                     "frac": achieved / (algo_bytes / probe_s / 1e9),
+                                     "what": "same 8-corner gathers, same layout, random cells, no other work"}},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,

@@ -274,6 +274,14 @@ GDRR_API int gdrr_noise_calibrate(gdrr_ctx* ctx, const double* P_hat_dev, const 
 GDRR_API int gdrr_fit_zeta(const double* inv_sqrt_mAs, const double* ratio, int32_t n,
                            uint64_t n_sim, double* zeta_out, double* k_out);
 
+/* Memory-roofline probe of the transport: n_cells trilinear cells at
+ * pseudo-random positions, each gathering the same eight voxel records with
+ * the same layout and index arithmetic as a Woodcock free flight, and nothing
+ * else.  *seconds_out (host) receives the device time of those gathers; the
+ * call synchronises the context stream.  Not part of the paper's method: it
+ * measures the ceiling against which the transport's gather rate is judged. */
+GDRR_API int gdrr_gather_roofline(gdrr_ctx* ctx, uint64_t n_cells, double* seconds_out);
+
 /* Parity hook: the Philox words of n_hist history streams (ids hid0 ..),
  * n_blocks blocks each, exactly as the transport draws them.  out_dev:
  * device uint32[n_hist][4 * n_blocks].  Runs on cuda_stream. */

@@ -24,6 +24,7 @@ struct gdrr_ctx {
     // inputs (host copies of the scalars)
     gdrr_geometry geo{};
     int nx = 0, ny = 0, nz = 0;
+    int bsy = 0, bsz = 0;          // brick strides of the staged voxel records
     double vox[3] = {0, 0, 0};
     int n_mat = 0, n_e = 0, n_r = 0, n_bins = 0;
     double e0 = 0, de = 0, r0 = 0, dr = 0;
@@ -227,7 +228,8 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         || !ph.material || !ph.density)
         return GDRR_ERR_INVALID_ARG;
     const int64_t nvox = (int64_t)ph.nx * ph.ny * ph.nz;
-    if (nvox >= ((int64_t)1 << 31)) return GDRR_ERR_UNSUPPORTED;
+    const int64_t nbrick_rec = (int64_t)16 * ((ph.nx + 3) / 4) * ((ph.ny + 1) / 2) * ((ph.nz + 1) / 2);
+    if (nbrick_rec >= ((int64_t)1 << 31)) return GDRR_ERR_UNSUPPORTED;
     const gdrr_materials& mt = *materials;
     if (mt.n_materials <= 0 || mt.n_energies < 2 || !(mt.de_kev > 0) || !mt.mu_hat) return GDRR_ERR_INVALID_ARG;
     if (mt.n_materials > GDRR_MAX_MATERIALS) return GDRR_ERR_UNSUPPORTED;
@@ -319,12 +321,20 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         for (int i = 0; i < npix; ++i) wnorm[i] = bowtie->fluence[i] / fsum;
 
         cudaStream_t s = c->stream;
-        std::vector<uint2> vox((size_t)nvox);
-        for (int64_t v = 0; v < nvox; ++v) {
-            uint32_t bits;
-            memcpy(&bits, &ph.density[v], sizeof bits);
-            vox[v] = make_uint2(bits, (uint32_t)ph.material[v]);
-        }
+        // bricked records: 4 x 2 x 2 voxels per 128-byte line, padding zero
+        const int nbx = (ph.nx + 3) / 4, nby = (ph.ny + 1) / 2, nbz = (ph.nz + 1) / 2;
+        c->bsy = 16 * nbx;
+        c->bsz = 16 * nbx * nby;
+        std::vector<uint2> vox((size_t)16 * nbx * nby * nbz, make_uint2(0u, 0u));
+        for (int z = 0; z < ph.nz; ++z)
+            for (int y = 0; y < ph.ny; ++y)
+                for (int x = 0; x < ph.nx; ++x) {
+                    const int64_t v = x + (int64_t)ph.nx * (y + (int64_t)ph.ny * z);
+                    uint32_t bits;
+                    memcpy(&bits, &ph.density[v], sizeof bits);
+                    vox[(size_t)brick_x(x) + brick_y(y, c->bsy) + brick_z(z, c->bsz)] =
+                        make_uint2(bits, (uint32_t)ph.material[v]);
+                }
         if ((rc = upload(&c->d_vox, vox.data(), vox.size(), s))) break;
         if ((rc = upload(&c->d_tab, tab.data(), tab.size(), s))) break;
         if ((rc = upload(&c->d_major, major.data(), major.size(), s))) break;
@@ -381,6 +391,7 @@ GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_de
     p.nx = ctx->nx; p.ny = ctx->ny; p.nz = ctx->nz;
     fill_box(ctx, p.lo, p.hi, p.ivox);
     p.vox = ctx->d_vox;
+    p.bsy = ctx->bsy; p.bsz = ctx->bsz;
     p.n_mat = ctx->n_mat; p.n_bins = ctx->n_bins;
     p.mu_rt = ctx->d_mu_rt; p.wr = ctx->d_wr; p.wnorm = ctx->d_wnorm;
     p.nu = ctx->geo.nu; p.nv = ctx->geo.nv;
@@ -391,22 +402,14 @@ GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_de
     return cuda_err(launch_rt(p, P_dev, ctx->stream));
 }
 
-static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total, uint64_t seed,
-                     uint64_t* stats_dev, gdrr_history_record* records_dev) {
-    if (total == 0) return GDRR_OK;
-    const int nj = (int)jobs.size();
-    if (nj > ctx->jobs_cap) {
-        if (ctx->d_jobs) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->d_jobs); ctx->d_jobs = nullptr; }
-        TRY_CUDA(cudaMalloc((void**)&ctx->d_jobs, sizeof(Job) * nj));
-        ctx->jobs_cap = nj;
-    }
-    // pageable source: staged before the call returns, so the vector may die
-    TRY_CUDA(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(Job) * nj, cudaMemcpyHostToDevice, ctx->stream));
-    TRY_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
+// The launch-independent part of the transport parameters.
+static McParams static_mc_params(const gdrr_ctx* ctx) {
     McParams p;
+    memset(&p, 0, sizeof p);
     p.nx = ctx->nx; p.ny = ctx->ny; p.nz = ctx->nz;
     fill_box(ctx, p.lo, p.hi, p.ivox);
     p.vox = ctx->d_vox;
+    p.bsy = ctx->bsy; p.bsz = ctx->bsz;
     p.n_mat = ctx->n_mat; p.n_e = ctx->n_e;
     p.e0 = (float)ctx->e0; p.inv_de = (float)(1.0 / ctx->de);
     p.tab = ctx->d_tab; p.major = ctx->d_major;
@@ -421,6 +424,22 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     p.idu = (float)(1.0 / ctx->geo.du_mm); p.idv = (float)(1.0 / ctx->geo.dv_mm);
     p.e_cut = (float)ctx->opt.e_cut_kev;
     p.max_steps = ctx->opt.max_steps;
+    return p;
+}
+
+static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total, uint64_t seed,
+                     uint64_t* stats_dev, gdrr_history_record* records_dev) {
+    if (total == 0) return GDRR_OK;
+    const int nj = (int)jobs.size();
+    if (nj > ctx->jobs_cap) {
+        if (ctx->d_jobs) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->d_jobs); ctx->d_jobs = nullptr; }
+        TRY_CUDA(cudaMalloc((void**)&ctx->d_jobs, sizeof(Job) * nj));
+        ctx->jobs_cap = nj;
+    }
+    // pageable source: staged before the call returns, so the vector may die
+    TRY_CUDA(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(Job) * nj, cudaMemcpyHostToDevice, ctx->stream));
+    TRY_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
+    McParams p = static_mc_params(ctx);
     p.seed = seed;
     p.jobs = ctx->d_jobs; p.n_jobs = nj; p.total = total;
     p.counter = ctx->d_counter;
@@ -555,6 +574,31 @@ GDRR_API int gdrr_fit_zeta(const double* inv_sqrt_mAs, const double* ratio, int3
     if (!(k != 0.0)) return GDRR_ERR_INVALID_ARG;
     *zeta_out = (double)n_sim / (k * k);
     if (k_out) *k_out = k;
+    return GDRR_OK;
+}
+
+GDRR_API int gdrr_gather_roofline(gdrr_ctx* ctx, uint64_t n_cells, double* seconds_out) {
+    if (!ctx || !seconds_out || n_cells == 0) return GDRR_ERR_INVALID_ARG;
+    McParams p = static_mc_params(ctx);
+    const int per_sm = 4;
+    cudaEvent_t e0, e1;
+    TRY_CUDA(cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    if (err != cudaSuccess) { cudaEventDestroy(e0); return cuda_err(err); }
+    err = cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
+    if (err == cudaSuccess) err = launch_gather_probe(p, n_cells / 8 + 1, per_sm * ctx->n_sm,
+                                                      reinterpret_cast<unsigned int*>(ctx->d_flag), ctx->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, ctx->stream);
+    if (err == cudaSuccess) err = launch_gather_probe(p, n_cells, per_sm * ctx->n_sm,
+                                                      reinterpret_cast<unsigned int*>(ctx->d_flag), ctx->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, ctx->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_err(err);
+    *seconds_out = 1e-3 * (double)ms;
     return GDRR_OK;
 }
 

@@ -8,6 +8,14 @@
 
 namespace gdrr {
 
+// Voxel records are stored in bricks of 4 x 2 x 2 voxels (16 records of 8
+// bytes = one 128-byte line), bricks x fastest.  The record of voxel (x, y, z)
+// sits at brick_x(x) + brick_y(y, bsy) + brick_z(z, bsz) with bsy = 16 * nbx,
+// bsz = 16 * nbx * nby (nbx, nby: bricks per row and per column).
+__host__ __device__ __forceinline__ int brick_x(int x) { return ((x >> 2) << 4) + (x & 3); }
+__host__ __device__ __forceinline__ int brick_y(int y, int bsy) { return (y >> 1) * bsy + ((y & 1) << 2); }
+__host__ __device__ __forceinline__ int brick_z(int z, int bsz) { return (z >> 1) * bsz + ((z & 1) << 3); }
+
 // Per-angle imager frame in FP32 (Section 2.1, Fig. 1).
 struct Frame {
     float S[3];    // source position
@@ -31,8 +39,9 @@ struct Job {
 
 // Everything the transport kernel reads, by value.
 struct McParams {
-    // phantom box and voxel records {density bits, material}
+    // phantom box and bricked voxel records {density bits, material}
     int nx, ny, nz;
+    int bsy, bsz;
     float lo[3], hi[3], ivox[3];
     const uint2* vox;
     // material tables, mm^-1 per g/cm^3, [m][k][e]; majorant nodes [e]
@@ -73,6 +82,7 @@ struct McParams {
 // Ray-tracing parameters.
 struct RtParams {
     int nx, ny, nz;
+    int bsy, bsz;
     float lo[3], hi[3], ivox[3];
     const uint2* vox;
     int n_mat, n_bins;
@@ -88,6 +98,7 @@ struct RtParams {
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s);
 int mc_occupancy_blocks(int n_mat, int block, bool records);
 cudaError_t launch_rt(const RtParams& p, double* out, cudaStream_t s);
+cudaError_t launch_gather_probe(const McParams& p, uint64_t n_cells, int grid, unsigned int* sink, cudaStream_t s);
 cudaError_t launch_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist,
                                 int n_blocks, uint32_t* out, cudaStream_t s);
 

@@ -13,9 +13,11 @@
 // order.
 //
 // Data layout: one 8-byte record {density bits, material index} per voxel,
-// x fastest, so each trilinear corner is a single 8-byte gather from L2; the
-// per-lane energy-dependent coefficients live in shared memory, indexed by
-// material, one column per thread.
+// in bricks of 4 x 2 x 2 voxels (one 128-byte cache line each), so each
+// trilinear corner is a single 8-byte gather and the eight corners of a cell
+// touch about 2.8 distinct lines instead of about 4.3 for a row-major layout;
+// the per-lane energy-dependent coefficients live in shared memory, indexed
+// by material, one column per thread.
 //
 // Arithmetic contract.  This file is compiled with -fmad=false: every FP32
 // operation below is one IEEE-rounded operation, evaluated in the order
@@ -150,8 +152,9 @@ __device__ __forceinline__ void azimuth(Stream& rs, uint64_t seed, float& cp, fl
         const float b = 2.0f * uniform(w.y) - 1.0f;
         const float r2 = a * a + b * b;
         if (r2 <= 1.0f && r2 > 0.0f) {
-            cp = (a * a - b * b) / r2;
-            sp = 2.0f * a * b / r2;
+            const float inv = 1.0f / r2;
+            cp = (a * a - b * b) * inv;
+            sp = 2.0f * a * b * inv;
             return;
         }
     }
@@ -163,22 +166,24 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float ct, f
     float nu_, nv_, nw_;
     if (w < (float)0.99999 && w > (float)-0.99999) {
         const float t = sqrtf(1.0f - w * w);
-        nu_ = u * ct + st * (u * w * cp - v * sp) / t;
-        nv_ = v * ct + st * (v * w * cp + u * sp) / t;
+        const float sti = st / t;
+        nu_ = u * ct + sti * (u * w * cp - v * sp);
+        nv_ = v * ct + sti * (v * w * cp + u * sp);
         nw_ = w * ct - st * t * cp;
     } else {
         nu_ = st * cp;
         nv_ = st * sp;
         nw_ = w > 0.0f ? ct : -ct;
     }
-    const float len = sqrtf(nu_ * nu_ + nv_ * nv_ + nw_ * nw_);
-    u = nu_ / len;
-    v = nv_ / len;
-    w = nw_ / len;
+    const float il = 1.0f / sqrtf(nu_ * nu_ + nv_ * nv_ + nw_ * nw_);
+    u = nu_ * il;
+    v = nv_ * il;
+    w = nw_ * il;
 }
 
 __device__ __forceinline__ void compton(Stream& rs, uint64_t seed, float e, float& ct_out, float& e_out) {
-    const float alpha = e / (float)510.99895;
+    const float alpha = e * (float)(1.0 / 510.99895);
+    const float ialpha = (float)510.99895 / e;
     const float ta = 2.0f * alpha;
     float x;
     for (;;) {
@@ -191,11 +196,11 @@ __device__ __forceinline__ void compton(Stream& rs, uint64_t seed, float e, floa
             if (r3 <= 4.0f * (x - 1.0f) / (x * x)) break;
         } else {
             x = (1.0f + ta) / (1.0f + ta * r2);
-            const float ct = 1.0f - (x - 1.0f) / alpha;
+            const float ct = 1.0f - (x - 1.0f) * ialpha;
             if (r3 <= 0.5f * (ct * ct + 1.0f / x)) break;
         }
     }
-    ct_out = 1.0f - (x - 1.0f) / alpha;
+    ct_out = 1.0f - (x - 1.0f) * ialpha;
     e_out = e / x;
 }
 
@@ -366,10 +371,10 @@ struct Lane {
         dx = t0 - J.f.S[0];
         dy = t1 - J.f.S[1];
         dz = t2 - J.f.S[2];
-        const float len = sqrtf(dx * dx + dy * dy + dz * dz);
-        dx = dx / len;
-        dy = dy / len;
-        dz = dz / len;
+        const float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+        dx = dx * il;
+        dy = dy * il;
+        dz = dz * il;
         px = J.f.S[0]; py = J.f.S[1]; pz = J.f.S[2];
         e = en;
 
@@ -380,8 +385,9 @@ struct Lane {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (d[a] != 0.0f) {
-                float t1a = (P.lo[a] - p[a]) / d[a];
-                float t2a = (P.hi[a] - p[a]) / d[a];
+                const float id = 1.0f / d[a];
+                float t1a = (P.lo[a] - p[a]) * id;
+                float t2a = (P.hi[a] - p[a]) * id;
                 if (t1a > t2a) { const float t = t1a; t1a = t2a; t2a = t; }
                 if (t1a > tmin) tmin = t1a;
                 if (t2a < tmax) tmax = t2a;
@@ -434,13 +440,15 @@ struct Lane {
         const int z0 = min(max(gz, 0), P.nz - 1), z1 = min(max(gz + 1, 0), P.nz - 1);
         const float wx0 = 1.0f - tx, wy0 = 1.0f - ty, wz0 = 1.0f - tz;
         const float wxy[4] = {wx0 * wy0, tx * wy0, wx0 * ty, tx * ty};
-        const int sy = P.nx, sz = P.nx * P.ny;
-        const int rows[4] = {y0 * sy + z0 * sz, y1 * sy + z0 * sz, y0 * sy + z1 * sz, y1 * sy + z1 * sz};
+        const int bx[2] = {brick_x(x0), brick_x(x1)};
+        const int by[2] = {brick_y(y0, P.bsy), brick_y(y1, P.bsy)};
+        const int bz[2] = {brick_z(z0, P.bsz), brick_z(z1, P.bsz)};
+        const int rows[4] = {by[0] + bz[0], by[1] + bz[0], by[0] + bz[1], by[1] + bz[1]};
         float a[8];
         int mc[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int v = rows[c >> 1] + ((c & 1) ? x1 : x0);
+            const int v = rows[c >> 1] + bx[c & 1];
             const uint2 vx = __ldg(P.vox + v);
             a[c] = (wxy[c & 3] * ((c >> 2) ? tz : wz0)) * __uint_as_float(vx.x);
             mc[c] = (int)vx.y;
@@ -560,6 +568,41 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams P) {
         if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
 }
 
+// Gather roofline probe: the transport's trilinear corner gather (same
+// layout, same index arithmetic) at pseudo-random cells, with nothing else,
+// so the memory system's ceiling for this access pattern can be measured.
+__global__ void __launch_bounds__(256) gather_probe_kernel(const McParams P, uint64_t n_cells,
+                                                         unsigned int* sink) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+    float acc = 0.0f;
+    for (uint64_t i = tid; i < n_cells; i += nth) {
+        uint32_t h = (uint32_t)i * 0x9E3779B1u;
+        h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+        const uint32_t h2 = h * 0x85EBCA6Bu ^ (h >> 13);
+        const uint32_t h3 = h2 * 0xC2B2AE35u ^ (h2 >> 16);
+        const float fx = (float)(h & 0xffffu) * (1.0f / 65536.0f) * (float)P.nx - 0.5f;
+        const float fy = (float)(h2 & 0xffffu) * (1.0f / 65536.0f) * (float)P.ny - 0.5f;
+        const float fz = (float)(h3 & 0xffffu) * (1.0f / 65536.0f) * (float)P.nz - 0.5f;
+        const int gx = (int)floorf(fx), gy = (int)floorf(fy), gz = (int)floorf(fz);
+        const float tx = fx - (float)gx, ty = fy - (float)gy, tz = fz - (float)gz;
+        const int x0 = min(max(gx, 0), P.nx - 1), x1 = min(max(gx + 1, 0), P.nx - 1);
+        const int y0 = min(max(gy, 0), P.ny - 1), y1 = min(max(gy + 1, 0), P.ny - 1);
+        const int z0 = min(max(gz, 0), P.nz - 1), z1 = min(max(gz + 1, 0), P.nz - 1);
+        const float wxy[4] = {(1.0f - tx) * (1.0f - ty), tx * (1.0f - ty), (1.0f - tx) * ty, tx * ty};
+        const int bx[2] = {brick_x(x0), brick_x(x1)};
+        const int by[2] = {brick_y(y0, P.bsy), brick_y(y1, P.bsy)};
+        const int bz[2] = {brick_z(z0, P.bsz), brick_z(z1, P.bsz)};
+        const int rows[4] = {by[0] + bz[0], by[1] + bz[0], by[0] + bz[1], by[1] + bz[1]};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint2 vx = __ldg(P.vox + rows[c >> 1] + bx[c & 1]);
+            acc = acc + (wxy[c & 3] * ((c >> 2) ? tz : 1.0f - tz)) * __uint_as_float(vx.x) * (float)(vx.y + 1u);
+        }
+    }
+    if (acc == -1.0f) atomicAdd(sink, 1u);   // keeps the loads; never true for densities >= 0
+}
+
 __global__ void stream_words_kernel(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist,
                                     int n_blocks, uint32_t* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -613,6 +656,11 @@ int mc_occupancy_blocks(int n_mat, int block, bool records) {
     if (n_mat <= 2) return occupancy_t<2, false>(block);
     if (n_mat <= 4) return occupancy_t<4, false>(block);
     return occupancy_t<8, false>(block);
+}
+
+cudaError_t launch_gather_probe(const McParams& p, uint64_t n_cells, int grid, unsigned int* sink, cudaStream_t s) {
+    gather_probe_kernel<<<grid, 256, 0, s>>>(p, n_cells, sink);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist, int n_blocks,

@@ -69,7 +69,6 @@ __global__ void __launch_bounds__(128) rt_kernel(const RtParams P, double* __res
         const int n = (int)ceilf(chord / P.half_step);
         const float dl = chord / (float)n;
         const int dims[3] = {P.nx, P.ny, P.nz};
-        const int sy = P.nx, sz = P.nx * P.ny;
         // voxel-coordinate start and increment of the midpoints
         float f0[3], df[3];
 #pragma unroll
@@ -94,7 +93,8 @@ __global__ void __launch_bounds__(128) rt_kernel(const RtParams P, double* __res
 #pragma unroll
             for (int corner = 0; corner < 8; ++corner) {
                 const int cx = corner & 1, cy = (corner >> 1) & 1, cz = corner >> 2;
-                const int v = (cx ? i1[0] : i0[0]) + sy * (cy ? i1[1] : i0[1]) + sz * (cz ? i1[2] : i0[2]);
+                const int v = brick_x(cx ? i1[0] : i0[0]) + brick_y(cy ? i1[1] : i0[1], P.bsy)
+                            + brick_z(cz ? i1[2] : i0[2], P.bsz);
                 const float w = (cx ? w1[0] : 1.0f - w1[0]) * (cy ? w1[1] : 1.0f - w1[1])
                               * (cz ? w1[2] : 1.0f - w1[2]);
                 const uint2 vx = __ldg(P.vox + v);

@@ -104,6 +104,7 @@ def lib():
             "gdrr_noise_calibrate": [vp, vp, vp, vp, vp, i64, u64, dbl, dbl, vp],
             "gdrr_fit_zeta": [vp, vp, i32, u64, vp, vp],
             "gdrr_stream_words": [u64, u32, u64, i32, i32, vp, vp],
+            "gdrr_gather_roofline": [vp, u64, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -371,6 +372,13 @@ def gdrr_stream_words(seed: int, angle_index: int, hid0: int, n_hist: int, n_blo
     _check("gdrr_stream_words", lib().gdrr_stream_words(int(seed), int(angle_index), int(hid0), int(n_hist),
                                                         int(n_blocks), _dev_ptr(out, torch.int32, None, "out"), h))
     return out
+
+
+def gdrr_gather_roofline(ctx: Context, n_cells: int) -> float:
+    """Seconds the transport's corner gathers alone take for n_cells cells."""
+    sec = ctypes.c_double()
+    _check("gdrr_gather_roofline", lib().gdrr_gather_roofline(ctx.handle, int(n_cells), ctypes.byref(sec)))
+    return sec.value
 
 
 def stats_dict(stats) -> dict:

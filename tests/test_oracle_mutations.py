@@ -22,7 +22,7 @@ MUTATIONS = [
      "Kahn second-branch acceptance", "test_oracle_sampling.py"),
     ("mc_history.inc", "nw_ = w * ct - st * t * cp;", "nw_ = w * ct + st * t * cp;",
      "rotation sign", "test_oracle_sampling.py"),
-    ("mc_history.inc", "*sp = RC(2) * a * b / r2;", "*sp = RC(2) * a * a / r2;",
+    ("mc_history.inc", "*sp = RC(2) * a * b * inv;", "*sp = RC(2) * a * a * inv;",
      "azimuth sine", "test_oracle_sampling.py"),
     ("mc_history.inc", "if (RC(2) * b <= RC(1) + mu * mu) return mu;", "if (b <= RC(1) + mu * mu) return mu;",
      "Thomson acceptance", "test_oracle_sampling.py"),
