@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scan", action="store_true", help="skip the 64-angle batched-scan comparison")
     return ap.parse_args()
 
 
@@ -101,6 +102,23 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_traffic():
+    """DRAM bytes per transport launch from the committed ncu summary, or None
+    when the kernel source changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "mc_kernel_torso2mm_traffic.txt")
+    try:
+        vals = dict(l.split() for l in open(path) if l.strip() and not l.startswith("#"))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in ("mc_transport.cu", "gdrr_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1204_6367_gb300", "csrc", f), "rb").read())
+    if h.hexdigest()[:16] != vals.get("source_sha256_16"):
+        return None
+    return int(vals["bytes_per_launch"])
 
 
 def dist_env():
@@ -193,6 +211,10 @@ def run_ours(args):
     def step(stats_buf):
         return gdrr.project(ctx, n_hist, seed, angle, bin_factor=4, beta=0.02, iters=iters, stats=stats_buf)
 
+    # launch configuration from the project's autotuner (tallies do not
+    # depend on it)
+    tuned = gdrr.gdrr_autotune(ctx, angle, 20_000_000, seed)
+
     # count scale needs one host read of the scatter photon count; take it from
     # a warm-up projection so the timed step stays asynchronous
     for _ in range(max(args.warmup, 3)):
@@ -280,6 +302,39 @@ def run_ours(args):
         e2e = {"value": n_hist * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "s_per_projection": e2e_s}
 
+    # multi-angle scan: 64 angles over 360 degrees with per-angle budgets
+    # drawn from U(1e7, 5e7), one persistent launch replayed from a CUDA
+    # graph, against 64 plain per-angle launches of the same histories
+    batched = None
+    if not args.no_scan:
+        angles, budgets = inputs.batched_budgets(64, 1e7, 5e7, seed=1)
+        angles = angles + angle
+        tot_hist = int(budgets.sum())
+        sp, ss = gdrr.new_tallies(ctx, angles.size)
+        scan = gdrr.gdrr_scan_create(ctx, angles, budgets, seed, sp, ss, zero_tallies=True)
+        scan.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        scan.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_s = e0.elapsed_time(e1) / 1e3
+        pp, ps = gdrr.new_tallies(ctx, angles.size)
+        e0.record(stream)
+        for a in range(angles.size):
+            gdrr.gdrr_mc_project(ctx, int(budgets[a]), seed, float(angles[a]), a, prim=pp[a], scat=ps[a])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_s = e0.elapsed_time(e1) / 1e3
+        same = bool(torch.equal(sp, pp) and torch.equal(ss, ps))
+        scan.close()
+        del sp, ss, pp, ps
+        batched = {"angles": int(angles.size), "histories": tot_hist,
+                   "graph_s": graph_s, "plain_64_launches_s": plain_s,
+                   "graph_histories_per_s": tot_hist / graph_s, "plain_histories_per_s": tot_hist / plain_s,
+                   "speedup": plain_s / graph_s, "tallies_identical": same}
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -296,13 +351,7 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = algo_bytes / mc_avg_s / 1e9
     value = n_hist * world * args.steps / (tot_ms / 1e3)
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "mc_transport_traffic.json")
-    if os.path.exists(tf):
-        try:
-            traffic = json.load(open(tf)).get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = kernel_traffic()
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -328,6 +377,8 @@ def run_ours(args):
                                      "what": "same 8-corner gathers, same layout, random cells, no other work"}},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
+        "autotuned": tuned,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "wall_s_timed": t_wall,

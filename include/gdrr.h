@@ -202,6 +202,32 @@ GDRR_API int gdrr_mc_project_batched(gdrr_ctx* ctx, int32_t n_angles, const doub
                                      const uint64_t* budgets, uint64_t seed, int64_t* prim_dev,
                                      int64_t* scat_dev, uint64_t* stats_dev);
 
+/* A multi-angle scan captured once as a CUDA graph and replayed by
+ * gdrr_scan_launch: each replay runs the same work as
+ * gdrr_mc_project_batched(angles_rad, budgets, seed) in one persistent launch
+ * (work counter reset + transport kernel), preceded by zeroing prim_dev /
+ * scat_dev when zero_tallies != 0 (else replays accumulate).  The job table,
+ * launch configuration (the context's options at creation) and buffers are
+ * fixed at creation; prim_dev / scat_dev / stats_dev (device, caller-owned,
+ * as for the batched call; stats_dev may be NULL) must outlive the scan.
+ * Creation allocates the job table and counters and synchronises. */
+typedef struct gdrr_scan gdrr_scan;
+GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* angles_rad, const uint64_t* budgets,
+                              uint64_t seed, int64_t* prim_dev, int64_t* scat_dev, uint64_t* stats_dev,
+                              int32_t zero_tallies, gdrr_scan** out);
+/* Enqueue one replay of the scan on its context's stream. */
+GDRR_API int gdrr_scan_launch(gdrr_scan* scan);
+/* Release the scan (synchronises its context's stream). */
+GDRR_API void gdrr_scan_destroy(gdrr_scan* scan);
+
+/* Autotuner: time gdrr_mc_project of n_probe histories at angle_rad for each
+ * launch configuration of a fixed grid (block size 64 / 128 / 256, batch_min
+ * 8 .. 32, hist_per_thread 1 / 8 / 64), into scratch tallies, and keep the
+ * fastest as the context's options (also copied to *best_out when not NULL).
+ * Tallies do not depend on these options, only the speed does.  Synchronises. */
+GDRR_API int gdrr_autotune(gdrr_ctx* ctx, double angle_rad, uint64_t n_probe, uint64_t seed,
+                           gdrr_mc_options* best_out);
+
 /* Tally -> signal per source photon in FP64 (Section 2.6: MC results are
  * normalised by the number of source photons): out = tally * 2^-24 / n_photons.
  * n elements; tally_dev int64, signal_dev double, both caller-owned device.

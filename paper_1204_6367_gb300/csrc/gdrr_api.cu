@@ -50,7 +50,21 @@ struct gdrr_ctx {
     int jobs_cap = 0;
     double* d_denoise = nullptr;
     size_t denoise_cap = 0;
+    int64_t* d_tune = nullptr;       // autotuner scratch tallies, 2 * nu * nv
     gdrr_mc_options opt{};
+};
+
+// A multi-angle scan captured once as a CUDA graph: (optionally) zero the
+// tallies, reset the work counter, run the persistent transport kernel over
+// all angles.  Replays reuse the captured launch configuration and buffers.
+struct gdrr_scan {
+    gdrr_ctx* ctx = nullptr;
+    gdrr::Job* d_jobs = nullptr;
+    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_stats = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t total = 0;
 };
 
 namespace {
@@ -188,7 +202,7 @@ int free_ctx(gdrr_ctx* c) {
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->d_vox, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_kcdf_pix,
                     c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr,
-                    c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise};
+                    c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise, c->d_tune};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -402,6 +416,15 @@ GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_de
     return cuda_err(launch_rt(p, P_dev, ctx->stream));
 }
 
+static int launch_grid(const gdrr_ctx* ctx, uint64_t total, bool rec) {
+    const int block = ctx->opt.block_size;
+    const int per_sm = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : mc_occupancy_blocks(ctx->n_mat, block, rec);
+    int64_t grid = (int64_t)per_sm * ctx->n_sm;
+    const int64_t useful = (int64_t)((total + 31) / 32 * 32 + block - 1) / block;
+    if (grid > useful) grid = useful;
+    return grid < 1 ? 1 : (int)grid;
+}
+
 // The launch-independent part of the transport parameters.
 static McParams static_mc_params(const gdrr_ctx* ctx) {
     McParams p;
@@ -440,7 +463,7 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     TRY_CUDA(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(Job) * nj, cudaMemcpyHostToDevice, ctx->stream));
     TRY_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
     McParams p = static_mc_params(ctx);
-    p.seed = seed;
+    p.rk = round_keys(seed);
     p.jobs = ctx->d_jobs; p.n_jobs = nj; p.total = total;
     p.counter = ctx->d_counter;
     if (stats_dev) {
@@ -453,13 +476,7 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     p.chunk = 32 * ctx->opt.hist_per_thread;
     p.batch_min = ctx->opt.batch_min;
     const bool rec = records_dev != nullptr;
-    const int block = ctx->opt.block_size;
-    int per_sm = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : mc_occupancy_blocks(ctx->n_mat, block, rec);
-    int64_t grid = (int64_t)per_sm * ctx->n_sm;
-    const int64_t useful = (int64_t)((total + 31) / 32 * 32 + block - 1) / block;
-    if (grid > useful) grid = useful;
-    if (grid < 1) grid = 1;
-    return cuda_err(launch_mc(p, block, (int)grid, rec, ctx->stream));
+    return cuda_err(launch_mc(p, ctx->opt.block_size, launch_grid(ctx, total, rec), rec, ctx->stream));
 }
 
 GDRR_API int gdrr_mc_project(gdrr_ctx* ctx, double angle_rad, uint32_t angle_index, uint64_t n_photons,
@@ -480,12 +497,13 @@ GDRR_API int gdrr_mc_project(gdrr_ctx* ctx, double angle_rad, uint32_t angle_ind
     return mc_launch(ctx, std::vector<Job>(1, j), n_photons, seed, stats_dev, records_dev);
 }
 
-GDRR_API int gdrr_mc_project_batched(gdrr_ctx* ctx, int32_t n_angles, const double* angles_rad,
-                                     const uint64_t* budgets, uint64_t seed, int64_t* prim_dev, int64_t* scat_dev,
-                                     uint64_t* stats_dev) {
+// The job table of a multi-angle scan: angle a transports budgets[a]
+// histories with angle index a and history ids 0 .. budgets[a] - 1.
+static int scan_jobs(const gdrr_ctx* ctx, int32_t n_angles, const double* angles_rad, const uint64_t* budgets,
+                     int64_t* prim_dev, int64_t* scat_dev, std::vector<Job>* jobs, uint64_t* total_out) {
     if (!ctx || n_angles <= 0 || !angles_rad || !budgets || !prim_dev || !scat_dev) return GDRR_ERR_INVALID_ARG;
-    std::vector<Job> jobs;
-    jobs.reserve(n_angles);
+    jobs->clear();
+    jobs->reserve(n_angles);
     const size_t npix = (size_t)ctx->geo.nu * ctx->geo.nv;
     uint64_t total = 0;
     for (int a = 0; a < n_angles; ++a) {
@@ -502,10 +520,140 @@ GDRR_API int gdrr_mc_project_batched(gdrr_ctx* ctx, int32_t n_angles, const doub
         j.tally_s = scat_dev + (size_t)a * npix;
         if (total + budgets[a] < total) return GDRR_ERR_INVALID_ARG;
         total += budgets[a];
-        jobs.push_back(j);
+        jobs->push_back(j);
     }
+    *total_out = total;
+    return GDRR_OK;
+}
+
+GDRR_API int gdrr_mc_project_batched(gdrr_ctx* ctx, int32_t n_angles, const double* angles_rad,
+                                     const uint64_t* budgets, uint64_t seed, int64_t* prim_dev, int64_t* scat_dev,
+                                     uint64_t* stats_dev) {
+    std::vector<Job> jobs;
+    uint64_t total = 0;
+    const int rc = scan_jobs(ctx, n_angles, angles_rad, budgets, prim_dev, scat_dev, &jobs, &total);
+    if (rc) return rc;
     if (jobs.empty()) return GDRR_OK;
     return mc_launch(ctx, jobs, total, seed, stats_dev, nullptr);
+}
+
+GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* angles_rad, const uint64_t* budgets,
+                              uint64_t seed, int64_t* prim_dev, int64_t* scat_dev, uint64_t* stats_dev,
+                              int32_t zero_tallies, gdrr_scan** out) {
+    if (!out) return GDRR_ERR_INVALID_ARG;
+    std::vector<Job> jobs;
+    uint64_t total = 0;
+    int rc = scan_jobs(ctx, n_angles, angles_rad, budgets, prim_dev, scat_dev, &jobs, &total);
+    if (rc) return rc;
+    if (jobs.empty()) return GDRR_ERR_INVALID_ARG;
+    gdrr_scan* sc = new (std::nothrow) gdrr_scan();
+    if (!sc) return GDRR_ERR_OOM;
+    sc->ctx = ctx;
+    sc->total = total;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMalloc((void**)&sc->d_jobs, sizeof(Job) * jobs.size())) != cudaSuccess) break;
+        if ((e = cudaMalloc((void**)&sc->d_counter, sizeof(unsigned long long))) != cudaSuccess) break;
+        if (!stats_dev && (e = cudaMalloc((void**)&sc->d_stats, GDRR_NSTATS * sizeof(unsigned long long))) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpy(sc->d_jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            break;
+        McParams p = static_mc_params(ctx);
+        p.rk = round_keys(seed);
+        p.jobs = sc->d_jobs; p.n_jobs = (int)jobs.size(); p.total = total;
+        p.counter = sc->d_counter;
+        p.stats = stats_dev ? reinterpret_cast<unsigned long long*>(stats_dev) : sc->d_stats;
+        p.records = nullptr;
+        p.chunk = 32 * ctx->opt.hist_per_thread;
+        p.batch_min = ctx->opt.batch_min;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        const size_t tally_bytes = (size_t)n_angles * ctx->geo.nu * ctx->geo.nv * sizeof(int64_t);
+        cudaError_t ce = cudaSuccess;
+        if (zero_tallies) {
+            ce = cudaMemsetAsync(prim_dev, 0, tally_bytes, cs);
+            if (ce == cudaSuccess) ce = cudaMemsetAsync(scat_dev, 0, tally_bytes, cs);
+        }
+        if (ce == cudaSuccess && !stats_dev)
+            ce = cudaMemsetAsync(sc->d_stats, 0, GDRR_NSTATS * sizeof(unsigned long long), cs);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), cs);
+        if (ce == cudaSuccess) ce = launch_mc(p, ctx->opt.block_size, launch_grid(ctx, total, false), false, cs);
+        e = cudaStreamEndCapture(cs, &sc->graph);
+        if (ce != cudaSuccess) { e = ce; break; }
+        if (e != cudaSuccess) break;
+        e = cudaGraphInstantiate(&sc->exec, sc->graph, 0);
+    } while (0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        gdrr_scan_destroy(sc);
+        return cuda_err(e);
+    }
+    *out = sc;
+    return GDRR_OK;
+}
+
+GDRR_API int gdrr_scan_launch(gdrr_scan* scan) {
+    if (!scan || !scan->exec) return GDRR_ERR_INVALID_ARG;
+    return cuda_err(cudaGraphLaunch(scan->exec, scan->ctx->stream));
+}
+
+GDRR_API void gdrr_scan_destroy(gdrr_scan* scan) {
+    if (!scan) return;
+    if (scan->ctx) cudaStreamSynchronize(scan->ctx->stream);
+    if (scan->exec) cudaGraphExecDestroy(scan->exec);
+    if (scan->graph) cudaGraphDestroy(scan->graph);
+    if (scan->d_jobs) cudaFree(scan->d_jobs);
+    if (scan->d_counter) cudaFree(scan->d_counter);
+    if (scan->d_stats) cudaFree(scan->d_stats);
+    delete scan;
+}
+
+GDRR_API int gdrr_autotune(gdrr_ctx* ctx, double angle_rad, uint64_t n_probe, uint64_t seed,
+                           gdrr_mc_options* best_out) {
+    if (!ctx || n_probe == 0 || !std::isfinite(angle_rad) || !geometry_ok(ctx, angle_rad)) return GDRR_ERR_INVALID_ARG;
+    const size_t npix = (size_t)ctx->geo.nu * ctx->geo.nv;
+    if (!ctx->d_tune) TRY_CUDA(cudaMalloc((void**)&ctx->d_tune, 2 * npix * sizeof(int64_t)));
+    Job j;
+    memset(&j, 0, sizeof j);
+    j.f = make_frame(ctx->geo, angle_rad);
+    j.count = n_probe;
+    j.tally_p = ctx->d_tune;
+    j.tally_s = ctx->d_tune + npix;
+    const std::vector<Job> jobs(1, j);
+    const gdrr_mc_options base = ctx->opt;
+    static const int blocks[] = {64, 128, 256};
+    static const int batch[] = {8, 12, 16, 20, 24, 28, 32};
+    static const int hpt[] = {1, 8, 64};
+    cudaEvent_t e0, e1;
+    TRY_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return GDRR_ERR_CUDA; }
+    gdrr_mc_options best = base;
+    float best_ms = 3.0e38f;
+    int rc = mc_launch(ctx, jobs, n_probe, seed, nullptr, nullptr);   // warm-up
+    for (int b : blocks)
+        for (int m : batch)
+            for (int h : hpt) {
+                if (rc) break;
+                gdrr_mc_options o = base;
+                o.block_size = b; o.batch_min = m; o.hist_per_thread = h; o.blocks_per_sm = 0;
+                ctx->opt = o;
+                float ms = 0.0f;
+                if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
+                rc = mc_launch(ctx, jobs, n_probe, seed, nullptr, nullptr);
+                if (rc) break;
+                if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess
+                    || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    rc = GDRR_ERR_CUDA;
+                    break;
+                }
+                if (ms < best_ms) { best_ms = ms; best = o; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->opt = rc ? base : best;
+    if (!rc && best_out) *best_out = best;
+    return rc;
 }
 
 GDRR_API int gdrr_finalize(gdrr_ctx* ctx, const int64_t* tally_dev, int64_t n, uint64_t n_photons,

@@ -16,6 +16,20 @@ __host__ __device__ __forceinline__ int brick_x(int x) { return ((x >> 2) << 4) 
 __host__ __device__ __forceinline__ int brick_y(int y, int bsy) { return (y >> 1) * bsy + ((y & 1) << 2); }
 __host__ __device__ __forceinline__ int brick_z(int z, int bsz) { return (z >> 1) * bsz + ((z & 1) << 3); }
 
+// Philox4x32-10 round keys of a seed: k_r = (lo + r * 0x9E3779B9, hi + r * 0xBB67AE85).
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+inline RoundKeys round_keys(uint64_t seed) {
+    RoundKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = (uint32_t)seed + (uint32_t)r * 0x9E3779B9u;
+        rk.k1[r] = (uint32_t)(seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+    }
+    return rk;
+}
+
 // Per-angle imager frame in FP32 (Section 2.1, Fig. 1).
 struct Frame {
     float S[3];    // source position
@@ -67,7 +81,7 @@ struct McParams {
     // options
     float e_cut;
     int max_steps;
-    uint64_t seed;
+    RoundKeys rk;                  // Philox round keys of the seed
     // jobs
     const Job* jobs;
     int n_jobs;

@@ -53,17 +53,18 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Ten Philox rounds with the round keys k_r = key + r (0x9E3779B9, 0xBB67AE85)
+// precomputed on the host (they depend only on the seed), so each round is
+// two wide multiplies and two three-input XORs with a constant-bank operand.
 __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
-                                              uint32_t k0, uint32_t k1) {
+                                              const RoundKeys& rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
         const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0;
-        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        const uint32_t n0 = hi1 ^ c1 ^ rk.k0[r];
+        const uint32_t n2 = hi0 ^ c3 ^ rk.k1[r];
         c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
     }
 }
 
@@ -78,9 +79,9 @@ struct Stream {
         angle = angle_index; hlo = (uint32_t)hid; hhi = (uint32_t)(hid >> 32);
         blk = 0;
     }
-    __device__ __forceinline__ uint4 block(uint64_t seed) {
+    __device__ __forceinline__ uint4 block(const RoundKeys& rk) {
         uint32_t c0 = blk, c1 = angle, c2 = hlo, c3 = hhi;
-        philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+        philox4x32_10(c0, c1, c2, c3, rk);
         ++blk;
         return make_uint4(c0, c1, c2, c3);
     }
@@ -145,9 +146,9 @@ __device__ __forceinline__ float response(const McParams& P, float e) {
     return a + f * (b - a);
 }
 
-__device__ __forceinline__ void azimuth(Stream& rs, uint64_t seed, float& cp, float& sp) {
+__device__ __forceinline__ void azimuth(Stream& rs, const RoundKeys& rk, float& cp, float& sp) {
     for (;;) {
-        const uint4 w = rs.block(seed);
+        const uint4 w = rs.block(rk);
         const float a = 2.0f * uniform(w.x) - 1.0f;
         const float b = 2.0f * uniform(w.y) - 1.0f;
         const float r2 = a * a + b * b;
@@ -181,13 +182,13 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float ct, f
     w = nw_ * il;
 }
 
-__device__ __forceinline__ void compton(Stream& rs, uint64_t seed, float e, float& ct_out, float& e_out) {
+__device__ __forceinline__ void compton(Stream& rs, const RoundKeys& rk, float e, float& ct_out, float& e_out) {
     const float alpha = e * (float)(1.0 / 510.99895);
     const float ialpha = (float)510.99895 / e;
     const float ta = 2.0f * alpha;
     float x;
     for (;;) {
-        const uint4 w = rs.block(seed);
+        const uint4 w = rs.block(rk);
         const float r1 = uniform(w.x);
         const float r2 = uniform(w.y);
         const float r3 = uniform(w.z);
@@ -204,9 +205,9 @@ __device__ __forceinline__ void compton(Stream& rs, uint64_t seed, float e, floa
     e_out = e / x;
 }
 
-__device__ __forceinline__ float rayleigh(Stream& rs, uint64_t seed) {
+__device__ __forceinline__ float rayleigh(Stream& rs, const RoundKeys& rk) {
     for (;;) {
-        const uint4 w = rs.block(seed);
+        const uint4 w = rs.block(rk);
         const float a = uniform(w.x);
         const float b = uniform(w.y);
         const float mu = 2.0f * a - 1.0f;
@@ -355,7 +356,7 @@ struct Lane {
         scattered = 0;
         if (REC) { r_virt = 0; r_ray = 0; r_comp = 0; r_first = 0; r_dep = 0.0; }
 
-        const uint4 w0 = rs.block(P.seed);
+        const uint4 w0 = rs.block(P.rk);
         const float xi_u = uniform(w0.y);
         const float xi_v = uniform(w0.z);
         const int j = cdf_search(P.kcdf_pix, P.guide_pix, P.n_guide_pix, w0.x);
@@ -416,7 +417,7 @@ struct Lane {
             state = S_DEAD;
             return;
         }
-        const uint4 wf = rs.block(P.seed);            // this flight's block
+        const uint4 wf = rs.block(P.rk);            // this flight's block
         const float s = -gd_logf(uniform(wf.x)) * inv_mumax;
         ++nsteps;
         ++c_steps;
@@ -484,8 +485,8 @@ struct Lane {
     __device__ __forceinline__ void interact(const McParams& P, unsigned long long* cnt) {
         float cp, sp;
         if (state == S_RAY) {
-            const float ct = rayleigh(rs, P.seed);
-            azimuth(rs, P.seed, cp, sp);
+            const float ct = rayleigh(rs, P.rk);
+            azimuth(rs, P.rk, cp, sp);
             rotate(dx, dy, dz, ct, cp, sp);
             scattered = 1;
             count(cnt, GDRR_ST_RAYLEIGH);
@@ -494,8 +495,8 @@ struct Lane {
             return;
         }
         float ct, e2;
-        compton(rs, P.seed, e, ct, e2);
-        azimuth(rs, P.seed, cp, sp);
+        compton(rs, P.rk, e, ct, e2);
+        azimuth(rs, P.rk, cp, sp);
         rotate(dx, dy, dz, ct, cp, sp);
         scattered = 1;
         count(cnt, GDRR_ST_COMPTON);
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(256) gather_probe_kernel(const McParams P, uin
     if (acc == -1.0f) atomicAdd(sink, 1u);   // keeps the loads; never true for densities >= 0
 }
 
-__global__ void stream_words_kernel(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist,
+__global__ void stream_words_kernel(const RoundKeys rk, uint32_t angle_index, uint64_t hid0, int n_hist,
                                     int n_blocks, uint32_t* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_hist) return;
@@ -611,7 +612,7 @@ __global__ void stream_words_kernel(uint64_t seed, uint32_t angle_index, uint64_
     rs.init(angle_index, hid0 + (uint64_t)i);
     uint32_t* o = out + (size_t)i * 4 * n_blocks;
     for (int b = 0; b < n_blocks; ++b) {
-        const uint4 w = rs.block(seed);
+        const uint4 w = rs.block(rk);
         o[4 * b] = w.x; o[4 * b + 1] = w.y; o[4 * b + 2] = w.z; o[4 * b + 3] = w.w;
     }
 }
@@ -666,7 +667,8 @@ cudaError_t launch_gather_probe(const McParams& p, uint64_t n_cells, int grid, u
 cudaError_t launch_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist, int n_blocks,
                                 uint32_t* out, cudaStream_t s) {
     if (n_hist <= 0) return cudaSuccess;
-    stream_words_kernel<<<(n_hist + 127) / 128, 128, 0, s>>>(seed, angle_index, hid0, n_hist, n_blocks, out);
+    stream_words_kernel<<<(n_hist + 127) / 128, 128, 0, s>>>(round_keys(seed), angle_index, hid0, n_hist, n_blocks,
+                                                             out);
     return cudaGetLastError();
 }
 

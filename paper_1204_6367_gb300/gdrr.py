@@ -105,11 +105,15 @@ def lib():
             "gdrr_fit_zeta": [vp, vp, i32, u64, vp, vp],
             "gdrr_stream_words": [u64, u32, u64, i32, i32, vp, vp],
             "gdrr_gather_roofline": [vp, u64, vp],
+            "gdrr_scan_create": [vp, i32, vp, vp, u64, vp, vp, vp, i32, vp],
+            "gdrr_scan_launch": [vp],
+            "gdrr_scan_destroy": [vp],
+            "gdrr_autotune": [vp, dbl, u64, u64, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = None if name == "gdrr_destroy" else ctypes.c_int
+            f.restype = None if name in ("gdrr_destroy", "gdrr_scan_destroy") else ctypes.c_int
         L.gdrr_error_string.argtypes = [ctypes.c_int]
         L.gdrr_error_string.restype = ctypes.c_char_p
         _lib = L
@@ -282,6 +286,64 @@ def gdrr_mc_project_batched(ctx: Context, angles_rad, budgets, seed: int, prim=N
                                          _dev_ptr(prim, torch.int64, n, "prim"), _dev_ptr(scat, torch.int64, n, "scat"),
                                          sp))
     return prim, scat
+
+
+class Scan:
+    """A multi-angle scan captured as a CUDA graph (gdrr_scan_create)."""
+
+    def __init__(self, ctx: Context, angles_rad, budgets, seed: int, prim=None, scat=None, stats=None,
+                 zero_tallies: bool = True):
+        import torch
+        self.ctx = ctx
+        self.angles = np.ascontiguousarray(angles_rad, np.float64)
+        self.budgets = np.ascontiguousarray(budgets, np.uint64)
+        if prim is None or scat is None:
+            prim, scat = new_tallies(ctx, self.angles.size)
+        self.prim, self.scat, self.stats = prim, scat, stats
+        n = self.angles.size * ctx.nu * ctx.nv
+        h = ctypes.c_void_p()
+        sp = _dev_ptr(stats, torch.int64, GDRR_NSTATS, "stats") if stats is not None else None
+        _check("gdrr_scan_create",
+               lib().gdrr_scan_create(ctx.handle, self.angles.size, _np_ptr(self.angles), _np_ptr(self.budgets),
+                                      int(seed), _dev_ptr(prim, torch.int64, n, "prim"),
+                                      _dev_ptr(scat, torch.int64, n, "scat"), sp, int(bool(zero_tallies)),
+                                      ctypes.byref(h)))
+        self._h = h
+
+    def launch(self):
+        _check("gdrr_scan_launch", lib().gdrr_scan_launch(self._h))
+        return self.prim, self.scat
+
+    def close(self):
+        if self._h is not None:
+            lib().gdrr_scan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gdrr_scan_create(ctx: Context, angles_rad, budgets, seed: int, prim=None, scat=None, stats=None,
+                     zero_tallies: bool = True) -> Scan:
+    return Scan(ctx, angles_rad, budgets, seed, prim, scat, stats, zero_tallies)
+
+
+def gdrr_scan_launch(scan: Scan):
+    return scan.launch()
+
+
+def gdrr_scan_destroy(scan: Scan):
+    scan.close()
+
+
+def gdrr_autotune(ctx: Context, angle_rad: float = 0.0, n_probe: int = 10_000_000, seed: int = 1) -> dict:
+    o = McOptions()
+    _check("gdrr_autotune", lib().gdrr_autotune(ctx.handle, float(angle_rad), int(n_probe), int(seed),
+                                                ctypes.byref(o)))
+    return {k: getattr(o, k) for k, _ in McOptions._fields_}
 
 
 def gdrr_finalize(ctx: Context, tally, n_photons: int, out=None):

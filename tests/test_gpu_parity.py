@@ -269,3 +269,34 @@ def test_statistical_agreement_with_fp64_oracle(gd, small):
     sg, so = np.sum(cg_s) / n_g, np.sum(co_s) / n_o
     sig = math.sqrt(_pooled(cg_s)[1].sum() / n_g**2 + _pooled(co_s)[1].sum() / n_o**2)
     assert abs(sg - so) <= 0.005 * so + 3 * sig, (sg, so, sig)
+
+
+def test_scan_graph_replays_equal_batched(gd, small):
+    angles = np.linspace(0, 2 * math.pi, 5, endpoint=False)
+    budgets = np.array([20_000, 7, 0, 55_555, 31_000], np.uint64)
+    with gd.Context(small) as ctx:
+        bp, bs = gd.gdrr_mc_project_batched(ctx, angles, budgets, 23)
+        scan = gd.gdrr_scan_create(ctx, angles, budgets, 23, zero_tallies=True)
+        scan.launch()
+        scan.launch()
+        gd.gdrr_sync(ctx)
+        assert torch.equal(scan.prim, bp) and torch.equal(scan.scat, bs)
+        acc = gd.gdrr_scan_create(ctx, angles, budgets, 23, zero_tallies=False)
+        acc.launch()
+        acc.launch()
+        gd.gdrr_sync(ctx)
+        assert torch.equal(acc.prim, 2 * bp) and torch.equal(acc.scat, 2 * bs)
+        scan.close()
+        acc.close()
+
+
+def test_autotune_keeps_results(gd, small):
+    with gd.Context(small) as ctx:
+        ref = gd.gdrr_mc_project(ctx, 150_000, 8)
+        best = gd.gdrr_autotune(ctx, 0.0, 200_000, 3)
+        assert best["block_size"] in (64, 128, 256) and 8 <= best["batch_min"] <= 32
+        assert best["hist_per_thread"] in (1, 8, 64)
+        assert gd.gdrr_get_options(ctx)["batch_min"] == best["batch_min"]
+        got = gd.gdrr_mc_project(ctx, 150_000, 8)
+        gd.gdrr_sync(ctx)
+        assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])
