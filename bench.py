@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scan", action="store_true", help="skip the 64-angle batched-scan comparison")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 1 mm / 4 mm voxel-size timings")
     return ap.parse_args()
 
 
@@ -335,6 +336,33 @@ def run_ours(args):
                    "graph_histories_per_s": tot_hist / graph_s, "plain_histories_per_s": tot_hist / plain_s,
                    "speedup": plain_s / graph_s, "tallies_identical": same}
 
+    # voxel-size sweep: the same torso at 1 mm (512x512x256, 537 MB of
+    # records: beyond L2) and 4 mm (128x128x64), transport only, 1e8 histories
+    voxel_sweep = None
+    if not args.no_sweep:
+        voxel_sweep = {}
+        for vox in (1.0, 4.0):
+            pv = inputs.torso_problem(vox=vox)
+            with gdrr.Context(pv, stream) as cv:
+                vstats = torch.zeros(gdrr.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+                vp, vs = gdrr.gdrr_mc_project(cv, n_hist, seed, angle, stats=vstats)
+                torch.cuda.synchronize()
+                vstats.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(1.0)
+                e0.record(stream)
+                gdrr.gdrr_mc_project(cv, n_hist, seed, angle, prim=vp, scat=vs, stats=vstats)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_v = e0.elapsed_time(e1)
+                sv = gdrr.stats_dict(vstats)
+                probe_v = gdrr.gdrr_gather_roofline(cv, sv["steps"])
+                voxel_sweep[f"{vox:g}mm"] = {
+                    "shape_zyx": list(pv.material.shape), "mc_ms": ms_v, "histories_per_s": n_hist / ms_v * 1e3,
+                    "free_flights": sv["steps"], "algorithmic_gbs": sv["steps"] * BYTES_PER_STEP_ALGO / ms_v / 1e6,
+                    "gather_roof_frac": (probe_v * 1e3) / ms_v}
+            del pv
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -378,6 +406,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "voxel_sweep": voxel_sweep,
         "autotuned": tuned,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
