@@ -308,6 +308,45 @@ GDRR_API int gdrr_fit_zeta(const double* inv_sqrt_mAs, const double* ratio, int3
  * measures the ceiling against which the transport's gather rate is judged. */
 GDRR_API int gdrr_gather_roofline(gdrr_ctx* ctx, uint64_t n_cells, double* seconds_out);
 
+/* BF16 tensor-core GEMM (tcgen05): C[M x N] (FP32, row length ldc) = A[M x K]
+ * . B[N x K]^T with A and B BF16 device matrices whose rows are K-contiguous
+ * (row lengths lda, ldb, multiples of 8 elements); K a multiple of 64.  With
+ * splits > 1 the K range is split across CTAs that add into C, which the
+ * caller zeroes first.  Synchronises; GDRR_ERR_CUDA also reports a tensor-core
+ * wait that timed out.  Not in the paper: the building block of the learned
+ * scatter estimator's convolutions. */
+GDRR_API int gdrr_gemm_bf16(const void* A_dev, int32_t lda, const void* B_dev, int32_t ldb, float* C_dev, int32_t ldc,
+                            int32_t M, int32_t N, int32_t K, int32_t splits, void* cuda_stream);
+
+/* ---- Learned scatter estimator ----------------------------------------------
+ * Not in the paper.  A 4-level convolutional encoder-decoder (base_channels
+ * channels at full resolution, doubling per level; 2 x 2 average pooling,
+ * nearest 2x upsampling with skip concatenation, ReLU, a 1x1 output layer)
+ * that maps (low-photon MC scatter, ray-traced primary) to scatter, trained
+ * on pairs the method itself generates.  BF16 weights and activations, FP32
+ * accumulation on the tensor cores; FP32 master weights, gradients and Adam
+ * state.  Inputs are device FP32 [batch][2][height][width], outputs and
+ * targets [batch][1][height][width]; height and width multiples of 8.
+ * Parameters flatten layer by layer as (weights [co][ci][ky][kx], biases
+ * [co]), encoder first, then decoder, then the 1x1 layer. */
+typedef struct gdrr_cnn gdrr_cnn;
+GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, int32_t base_channels, uint64_t seed,
+                             void* cuda_stream, gdrr_cnn** out);
+GDRR_API void gdrr_cnn_destroy(gdrr_cnn* net);
+GDRR_API int gdrr_cnn_num_params(const gdrr_cnn* net, int64_t* count);
+/* Host FP32 copies of the parameters / of the last backward's gradients. */
+GDRR_API int gdrr_cnn_get_params(gdrr_cnn* net, float* host);
+GDRR_API int gdrr_cnn_set_params(gdrr_cnn* net, const float* host);   /* also resets the Adam state */
+GDRR_API int gdrr_cnn_get_grads(gdrr_cnn* net, float* host);
+/* Forward pass of batch inputs; out_dev may be NULL (activations are kept for backward). */
+GDRR_API int gdrr_cnn_forward(gdrr_cnn* net, int32_t batch, const float* in_dev, float* out_dev);
+/* Mean-squared-error loss against target_dev and the gradients of every
+ * parameter for the last forward pass (overwritten, not accumulated);
+ * *loss_out (host) receives the loss.  Synchronises. */
+GDRR_API int gdrr_cnn_backward(gdrr_cnn* net, const float* target_dev, double* loss_out);
+/* One Adam update of every parameter from the last gradients. */
+GDRR_API int gdrr_cnn_adam_step(gdrr_cnn* net, float lr, float beta1, float beta2, float eps);
+
 /* Parity hook: the Philox words of n_hist history streams (ids hid0 ..),
  * n_blocks blocks each, exactly as the transport draws them.  out_dev:
  * device uint32[n_hist][4 * n_blocks].  Runs on cuda_stream. */

@@ -27,6 +27,8 @@ SOURCES = {
     "mc_transport.cu": ["-fmad=false"],
     "raytrace.cu": [],
     "image_ops.cu": [],
+    "cnn_gemm.cu": [],
+    "cnn.cu": [],
 }
 HEADERS = [os.path.join(INCLUDE, "gdrr.h"), os.path.join(CSRC, "gdrr_internal.cuh")]
 

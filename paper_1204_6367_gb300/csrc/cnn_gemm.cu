@@ -1,0 +1,235 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05) of sm_103a, for the
+// convolutions of the learned scatter estimator.
+//
+//   C[M x N] (FP32)  =  A[M x K] . B[N x K]^T      (A, B BF16, rows K-contiguous)
+//
+// One CTA of 128 threads computes a 128 x BN tile.  For each 64-wide slice of
+// K the threads stage the A and B tiles in shared memory in the canonical
+// no-swizzle K-major layout of the tensor core (8 x 8 "core matrices" of
+// 128 contiguous bytes: core (r/8, k/8) at ((r/8) * 8 + k/8) * 128 bytes, so
+// consecutive core matrices along K are 128 bytes apart and along M/N 1024
+// bytes apart); one elected thread issues four 128 x BN x 16 tcgen05.mma
+// instructions accumulating in tensor memory (TMEM) and commits them to an
+// mbarrier that every thread waits on before the slice is overwritten.  The
+// epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
+// 32w .. 32w + 31 = rows of the tile) and stores or atomically adds FP32.
+// grid.z splits K; with more than one split the CTAs add into C.
+//
+// Every wait is bounded: a wait that runs out sets *err and the CTA still
+// frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "gdrr_internal.cuh"
+
+namespace gdrr {
+namespace {
+
+constexpr int GEMM_BM = 128;
+constexpr int GEMM_BK = 64;
+constexpr int GEMM_THREADS = 128;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-dimension
+// byte offset (between core matrices adjacent along K), stride-dimension byte
+// offset (between core matrices adjacent along M or N), descriptor version 1,
+// no swizzling.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor for kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Stage rows [row0, row0 + R) x K-slice [k0, k0 + 64) of a K-contiguous BF16
+// matrix into the core-matrix layout; rows beyond nrows read as zero.
+template <int R>
+__device__ __forceinline__ void stage_tile(__nv_bfloat16* dst, const __nv_bfloat16* __restrict__ src, int ld,
+                                           int row0, int nrows, int k0) {
+    constexpr int VECS = R * (GEMM_BK / 8);            // 16-byte vectors in the tile
+    for (int v = threadIdx.x; v < VECS; v += GEMM_THREADS) {
+        const int r = v / (GEMM_BK / 8);
+        const int kc = v % (GEMM_BK / 8);               // core-matrix column along K
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        const int gr = row0 + r;
+        if (gr < nrows) val = *reinterpret_cast<const uint4*>(src + (size_t)gr * ld + k0 + kc * 8);
+        const int off = (((r >> 3) * (GEMM_BK / 8) + kc) * 64) + (r & 7) * 8;   // elements
+        *reinterpret_cast<uint4*>(dst + off) = val;
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
+                                                                const __nv_bfloat16* __restrict__ B, int ldb,
+                                                                float* __restrict__ C, int ldc, int M, int N, int K,
+                                                                int k_split, int atomic_out, int* err) {
+    __shared__ __align__(1024) __nv_bfloat16 sA[GEMM_BM * GEMM_BK];
+    __shared__ __align__(1024) __nv_bfloat16 sB[BN * GEMM_BK];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+
+    const int warp = threadIdx.x >> 5;
+    const int m0 = blockIdx.x * GEMM_BM;
+    const int n0 = blockIdx.y * BN;
+    const int k_begin = blockIdx.z * k_split;
+    const int k_end = min(K, k_begin + k_split);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_base)), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t bar = smem_addr(&mbar);
+    constexpr uint32_t idesc = instr_desc(GEMM_BM, BN);
+    bool ok = true;
+    uint32_t phase = 0;
+    int slices = 0;
+
+    for (int k0 = k_begin; k0 < k_end; k0 += GEMM_BK) {
+        stage_tile<GEMM_BM>(sA, A, lda, m0, M, k0);
+        stage_tile<BN>(sB, B, ldb, n0, N, k0);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+#pragma unroll
+            for (int kk = 0; kk < GEMM_BK / 16; ++kk) {
+                // one K16 step spans two core matrices along K (2 x 128 bytes)
+                const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
+                const uint64_t bd = smem_desc(b0 + kk * 256, 128, 1024);
+                const uint32_t acc = (slices > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                    :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(bar) : "memory");
+        }
+        ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;   // CTA-uniform outcome
+        phase ^= 1u;
+        ++slices;
+        if (!ok) break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (ok && slices > 0) {
+        const int row = m0 + warp * 32 + (threadIdx.x & 31);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                  "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < N) {
+                        const float v = __uint_as_float(r[j]);
+                        float* dst = C + (size_t)row * ldc + col;
+                        if (atomic_out) atomicAdd(dst, v); else *dst = v;
+                    }
+                }
+            }
+        }
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
+template <int BN>
+cudaError_t launch_gemm_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
+                          int M, int N, int K, int splits, int* err, cudaStream_t s) {
+    const int k_slices = K / GEMM_BK;
+    splits = max(1, min(splits, k_slices));
+    const int per = (k_slices + splits - 1) / splits;
+    splits = (k_slices + per - 1) / per;
+    dim3 grid((M + GEMM_BM - 1) / GEMM_BM, (N + BN - 1) / BN, splits);
+    gemm_bf16_kernel<BN><<<grid, GEMM_THREADS, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, per * GEMM_BK,
+                                                        splits > 1 ? 1 : 0, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// C = A . B^T; K a multiple of 64; lda, ldb multiples of 8 (16-byte rows);
+// with splits > 1 the caller zeroes C first (partial products are added).
+cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N, int K,
+                             int splits, int* err, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0 || K % GEMM_BK || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
+    const auto* a = static_cast<const __nv_bfloat16*>(A);
+    const auto* b = static_cast<const __nv_bfloat16*>(B);
+    if (N <= 32) return launch_gemm_t<32>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+    if (N <= 64) return launch_gemm_t<64>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+    return launch_gemm_t<128>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+}
+
+}  // namespace gdrr
+
+extern "C" GDRR_API int gdrr_gemm_bf16(const void* A_dev, int32_t lda, const void* B_dev, int32_t ldb, float* C_dev,
+                                      int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t splits, void* cuda_stream) {
+    if (!A_dev || !B_dev || !C_dev || M <= 0 || N <= 0 || K <= 0 || K % 64 || lda % 8 || ldb % 8 || ldc < N ||
+        lda < K || ldb < K || splits < 1)
+        return GDRR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int* err = nullptr;
+    // a 4-byte wait-timeout flag; allocated per call (this entry point is a test and utility hook)
+    if (cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess) return GDRR_ERR_OOM;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = gdrr::launch_gemm_bf16(A_dev, lda, B_dev, ldb, C_dev, ldc, M, N, K, splits, err, s);
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(err);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GDRR_ERR_OOM : GDRR_ERR_CUDA;
+    return bad ? GDRR_ERR_CUDA : GDRR_OK;
+}
+

@@ -109,11 +109,21 @@ def lib():
             "gdrr_scan_launch": [vp],
             "gdrr_scan_destroy": [vp],
             "gdrr_autotune": [vp, dbl, u64, u64, vp],
+            "gdrr_gemm_bf16": [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, vp],
+            "gdrr_cnn_create": [i32, i32, i32, i32, u64, vp, vp],
+            "gdrr_cnn_destroy": [vp],
+            "gdrr_cnn_num_params": [vp, vp],
+            "gdrr_cnn_get_params": [vp, vp],
+            "gdrr_cnn_set_params": [vp, vp],
+            "gdrr_cnn_get_grads": [vp, vp],
+            "gdrr_cnn_forward": [vp, i32, vp, vp],
+            "gdrr_cnn_backward": [vp, vp, vp],
+            "gdrr_cnn_adam_step": [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = None if name in ("gdrr_destroy", "gdrr_scan_destroy") else ctypes.c_int
+            f.restype = None if name in ("gdrr_destroy", "gdrr_scan_destroy", "gdrr_cnn_destroy") else ctypes.c_int
         L.gdrr_error_string.argtypes = [ctypes.c_int]
         L.gdrr_error_string.restype = ctypes.c_char_p
         _lib = L
@@ -483,3 +493,82 @@ def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin
     N = gdrr_noise_calibrate(ctx, P_hat, P, S_hat, S, n_photons, mas, zeta)
     return dict(P=P, P_hat=P_hat, S_hat=S_hat, S_hat_coarse=S_hat_c, S_coarse=S_c, S=S, N=N,
                 prim=prim, scat=scat, stats=stats)
+
+
+# ---- tensor-core GEMM and the learned scatter estimator ------------------
+
+def gdrr_gemm_bf16(a, b, splits: int = 1, out=None, stream=None):
+    """C = A . B^T for BF16 CUDA tensors A [M, K], B [N, K] (K a multiple of 64)."""
+    import torch
+    M, K = a.shape
+    N = b.shape[0]
+    if out is None:
+        out = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    h, _ = _stream_handle(stream)
+    _check("gdrr_gemm_bf16", lib().gdrr_gemm_bf16(_dev_ptr(a, torch.bfloat16, None, "A"), a.stride(0),
+                                                  _dev_ptr(b, torch.bfloat16, None, "B"), b.stride(0),
+                                                  _dev_ptr(out, torch.float32, None, "C"), out.stride(0),
+                                                  M, N, K, int(splits), h))
+    return out
+
+
+class Cnn:
+    """gdrr_cnn: the learned scatter estimator (forward, backward, Adam)."""
+
+    def __init__(self, max_batch: int, height: int, width: int, base_channels: int = 32, seed: int = 1,
+                 stream=None):
+        h, self.stream = _stream_handle(stream)
+        self.max_batch, self.height, self.width, self.c = max_batch, height, width, base_channels
+        self._h = ctypes.c_void_p()
+        _check("gdrr_cnn_create", lib().gdrr_cnn_create(max_batch, height, width, base_channels, int(seed), h,
+                                                        ctypes.byref(self._h)))
+        n = ctypes.c_int64()
+        _check("gdrr_cnn_num_params", lib().gdrr_cnn_num_params(self._h, ctypes.byref(n)))
+        self.n_params = n.value
+
+    def get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        _check("gdrr_cnn_get_params", lib().gdrr_cnn_get_params(self._h, _np_ptr(out)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        if p.size != self.n_params:
+            raise ValueError("wrong parameter count")
+        _check("gdrr_cnn_set_params", lib().gdrr_cnn_set_params(self._h, _np_ptr(p)))
+
+    def get_grads(self):
+        out = np.empty(self.n_params, np.float32)
+        _check("gdrr_cnn_get_grads", lib().gdrr_cnn_get_grads(self._h, _np_ptr(out)))
+        return out
+
+    def forward(self, x, out=None):
+        import torch
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty((B, 1, self.height, self.width), dtype=torch.float32, device="cuda")
+        _check("gdrr_cnn_forward", lib().gdrr_cnn_forward(self._h, B, _dev_ptr(x, torch.float32,
+                                                                                B * 2 * self.height * self.width, "x"),
+                                                          _dev_ptr(out, torch.float32, None, "out")))
+        return out
+
+    def backward(self, target) -> float:
+        import torch
+        loss = ctypes.c_double()
+        _check("gdrr_cnn_backward", lib().gdrr_cnn_backward(self._h, _dev_ptr(target, torch.float32, None, "target"),
+                                                            ctypes.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check("gdrr_cnn_adam_step", lib().gdrr_cnn_adam_step(self._h, lr, beta1, beta2, eps))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().gdrr_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

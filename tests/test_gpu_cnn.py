@@ -1,0 +1,90 @@
+"""GPU parity of the learned scatter estimator's kernels against the CPU
+oracle: the tcgen05 BF16 GEMM against a library matrix product of the same
+BF16 inputs, and the network's forward pass and parameter gradients against
+the FP64 oracle that rounds to BF16 at the same points.
+
+Tolerances: the GEMM accumulates in FP32, so each element is within
+2^-20 (16 FP32 ulps) of the sum of the absolute values of its products.  The network
+differs from the emulating oracle only by FP32 accumulation order and the
+rare BF16 rounding that this flips: 2e-3 relative (norm) on the output,
+2e-2 on each layer's gradients.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle.cnn as cnn  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gd():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1204_6367_gb300 import build, gdrr
+    build.build()
+    gdrr.lib()
+    return gdrr
+
+
+@pytest.mark.parametrize("M,N,K,splits", [(128, 32, 64, 1), (200, 37, 192, 1), (1000, 130, 640, 1),
+                                          (77, 300, 3456, 4), (4096, 64, 576, 1), (64, 896, 2048, 8)])
+def test_gemm_bf16(gd, M, N, K, splits):
+    rng = np.random.default_rng(M * 7 + N)
+    a = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    b = torch.from_numpy(rng.normal(size=(N, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    c = gd.gdrr_gemm_bf16(a, b, splits)
+    torch.cuda.synchronize()
+    ad, bd = a.double().cpu().numpy(), b.double().cpu().numpy()
+    ref = ad @ bd.T
+    # FP32 accumulation: error within a few ulps of the sum of |products|
+    bound = 2.0**-20 * (np.abs(ad) @ np.abs(bd).T)
+    err = np.abs(c.cpu().numpy() - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_cnn_forward_backward_against_oracle(gd):
+    c, H, W, B = 32, 32, 32, 2
+    rng = np.random.default_rng(9)
+    x = rng.normal(size=(B, 2, H, W)).astype(np.float32)
+    t = rng.normal(size=(B, 1, H, W)).astype(np.float32)
+    p = cnn.init_params(c, 5).astype(np.float32)
+    p += (0.01 * rng.normal(size=p.size)).astype(np.float32)      # non-zero biases
+    net = gd.Cnn(B, H, W, c)
+    assert net.n_params == cnn.n_params(c)
+    net.set_params(p)
+    out = net.forward(torch.from_numpy(x).cuda())
+    loss = net.backward(torch.from_numpy(t).cuda())
+    g = net.get_grads()
+    o_out, cache = cnn.forward(x.astype(np.float64), p.astype(np.float64), c, emulate=True)
+    o_loss, o_g = cnn.backward(cache, t.astype(np.float64))
+    out = out.cpu().numpy()
+    assert np.linalg.norm(out - o_out) / np.linalg.norm(o_out) < 2e-3
+    assert loss == pytest.approx(o_loss, rel=5e-3)
+    off = 0
+    for i, (ci, co, k, _) in enumerate(cnn.specs(c)):
+        for name, size in (("w", co * ci * k * k), ("b", co)):
+            gg, og = g[off:off + size], o_g[off:off + size]
+            off += size
+            rel = np.linalg.norm(gg - og) / max(np.linalg.norm(og), 1e-30)
+            assert rel < 2e-2, (i, name, rel)
+    net.close()
+
+
+def test_cnn_training_reduces_loss(gd):
+    c, H, W, B = 32, 32, 48, 4
+    rng = np.random.default_rng(2)
+    yy, xx = np.mgrid[0:H, 0:W]
+    base = np.exp(-((xx - W / 2) ** 2 + (yy - H / 2) ** 2) / 200.0)
+    t = np.stack([base * (1 + 0.2 * i) for i in range(B)])[:, None].astype(np.float32)
+    x = np.concatenate([t + 0.3 * rng.normal(size=t.shape), 0.5 * t], axis=1).astype(np.float32)
+    net = gd.Cnn(B, H, W, c, seed=3)
+    xt, tt = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    losses = []
+    for _ in range(60):
+        net.forward(xt)
+        losses.append(net.backward(tt))
+        net.adam_step(1e-3)
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+    net.close()
