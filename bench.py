@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scan", action="store_true", help="skip the 64-angle batched-scan comparison")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1 mm / 4 mm voxel-size timings")
+    ap.add_argument("--no-learned", action="store_true", help="skip training / evaluating the learned estimator")
     return ap.parse_args()
 
 
@@ -363,6 +364,63 @@ def run_ours(args):
                     "gather_roof_frac": (probe_v * 1e3) / ms_v}
             del pv
 
+    # learned scatter estimator against the plain method: train on pairs the
+    # method generates (32 torsos x 4 angles), evaluate on held-out torsos
+    # against a denoised 1e9-history reference; per-projection cost of each
+    learned = None
+    if not args.no_learned:
+        from paper_1204_6367_gb300 import scatter_net as sn
+        t_data = time.perf_counter()
+        LX, LY = sn.make_dataset(range(100, 132), 4, 10**6, 10**8, rng_seed=1)
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t_data
+        net = gdrr.Cnn(64, sn.H, sn.W, 32, seed=1)
+        t_train = time.perf_counter()
+        losses = sn.train(net, LX, LY, 1500, 16, 1e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t_train
+        rng_l = np.random.default_rng(7)
+        e_net, e_plain, e_judge, cost = [], [], [], {}
+        for sd in (900, 901):
+            with gdrr.Context(sn.coarse_problem(sd)) as cl:
+                for a in range(2):
+                    ang = float(rng_l.uniform(0, 2 * math.pi))
+                    xl = torch.empty((1, 2, sn.H, sn.W), dtype=torch.float32, device="cuda")
+                    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                    e0.record(stream)
+                    d_low = sn.low_input(cl, 10**6, 31 + 10 * sd + a, ang, a, xl[0])
+                    pred = sn.predict(net, xl)
+                    e1.record(stream)
+                    s8, st8 = sn.simulate(cl, 10**8, 57 + 10 * sd + a, ang, a)
+                    judge = sn.denoise(cl, s8, st8, 10**8, sn.HIGH_LENGTH)
+                    e2.record(stream)
+                    torch.cuda.synchronize()
+                    cost.setdefault("learned_ms", []).append(e0.elapsed_time(e1))
+                    cost.setdefault("plain_1e8_ms", []).append(e1.elapsed_time(e2))
+                    sr, str_ = sn.simulate(cl, 10**9, 91 + 10 * sd + a, ang, a)
+                    ref = sn.denoise(cl, sr, str_, 10**9, 1.5).cpu().numpy()
+                    e_net.append(sn.rel_l2(pred.cpu().numpy()[0], ref))
+                    e_plain.append(sn.rel_l2(d_low.cpu().numpy(), ref))
+                    e_judge.append(sn.rel_l2(judge.cpu().numpy(), ref))
+        xb = LX[:64]
+        net.forward(xb)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        net.forward(xb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        learned = {"train_pairs": int(LX.shape[0]), "data_s": t_data, "train_steps": 1500, "train_s": t_train,
+                   "final_loss": float(np.mean(losses[-50:])),
+                   "rel_l2_vs_1e9_reference": {"learned_1e6": float(np.mean(e_net)),
+                                               "plain_denoised_1e6": float(np.mean(e_plain)),
+                                               "plain_denoised_1e8_judge": float(np.mean(e_judge))},
+                   "ms_per_projection": {"learned_1e6_plus_inference": float(np.mean(cost["learned_ms"])),
+                                         "plain_1e8_plus_denoise": float(np.mean(cost["plain_1e8_ms"]))},
+                   "inference_batch64_ms": e0.elapsed_time(e1)}
+        net.close()
+        del LX, LY
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -407,6 +465,7 @@ def run_ours(args):
         "e2e": e2e,
         "batched": batched,
         "voxel_sweep": voxel_sweep,
+        "learned": learned,
         "autotuned": tuned,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,

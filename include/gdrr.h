@@ -308,6 +308,12 @@ GDRR_API int gdrr_fit_zeta(const double* inv_sqrt_mAs, const double* ratio, int3
  * measures the ceiling against which the transport's gather rate is judged. */
 GDRR_API int gdrr_gather_roofline(gdrr_ctx* ctx, uint64_t n_cells, double* seconds_out);
 
+/* dst = (float)(src * scale) and dst = (double)src * scale over n device
+ * elements (packing images into the learned estimator's FP32 input and
+ * back); run on cuda_stream. */
+GDRR_API int gdrr_scale_to_f32(const double* src_dev, int64_t n, double scale, float* dst_dev, void* cuda_stream);
+GDRR_API int gdrr_scale_to_f64(const float* src_dev, int64_t n, double scale, double* dst_dev, void* cuda_stream);
+
 /* BF16 tensor-core GEMM (tcgen05): C[M x N] (FP32, row length ldc) = A[M x K]
  * . B[N x K]^T with A and B BF16 device matrices whose rows are K-contiguous
  * (row lengths lda, ldb, multiples of 8 elements); K a multiple of 64.  With
@@ -321,8 +327,10 @@ GDRR_API int gdrr_gemm_bf16(const void* A_dev, int32_t lda, const void* B_dev, i
 /* ---- Learned scatter estimator ----------------------------------------------
  * Not in the paper.  A 4-level convolutional encoder-decoder (base_channels
  * channels at full resolution, doubling per level; 2 x 2 average pooling,
- * nearest 2x upsampling with skip concatenation, ReLU, a 1x1 output layer)
- * that maps (low-photon MC scatter, ray-traced primary) to scatter, trained
+ * nearest 2x upsampling with skip concatenation, ReLU, a 1x1 output layer
+ * whose result is added to input channel 0, so the network learns a
+ * correction to that channel) that maps (low-photon scatter estimate,
+ * ray-traced primary) to scatter, trained
  * on pairs the method itself generates.  BF16 weights and activations, FP32
  * accumulation on the tensor cores; FP32 master weights, gradients and Adam
  * state.  Inputs are device FP32 [batch][2][height][width], outputs and

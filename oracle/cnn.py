@@ -2,7 +2,8 @@
 
 numpy FP64 forward and backward of the 4-level convolutional
 encoder-decoder (conv3x3 + ReLU per level, 2x2 average pooling, nearest 2x
-upsampling with skip concatenation, 1x1 output, mean-squared-error loss).
+upsampling with skip concatenation, 1x1 output added to input channel 0,
+mean-squared-error loss).
 With emulate=True the values the GPU stores in BF16 are rounded to BF16 at
 the same points: the network input, the weights, every stored activation,
 and the activation gradients that enter the two products of a convolution's
@@ -105,6 +106,7 @@ def forward(x, flat, c, emulate=True):
         y = np.maximum(z, 0.0) if specs(c)[i][3] else z
         return y
 
+    x_in = np.asarray(x, np.float64)
     x = r(x)
     e1 = r(layer(0, x)); p1 = r(pool(e1))
     e2 = r(layer(1, p1)); p2 = r(pool(e2))
@@ -113,7 +115,7 @@ def forward(x, flat, c, emulate=True):
     c3 = np.concatenate([up(e4), e3], axis=1); d3 = r(layer(4, c3))
     c2 = np.concatenate([up(d3), e2], axis=1); d2 = r(layer(5, c2))
     c1 = np.concatenate([up(d2), e1], axis=1); d1 = r(layer(6, c1))
-    out = layer(7, d1)
+    out = layer(7, d1) + x_in[:, 0:1]      # residual: a correction to input channel 0
     cache.update(x=x, e1=e1, p1=p1, e2=e2, p2=p2, e3=e3, p3=p3, e4=e4, c3=c3, d3=d3, c2=c2, d2=d2, c1=c1, d1=d1,
                  out=out)
     return out, cache

@@ -11,7 +11,7 @@
 //   d3 = relu(conv3x3([up(e4), e3], 12c -> 4c))
 //   d2 = relu(conv3x3([up(d3), e2],  6c -> 2c))
 //   d1 = relu(conv3x3([up(d2), e1],  3c -> c))
-//   y  = conv1x1(d1, c -> 1)
+//   y  = conv1x1(d1, c -> 1) + x[channel 0]   (residual: a correction to input 0)
 // pool = 2 x 2 average, up = nearest 2x, [a, b] = channel concatenation.
 // Loss: mean squared error against the target.
 //
@@ -205,6 +205,13 @@ __global__ void place_back_kernel(const float* __restrict__ dcat, int cat_channe
     for (int dy = 0; dy < s; ++dy)
         for (int dx = 0; dx < s; ++dx) acc += d[(int64_t)dy * W + dx];
     if (accumulate) dsrc[i] += acc; else dsrc[i] = acc;
+}
+
+// out[b][0][y][x] += in[b][0][y][x] (in has two channels)
+__global__ void residual_kernel(const float* __restrict__ in, int B, int HW, float* __restrict__ out) {
+    const int64_t n = (int64_t)B * HW;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += in[(i / HW) * 2 * HW + i % HW];
 }
 
 __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, int64_t n, float* __restrict__ dy,
@@ -549,6 +556,8 @@ GDRR_API int gdrr_cnn_forward(gdrr_cnn* n, int32_t batch, const float* in_dev, f
         place_kernel<<<nblk(c * s1), TB, 0, st>>>(n->e1, B, c, H, W, 1, n->c1, 3 * c, 2 * c);
         if ((e = conv_forward(n, L[6], B, n->c1, n->d1, c, nullptr))) break;
         if ((e = conv_forward(n, L[7], B, n->d1, nullptr, 1, n->out))) break;
+        residual_kernel<<<nblk(s1), TB, 0, st>>>(in_dev, B, H * W, n->out);
+        if ((e = cudaGetLastError())) break;
         if (out_dev) e = cudaMemcpyAsync(out_dev, n->out, s1 * sizeof(float), cudaMemcpyDeviceToDevice, st);
     } while (0);
     return err_code(e);

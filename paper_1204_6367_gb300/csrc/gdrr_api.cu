@@ -725,6 +725,16 @@ GDRR_API int gdrr_fit_zeta(const double* inv_sqrt_mAs, const double* ratio, int3
     return GDRR_OK;
 }
 
+GDRR_API int gdrr_scale_to_f32(const double* src_dev, int64_t n, double scale, float* dst_dev, void* cuda_stream) {
+    if ((n > 0 && (!src_dev || !dst_dev)) || n < 0 || !std::isfinite(scale)) return GDRR_ERR_INVALID_ARG;
+    return cuda_err(launch_scale_to_f32(src_dev, n, scale, dst_dev, (cudaStream_t)cuda_stream));
+}
+
+GDRR_API int gdrr_scale_to_f64(const float* src_dev, int64_t n, double scale, double* dst_dev, void* cuda_stream) {
+    if ((n > 0 && (!src_dev || !dst_dev)) || n < 0 || !std::isfinite(scale)) return GDRR_ERR_INVALID_ARG;
+    return cuda_err(launch_scale_to_f64(src_dev, n, scale, dst_dev, (cudaStream_t)cuda_stream));
+}
+
 GDRR_API int gdrr_gather_roofline(gdrr_ctx* ctx, uint64_t n_cells, double* seconds_out) {
     if (!ctx || !seconds_out || n_cells == 0) return GDRR_ERR_INVALID_ARG;
     McParams p = static_mc_params(ctx);

@@ -124,5 +124,7 @@ cudaError_t launch_noise(const double* ph, const double* p, const double* sh, co
 cudaError_t launch_denoise(const double* s_hat, double* s, int nu, int nv, double count_scale, double beta,
                            double omega, int iters, double* scratch, cudaStream_t stream);
 size_t denoise_scratch_doubles(int nu, int nv);
+cudaError_t launch_scale_to_f32(const double* a, int64_t n, double scale, float* out, cudaStream_t s);
+cudaError_t launch_scale_to_f64(const float* a, int64_t n, double scale, double* out, cudaStream_t s);
 
 }  // namespace gdrr

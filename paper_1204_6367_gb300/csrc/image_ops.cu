@@ -122,6 +122,32 @@ cudaError_t launch_noise(const double* ph, const double* p, const double* sh, co
     return cudaGetLastError();
 }
 
+namespace {
+
+__global__ void scale_to_f32_kernel(const double* __restrict__ a, int64_t n, double scale, float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)(a[i] * scale);
+}
+
+__global__ void scale_to_f64_kernel(const float* __restrict__ a, int64_t n, double scale, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)a[i] * scale;
+}
+
+}  // namespace
+
+cudaError_t launch_scale_to_f32(const double* a, int64_t n, double scale, float* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    scale_to_f32_kernel<<<grid_for(n), BLOCK, 0, s>>>(a, n, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_to_f64(const float* a, int64_t n, double scale, double* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    scale_to_f64_kernel<<<grid_for(n), BLOCK, 0, s>>>(a, n, scale, out);
+    return cudaGetLastError();
+}
+
 size_t denoise_scratch_doubles(int nu, int nv) { return 2 * (size_t)nu * nv; }
 
 // scratch: 2 * nu * nv doubles (count-scale data, one ping-pong buffer); the

@@ -110,6 +110,8 @@ def lib():
             "gdrr_scan_destroy": [vp],
             "gdrr_autotune": [vp, dbl, u64, u64, vp],
             "gdrr_gemm_bf16": [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, vp],
+            "gdrr_scale_to_f32": [vp, i64, dbl, vp, vp],
+            "gdrr_scale_to_f64": [vp, i64, dbl, vp, vp],
             "gdrr_cnn_create": [i32, i32, i32, i32, u64, vp, vp],
             "gdrr_cnn_destroy": [vp],
             "gdrr_cnn_num_params": [vp, vp],
@@ -496,6 +498,24 @@ def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin
 
 
 # ---- tensor-core GEMM and the learned scatter estimator ------------------
+
+def gdrr_scale_to_f32(src, scale: float, out, stream=None):
+    import torch
+    h, _ = _stream_handle(stream)
+    _check("gdrr_scale_to_f32", lib().gdrr_scale_to_f32(_dev_ptr(src, torch.float64, None, "src"), src.numel(),
+                                                        float(scale), _dev_ptr(out, torch.float32, src.numel(), "out"),
+                                                        h))
+    return out
+
+
+def gdrr_scale_to_f64(src, scale: float, out, stream=None):
+    import torch
+    h, _ = _stream_handle(stream)
+    _check("gdrr_scale_to_f64", lib().gdrr_scale_to_f64(_dev_ptr(src, torch.float32, None, "src"), src.numel(),
+                                                        float(scale), _dev_ptr(out, torch.float64, src.numel(), "out"),
+                                                        h))
+    return out
+
 
 def gdrr_gemm_bf16(a, b, splits: int = 1, out=None, stream=None):
     """C = A . B^T for BF16 CUDA tensors A [M, K], B [N, K] (K a multiple of 64)."""

@@ -1,0 +1,124 @@
+"""Learned scatter estimator on top of the gDRR method.
+
+The plain method (Section 2.4 Monte Carlo + the Poisson denoiser of Section
+2.5) needs many photons for a smooth scatter image.  This module trains the
+library's convolutional encoder-decoder (gdrr_cnn_*) to map a cheap,
+low-photon Monte Carlo scatter image plus the ray-traced primary to the
+scatter image of a high-photon run, on pairs the method itself generates;
+the plain method stays the reference and the judge of the error.
+
+Everything that computes runs in libgdrr kernels: Monte Carlo, ray tracing,
+finalisation, denoising, scaling into the network's FP32 input, and the
+network's forward, backward and Adam passes.  The error metric is the
+relative l2 norm the paper uses for scatter images (Section 3.2).
+
+Images live on the coarse scatter grid: the 512 x 384 detector of 0.776 mm
+pixels binned 4 x 4, i.e. 128 x 96 pixels of 3.104 mm, simulated directly on
+that grid.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import gdrr, inputs
+
+H, W = 96, 128
+DET_PX = 0.776 * 4
+SCALE = 1.0e4          # signal per source photon per pixel -> O(1) network values
+
+
+def coarse_problem(seed: int, vox: float = 4.0):
+    """A seeded ellipsoid torso on the coarse scatter grid."""
+    return inputs.torso_problem(vox=vox, seed=seed, nu=W, nv=H, det_px=DET_PX,
+                                name=f"torso-seed{seed}-{vox:g}mm-coarse")
+
+
+def simulate(ctx, n: int, seed: int, angle: float, angle_index: int):
+    """MC scatter signal per source photon (device FP64 [H, W]) and counters."""
+    import torch
+    stats = torch.zeros(gdrr.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+    _, s = gdrr.gdrr_mc_project(ctx, n, seed, angle, angle_index, stats=stats)
+    return gdrr.gdrr_finalize(ctx, s, n), gdrr.stats_dict(stats)
+
+
+def denoise(ctx, s_hat, stats, n: int, length: float = 4.0, iters: int = 800):
+    """Poisson denoising (Eq. 5, omega = 0.8) on the count scale, with beta
+    set so that beta times the mean count is length^2: a smoothing length of
+    about `length` pixels at any photon count."""
+    n_det = max(1, stats["tally_scatter"])
+    total = float(s_hat.sum().item())
+    count_scale = total / n_det if total > 0 else 1.0 / n
+    mean_count = n_det / s_hat.numel()
+    beta = length * length / max(mean_count, 1e-6)
+    return gdrr.gdrr_denoise_scatter(ctx, s_hat, count_scale, beta, 0.8, iters)
+
+
+LOW_LENGTH = 12.0      # denoiser smoothing length (pixels) for the low-photon input
+HIGH_LENGTH = 2.0      # and for the high-photon targets and the judge
+
+
+def low_input(ctx, n_low: int, seed: int, angle: float, angle_index: int, x_slot):
+    """The network input for one projection: the plain method's low-photon
+    estimate (MC + Poisson denoising) and the ray-traced primary, scaled into
+    x_slot [2, H, W] FP32.  Returns the denoised low-photon estimate."""
+    P = gdrr.gdrr_raytrace_primary(ctx, angle)
+    s_low, st = simulate(ctx, n_low, seed, angle, angle_index)
+    d_low = denoise(ctx, s_low, st, n_low, LOW_LENGTH)
+    gdrr.gdrr_scale_to_f32(d_low, SCALE, x_slot[0])
+    gdrr.gdrr_scale_to_f32(P, SCALE, x_slot[1])
+    return d_low
+
+
+def make_dataset(seeds, angles_per_phantom: int, n_low: int, n_high: int, rng_seed: int = 0):
+    """Inputs X [N, 2, H, W] (denoised low-photon scatter, ray-traced primary)
+    and targets Y [N, 1, H, W] (denoised high-photon scatter), scaled by
+    SCALE, FP32; angles uniform over 360 degrees."""
+    import torch
+    rng = np.random.default_rng(rng_seed)
+    N = len(seeds) * angles_per_phantom
+    X = torch.empty((N, 2, H, W), dtype=torch.float32, device="cuda")
+    Y = torch.empty((N, 1, H, W), dtype=torch.float32, device="cuda")
+    k = 0
+    for s in seeds:
+        with gdrr.Context(coarse_problem(int(s))) as ctx:
+            for a in range(angles_per_phantom):
+                angle = float(rng.uniform(0.0, 2.0 * math.pi))
+                low_input(ctx, n_low, 1_000_003 + 7 * k, angle, a, X[k])
+                s_high, st = simulate(ctx, n_high, 2_000_029 + 11 * k, angle, a)
+                gdrr.gdrr_scale_to_f32(denoise(ctx, s_high, st, n_high, HIGH_LENGTH), SCALE, Y[k, 0])
+                k += 1
+    return X, Y
+
+
+def train(net, X, Y, steps: int, batch: int = 16, lr: float = 1e-3, log=None):
+    """Adam on consecutive batches of the (shuffled-by-construction) set,
+    learning rate halved at 1/2 and 3/4 of the run.  Returns the losses."""
+    N = X.shape[0]
+    losses = []
+    for step in range(steps):
+        i0 = (step * batch) % N
+        i1 = min(N, i0 + batch)
+        net.forward(X[i0:i1])
+        losses.append(net.backward(Y[i0:i1]))
+        f = 1.0 if step < steps // 2 else (0.5 if step < 3 * steps // 4 else 0.25)
+        net.adam_step(lr * f)
+        if log and step % max(1, steps // 10) == 0:
+            log(f"step {step} loss {losses[-1]:.5f}")
+    return losses
+
+
+def predict(net, X):
+    """Network scatter estimate per source photon, FP64 [N, H, W] on the device."""
+    import torch
+    out = net.forward(X)
+    S = torch.empty((X.shape[0], H, W), dtype=torch.float64, device="cuda")
+    gdrr.gdrr_scale_to_f64(out, 1.0 / SCALE, S)
+    return S
+
+
+def rel_l2(a, ref) -> float:
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
