@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-scan", action="store_true", help="skip the 64-angle batched-scan comparison")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1 mm / 4 mm voxel-size timings")
     ap.add_argument("--no-learned", action="store_true", help="skip training / evaluating the learned estimator")
+    ap.add_argument("--no-variants", action="store_true", help="skip the nearest-voxel / Siddon / filter timings")
     return ap.parse_args()
 
 
@@ -363,6 +364,37 @@ def run_ours(args):
                     "gather_roof_frac": (probe_v * 1e3) / ms_v}
             del pv
 
+    # the paper's speed variants (appendix): transport without density
+    # interpolation, and Siddon ray tracing, against the defaults
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for name, fn in (("rt_trilinear_ms", lambda: gdrr.gdrr_raytrace_primary(ctx, angle)),
+                         ("rt_siddon_ms", lambda: gdrr.gdrr_raytrace_primary_siddon(ctx, angle))):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            variants[name] = e0.elapsed_time(e1)
+        opts = gdrr.gdrr_get_options(ctx)
+        for name, kw in (("mc_nearest_voxel_ms", dict(nearest_voxel=1)),
+                         ("mc_first_order_compton_ms", dict(scatter_filter=1))):
+            gdrr.gdrr_set_options(ctx, **kw)
+            vp, vs = gdrr.gdrr_mc_project(ctx, n_hist, seed, angle)
+            torch.cuda.synchronize()
+            flush.fill_(2.0)
+            e0.record(stream)
+            gdrr.gdrr_mc_project(ctx, n_hist, seed, angle, prim=vp, scat=vs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            variants[name] = e0.elapsed_time(e1)
+            gdrr.gdrr_set_options(ctx, **opts)
+        variants["mc_trilinear_ms"] = statistics.mean(mc_ms)
+        del vp, vs
+
     # learned scatter estimator against the plain method: train on pairs the
     # method generates (32 torsos x 4 angles), evaluate on held-out torsos
     # against a denoised 1e9-history reference; per-projection cost of each
@@ -464,6 +496,7 @@ def run_ours(args):
         "e2e": e2e,
         "batched": batched,
         "voxel_sweep": voxel_sweep,
+        "variants": variants,
         "learned": learned,
         "autotuned": tuned,
         "gpu_launches": launches_per_step * args.steps,

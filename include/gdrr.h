@@ -119,6 +119,14 @@ typedef struct {
     int32_t batch_min;         /* lanes of a warp that must be waiting for an
                                   interaction, a tally or a new history before the
                                   warp serves them together, 1..32 [16]            */
+    int32_t nearest_voxel;     /* 1: no density interpolation, each point takes its
+                                  voxel's density and material (the speed variant of
+                                  the paper's appendix); 0: trilinear [0]           */
+    int32_t scatter_filter;    /* scattered photons the scatter counter takes
+                                  (Section 2.4): 0 all, 1 exactly one Compton and no
+                                  Rayleigh, 2 exactly one Rayleigh and no Compton,
+                                  3 two or more interactions; the others count as
+                                  missing the detector [0]                           */
 } gdrr_mc_options;
 
 /* Transport counters, accumulated by every gdrr_mc_project* call (device
@@ -175,6 +183,12 @@ GDRR_API int gdrr_sync(gdrr_ctx* ctx);
  * with the trilinear field.  P_dev: caller-owned device double[nv*nu],
  * overwritten, per source photon (keV). */
 GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_dev);
+
+/* Step 1 with Siddon's algorithm (the paper's faster alternative, Section
+ * 2.3 and appendix): exact path lengths through the piecewise-constant voxel
+ * field (each voxel's own density and material) along the ray to each pixel
+ * centre.  P_dev as for gdrr_raytrace_primary. */
+GDRR_API int gdrr_raytrace_primary_siddon(gdrr_ctx* ctx, double angle_rad, double* P_dev);
 
 /* Step 2, Section 2.4: transport n_photons source photons with Woodcock
  * tracking, photoelectric / Compton (Klein-Nishina) / Rayleigh (Thomson)

@@ -451,6 +451,108 @@ static double orc_interp_d(const double* t, double e0, double de, int n, double 
     return t[i] + f * (t[i + 1] - t[i]);
 }
 
+/* Siddon's algorithm (Siddon, Med. Phys. 12, 1985): the parametric values
+ * where the ray crosses the voxel planes x = lo + i dx (and y, z) inside the
+ * box, merged in increasing order; each consecutive pair bounds a segment
+ * inside one voxel, found from the segment midpoint; the radiological length
+ * is the sum of segment length times that voxel's mu. */
+static int orc_cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int orc_rt_primary_siddon(const orc_problem* p, double phi, const int32_t* pixels, int n_pixels, double* out) {
+    orc_ctx c;
+    if (orc_ctx_init(&c, p, phi)) { orc_ctx_free(&c); return -1; }
+    int npix_all = p->nu * p->nv;
+    if (!pixels) n_pixels = npix_all;
+    double* mu_e = (double*)malloc(sizeof(double) * (size_t)p->n_bins * p->n_mat);
+    double* wr = (double*)malloc(sizeof(double) * (size_t)p->n_bins);
+    double* tot = (double*)malloc(sizeof(double) * (size_t)p->n_e);
+    double* rsp = (double*)malloc(sizeof(double) * (size_t)p->n_r);
+    double wsum = 0.0, fsum = 0.0;
+    for (int b = 0; b < p->n_bins; ++b) wsum += p->bin_w[b];
+    for (int i = 0; i < p->n_r; ++i) rsp[i] = p->response[i];
+    for (int m = 0; m < p->n_mat; ++m) {
+        for (int e = 0; e < p->n_e; ++e) {
+            const float* t = p->mu_hat + (size_t)m * 3 * p->n_e;
+            tot[e] = 0.1 * ((double)t[e] + (double)t[p->n_e + e] + (double)t[2 * p->n_e + e]);
+        }
+        for (int b = 0; b < p->n_bins; ++b)
+            mu_e[(size_t)b * p->n_mat + m] = orc_interp_d(tot, p->e0, p->de, p->n_e, p->bin_e[b]);
+    }
+    for (int b = 0; b < p->n_bins; ++b)
+        wr[b] = (p->bin_w[b] / wsum) * orc_interp_d(rsp, p->r0, p->dr, p->n_r, p->bin_e[b]);
+    for (int i = 0; i < npix_all; ++i) fsum += p->fluence[i];
+    const int dims[3] = {p->nx, p->ny, p->nz};
+    const double vox[3] = {p->vx, p->vy, p->vz};
+    double* alpha = (double*)malloc(sizeof(double) * (size_t)(p->nx + p->ny + p->nz + 8));
+    double* seg_len = (double*)malloc(sizeof(double) * (size_t)(p->nx + p->ny + p->nz + 8));
+    int64_t* seg_vox = (int64_t*)malloc(sizeof(int64_t) * (size_t)(p->nx + p->ny + p->nz + 8));
+    for (int k = 0; k < n_pixels; ++k) {
+        int j = pixels ? pixels[k] : k;
+        int iu = j % p->nu, iv = j / p->nu;
+        double au = (iu + 0.5 - 0.5 * p->nu) * p->du, av = (iv + 0.5 - 0.5 * p->nv) * p->dv;
+        double S[3], d[3], L = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            S[a] = c.gd.S[a];
+            d[a] = c.gd.P[a] + au * c.gd.eu[a] + av * c.gd.ev[a] - S[a];
+            L += d[a] * d[a];
+        }
+        L = sqrt(L);
+        for (int a = 0; a < 3; ++a) d[a] /= L;
+        double tmin = 0.0, tmax = L;
+        int hit = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] != 0.0) {
+                double t1 = (c.gd.lo[a] - S[a]) / d[a], t2 = (c.gd.hi[a] - S[a]) / d[a];
+                if (t1 > t2) { double t = t1; t1 = t2; t2 = t; }
+                if (t1 > tmin) tmin = t1;
+                if (t2 < tmax) tmax = t2;
+            } else if (S[a] < c.gd.lo[a] || S[a] > c.gd.hi[a]) {
+                hit = 0;
+            }
+        }
+        int na = 0, nseg = 0;
+        if (hit && tmax > tmin) {
+            alpha[na++] = tmin;
+            alpha[na++] = tmax;
+            for (int a = 0; a < 3; ++a) {
+                if (d[a] == 0.0) continue;
+                for (int i = 0; i <= dims[a]; ++i) {
+                    double t = (c.gd.lo[a] + i * vox[a] - S[a]) / d[a];
+                    if (t > tmin && t < tmax) alpha[na++] = t;
+                }
+            }
+            qsort(alpha, (size_t)na, sizeof(double), orc_cmp_double);
+            for (int i = 0; i + 1 < na; ++i) {
+                double len = alpha[i + 1] - alpha[i];
+                if (len <= 0.0) continue;
+                double tm = 0.5 * (alpha[i] + alpha[i + 1]);
+                int64_t vi[3];
+                for (int a = 0; a < 3; ++a) {
+                    int g = (int)floor((S[a] + tm * d[a] - c.gd.lo[a]) / vox[a]);
+                    vi[a] = g < 0 ? 0 : (g > dims[a] - 1 ? dims[a] - 1 : g);
+                }
+                seg_len[nseg] = len;
+                seg_vox[nseg++] = vi[0] + (int64_t)p->nx * (vi[1] + (int64_t)p->ny * vi[2]);
+            }
+        }
+        double sig = 0.0;
+        for (int b = 0; b < p->n_bins; ++b) {
+            double rad = 0.0;
+            for (int s = 0; s < nseg; ++s)
+                rad += seg_len[s] * (double)p->density[seg_vox[s]] * mu_e[(size_t)b * p->n_mat + p->material[seg_vox[s]]];
+            sig += wr[b] * exp(-rad);
+        }
+        out[k] = (p->fluence[j] / fsum) * sig;
+    }
+    free(alpha); free(seg_len); free(seg_vox);
+    free(mu_e); free(wr); free(tot); free(rsp);
+    orc_ctx_free(&c);
+    return 0;
+}
+
 int orc_rt_primary(const orc_problem* p, double phi, const int32_t* pixels, int n_pixels, double* out) {
     orc_ctx c;
     if (orc_ctx_init(&c, p, phi)) { orc_ctx_free(&c); return -1; }

@@ -48,6 +48,10 @@ typedef struct {
     /* transport options */
     double e_cut;      /* photons below this energy are absorbed (keV) */
     int max_steps;     /* per-history free-flight limit */
+    int nearest_voxel; /* 0: trilinear density interpolation (Section 2.4); 1: the voxel's own value */
+    int scatter_filter;/* which scattered photons the scatter counter takes (Section 2.4 option):
+                          0 all, 1 exactly one Compton and no Rayleigh, 2 exactly one Rayleigh and no
+                          Compton, 3 two or more interactions; others count as missing the detector */
 } orc_problem;
 
 /* One record per history, for tiny-run event-by-event parity. */
@@ -98,6 +102,11 @@ int orc_mc_run(const orc_problem* p, double phi, uint32_t angle_index, uint64_t 
  * pixels when pixels == NULL).  out[i] is P at pixels[i] per source photon. */
 int orc_rt_primary(const orc_problem* p, double phi, const int32_t* pixels, int n_pixels,
                    double* out);
+
+/* Siddon ray-traced primary (Section 2.3's alternative; Siddon 1985), FP64:
+ * exact path lengths through the piecewise-constant voxel field, one trace
+ * per energy channel. */
+int orc_rt_primary_siddon(const orc_problem* p, double phi, const int32_t* pixels, int n_pixels, double* out);
 
 /* Derived tables, exposed for the pins. */
 int orc_majorant(const orc_problem* p, float* node_out /* n_e */);

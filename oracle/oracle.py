@@ -70,6 +70,7 @@ class _Problem(ctypes.Structure):
         ("n_r", ctypes.c_int), ("r0", ctypes.c_double), ("dr", ctypes.c_double),
         ("response", ctypes.c_void_p),
         ("e_cut", ctypes.c_double), ("max_steps", ctypes.c_int),
+        ("nearest_voxel", ctypes.c_int), ("scatter_filter", ctypes.c_int),
     ]
 
 
@@ -83,6 +84,8 @@ def lib():
         L.orc_mc_run.restype = i32
         L.orc_rt_primary.argtypes = [vp, ctypes.c_double, vp, i32, vp]
         L.orc_rt_primary.restype = i32
+        L.orc_rt_primary_siddon.argtypes = [vp, ctypes.c_double, vp, i32, vp]
+        L.orc_rt_primary_siddon.restype = i32
         L.orc_majorant.argtypes = [vp, vp]
         L.orc_majorant.restype = i32
         L.orc_logf.argtypes = [ctypes.c_float]
@@ -105,7 +108,7 @@ def _ptr(a):
 class _Marshalled:
     """Keeps the contiguous arrays alive while C reads them."""
 
-    def __init__(self, prob, e_cut=1.0, max_steps=100000):
+    def __init__(self, prob, e_cut=1.0, max_steps=100000, nearest_voxel=0, scatter_filter=0):
         self.material = np.ascontiguousarray(prob.material, np.uint8)
         self.density = np.ascontiguousarray(prob.density, np.float32)
         self.mu_hat = np.ascontiguousarray(prob.mu_hat, np.float32)
@@ -129,14 +132,17 @@ class _Marshalled:
         s.n_r, s.r0, s.dr = self.response.size, prob.r0, prob.dr
         s.response = _ptr(self.response).value
         s.e_cut, s.max_steps = e_cut, max_steps
+        s.nearest_voxel, s.scatter_filter = int(nearest_voxel), int(scatter_filter)
         self.struct = s
 
 
 def mc_run(prob, n_histories, seed=1, phi=0.0, angle_index=0, history_offset=0, precision=32,
-           threads=1, records=False, e_cut=1.0, max_steps=100000):
+           threads=1, records=False, e_cut=1.0, max_steps=100000, nearest_voxel=False, scatter_filter=0):
     """Monte Carlo projection (Section 2.4).  Returns (tally_p, tally_s, stats, records)
-    with int64 fixed-point tallies shaped [nv, nu]."""
-    m = _Marshalled(prob, e_cut, max_steps)
+    with int64 fixed-point tallies shaped [nv, nu].  nearest_voxel: no density
+    interpolation (the paper's speed variant); scatter_filter: 0 all scatter,
+    1 single Compton, 2 single Rayleigh, 3 multiple scatter."""
+    m = _Marshalled(prob, e_cut, max_steps, nearest_voxel, scatter_filter)
     tp = np.zeros((prob.nv, prob.nu), np.int64)
     ts = np.zeros((prob.nv, prob.nu), np.int64)
     st = np.zeros(N_STATS, np.uint64)
@@ -162,6 +168,22 @@ def rt_primary(prob, phi=0.0, pixels=None):
         rc = lib().orc_rt_primary(ctypes.byref(m.struct), phi, _ptr(px), px.size, _ptr(out))
     if rc:
         raise ValueError(f"oracle rt_primary rejected the problem (rc={rc})")
+    return out
+
+
+def rt_primary_siddon(prob, phi=0.0, pixels=None):
+    """Siddon ray-traced primary (exact voxel path lengths), FP64; per source photon."""
+    m = _Marshalled(prob)
+    if pixels is None:
+        out = np.zeros(prob.nv * prob.nu)
+        rc = lib().orc_rt_primary_siddon(ctypes.byref(m.struct), phi, None, 0, _ptr(out))
+        out = out.reshape(prob.nv, prob.nu)
+    else:
+        px = np.ascontiguousarray(pixels, np.int32)
+        out = np.zeros(px.size)
+        rc = lib().orc_rt_primary_siddon(ctypes.byref(m.struct), phi, _ptr(px), px.size, _ptr(out))
+    if rc:
+        raise ValueError(f"oracle rt_primary_siddon rejected the problem (rc={rc})")
     return out
 
 

@@ -383,6 +383,8 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
     if (n.hist_per_thread > 4096 || n.batch_min > 32 || n.blocks_per_sm < 0 || n.blocks_per_sm > 64)
         return GDRR_ERR_INVALID_ARG;
     if (!(n.e_cut_kev < 1e6)) return GDRR_ERR_INVALID_ARG;
+    if (n.nearest_voxel < 0 || n.nearest_voxel > 1 || n.scatter_filter < 0 || n.scatter_filter > 3)
+        return GDRR_ERR_INVALID_ARG;
     ctx->opt = n;
     return GDRR_OK;
 }
@@ -398,7 +400,7 @@ GDRR_API int gdrr_sync(gdrr_ctx* ctx) {
     return cuda_err(cudaStreamSynchronize(ctx->stream));
 }
 
-GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_dev) {
+static int raytrace(gdrr_ctx* ctx, double angle_rad, double* P_dev, bool siddon) {
     if (!ctx || !P_dev || !std::isfinite(angle_rad)) return GDRR_ERR_INVALID_ARG;
     if (!geometry_ok(ctx, angle_rad)) return GDRR_ERR_INVALID_ARG;
     RtParams p;
@@ -413,7 +415,15 @@ GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_de
     p.du = (float)ctx->geo.du_mm; p.dv = (float)ctx->geo.dv_mm;
     p.half_step = (float)(0.5 * std::min(ctx->vox[0], std::min(ctx->vox[1], ctx->vox[2])));
     p.f = make_frame(ctx->geo, angle_rad);
-    return cuda_err(launch_rt(p, P_dev, ctx->stream));
+    return cuda_err(siddon ? launch_rt_siddon(p, P_dev, ctx->stream) : launch_rt(p, P_dev, ctx->stream));
+}
+
+GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_dev) {
+    return raytrace(ctx, angle_rad, P_dev, false);
+}
+
+GDRR_API int gdrr_raytrace_primary_siddon(gdrr_ctx* ctx, double angle_rad, double* P_dev) {
+    return raytrace(ctx, angle_rad, P_dev, true);
 }
 
 static int launch_grid(const gdrr_ctx* ctx, uint64_t total, bool rec) {
@@ -475,6 +485,8 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     p.records = records_dev;
     p.chunk = 32 * ctx->opt.hist_per_thread;
     p.batch_min = ctx->opt.batch_min;
+    p.nearest_voxel = ctx->opt.nearest_voxel;
+    p.scatter_filter = ctx->opt.scatter_filter;
     const bool rec = records_dev != nullptr;
     return cuda_err(launch_mc(p, ctx->opt.block_size, launch_grid(ctx, total, rec), rec, ctx->stream));
 }
@@ -567,6 +579,8 @@ GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* ang
         p.records = nullptr;
         p.chunk = 32 * ctx->opt.hist_per_thread;
         p.batch_min = ctx->opt.batch_min;
+        p.nearest_voxel = ctx->opt.nearest_voxel;
+        p.scatter_filter = ctx->opt.scatter_filter;
         if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
         const size_t tally_bytes = (size_t)n_angles * ctx->geo.nu * ctx->geo.nv * sizeof(int64_t);

@@ -91,6 +91,8 @@ struct McParams {
     gdrr_history_record* records;  // NULL or [total]
     int chunk;                     // histories a warp claims at a time
     int batch_min;                 // waiting lanes that trigger a warp's service batch
+    int nearest_voxel;             // 1: each point takes its voxel's value (no interpolation)
+    int scatter_filter;            // 0 all scatter, 1 single Compton, 2 single Rayleigh, 3 multiple
 };
 
 // Ray-tracing parameters.
@@ -112,6 +114,7 @@ struct RtParams {
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s);
 int mc_occupancy_blocks(int n_mat, int block, bool records);
 cudaError_t launch_rt(const RtParams& p, double* out, cudaStream_t s);
+cudaError_t launch_rt_siddon(const RtParams& p, double* out, cudaStream_t s);
 cudaError_t launch_gather_probe(const McParams& p, uint64_t n_cells, int grid, unsigned int* sink, cudaStream_t s);
 cudaError_t launch_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist,
                                 int n_blocks, uint32_t* out, cudaStream_t s);

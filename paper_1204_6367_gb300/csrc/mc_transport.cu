@@ -226,12 +226,15 @@ enum : int { S_DEAD = 0, S_FLY = 1, S_RAY = 2, S_COMP = 3, S_ESC = 4 };
 // Block-shared counters (GDRR_NSTATS), flushed to the stats array at exit.
 __device__ __forceinline__ void count(unsigned long long* c, int k) { atomicAdd(c + k, 1ull); }
 
-template <int NM, bool REC>
+// GEN: the general kernel, which honours the nearest-voxel and scatter-filter
+// options; the default kernel (GEN = false) carries neither.
+template <int NM, bool REC, bool GEN>
 struct Lane {
     float px, py, pz, dx, dy, dz, e;
     float mumax, inv_mumax;
     int state, scattered, job;
     uint32_t nsteps;
+    uint32_t n_int;      // Compton interactions (low 16 bits) and Rayleigh (high 16 bits)
     Stream rs;
     // per-thread coefficient tables in shared memory: coef[k][m][tid],
     // k = 0 total, 1 Rayleigh, 2 Compton (photoelectric is the remainder)
@@ -303,7 +306,13 @@ struct Lane {
                 const float av = rel0 * J.f.ev[0] + rel1 * J.f.ev[1] + rel2 * J.f.ev[2];
                 const float fu = au * P.idu + P.hu;
                 const float fv = av * P.idv + P.hv;
-                if (fu >= 0.0f && fu < (float)P.nu && fv >= 0.0f && fv < (float)P.nv) {
+                bool take = true;            // scatter filter (Section 2.4)
+                if (GEN && scattered && P.scatter_filter) {
+                    const uint32_t nc = n_int & 0xffffu, nr = n_int >> 16;
+                    take = P.scatter_filter == 1 ? (nc == 1 && nr == 0)
+                         : (P.scatter_filter == 2 ? (nr == 1 && nc == 0) : (nc + nr >= 2));
+                }
+                if (take && fu >= 0.0f && fu < (float)P.nu && fv >= 0.0f && fv < (float)P.nv) {
                     pixel = (int)fv * P.nu + (int)fu;
                     const long long q = llrintf(response(P, e) * 16777216.0f);
                     int64_t* t = scattered ? J.tally_s : J.tally_p;
@@ -354,6 +363,7 @@ struct Lane {
         count(cnt, GDRR_ST_HISTORIES);
         nsteps = 0;
         scattered = 0;
+        if (GEN) n_int = 0;
         if (REC) { r_virt = 0; r_ray = 0; r_comp = 0; r_first = 0; r_dep = 0.0; }
 
         const uint4 w0 = rs.block(P.rk);
@@ -430,15 +440,36 @@ struct Lane {
         }
         px = qx; py = qy; pz = qz;
 
+        if (GEN && P.nearest_voxel) {
+            // no density interpolation: the voxel containing the point
+            const int gx = min(max((int)floorf((px - P.lo[0]) * P.ivox[0]), 0), P.nx - 1);
+            const int gy = min(max((int)floorf((py - P.lo[1]) * P.ivox[1]), 0), P.ny - 1);
+            const int gz = min(max((int)floorf((pz - P.lo[2]) * P.ivox[2]), 0), P.nz - 1);
+            const uint2 vx = __ldg(P.vox + brick_x(gx) + brick_y(gy, P.bsy) + brick_z(gz, P.bsz));
+            const float a0 = __uint_as_float(vx.x);
+            const int m0 = (int)vx.y;
+            const float t = uniform(wf.y) * mumax;
+            if (t > a0 * cf(0, m0)) {
+                ++c_virt;
+                if (REC) ++r_virt;
+                return;
+            }
+            const float muR = a0 * cf(1, m0), muC = a0 * cf(2, m0);
+            real_collision(P, t, muR, muC, cnt);
+            return;
+        }
+
         // trilinear corner weights (w_x w_y) w_z and clamped corner indices
         const float fx = (px - P.lo[0]) * P.ivox[0] - 0.5f;
         const float fy = (py - P.lo[1]) * P.ivox[1] - 0.5f;
         const float fz = (pz - P.lo[2]) * P.ivox[2] - 0.5f;
         const int gx = (int)floorf(fx), gy = (int)floorf(fy), gz = (int)floorf(fz);
         const float tx = fx - (float)gx, ty = fy - (float)gy, tz = fz - (float)gz;
-        const int x0 = min(max(gx, 0), P.nx - 1), x1 = min(max(gx + 1, 0), P.nx - 1);
-        const int y0 = min(max(gy, 0), P.ny - 1), y1 = min(max(gy + 1, 0), P.ny - 1);
-        const int z0 = min(max(gz, 0), P.nz - 1), z1 = min(max(gz + 1, 0), P.nz - 1);
+        // inside the box f lies in [-1/2, n - 1/2], so g in [-1, n - 1]: the
+        // lower corner clamps only from below, the upper only from above
+        const int x0 = max(gx, 0), x1 = min(gx + 1, P.nx - 1);
+        const int y0 = max(gy, 0), y1 = min(gy + 1, P.ny - 1);
+        const int z0 = max(gz, 0), z1 = min(gz + 1, P.nz - 1);
         const float wx0 = 1.0f - tx, wy0 = 1.0f - ty, wz0 = 1.0f - tz;
         const float wxy[4] = {wx0 * wy0, tx * wy0, wx0 * ty, tx * ty};
         const int bx[2] = {brick_x(x0), brick_x(x1)};
@@ -469,6 +500,13 @@ struct Lane {
         float muC = a[0] * cf(2, mc[0]);
 #pragma unroll
         for (int c = 1; c < 8; ++c) muC = muC + a[c] * cf(2, mc[c]);
+        real_collision(P, t, muR, muC, cnt);
+    }
+
+    // A real collision: Rayleigh if t <= mu_R, Compton if t <= mu_R + mu_C,
+    // else photoelectric absorption.
+    __device__ __forceinline__ void real_collision(const McParams& P, float t, float muR, float muC,
+                                                   unsigned long long* cnt) {
         if (t <= muR) {
             state = S_RAY;
         } else if (t <= muR + muC) {
@@ -489,6 +527,7 @@ struct Lane {
             azimuth(rs, P.rk, cp, sp);
             rotate(dx, dy, dz, ct, cp, sp);
             scattered = 1;
+            if (GEN) n_int += 0x10000u;
             count(cnt, GDRR_ST_RAYLEIGH);
             if (REC) { ++r_ray; if (!r_first) r_first = 1; }
             state = S_FLY;
@@ -499,6 +538,7 @@ struct Lane {
         azimuth(rs, P.rk, cp, sp);
         rotate(dx, dy, dz, ct, cp, sp);
         scattered = 1;
+        if (GEN) n_int += 1u;
         count(cnt, GDRR_ST_COMPTON);
         if (REC) { ++r_comp; if (!r_first) r_first = 2; r_dep += (double)e - (double)e2; }
         if (e2 < P.e_cut) {
@@ -514,7 +554,7 @@ struct Lane {
     }
 };
 
-template <int NM, bool REC>
+template <int NM, bool REC, bool GEN>
 __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams P) {
     extern __shared__ float smem[];
     __shared__ unsigned long long cnt[GDRR_NSTATS];
@@ -522,7 +562,7 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams P) {
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    Lane<NM, REC> L;
+    Lane<NM, REC, GEN> L;
     L.coef = smem + threadIdx.x;
     L.stride = blockDim.x;
     L.state = S_DEAD;
@@ -620,43 +660,45 @@ __global__ void stream_words_kernel(const RoundKeys rk, uint32_t angle_index, ui
 template <int NM>
 constexpr size_t smem_bytes(int block) { return (size_t)3 * NM * block * sizeof(float); }
 
-template <int NM, bool REC>
+template <int NM, bool REC, bool GEN>
 cudaError_t launch_t(const McParams& p, int block, int grid, cudaStream_t s) {
-    mc_kernel<NM, REC><<<grid, block, smem_bytes<NM>(block), s>>>(p);
+    mc_kernel<NM, REC, GEN><<<grid, block, smem_bytes<NM>(block), s>>>(p);
     return cudaGetLastError();
 }
 
-template <int NM, bool REC>
+template <int NM, bool REC, bool GEN>
 int occupancy_t(int block) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_kernel<NM, REC>, block, smem_bytes<NM>(block))
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_kernel<NM, REC, GEN>, block, smem_bytes<NM>(block))
         != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
+template <bool REC, bool GEN>
+cudaError_t launch_nm(const McParams& p, int block, int grid, cudaStream_t s) {
+    if (p.n_mat <= 2) return launch_t<2, REC, GEN>(p, block, grid, s);
+    if (p.n_mat <= 4) return launch_t<4, REC, GEN>(p, block, grid, s);
+    return launch_t<8, REC, GEN>(p, block, grid, s);
+}
+
+template <bool REC, bool GEN>
+int occupancy_nm(int n_mat, int block) {
+    if (n_mat <= 2) return occupancy_t<2, REC, GEN>(block);
+    if (n_mat <= 4) return occupancy_t<4, REC, GEN>(block);
+    return occupancy_t<8, REC, GEN>(block);
+}
+
 }  // namespace
 
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s) {
-    if (records) {
-        if (p.n_mat <= 2) return launch_t<2, true>(p, block, grid, s);
-        if (p.n_mat <= 4) return launch_t<4, true>(p, block, grid, s);
-        return launch_t<8, true>(p, block, grid, s);
-    }
-    if (p.n_mat <= 2) return launch_t<2, false>(p, block, grid, s);
-    if (p.n_mat <= 4) return launch_t<4, false>(p, block, grid, s);
-    return launch_t<8, false>(p, block, grid, s);
+    const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0;
+    if (records) return gen ? launch_nm<true, true>(p, block, grid, s) : launch_nm<true, false>(p, block, grid, s);
+    return gen ? launch_nm<false, true>(p, block, grid, s) : launch_nm<false, false>(p, block, grid, s);
 }
 
 int mc_occupancy_blocks(int n_mat, int block, bool records) {
-    if (records) {
-        if (n_mat <= 2) return occupancy_t<2, true>(block);
-        if (n_mat <= 4) return occupancy_t<4, true>(block);
-        return occupancy_t<8, true>(block);
-    }
-    if (n_mat <= 2) return occupancy_t<2, false>(block);
-    if (n_mat <= 4) return occupancy_t<4, false>(block);
-    return occupancy_t<8, false>(block);
+    return records ? occupancy_nm<true, false>(n_mat, block) : occupancy_nm<false, false>(n_mat, block);
 }
 
 cudaError_t launch_gather_probe(const McParams& p, uint64_t n_cells, int grid, unsigned int* sink, cudaStream_t s) {

@@ -67,7 +67,8 @@ class Detector(ctypes.Structure):
 class McOptions(ctypes.Structure):
     _fields_ = [("e_cut_kev", ctypes.c_double), ("max_steps", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("hist_per_thread", ctypes.c_int32),
-                ("batch_min", ctypes.c_int32)]
+                ("batch_min", ctypes.c_int32), ("nearest_voxel", ctypes.c_int32),
+                ("scatter_filter", ctypes.c_int32)]
 
 
 _lib = None
@@ -94,6 +95,7 @@ def lib():
             "gdrr_get_options": [vp, vp],
             "gdrr_sync": [vp],
             "gdrr_raytrace_primary": [vp, dbl, vp],
+            "gdrr_raytrace_primary_siddon": [vp, dbl, vp],
             "gdrr_mc_project": [vp, dbl, u32, u64, u64, u64, vp, vp, vp, vp],
             "gdrr_mc_project_batched": [vp, i32, vp, vp, u64, vp, vp, vp],
             "gdrr_finalize": [vp, vp, i64, u64, vp],
@@ -253,6 +255,16 @@ def gdrr_raytrace_primary(ctx: Context, angle_rad: float, out=None):
         out = torch.empty((ctx.nv, ctx.nu), dtype=torch.float64, device="cuda")
     _check("gdrr_raytrace_primary",
            lib().gdrr_raytrace_primary(ctx.handle, float(angle_rad), _dev_ptr(out, torch.float64, ctx.nu * ctx.nv, "P")))
+    return out
+
+
+def gdrr_raytrace_primary_siddon(ctx: Context, angle_rad: float, out=None):
+    import torch
+    if out is None:
+        out = torch.empty((ctx.nv, ctx.nu), dtype=torch.float64, device="cuda")
+    _check("gdrr_raytrace_primary_siddon",
+           lib().gdrr_raytrace_primary_siddon(ctx.handle, float(angle_rad),
+                                              _dev_ptr(out, torch.float64, ctx.nu * ctx.nv, "P")))
     return out
 
 

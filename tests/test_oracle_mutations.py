@@ -32,8 +32,8 @@ MUTATIONS = [
      "interaction channels mixed up", "test_oracle_transport.py"),
     ("mc_history.inc", "REAL s = -LOGR(xi_s) * inv_mumax;", "REAL s = -LOGR(xi_s) * (RC(1.1) * inv_mumax);",
      "free path scale", "test_oracle_transport.py"),
-    ("mc_history.inc", "for (int corner = 0; corner < 8; ++corner) muT = muT + a[corner] * cT[mc[corner]];",
-     "for (int corner = 0; corner < 8; ++corner) muT = a[corner] * cT[mc[corner]];",
+    ("mc_history.inc", "for (int corner = 0; corner < n_corner; ++corner) muT = muT + a[corner] * cT[mc[corner]];",
+     "for (int corner = 0; corner < n_corner; ++corner) muT = a[corner] * cT[mc[corner]];",
      "dropped corner terms", "test_oracle_transport.py"),
     ("mc_history.inc", "cT[m] = (cR[m] + cC[m]) + cP[m];", "cT[m] = cR[m] + cC[m];",
      "photoelectric missing from the total", "test_oracle_transport.py"),
