@@ -147,6 +147,7 @@ typedef struct {
     int dims[3];
     double* cdf_pix;
     double* cdf_e;
+    double* cdf_e_cols;   /* [nu][n_bins] when the spectrum depends on the column */
     orc_geo_f gf;
     orc_geo_d gd;
 } orc_ctx;
@@ -201,6 +202,15 @@ static int orc_ctx_init(orc_ctx* c, const orc_problem* p, double phi) {
     c->cdf_pix = orc_build_cdf(p->fluence, p->nu * p->nv);
     c->cdf_e = orc_build_cdf(p->bin_w, p->n_bins);
     if (!c->cdf_pix || !c->cdf_e) return -1;
+    if (p->bin_w_cols) {
+        c->cdf_e_cols = (double*)malloc(sizeof(double) * (size_t)p->nu * p->n_bins);
+        for (int u = 0; u < p->nu; ++u) {
+            double* col = orc_build_cdf(p->bin_w_cols + (size_t)u * p->n_bins, p->n_bins);
+            if (!col) return -1;
+            memcpy(c->cdf_e_cols + (size_t)u * p->n_bins, col, sizeof(double) * (size_t)p->n_bins);
+            free(col);
+        }
+    }
 
     /* geometry (Fig. 1): source at SAD on the -SO side, imager at AID = SDD - SAD
      * along OP, which makes angle theta with SO; v axis parallel to z. */
@@ -271,7 +281,7 @@ static int orc_ctx_init(orc_ctx* c, const orc_problem* p, double phi) {
 }
 
 static void orc_ctx_free(orc_ctx* c) {
-    free(c->cdf_pix); free(c->cdf_e);
+    free(c->cdf_pix); free(c->cdf_e); free(c->cdf_e_cols);
     free(c->gf.tab); free(c->gd.tab); free(c->gf.major); free(c->gd.major);
     free(c->gf.resp); free(c->gd.resp); free(c->gf.bin_e); free(c->gd.bin_e);
 }
@@ -483,6 +493,18 @@ int orc_rt_primary_siddon(const orc_problem* p, double phi, const int32_t* pixel
     }
     for (int b = 0; b < p->n_bins; ++b)
         wr[b] = (p->bin_w[b] / wsum) * orc_interp_d(rsp, p->r0, p->dr, p->n_r, p->bin_e[b]);
+    /* per-column spectra: channel weights phi_u(E) r(E) of each column */
+    double* wr_cols = NULL;
+    if (p->bin_w_cols) {
+        wr_cols = (double*)malloc(sizeof(double) * (size_t)p->nu * p->n_bins);
+        for (int u = 0; u < p->nu; ++u) {
+            const double* wc = p->bin_w_cols + (size_t)u * p->n_bins;
+            double cs = 0.0;
+            for (int b = 0; b < p->n_bins; ++b) cs += wc[b];
+            for (int b = 0; b < p->n_bins; ++b)
+                wr_cols[(size_t)u * p->n_bins + b] = (wc[b] / cs) * orc_interp_d(rsp, p->r0, p->dr, p->n_r, p->bin_e[b]);
+        }
+    }
     for (int i = 0; i < npix_all; ++i) fsum += p->fluence[i];
     const int dims[3] = {p->nx, p->ny, p->nz};
     const double vox[3] = {p->vx, p->vy, p->vz};
@@ -543,12 +565,12 @@ int orc_rt_primary_siddon(const orc_problem* p, double phi, const int32_t* pixel
             double rad = 0.0;
             for (int s = 0; s < nseg; ++s)
                 rad += seg_len[s] * (double)p->density[seg_vox[s]] * mu_e[(size_t)b * p->n_mat + p->material[seg_vox[s]]];
-            sig += wr[b] * exp(-rad);
+            sig += (wr_cols ? wr_cols[(size_t)iu * p->n_bins + b] : wr[b]) * exp(-rad);
         }
         out[k] = (p->fluence[j] / fsum) * sig;
     }
     free(alpha); free(seg_len); free(seg_vox);
-    free(mu_e); free(wr); free(tot); free(rsp);
+    free(mu_e); free(wr); free(wr_cols); free(tot); free(rsp);
     orc_ctx_free(&c);
     return 0;
 }
@@ -577,6 +599,18 @@ int orc_rt_primary(const orc_problem* p, double phi, const int32_t* pixels, int 
     }
     for (int b = 0; b < p->n_bins; ++b)
         wr[b] = (p->bin_w[b] / wsum) * orc_interp_d(rsp, p->r0, p->dr, p->n_r, p->bin_e[b]);
+    /* per-column spectra: channel weights phi_u(E) r(E) of each column */
+    double* wr_cols = NULL;
+    if (p->bin_w_cols) {
+        wr_cols = (double*)malloc(sizeof(double) * (size_t)p->nu * p->n_bins);
+        for (int u = 0; u < p->nu; ++u) {
+            const double* wc = p->bin_w_cols + (size_t)u * p->n_bins;
+            double cs = 0.0;
+            for (int b = 0; b < p->n_bins; ++b) cs += wc[b];
+            for (int b = 0; b < p->n_bins; ++b)
+                wr_cols[(size_t)u * p->n_bins + b] = (wc[b] / cs) * orc_interp_d(rsp, p->r0, p->dr, p->n_r, p->bin_e[b]);
+        }
+    }
     double fsum = 0.0;
     for (int i = 0; i < npix_all; ++i) fsum += p->fluence[i];
     double vmin = p->vx < p->vy ? p->vx : p->vy;
@@ -619,11 +653,11 @@ int orc_rt_primary(const orc_problem* p, double phi, const int32_t* pixels, int 
                 for (int a = 0; a < 3; ++a) x[a] = S[a] + tt * d[a];
                 rad += dl * orc_mu_at(&c, x, &mu_e[(size_t)b * p->n_mat]);
             }
-            sig += wr[b] * exp(-rad);
+            sig += (wr_cols ? wr_cols[(size_t)iu * p->n_bins + b] : wr[b]) * exp(-rad);
         }
         out[k] = (p->fluence[j] / fsum) * sig;
     }
-    free(mu_e); free(wr); free(tot); free(rsp);
+    free(mu_e); free(wr); free(wr_cols); free(tot); free(rsp);
     orc_ctx_free(&c);
     return 0;
 }

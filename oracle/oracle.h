@@ -35,10 +35,12 @@ typedef struct {
     int n_mat, n_e;
     double e0, de;
     const float* mu_hat;
-    /* source spectrum phi(E): bin energies and weights */
+    /* source spectrum phi(E): bin energies and weights; optionally one spectrum
+     * per detector column [nu][n_bins] (bowtie hardening), else NULL */
     int n_bins;
     const double* bin_e;
     const double* bin_w;
+    const double* bin_w_cols;
     /* fluence map w(u) after the bowtie, [nv][nu] */
     const double* fluence;
     /* detector response r(E) on r0 + i*dr */

@@ -66,6 +66,7 @@ class _Problem(ctypes.Structure):
         ("n_mat", ctypes.c_int), ("n_e", ctypes.c_int), ("e0", ctypes.c_double), ("de", ctypes.c_double),
         ("mu_hat", ctypes.c_void_p),
         ("n_bins", ctypes.c_int), ("bin_e", ctypes.c_void_p), ("bin_w", ctypes.c_void_p),
+        ("bin_w_cols", ctypes.c_void_p),
         ("fluence", ctypes.c_void_p),
         ("n_r", ctypes.c_int), ("r0", ctypes.c_double), ("dr", ctypes.c_double),
         ("response", ctypes.c_void_p),
@@ -116,6 +117,8 @@ class _Marshalled:
         self.spec_w = np.ascontiguousarray(prob.spec_w, np.float64)
         self.fluence = np.ascontiguousarray(prob.fluence, np.float64)
         self.response = np.ascontiguousarray(prob.response, np.float32)
+        cols = getattr(prob, "spec_cols", None)
+        self.spec_cols = None if cols is None else np.ascontiguousarray(cols, np.float64)
         nz, ny, nx = self.material.shape
         s = _Problem()
         s.sad, s.sdd, s.theta = prob.sad, prob.sdd, prob.theta
@@ -128,6 +131,7 @@ class _Marshalled:
         s.mu_hat = _ptr(self.mu_hat).value
         s.n_bins = self.spec_e.size
         s.bin_e, s.bin_w = _ptr(self.spec_e).value, _ptr(self.spec_w).value
+        s.bin_w_cols = None if self.spec_cols is None else _ptr(self.spec_cols).value
         s.fluence = _ptr(self.fluence).value
         s.n_r, s.r0, s.dr = self.response.size, prob.r0, prob.dr
         s.response = _ptr(self.response).value

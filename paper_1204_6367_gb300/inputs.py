@@ -103,6 +103,9 @@ class Problem:
     dr: float
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # optional per-detector-column spectra [nu, n_bins] (energy-dependent bowtie
+    # hardening); None keeps the separable phi(E) w(u) source of Section 2.1
+    spec_cols: np.ndarray | None = None
 
     @property
     def shape(self):
@@ -169,6 +172,19 @@ def fluence_map(nu, nv, du, dv, sdd, spec_e=None, spec_w=None, bowtie_mm=0.0):
         trans = (spec_w[None, None, :] * np.exp(-mu_al[None, None, :] * t_cm[..., None])).sum(-1)
         w = w * trans
     return w / w.sum()
+
+
+def bowtie_column_spectra(nu, du, sdd, spec_e, spec_w, bowtie_mm=30.0):
+    """Spectrum of each detector column behind the aluminium bowtie: the
+    primary spectrum times the transmission of that column's thickness
+    (0 at the centre, bowtie_mm at the edge, quadratic in fan angle).
+    Rows are the column spectra [nu, n_bins], not normalised."""
+    u = (np.arange(nu) + 0.5 - 0.5 * nu) * du
+    gamma = np.arctan(np.abs(u) / sdd)
+    gmax = math.atan(0.5 * nu * du / sdd)
+    t_cm = 0.1 * bowtie_mm * (gamma / gmax) ** 2
+    mu_al = mass_attenuation(ALUMINIUM, spec_e).sum(axis=0) * ALUMINIUM.nominal_density
+    return spec_w[None, :] * np.exp(-mu_al[None, :] * t_cm[:, None])
 
 
 def _voxel_centres(n, d):
@@ -245,7 +261,7 @@ def small_problem(n_vox=32, vox=4.0, n_det=64, det_px=4.0, energy=60.0, name="cy
 
 
 def torso_problem(vox=2.0, seed=1, kvp=120.0, nu=512, nv=384, det_px=0.776, bowtie_mm=30.0,
-                  name=None):
+                  name=None, hardened_bowtie=False):
     """Ellipsoid torso at ``vox`` mm (256x256x128 at 2 mm), 120 kVp Kramers
     spectrum with 2.5 mm Al, aluminium bowtie 0-30 mm, 512x384 detector of
     0.776 mm pixels, CsI-like response."""
@@ -261,7 +277,8 @@ def torso_problem(vox=2.0, seed=1, kvp=120.0, nu=512, nv=384, det_px=0.776, bowt
         spec_e=spec_e, spec_w=spec_w,
         fluence=fluence_map(nu, nv, det_px, det_px, sdd, spec_e, spec_w, bowtie_mm),
         response=response_table("csi"), r0=ENERGY_GRID[0], dr=ENERGY_GRID[1],
-        name=name or f"torso-{shape[2]}x{shape[1]}x{shape[0]}-{vox:g}mm")
+        name=name or f"torso-{shape[2]}x{shape[1]}x{shape[0]}-{vox:g}mm",
+        spec_cols=bowtie_column_spectra(nu, det_px, sdd, spec_e, spec_w, bowtie_mm) if hardened_bowtie else None)
 
 
 def uniform_slab_problem(nx=16, ny=16, nz=16, vox=2.0, mat_id=1, density=1.0, energy=60.0,

@@ -300,3 +300,27 @@ def test_autotune_keeps_results(gd, small):
         got = gd.gdrr_mc_project(ctx, 150_000, 8)
         gd.gdrr_sync(ctx)
         assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])
+
+
+def test_anisotropic_voxels_and_rotated_imager(gd):
+    # voxels of 2 x 3 x 2.5 mm, imager turned by theta = 0.2 rad off the
+    # source-opposite position, gantry at 0.8 rad
+    prob = inputs.uniform_slab_problem(mat_id=1, density=1.0, nx=20, ny=14, nz=12, nu=40, nv=30, det_px=2.0,
+                                       pencil=False)
+    prob.voxel = (2.0, 3.0, 2.5)
+    prob.theta = 0.2
+    rng = np.random.default_rng(8)
+    prob.material[:] = rng.integers(0, 3, prob.material.shape).astype(np.uint8)
+    prob.density[:] = rng.uniform(0.05, 2.0, prob.density.shape).astype(np.float32)
+    tp, ts, st, _ = _run_gpu(gd, prob, 300_000, seed=19, phi=0.8, angle_index=3)
+    otp, ots, ost, _ = oracle.mc_run(prob, 300_000, seed=19, phi=0.8, angle_index=3, threads=NTH)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
+    with gd.Context(prob) as ctx:
+        P = gd.gdrr_raytrace_primary(ctx, 0.8).cpu().numpy()
+        Ps = gd.gdrr_raytrace_primary_siddon(ctx, 0.8).cpu().numpy()
+    ref = oracle.rt_primary(prob, phi=0.8)
+    refs = oracle.rt_primary_siddon(prob, phi=0.8)
+    np.testing.assert_allclose(P, ref, rtol=RT_RTOL, atol=1e-12 * ref.max())
+    np.testing.assert_allclose(Ps, refs, rtol=RT_RTOL, atol=1e-12 * refs.max())

@@ -59,6 +59,11 @@ MUTATIONS = [
      "ray-tracing interval length", "test_oracle_rt.py"),
     ("gdrr_oracle.c", "double tt = tmin + (s + 0.5) * dl, x[3];", "double tt = tmin + s * dl, x[3];",
      "interval end point instead of midpoint", "test_oracle_rt.py"),
+    ("mc_history.inc", "c->cdf_e_cols + (size_t)iu * p->n_bins", "c->cdf_e_cols + (size_t)iv * p->n_bins",
+     "column spectrum indexed by the detector row", "test_oracle_bowtie.py"),
+    ("gdrr_oracle.c", "double* col = orc_build_cdf(p->bin_w_cols + (size_t)u * p->n_bins, p->n_bins);",
+     "double* col = orc_build_cdf(p->bin_w, p->n_bins);",
+     "column spectra ignored by the energy sampler", "test_oracle_bowtie.py"),
     ("oracle.py", "sigma - (1.0 / beta) * (1.0 - s_hat / s)", "sigma - (1.0 / beta) * (1.0 - s / s_hat)",
      "denoiser fidelity term", "test_oracle_image.py"),
     ("oracle.py", "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[:-2, 1:-1]\n        s = ",
