@@ -87,11 +87,18 @@ typedef struct {
 } gdrr_materials;
 
 /* Source spectrum phi(E) after the bowtie, Section 2.1: n_bins energy
- * channels (keV) and non-negative weights (normalised by the library). */
+ * channels (keV) and non-negative weights (normalised by the library).
+ * column_weight (host, may be NULL) makes the spectrum depend on the detector
+ * column, as behind a bowtie that hardens the beam off axis: [nu][n_bins]
+ * non-negative weights, each column normalised by the library and each with a
+ * positive sum; the photon heading for pixel (iu, iv) then draws its energy
+ * from column iu, and the ray tracer weights pixel (iu, iv) by that column's
+ * spectrum.  With NULL, weight serves every column (the separable source). */
 typedef struct {
     int32_t n_bins;
     const double* energy_kev;
     const double* weight;
+    const double* column_weight;
 } gdrr_spectrum;
 
 /* Photon fluence map w(u) after the bowtie, Section 2.1: the probability of

@@ -41,6 +41,8 @@ struct gdrr_ctx {
     double* d_wnorm = nullptr;
     float* d_mu_rt = nullptr;
     float* d_wr = nullptr;
+    float* d_wr_cols = nullptr;   // [nu][n_bins] with per-column spectra, else NULL
+    int e_col = 0;                // 1: energy CDFs hold one row per detector column
     int n_guide_pix = 0, n_guide_e = 0;
     // scratch owned by the context
     unsigned long long* d_counter = nullptr;
@@ -201,7 +203,7 @@ int free_ctx(gdrr_ctx* c) {
     if (!c) return GDRR_OK;
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->d_vox, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_kcdf_pix,
-                    c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr,
+                    c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr, c->d_wr_cols,
                     c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise, c->d_tune};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -268,6 +270,16 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
     std::vector<double> cdf_pix = build_cdf(bowtie->fluence, npix);
     std::vector<double> cdf_e = build_cdf(sp.weight, sp.n_bins);
     if (cdf_pix.empty() || cdf_e.empty()) return GDRR_ERR_INVALID_ARG;
+    // per-column spectra (energy-dependent bowtie): one CDF row per column
+    const bool e_col = sp.column_weight != nullptr;
+    std::vector<std::vector<double>> cdf_cols;
+    if (e_col) {
+        cdf_cols.resize(g.nu);
+        for (int u = 0; u < g.nu; ++u) {
+            cdf_cols[u] = build_cdf(sp.column_weight + (size_t)u * sp.n_bins, sp.n_bins);
+            if (cdf_cols[u].empty()) return GDRR_ERR_INVALID_ARG;
+        }
+    }
 
     gdrr_ctx* c = new (std::nothrow) gdrr_ctx();
     if (!c) return GDRR_ERR_OOM;
@@ -311,7 +323,20 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         c->n_guide_pix = npix;
         c->n_guide_e = std::max(sp.n_bins, 16);
         std::vector<int> guide_pix = build_guide(cdf_pix, c->n_guide_pix);
-        std::vector<int> guide_e = build_guide(cdf_e, c->n_guide_e);
+        std::vector<int> guide_e;
+        std::vector<uint32_t> kcdf_e;
+        if (e_col) {
+            for (int u = 0; u < g.nu; ++u) {
+                const std::vector<int> gu = build_guide(cdf_cols[u], c->n_guide_e);
+                const std::vector<uint32_t> ku = kcdf_of(cdf_cols[u]);
+                guide_e.insert(guide_e.end(), gu.begin(), gu.end());
+                kcdf_e.insert(kcdf_e.end(), ku.begin(), ku.end());
+            }
+        } else {
+            guide_e = build_guide(cdf_e, c->n_guide_e);
+            kcdf_e = kcdf_of(cdf_e);
+        }
+        c->e_col = e_col ? 1 : 0;
         // ray-tracing channel tables: total mu_hat per material at each
         // channel energy (FP64 interpolation), and phi_b r(E_b)
         std::vector<float> mu_rt((size_t)sp.n_bins * mt.n_materials);
@@ -329,6 +354,18 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         }
         for (int b = 0; b < sp.n_bins; ++b)
             wr[b] = (float)((sp.weight[b] / wsum) * interp_d(rsp, dt.e0_kev, dt.de_kev, sp.energy_kev[b]));
+        std::vector<float> wr_cols;
+        if (e_col) {
+            wr_cols.resize((size_t)g.nu * sp.n_bins);
+            for (int u = 0; u < g.nu; ++u) {
+                const double* wc = sp.column_weight + (size_t)u * sp.n_bins;
+                double cs = 0.0;
+                for (int b = 0; b < sp.n_bins; ++b) cs += wc[b];
+                for (int b = 0; b < sp.n_bins; ++b)
+                    wr_cols[(size_t)u * sp.n_bins + b] =
+                        (float)((wc[b] / cs) * interp_d(rsp, dt.e0_kev, dt.de_kev, sp.energy_kev[b]));
+            }
+        }
         double fsum = 0.0;
         for (int i = 0; i < npix; ++i) fsum += bowtie->fluence[i];
         std::vector<double> wnorm(npix);
@@ -354,7 +391,7 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         if ((rc = upload(&c->d_major, major.data(), major.size(), s))) break;
         if ((rc = upload(&c->d_resp, dt.response, (size_t)dt.n_energies, s))) break;
         if ((rc = upload(&c->d_bin_e, bin_e.data(), bin_e.size(), s))) break;
-        const std::vector<uint32_t> kcdf_pix = kcdf_of(cdf_pix), kcdf_e = kcdf_of(cdf_e);
+        const std::vector<uint32_t> kcdf_pix = kcdf_of(cdf_pix);
         if ((rc = upload(&c->d_kcdf_pix, kcdf_pix.data(), kcdf_pix.size(), s))) break;
         if ((rc = upload(&c->d_guide_pix, guide_pix.data(), guide_pix.size(), s))) break;
         if ((rc = upload(&c->d_kcdf_e, kcdf_e.data(), kcdf_e.size(), s))) break;
@@ -362,6 +399,7 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         if ((rc = upload(&c->d_wnorm, wnorm.data(), wnorm.size(), s))) break;
         if ((rc = upload(&c->d_mu_rt, mu_rt.data(), mu_rt.size(), s))) break;
         if ((rc = upload(&c->d_wr, wr.data(), wr.size(), s))) break;
+        if (e_col && (rc = upload(&c->d_wr_cols, wr_cols.data(), wr_cols.size(), s))) break;
         if ((rc = cuda_err(cudaMalloc((void**)&c->d_counter, sizeof(unsigned long long))))) break;
         if ((rc = cuda_err(cudaMalloc((void**)&c->d_stats, GDRR_NSTATS * sizeof(unsigned long long))))) break;
         if ((rc = cuda_err(cudaMalloc((void**)&c->d_flag, sizeof(int))))) break;
@@ -409,7 +447,7 @@ static int raytrace(gdrr_ctx* ctx, double angle_rad, double* P_dev, bool siddon)
     p.vox = ctx->d_vox;
     p.bsy = ctx->bsy; p.bsz = ctx->bsz;
     p.n_mat = ctx->n_mat; p.n_bins = ctx->n_bins;
-    p.mu_rt = ctx->d_mu_rt; p.wr = ctx->d_wr; p.wnorm = ctx->d_wnorm;
+    p.mu_rt = ctx->d_mu_rt; p.wr = ctx->d_wr; p.wr_cols = ctx->d_wr_cols; p.wnorm = ctx->d_wnorm;
     p.nu = ctx->geo.nu; p.nv = ctx->geo.nv;
     p.hu = (float)(0.5 * ctx->geo.nu); p.hv = (float)(0.5 * ctx->geo.nv);
     p.du = (float)ctx->geo.du_mm; p.dv = (float)ctx->geo.dv_mm;
@@ -450,7 +488,7 @@ static McParams static_mc_params(const gdrr_ctx* ctx) {
     p.npix = ctx->geo.nu * ctx->geo.nv; p.n_guide_pix = ctx->n_guide_pix;
     p.kcdf_pix = ctx->d_kcdf_pix; p.guide_pix = ctx->d_guide_pix;
     p.n_bins = ctx->n_bins; p.n_guide_e = ctx->n_guide_e;
-    p.kcdf_e = ctx->d_kcdf_e; p.guide_e = ctx->d_guide_e; p.bin_e = ctx->d_bin_e;
+    p.kcdf_e = ctx->d_kcdf_e; p.guide_e = ctx->d_guide_e; p.e_col = ctx->e_col; p.bin_e = ctx->d_bin_e;
     p.nu = ctx->geo.nu; p.nv = ctx->geo.nv;
     p.hu = (float)(0.5 * ctx->geo.nu); p.hv = (float)(0.5 * ctx->geo.nv);
     p.du = (float)ctx->geo.du_mm; p.dv = (float)ctx->geo.dv_mm;

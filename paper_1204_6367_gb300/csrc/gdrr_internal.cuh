@@ -72,8 +72,9 @@ struct McParams {
     const uint32_t* kcdf_pix;      // floor(cdf * 2^24): integer thresholds of the inverse CDF
     const int* guide_pix;
     int n_bins, n_guide_e;
-    const uint32_t* kcdf_e;
-    const int* guide_e;
+    const uint32_t* kcdf_e;        // [n_bins], or [nu][n_bins] with per-column spectra
+    const int* guide_e;            // [n_guide_e], or [nu][n_guide_e]
+    int e_col;                     // 1: the energy tables hold one row per detector column
     const float* bin_e;
     // detector grid
     int nu, nv;
@@ -104,6 +105,7 @@ struct RtParams {
     int n_mat, n_bins;
     const float* mu_rt;     // [n_bins][n_mat] total mu_hat at the channel energy, mm^-1 per g/cm^3
     const float* wr;        // [n_bins] phi_b r(E_b), phi normalised
+    const float* wr_cols;   // NULL, or [nu][n_bins] per-column phi_b r(E_b)
     const double* wnorm;    // [npix] normalised fluence
     int nu, nv;
     float hu, hv, du, dv;

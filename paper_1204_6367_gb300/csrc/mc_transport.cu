@@ -371,7 +371,8 @@ struct Lane {
         const float xi_v = uniform(w0.z);
         const int j = cdf_search(P.kcdf_pix, P.guide_pix, P.n_guide_pix, w0.x);
         const int iu = j % P.nu, iv = j / P.nu;
-        const int eb = cdf_search(P.kcdf_e, P.guide_e, P.n_guide_e, w0.w);
+        const int ecol = P.e_col ? iu : 0;   // per-column spectrum row (energy-dependent bowtie)
+        const int eb = cdf_search(P.kcdf_e + ecol * P.n_bins, P.guide_e + ecol * P.n_guide_e, P.n_guide_e, w0.w);
         const float en = __ldg(P.bin_e + eb);
         if (REC) r_esrc = en;
         const float a_u = ((float)iu + xi_u - P.hu) * P.du;

@@ -107,12 +107,14 @@ __global__ void __launch_bounds__(128) rt_kernel(const RtParams P, double* __res
 #pragma unroll
         for (int m = 0; m < NM; ++m) ell[m] *= dl;
     }
+    // channel weights: the shared separable spectrum, or this column's own
+    const float* wcol = P.wr_cols ? P.wr_cols + (size_t)iu * P.n_bins : nullptr;
     float sig = 0.0f;
     for (int b = 0; b < P.n_bins; ++b) {
         float rad = 0.0f;
 #pragma unroll
         for (int m = 0; m < NM; ++m) rad += s_mu[b * NM + m] * ell[m];
-        sig += s_wr[b] * expf(-rad);
+        sig += (wcol ? __ldg(wcol + b) : s_wr[b]) * expf(-rad);
     }
     out[j] = P.wnorm[j] * (double)sig;
 }
@@ -207,12 +209,14 @@ __global__ void __launch_bounds__(128) rt_siddon_kernel(const RtParams P, double
             if (idx[ax] < 0 || idx[ax] >= dims[ax]) break;
         }
     }
+    // channel weights: the shared separable spectrum, or this column's own
+    const float* wcol = P.wr_cols ? P.wr_cols + (size_t)iu * P.n_bins : nullptr;
     float sig = 0.0f;
     for (int b = 0; b < P.n_bins; ++b) {
         float rad = 0.0f;
 #pragma unroll
         for (int m = 0; m < NM; ++m) rad += s_mu[b * NM + m] * ell[m];
-        sig += s_wr[b] * expf(-rad);
+        sig += (wcol ? __ldg(wcol + b) : s_wr[b]) * expf(-rad);
     }
     out[j] = P.wnorm[j] * (double)sig;
 }

@@ -52,7 +52,8 @@ class Materials(ctypes.Structure):
 
 
 class Spectrum(ctypes.Structure):
-    _fields_ = [("n_bins", ctypes.c_int32), ("energy_kev", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+    _fields_ = [("n_bins", ctypes.c_int32), ("energy_kev", ctypes.c_void_p), ("weight", ctypes.c_void_p),
+                ("column_weight", ctypes.c_void_p)]
 
 
 class Bowtie(ctypes.Structure):
@@ -185,7 +186,13 @@ class Context:
         ph = Phantom(nx, ny, nz, prob.voxel[0], prob.voxel[1], prob.voxel[2],
                      _np_ptr(keep["material"]), _np_ptr(keep["density"]))
         mt = Materials(keep["mu_hat"].shape[0], keep["mu_hat"].shape[2], prob.e0, prob.de, _np_ptr(keep["mu_hat"]))
-        sp = Spectrum(keep["spec_e"].size, _np_ptr(keep["spec_e"]), _np_ptr(keep["spec_w"]))
+        cols = getattr(prob, "spec_cols", None)
+        if cols is not None:
+            keep["spec_cols"] = np.ascontiguousarray(cols, np.float64)
+            if keep["spec_cols"].shape != (self.nu, keep["spec_e"].size):
+                raise ValueError("spec_cols must be [nu, n_bins]")
+        sp = Spectrum(keep["spec_e"].size, _np_ptr(keep["spec_e"]), _np_ptr(keep["spec_w"]),
+                      _np_ptr(keep["spec_cols"]) if cols is not None else None)
         bt = Bowtie(_np_ptr(keep["fluence"]))
         dt = Detector(keep["response"].size, prob.r0, prob.dr, _np_ptr(keep["response"]))
         handle = ctypes.c_void_p()

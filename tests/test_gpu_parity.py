@@ -324,3 +324,41 @@ def test_anisotropic_voxels_and_rotated_imager(gd):
     refs = oracle.rt_primary_siddon(prob, phi=0.8)
     np.testing.assert_allclose(P, ref, rtol=RT_RTOL, atol=1e-12 * ref.max())
     np.testing.assert_allclose(Ps, refs, rtol=RT_RTOL, atol=1e-12 * refs.max())
+
+
+def test_hardened_bowtie_columns(gd):
+    # per-column spectra behind an aluminium bowtie: the source energy depends
+    # on the detector column the photon heads for
+    prob = inputs.torso_problem(vox=8.0, seed=3, kvp=120.0, nu=64, nv=48, det_px=6.208, hardened_bowtie=True)
+    assert prob.spec_cols is not None
+    tp, ts, st, _ = _run_gpu(gd, prob, 400_000, seed=31, phi=1.1, angle_index=2)
+    otp, ots, ost, _ = oracle.mc_run(prob, 400_000, seed=31, phi=1.1, angle_index=2, threads=NTH)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
+    with gd.Context(prob) as ctx:
+        P = gd.gdrr_raytrace_primary(ctx, 1.1).cpu().numpy()
+        Ps = gd.gdrr_raytrace_primary_siddon(ctx, 1.1).cpu().numpy()
+    ref = oracle.rt_primary(prob, phi=1.1)
+    refs = oracle.rt_primary_siddon(prob, phi=1.1)
+    np.testing.assert_allclose(P, ref, rtol=RT_RTOL, atol=1e-12 * ref.max())
+    np.testing.assert_allclose(Ps, refs, rtol=RT_RTOL, atol=1e-12 * refs.max())
+
+
+def test_single_bin_columns_event_by_event(gd):
+    # one energy per column: every record's source energy is fixed by its column
+    prob = inputs.uniform_slab_problem(mat_id=1, density=1.0, nx=16, ny=16, nz=8, nu=24, nv=6, det_px=1.2,
+                                       pencil=False)
+    e, _ = inputs.kramers_spectrum(kvp=100.0, bin_kev=5.0)
+    prob.spec_e, prob.spec_w = e, np.ones(e.size) / e.size
+    cols = np.zeros((prob.nu, e.size))
+    cols[np.arange(prob.nu), (np.arange(prob.nu) * 5) % e.size] = 1.0
+    prob.spec_cols = cols
+    n = 5000
+    tp, ts, st, rec = _run_gpu(gd, prob, n, seed=4, records=True)
+    otp, ots, ost, orec = oracle.mc_run(prob, n, seed=4, records=True)
+    for f in oracle.RECORD_DTYPE.names:
+        np.testing.assert_array_equal(rec[f], orec[f], err_msg=f)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
