@@ -137,7 +137,11 @@ static int orc_cdf_search(const double* cdf, int n, double xi) {
     T* tab;   /* [m][k][e] mm^-1 per g/cm^3 */                                \
     T* major; /* [e] majorant node values, mm^-1 */                           \
     T* resp;  /* [n_r] keV */                                                 \
-    T* bin_e; /* [n_bins] keV */
+    T* bin_e; /* [n_bins] keV */                                              \
+    T* ff_s;  /* [n_ff] squared momentum transfer x_j^2, 1/Angstrom^2 */       \
+    T* ff_a;  /* [m][n_ff] cumulative of F^2 over x^2 (trapezoid) */           \
+    T* ff_g;  /* [m][n_ff] F^2 on the nodes */                                 \
+    T inv_hc, ff_idx;  /* 1/(hc) in 1/(keV Angstrom); 1/ff_dx */
 
 typedef struct { GEO_FIELDS(float) } orc_geo_f;
 typedef struct { GEO_FIELDS(double) } orc_geo_d;
@@ -277,6 +281,52 @@ static int orc_ctx_init(orc_ctx* c, const orc_problem* p, double phi) {
     c->gf.bin_e = (float*)malloc(sizeof(float) * (size_t)p->n_bins);
     c->gd.bin_e = (double*)malloc(sizeof(double) * (size_t)p->n_bins);
     for (int i = 0; i < p->n_bins; ++i) { c->gf.bin_e[i] = (float)p->bin_e[i]; c->gd.bin_e[i] = p->bin_e[i]; }
+
+    /* Rayleigh form factors: the polar angle follows (1 + cos^2) F^2(x) with
+     * x = sin(theta/2) E / (hc), i.e. x^2 = x_max^2 (1 - cos) / 2; x^2 is drawn
+     * from F^2 taken linear in x^2 between the table's nodes (its cumulative
+     * A(x^2) is the trapezoid sum, quadratic within an interval) and accepted
+     * with (1 + cos^2) / 2.  The grid must reach x_max of the table's largest
+     * energy; F(0) > 0. */
+    if (p->rayleigh_ff) {
+        const double hc = 12.398419843320026;   /* keV Angstrom (CODATA 2018) */
+        if (!p->ff || p->n_ff < 2 || !(p->ff_dx > 0.0)) return -1;
+        double e_max = p->e0 + (double)(p->n_e - 1) * p->de;
+        if ((double)(p->n_ff - 1) * p->ff_dx < e_max / hc) return -1;
+        size_t nf = (size_t)p->n_ff;
+        c->gf.ff_s = (float*)malloc(sizeof(float) * nf);
+        c->gd.ff_s = (double*)malloc(sizeof(double) * nf);
+        c->gf.ff_a = (float*)malloc(sizeof(float) * nf * (size_t)p->n_mat);
+        c->gd.ff_a = (double*)malloc(sizeof(double) * nf * (size_t)p->n_mat);
+        c->gf.ff_g = (float*)malloc(sizeof(float) * nf * (size_t)p->n_mat);
+        c->gd.ff_g = (double*)malloc(sizeof(double) * nf * (size_t)p->n_mat);
+        for (int j = 0; j < p->n_ff; ++j) {
+            double x = (double)j * p->ff_dx;
+            c->gd.ff_s[j] = x * x;
+            c->gf.ff_s[j] = (float)(x * x);
+        }
+        for (int m = 0; m < p->n_mat; ++m) {
+            const float* F = p->ff + (size_t)m * nf;
+            if (!(F[0] > 0.0f)) return -1;
+            double acc = 0.0;
+            for (int j = 0; j < p->n_ff; ++j) {
+                if (!(F[j] >= 0.0f) || !isfinite(F[j])) return -1;
+                if (j > 0) {
+                    double f0 = (double)F[j - 1], f1 = (double)F[j];
+                    acc += 0.5 * (f0 * f0 + f1 * f1) * (c->gd.ff_s[j] - c->gd.ff_s[j - 1]);
+                }
+                c->gd.ff_a[(size_t)m * nf + j] = acc;
+                c->gf.ff_a[(size_t)m * nf + j] = (float)acc;
+                double g = (double)F[j] * (double)F[j];
+                c->gd.ff_g[(size_t)m * nf + j] = g;
+                c->gf.ff_g[(size_t)m * nf + j] = (float)g;
+            }
+        }
+        c->gd.inv_hc = 1.0 / hc;
+        c->gf.inv_hc = (float)(1.0 / hc);
+        c->gd.ff_idx = 1.0 / p->ff_dx;
+        c->gf.ff_idx = (float)(1.0 / p->ff_dx);
+    }
     return 0;
 }
 
@@ -284,6 +334,8 @@ static void orc_ctx_free(orc_ctx* c) {
     free(c->cdf_pix); free(c->cdf_e); free(c->cdf_e_cols);
     free(c->gf.tab); free(c->gd.tab); free(c->gf.major); free(c->gd.major);
     free(c->gf.resp); free(c->gd.resp); free(c->gf.bin_e); free(c->gd.bin_e);
+    free(c->gf.ff_s); free(c->gd.ff_s); free(c->gf.ff_a); free(c->gd.ff_a);
+    free(c->gf.ff_g); free(c->gd.ff_g);
 }
 
 int orc_majorant(const orc_problem* p, float* node_out) {
@@ -344,6 +396,19 @@ void orc_sample_rayleigh(uint64_t seed, int n, float* cos_out) {
         orc_stream_init(&s, seed, 0, (uint64_t)i);
         cos_out[i] = rayleigh_f32(&s);
     }
+}
+
+int orc_sample_rayleigh_ff(const orc_problem* p, float e_kev, int material, uint64_t seed, int n,
+                           float* cos_out) {
+    orc_ctx c;
+    if (!p->rayleigh_ff || material < 0 || material >= p->n_mat || orc_ctx_init(&c, p, 0.0)) return -1;
+    for (int i = 0; i < n; ++i) {
+        orc_stream s;
+        orc_stream_init(&s, seed, 0, (uint64_t)i);
+        cos_out[i] = rayleigh_ff_f32(&c, &s, e_kev, material);
+    }
+    orc_ctx_free(&c);
+    return 0;
 }
 
 void orc_sample_azimuth(uint64_t seed, int n, float* cos_out, float* sin_out) {

@@ -54,6 +54,13 @@ typedef struct {
     int scatter_filter;/* which scattered photons the scatter counter takes (Section 2.4 option):
                           0 all, 1 exactly one Compton and no Rayleigh, 2 exactly one Rayleigh and no
                           Compton, 3 two or more interactions; others count as missing the detector */
+    /* Rayleigh angular law: 0 Thomson (1 + cos^2); 1 (1 + cos^2) F^2(x) with the
+     * form factor F(x, i) of each material on x_j = j * ff_dx (1/Angstrom,
+     * x = sin(theta/2) / lambda), [n_mat][n_ff] */
+    int rayleigh_ff;
+    int n_ff;
+    double ff_dx;
+    const float* ff;
 } orc_problem;
 
 /* One record per history, for tiny-run event-by-event parity. */
@@ -62,7 +69,7 @@ typedef struct {
     uint32_t n_photo, outcome, rng_blocks, first_interaction;
     int32_t pixel;
     float e_source, e_final;
-    uint32_t pad;
+    uint32_t ray_material;   /* material of the last form-factor Rayleigh event, else 0 */
     double e_deposited;
 } orc_record;
 

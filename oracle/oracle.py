@@ -37,7 +37,7 @@ OUTCOMES = ("primary", "scatter", "photo", "cutoff", "miss", "step_limit")
 RECORD_DTYPE = np.dtype([
     ("n_steps", "<u4"), ("n_virtual", "<u4"), ("n_rayleigh", "<u4"), ("n_compton", "<u4"),
     ("n_photo", "<u4"), ("outcome", "<u4"), ("rng_blocks", "<u4"), ("first_interaction", "<u4"),
-    ("pixel", "<i4"), ("e_source", "<f4"), ("e_final", "<f4"), ("pad", "<u4"),
+    ("pixel", "<i4"), ("e_source", "<f4"), ("e_final", "<f4"), ("ray_material", "<u4"),
     ("e_deposited", "<f8")])
 
 
@@ -72,6 +72,8 @@ class _Problem(ctypes.Structure):
         ("response", ctypes.c_void_p),
         ("e_cut", ctypes.c_double), ("max_steps", ctypes.c_int),
         ("nearest_voxel", ctypes.c_int), ("scatter_filter", ctypes.c_int),
+        ("rayleigh_ff", ctypes.c_int), ("n_ff", ctypes.c_int), ("ff_dx", ctypes.c_double),
+        ("ff", ctypes.c_void_p),
     ]
 
 
@@ -96,6 +98,8 @@ def lib():
         L.orc_stream_words.argtypes = [u64, ctypes.c_uint32, u64, i32, vp]
         L.orc_sample_compton.argtypes = [ctypes.c_float, u64, i32, vp, vp]
         L.orc_sample_rayleigh.argtypes = [u64, i32, vp]
+        L.orc_sample_rayleigh_ff.argtypes = [vp, ctypes.c_float, i32, u64, i32, vp]
+        L.orc_sample_rayleigh_ff.restype = i32
         L.orc_sample_azimuth.argtypes = [u64, i32, vp, vp]
         L.orc_rotate.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
         _lib = L
@@ -109,7 +113,7 @@ def _ptr(a):
 class _Marshalled:
     """Keeps the contiguous arrays alive while C reads them."""
 
-    def __init__(self, prob, e_cut=1.0, max_steps=100000, nearest_voxel=0, scatter_filter=0):
+    def __init__(self, prob, e_cut=1.0, max_steps=100000, nearest_voxel=0, scatter_filter=0, rayleigh_ff=0):
         self.material = np.ascontiguousarray(prob.material, np.uint8)
         self.density = np.ascontiguousarray(prob.density, np.float32)
         self.mu_hat = np.ascontiguousarray(prob.mu_hat, np.float32)
@@ -137,16 +141,25 @@ class _Marshalled:
         s.response = _ptr(self.response).value
         s.e_cut, s.max_steps = e_cut, max_steps
         s.nearest_voxel, s.scatter_filter = int(nearest_voxel), int(scatter_filter)
+        s.rayleigh_ff = int(rayleigh_ff)
+        ff = getattr(prob, "form_factor", None)
+        if rayleigh_ff and ff is None:
+            raise ValueError("rayleigh_ff needs the problem's form_factor table")
+        if ff is not None:
+            self.ff = np.ascontiguousarray(ff, np.float32)
+            s.n_ff, s.ff_dx, s.ff = self.ff.shape[1], float(prob.ff_dx), _ptr(self.ff).value
         self.struct = s
 
 
 def mc_run(prob, n_histories, seed=1, phi=0.0, angle_index=0, history_offset=0, precision=32,
-           threads=1, records=False, e_cut=1.0, max_steps=100000, nearest_voxel=False, scatter_filter=0):
+           threads=1, records=False, e_cut=1.0, max_steps=100000, nearest_voxel=False, scatter_filter=0,
+           rayleigh_ff=False):
     """Monte Carlo projection (Section 2.4).  Returns (tally_p, tally_s, stats, records)
     with int64 fixed-point tallies shaped [nv, nu].  nearest_voxel: no density
     interpolation (the paper's speed variant); scatter_filter: 0 all scatter,
-    1 single Compton, 2 single Rayleigh, 3 multiple scatter."""
-    m = _Marshalled(prob, e_cut, max_steps, nearest_voxel, scatter_filter)
+    1 single Compton, 2 single Rayleigh, 3 multiple scatter; rayleigh_ff: the
+    Rayleigh angle takes the problem's form factors (else Thomson)."""
+    m = _Marshalled(prob, e_cut, max_steps, nearest_voxel, scatter_filter, rayleigh_ff)
     tp = np.zeros((prob.nv, prob.nu), np.int64)
     ts = np.zeros((prob.nv, prob.nu), np.int64)
     st = np.zeros(N_STATS, np.uint64)
@@ -231,6 +244,16 @@ def sample_compton(e_kev, n, seed=1):
 def sample_rayleigh(n, seed=1):
     c = np.empty(n, np.float32)
     lib().orc_sample_rayleigh(seed, n, _ptr(c))
+    return c
+
+
+def sample_rayleigh_ff(prob, e_kev, material, n, seed=1):
+    """Rayleigh cos(theta) with the form factor of `material` at e_kev (FP32 path)."""
+    m = _Marshalled(prob, rayleigh_ff=1)
+    c = np.empty(n, np.float32)
+    rc = lib().orc_sample_rayleigh_ff(ctypes.byref(m.struct), e_kev, material, seed, n, _ptr(c))
+    if rc:
+        raise ValueError("oracle rejected the form-factor problem")
     return c
 
 

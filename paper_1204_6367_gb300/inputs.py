@@ -106,6 +106,10 @@ class Problem:
     # optional per-detector-column spectra [nu, n_bins] (energy-dependent bowtie
     # hardening); None keeps the separable phi(E) w(u) source of Section 2.1
     spec_cols: np.ndarray | None = None
+    # optional Rayleigh form factors F(x) per material [n_mat, n_x] float32 on
+    # x_j = j * ff_dx (1/Angstrom, x = sin(theta/2) / lambda)
+    form_factor: np.ndarray | None = None
+    ff_dx: float = 0.02
 
     @property
     def shape(self):
@@ -119,6 +123,24 @@ def material_table(materials) -> np.ndarray:
     e0, de, n = ENERGY_GRID
     e = e0 + de * np.arange(n)
     return np.stack([mass_attenuation(m, e) for m in materials]).astype(np.float32)
+
+
+FF_GRID = (0.02, 640)   # x_j = j * 0.02 1/Angstrom, j < 640 (to 12.78; 150 keV backscatter is 12.1)
+
+
+def form_factor(mat: Material, x: np.ndarray) -> np.ndarray:
+    """Synthetic coherent form factor F(x): Z_eff (1 + (x/x0)^2)^-2 with
+    x0 = 0.45 (Z_eff / 7.42)^(1/3) 1/Angstrom, a hydrogen-like fall-off that
+    halves F near x = 0.29 1/Angstrom for water.  Stands in for tabulated
+    (Hubbell) form factors, which are not available here."""
+    x0 = 0.45 * (mat.z_eff / WATER.z_eff) ** (1.0 / 3.0)
+    return mat.z_eff / (1.0 + (np.asarray(x, np.float64) / x0) ** 2) ** 2
+
+
+def form_factor_table(materials) -> np.ndarray:
+    dx, n = FF_GRID
+    x = dx * np.arange(n)
+    return np.stack([form_factor(m, x) for m in materials]).astype(np.float32)
 
 
 def response_table(kind: str) -> np.ndarray:
@@ -254,6 +276,7 @@ def small_problem(n_vox=32, vox=4.0, n_det=64, det_px=4.0, energy=60.0, name="cy
         sad=1000.0, sdd=sdd, theta=0.0, nu=n_det, nv=n_det, du=det_px, dv=det_px,
         material=mat, density=den, voxel=(vox, vox, vox),
         mu_hat=material_table([AIR, WATER, BONE]), e0=ENERGY_GRID[0], de=ENERGY_GRID[1],
+        form_factor=form_factor_table([AIR, WATER, BONE]), ff_dx=FF_GRID[0],
         spec_e=np.array([energy]), spec_w=np.array([1.0]),
         fluence=fluence_map(n_det, n_det, det_px, det_px, sdd),
         response=response_table("ideal"), r0=ENERGY_GRID[0], dr=ENERGY_GRID[1],
@@ -274,6 +297,7 @@ def torso_problem(vox=2.0, seed=1, kvp=120.0, nu=512, nv=384, det_px=0.776, bowt
         sad=1000.0, sdd=sdd, theta=0.0, nu=nu, nv=nv, du=det_px, dv=det_px,
         material=mat, density=den, voxel=(vox, vox, vox),
         mu_hat=material_table([AIR, WATER, BONE, LUNG]), e0=ENERGY_GRID[0], de=ENERGY_GRID[1],
+        form_factor=form_factor_table([AIR, WATER, BONE, LUNG]), ff_dx=FF_GRID[0],
         spec_e=spec_e, spec_w=spec_w,
         fluence=fluence_map(nu, nv, det_px, det_px, sdd, spec_e, spec_w, bowtie_mm),
         response=response_table("csi"), r0=ENERGY_GRID[0], dr=ENERGY_GRID[1],
@@ -297,6 +321,7 @@ def uniform_slab_problem(nx=16, ny=16, nz=16, vox=2.0, mat_id=1, density=1.0, en
         sad=sad, sdd=sdd, theta=0.0, nu=nu, nv=nv, du=det_px, dv=det_px,
         material=mat, density=den, voxel=(vox, vox, vox),
         mu_hat=material_table(mats), e0=ENERGY_GRID[0], de=ENERGY_GRID[1],
+        form_factor=form_factor_table(mats), ff_dx=FF_GRID[0],
         spec_e=np.array([energy]), spec_w=np.array([1.0]), fluence=flu,
         response=response_table("ideal"), r0=ENERGY_GRID[0], dr=ENERGY_GRID[1],
         name="slab")

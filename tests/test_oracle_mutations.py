@@ -64,6 +64,15 @@ MUTATIONS = [
     ("gdrr_oracle.c", "double* col = orc_build_cdf(p->bin_w_cols + (size_t)u * p->n_bins, p->n_bins);",
      "double* col = orc_build_cdf(p->bin_w, p->n_bins);",
      "column spectra ignored by the energy sampler", "test_oracle_bowtie.py"),
+    ("mc_history.inc", "acc = acc + a[corner] * cR[mc[corner]];", "acc = acc + a[corner];",
+     "form-factor material picked by corner weight alone", "test_oracle_rayleigh_ff.py"),
+    ("mc_history.inc", "REAL s = S[lo - 1] + RC(2) * D / (g0 + SQRTR(q));", "REAL s = S[lo - 1] + D / g0;",
+     "form-factor interval inverted as if F^2 were constant", "test_oracle_rayleigh_ff.py"),
+    ("mc_history.inc", "REAL xmax = e * GEO(inv_hc);", "REAL xmax = RC(0.5) * e * GEO(inv_hc);",
+     "momentum transfer of a wavelength off by two", "test_oracle_rayleigh_ff.py"),
+    ("gdrr_oracle.c", "acc += 0.5 * (f0 * f0 + f1 * f1) * (c->gd.ff_s[j] - c->gd.ff_s[j - 1]);",
+     "acc += 0.5 * (f0 + f1) * (c->gd.ff_s[j] - c->gd.ff_s[j - 1]);",
+     "form factor not squared in the cumulative", "test_oracle_rayleigh_ff.py"),
     ("oracle.py", "sigma - (1.0 / beta) * (1.0 - s_hat / s)", "sigma - (1.0 / beta) * (1.0 - s / s_hat)",
      "denoiser fidelity term", "test_oracle_image.py"),
     ("oracle.py", "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[:-2, 1:-1]\n        s = ",
