@@ -134,6 +134,12 @@ typedef struct {
                                   Rayleigh, 2 exactly one Rayleigh and no Compton,
                                   3 two or more interactions; the others count as
                                   missing the detector [0]                           */
+    int32_t rayleigh_form_factor; /* 1: Rayleigh polar angle from (1 + cos^2) F^2(x)
+                                  with the form factors set by gdrr_set_form_factor
+                                  (the material picked among the interaction point's
+                                  corner voxels in proportion to their Rayleigh
+                                  coefficient); 0: Thomson (1 + cos^2), the paper's
+                                  default reading [0]                                 */
 } gdrr_mc_options;
 
 /* Transport counters, accumulated by every gdrr_mc_project* call (device
@@ -153,7 +159,7 @@ typedef struct {
     uint32_t n_photo, outcome, rng_blocks, first_interaction;
     int32_t pixel;
     float e_source, e_final;
-    uint32_t pad;
+    uint32_t ray_material;   /* material of the last form-factor Rayleigh event, else 0 */
     double e_deposited;
 } gdrr_history_record;
 
@@ -240,6 +246,23 @@ GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* ang
 GDRR_API int gdrr_scan_launch(gdrr_scan* scan);
 /* Release the scan (synchronises its context's stream). */
 GDRR_API void gdrr_scan_destroy(gdrr_scan* scan);
+
+/* Coherent (Rayleigh) form factors F(x, i) of each material, for the
+ * rayleigh_form_factor option: tabulated on x_j = j * dx_inv_angstrom,
+ * j < n_x, with x = sin(theta/2) / lambda in 1/Angstrom; layout
+ * [n_materials][n_x], host, finite, >= 0, F(0) > 0.  The grid must reach the
+ * backscatter momentum transfer E_max / hc of the largest energy of the
+ * material tables (hc = 12.398419843320026 keV Angstrom).  The library builds
+ * the cumulative of F^2 over x^2 (trapezoid sums, F^2 linear in x^2 between
+ * nodes) per material; the draw of x^2 inverts it exactly.  A second call
+ * replaces the tables; form_factor == NULL removes them (and is refused while
+ * the option is on).  Synchronises the context's stream. */
+typedef struct {
+    int32_t n_x;
+    double dx_inv_angstrom;
+    const float* form_factor;
+} gdrr_form_factor;
+GDRR_API int gdrr_set_form_factor(gdrr_ctx* ctx, const gdrr_form_factor* ff);
 
 /* Autotuner: time gdrr_mc_project of n_probe histories at angle_rad for each
  * launch configuration of a fixed grid (block size 64 / 128 / 256, batch_min

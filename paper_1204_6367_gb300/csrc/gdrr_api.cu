@@ -42,6 +42,13 @@ struct gdrr_ctx {
     float* d_mu_rt = nullptr;
     float* d_wr = nullptr;
     float* d_wr_cols = nullptr;   // [nu][n_bins] with per-column spectra, else NULL
+    // Rayleigh form factors: nodes s_j = x_j^2 [n_ff], cumulative and F^2 [m][n_ff]
+    float* d_ff_s = nullptr;
+    float* d_ff_a = nullptr;
+    float* d_ff_g = nullptr;
+    int n_ff = 0;
+    float ff_idx = 0.0f;
+    int n_scans = 0;              // live scans, which captured the table pointers
     int e_col = 0;                // 1: energy CDFs hold one row per detector column
     int n_guide_pix = 0, n_guide_e = 0;
     // scratch owned by the context
@@ -67,6 +74,7 @@ struct gdrr_scan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t total = 0;
+    bool counted = false;     // included in ctx->n_scans
 };
 
 namespace {
@@ -204,7 +212,8 @@ int free_ctx(gdrr_ctx* c) {
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->d_vox, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_kcdf_pix,
                     c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr, c->d_wr_cols,
-                    c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise, c->d_tune};
+                    c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise, c->d_tune,
+                    c->d_ff_s, c->d_ff_a, c->d_ff_g};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -423,7 +432,65 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
     if (!(n.e_cut_kev < 1e6)) return GDRR_ERR_INVALID_ARG;
     if (n.nearest_voxel < 0 || n.nearest_voxel > 1 || n.scatter_filter < 0 || n.scatter_filter > 3)
         return GDRR_ERR_INVALID_ARG;
+    if (n.rayleigh_form_factor < 0 || n.rayleigh_form_factor > 1 || (n.rayleigh_form_factor && !ctx->n_ff))
+        return GDRR_ERR_INVALID_ARG;
     ctx->opt = n;
+    return GDRR_OK;
+}
+
+GDRR_API int gdrr_set_form_factor(gdrr_ctx* ctx, const gdrr_form_factor* ff) {
+    if (!ctx || !ff) return GDRR_ERR_INVALID_ARG;
+    if (ctx->n_scans > 0) return GDRR_ERR_INVALID_ARG;     // scans hold the old table pointers
+    if (!ff->form_factor) {
+        if (ctx->opt.rayleigh_form_factor) return GDRR_ERR_INVALID_ARG;
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->d_ff_s); cudaFree(ctx->d_ff_a); cudaFree(ctx->d_ff_g);
+        ctx->d_ff_s = ctx->d_ff_a = ctx->d_ff_g = nullptr;
+        ctx->n_ff = 0;
+        return GDRR_OK;
+    }
+    const double hc = 12.398419843320026;   // keV Angstrom (CODATA 2018)
+    const int n = ff->n_x;
+    const double dx = ff->dx_inv_angstrom;
+    if (n < 2 || !(dx > 0.0) || !std::isfinite(dx)) return GDRR_ERR_INVALID_ARG;
+    const double e_max = ctx->e0 + (double)(ctx->n_e - 1) * ctx->de;
+    if ((double)(n - 1) * dx < e_max / hc) return GDRR_ERR_INVALID_ARG;
+    // nodes s_j = (j dx)^2; A_j = trapezoid sum of F^2 over s; G_j = F_j^2 (FP64, stored FP32)
+    std::vector<double> sd(n);
+    std::vector<float> s(n), A((size_t)ctx->n_mat * n), G((size_t)ctx->n_mat * n);
+    for (int j = 0; j < n; ++j) {
+        const double x = (double)j * dx;
+        sd[j] = x * x;
+        s[j] = (float)(x * x);
+    }
+    for (int m = 0; m < ctx->n_mat; ++m) {
+        const float* F = ff->form_factor + (size_t)m * n;
+        if (!(F[0] > 0.0f)) return GDRR_ERR_INVALID_ARG;
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (!(F[j] >= 0.0f) || !std::isfinite(F[j])) return GDRR_ERR_INVALID_ARG;
+            if (j > 0) {
+                const double f0 = (double)F[j - 1], f1 = (double)F[j];
+                acc += 0.5 * (f0 * f0 + f1 * f1) * (sd[j] - sd[j - 1]);
+            }
+            A[(size_t)m * n + j] = (float)acc;
+            const double g = (double)F[j] * (double)F[j];
+            G[(size_t)m * n + j] = (float)g;
+        }
+    }
+    float *ds = nullptr, *da = nullptr, *dg = nullptr;
+    int rc = GDRR_OK;
+    do {
+        if ((rc = upload(&ds, s.data(), s.size(), ctx->stream))) break;
+        if ((rc = upload(&da, A.data(), A.size(), ctx->stream))) break;
+        if ((rc = upload(&dg, G.data(), G.size(), ctx->stream))) break;
+        if ((rc = cuda_err(cudaStreamSynchronize(ctx->stream)))) break;
+    } while (0);
+    if (rc) { cudaFree(ds); cudaFree(da); cudaFree(dg); return rc; }
+    cudaFree(ctx->d_ff_s); cudaFree(ctx->d_ff_a); cudaFree(ctx->d_ff_g);
+    ctx->d_ff_s = ds; ctx->d_ff_a = da; ctx->d_ff_g = dg;
+    ctx->n_ff = n;
+    ctx->ff_idx = (float)(1.0 / dx);
     return GDRR_OK;
 }
 
@@ -495,6 +562,10 @@ static McParams static_mc_params(const gdrr_ctx* ctx) {
     p.idu = (float)(1.0 / ctx->geo.du_mm); p.idv = (float)(1.0 / ctx->geo.dv_mm);
     p.e_cut = (float)ctx->opt.e_cut_kev;
     p.max_steps = ctx->opt.max_steps;
+    p.n_ff = ctx->n_ff;
+    p.ff_s = ctx->d_ff_s; p.ff_a = ctx->d_ff_a; p.ff_g = ctx->d_ff_g;
+    p.inv_hc = (float)(1.0 / 12.398419843320026);
+    p.ff_idx = ctx->ff_idx;
     return p;
 }
 
@@ -525,6 +596,7 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     p.batch_min = ctx->opt.batch_min;
     p.nearest_voxel = ctx->opt.nearest_voxel;
     p.scatter_filter = ctx->opt.scatter_filter;
+    p.ray_ff = ctx->opt.rayleigh_form_factor;
     const bool rec = records_dev != nullptr;
     return cuda_err(launch_mc(p, ctx->opt.block_size, launch_grid(ctx, total, rec), rec, ctx->stream));
 }
@@ -619,6 +691,7 @@ GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* ang
         p.batch_min = ctx->opt.batch_min;
         p.nearest_voxel = ctx->opt.nearest_voxel;
         p.scatter_filter = ctx->opt.scatter_filter;
+        p.ray_ff = ctx->opt.rayleigh_form_factor;
         if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
         const size_t tally_bytes = (size_t)n_angles * ctx->geo.nu * ctx->geo.nv * sizeof(int64_t);
@@ -641,6 +714,8 @@ GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* ang
         gdrr_scan_destroy(sc);
         return cuda_err(e);
     }
+    sc->counted = true;
+    ++ctx->n_scans;
     *out = sc;
     return GDRR_OK;
 }
@@ -658,6 +733,7 @@ GDRR_API void gdrr_scan_destroy(gdrr_scan* scan) {
     if (scan->d_jobs) cudaFree(scan->d_jobs);
     if (scan->d_counter) cudaFree(scan->d_counter);
     if (scan->d_stats) cudaFree(scan->d_stats);
+    if (scan->counted && scan->ctx) --scan->ctx->n_scans;
     delete scan;
 }
 

@@ -94,6 +94,13 @@ struct McParams {
     int batch_min;                 // waiting lanes that trigger a warp's service batch
     int nearest_voxel;             // 1: each point takes its voxel's value (no interpolation)
     int scatter_filter;            // 0 all scatter, 1 single Compton, 2 single Rayleigh, 3 multiple
+    // Rayleigh form factors (ray_ff = 1): nodes s_j = x_j^2, cumulative A and
+    // F^2 per material [m][n_ff], 1/(hc) and 1/dx
+    int ray_ff, n_ff;
+    const float* ff_s;
+    const float* ff_a;
+    const float* ff_g;
+    float inv_hc, ff_idx;
 };
 
 // Ray-tracing parameters.

@@ -205,6 +205,48 @@ __device__ __forceinline__ void compton(Stream& rs, const RoundKeys& rk, float e
     e_out = e / x;
 }
 
+// Rayleigh polar angle with the form factor of material m at energy e: the
+// density of s = x^2 is F^2(s), linear in s between the table's nodes, so
+// its cumulative is the trapezoid sum on the nodes and quadratic within an
+// interval.  s is drawn on [0, s_max], s_max = (e / hc)^2, by inverse CDF
+// (binary search for the interval, the root of the quadratic within it),
+// cos = 1 - 2 s / s_max, and accepted with (1 + cos^2) / 2.  One block per
+// attempt: word 0 draws s, word 1 the acceptance.
+__device__ __forceinline__ float rayleigh_ff(Stream& rs, const McParams& P, float e, int m) {
+    const float* __restrict__ S = P.ff_s;
+    const float* __restrict__ A = P.ff_a + (size_t)m * P.n_ff;
+    const float* __restrict__ G = P.ff_g + (size_t)m * P.n_ff;
+    const float xmax = e * P.inv_hc;
+    const float smax = xmax * xmax;
+    int j = (int)(xmax * P.ff_idx);
+    if (j > P.n_ff - 2) j = P.n_ff - 2;
+    const float sj = __ldg(S + j), sj1 = __ldg(S + j + 1);
+    const float gj = __ldg(G + j), gj1 = __ldg(G + j + 1);
+    const float hj = sj1 - sj;
+    const float tj = smax - sj;
+    const float amax = __ldg(A + j) + tj * (gj + (gj1 - gj) * tj / (2.0f * hj));
+    for (;;) {
+        const uint4 w = rs.block(P.rk);
+        const float target = uniform(w.x) * amax;
+        int lo = 1, hi = j + 1;        // smallest k in [1, j+1] with A[k] >= target
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(A + mid) >= target) hi = mid; else lo = mid + 1;
+        }
+        const float s0 = __ldg(S + lo - 1);
+        const float h = __ldg(S + lo) - s0;
+        const float g0 = __ldg(G + lo - 1), g1 = __ldg(G + lo);
+        const float D = target - __ldg(A + lo - 1);
+        float q = g0 * g0 + 2.0f * (g1 - g0) * D / h;
+        if (q < 0.0f) q = 0.0f;
+        float s = s0 + 2.0f * D / (g0 + sqrtf(q));
+        if (s > smax) s = smax;
+        float ct = 1.0f - 2.0f * s / smax;
+        if (!(ct >= -1.0f)) ct = -1.0f;
+        if (2.0f * uniform(w.y) <= 1.0f + ct * ct) return ct;
+    }
+}
+
 __device__ __forceinline__ float rayleigh(Stream& rs, const RoundKeys& rk) {
     for (;;) {
         const uint4 w = rs.block(rk);
@@ -235,6 +277,7 @@ struct Lane {
     int state, scattered, job;
     uint32_t nsteps;
     uint32_t n_int;      // Compton interactions (low 16 bits) and Rayleigh (high 16 bits)
+    int m_ray;           // material of the pending form-factor Rayleigh event (GEN)
     Stream rs;
     // per-thread coefficient tables in shared memory: coef[k][m][tid],
     // k = 0 total, 1 Rayleigh, 2 Compton (photoelectric is the remainder)
@@ -242,7 +285,7 @@ struct Lane {
     int stride;          // blockDim.x
     // event record (REC only)
     uint64_t gidx;
-    uint32_t r_virt, r_ray, r_comp, r_first;
+    uint32_t r_virt, r_ray, r_comp, r_first, r_raymat;
     float r_esrc;
     double r_dep;
 
@@ -279,7 +322,7 @@ struct Lane {
         gdrr_history_record r;
         r.n_steps = nsteps; r.n_virtual = r_virt; r.n_rayleigh = r_ray; r.n_compton = r_comp;
         r.n_photo = photo; r.outcome = outcome; r.rng_blocks = rs.blk; r.first_interaction = r_first;
-        r.pixel = pixel; r.e_source = r_esrc; r.e_final = e; r.pad = 0; r.e_deposited = r_dep;
+        r.pixel = pixel; r.e_source = r_esrc; r.e_final = e; r.ray_material = r_raymat; r.e_deposited = r_dep;
         P.records[gidx] = r;
     }
 
@@ -364,7 +407,7 @@ struct Lane {
         nsteps = 0;
         scattered = 0;
         if (GEN) n_int = 0;
-        if (REC) { r_virt = 0; r_ray = 0; r_comp = 0; r_first = 0; r_dep = 0.0; }
+        if (REC) { r_virt = 0; r_ray = 0; r_comp = 0; r_first = 0; r_raymat = 0; r_dep = 0.0; }
 
         const uint4 w0 = rs.block(P.rk);
         const float xi_u = uniform(w0.y);
@@ -456,6 +499,7 @@ struct Lane {
                 return;
             }
             const float muR = a0 * cf(1, m0), muC = a0 * cf(2, m0);
+            m_ray = m0;
             real_collision(P, t, muR, muC, cnt);
             return;
         }
@@ -501,6 +545,18 @@ struct Lane {
         float muC = a[0] * cf(2, mc[0]);
 #pragma unroll
         for (int c = 1; c < 8; ++c) muC = muC + a[c] * cf(2, mc[c]);
+        if (GEN && P.ray_ff && t <= muR) {
+            // the form factor's material: the corner whose Rayleigh share of
+            // mu_R holds xi mu_R, xi the flight block's third word
+            const float target = uniform(wf.z) * muR;
+            float acc = 0.0f;
+            m_ray = mc[7];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                acc = acc + a[c] * cf(1, mc[c]);
+                if (target <= acc) { m_ray = mc[c]; break; }
+            }
+        }
         real_collision(P, t, muR, muC, cnt);
     }
 
@@ -524,7 +580,13 @@ struct Lane {
     __device__ __forceinline__ void interact(const McParams& P, unsigned long long* cnt) {
         float cp, sp;
         if (state == S_RAY) {
-            const float ct = rayleigh(rs, P.rk);
+            float ct;
+            if (GEN && P.ray_ff) {
+                ct = rayleigh_ff(rs, P, e, m_ray);
+                if (REC) r_raymat = (uint32_t)m_ray;
+            } else {
+                ct = rayleigh(rs, P.rk);
+            }
             azimuth(rs, P.rk, cp, sp);
             rotate(dx, dy, dz, ct, cp, sp);
             scattered = 1;
@@ -693,7 +755,7 @@ int occupancy_nm(int n_mat, int block) {
 }  // namespace
 
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s) {
-    const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0;
+    const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0 || p.ray_ff != 0;
     if (records) return gen ? launch_nm<true, true>(p, block, grid, s) : launch_nm<true, false>(p, block, grid, s);
     return gen ? launch_nm<false, true>(p, block, grid, s) : launch_nm<false, false>(p, block, grid, s);
 }

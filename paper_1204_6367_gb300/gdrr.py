@@ -24,7 +24,7 @@ TALLY_BITS = 24
 RECORD_DTYPE = np.dtype([
     ("n_steps", "<u4"), ("n_virtual", "<u4"), ("n_rayleigh", "<u4"), ("n_compton", "<u4"),
     ("n_photo", "<u4"), ("outcome", "<u4"), ("rng_blocks", "<u4"), ("first_interaction", "<u4"),
-    ("pixel", "<i4"), ("e_source", "<f4"), ("e_final", "<f4"), ("pad", "<u4"),
+    ("pixel", "<i4"), ("e_source", "<f4"), ("e_final", "<f4"), ("ray_material", "<u4"),
     ("e_deposited", "<f8")])
 
 
@@ -69,7 +69,11 @@ class McOptions(ctypes.Structure):
     _fields_ = [("e_cut_kev", ctypes.c_double), ("max_steps", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("hist_per_thread", ctypes.c_int32),
                 ("batch_min", ctypes.c_int32), ("nearest_voxel", ctypes.c_int32),
-                ("scatter_filter", ctypes.c_int32)]
+                ("scatter_filter", ctypes.c_int32), ("rayleigh_form_factor", ctypes.c_int32)]
+
+
+class FormFactor(ctypes.Structure):
+    _fields_ = [("n_x", ctypes.c_int32), ("dx_inv_angstrom", ctypes.c_double), ("form_factor", ctypes.c_void_p)]
 
 
 _lib = None
@@ -93,6 +97,7 @@ def lib():
             "gdrr_create": [vp, vp, vp, vp, vp, vp, vp, vp],
             "gdrr_destroy": [vp],
             "gdrr_set_options": [vp, vp],
+            "gdrr_set_form_factor": [vp, vp],
             "gdrr_get_options": [vp, vp],
             "gdrr_sync": [vp],
             "gdrr_raytrace_primary": [vp, dbl, vp],
@@ -201,6 +206,9 @@ class Context:
                                                 ctypes.byref(sp), ctypes.byref(bt), ctypes.byref(dt), h,
                                                 ctypes.byref(handle)))
         self._handle = handle
+        ff = getattr(prob, "form_factor", None)
+        if ff is not None:
+            gdrr_set_form_factor(self, ff, prob.ff_dx)
 
     @property
     def handle(self):
@@ -244,6 +252,18 @@ def gdrr_set_options(ctx: Context, **kw):
             raise KeyError(k)
         setattr(o, k, v)
     _check("gdrr_set_options", lib().gdrr_set_options(ctx.handle, ctypes.byref(o)))
+
+
+def gdrr_set_form_factor(ctx: Context, form_factor, dx_inv_angstrom: float):
+    """Rayleigh form factors F(x) [n_materials, n_x] on x_j = j * dx (1/Angstrom),
+    or None to remove them."""
+    if form_factor is None:
+        f = FormFactor(0, 0.0, None)
+        _check("gdrr_set_form_factor", lib().gdrr_set_form_factor(ctx.handle, ctypes.byref(f)))
+        return
+    t = np.ascontiguousarray(form_factor, np.float32)
+    f = FormFactor(t.shape[1], float(dx_inv_angstrom), _np_ptr(t))
+    _check("gdrr_set_form_factor", lib().gdrr_set_form_factor(ctx.handle, ctypes.byref(f)))
 
 
 def gdrr_get_options(ctx: Context) -> dict:

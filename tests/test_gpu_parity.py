@@ -362,3 +362,60 @@ def test_single_bin_columns_event_by_event(gd):
     assert st == ost
     np.testing.assert_array_equal(tp, otp)
     np.testing.assert_array_equal(ts, ots)
+
+
+@pytest.mark.parametrize("nearest", [False, True])
+def test_rayleigh_form_factor_event_by_event(gd, small, nearest):
+    # form-factor Rayleigh angles and the per-corner material pick, history by history
+    n = 3000
+    tp, ts, st, rec = _run_gpu(gd, small, n, seed=23, phi=0.5, records=True, rayleigh_form_factor=1,
+                               nearest_voxel=int(nearest))
+    otp, ots, ost, orec = oracle.mc_run(small, n, seed=23, phi=0.5, records=True, rayleigh_ff=True,
+                                        nearest_voxel=nearest)
+    for f in oracle.RECORD_DTYPE.names:
+        np.testing.assert_array_equal(rec[f], orec[f], err_msg=f)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
+    assert np.any(rec["ray_material"] > 0)
+
+
+def test_rayleigh_form_factor_mixture_bit_exact(gd):
+    # water / bone checkerboard: every Rayleigh event meets a mixture of materials
+    prob = inputs.uniform_slab_problem(mat_id=1, nx=16, ny=16, nz=16, nu=32, nv=32, det_px=1.0, pencil=False)
+    z, y, x = np.indices(prob.material.shape)
+    prob.material[:] = (1 + (x + y + z) % 2).astype(np.uint8)
+    tp, ts, st, _ = _run_gpu(gd, prob, 1_000_000, seed=29, rayleigh_form_factor=1)
+    otp, ots, ost, _ = oracle.mc_run(prob, 1_000_000, seed=29, threads=NTH, rayleigh_ff=True)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
+
+
+def test_rayleigh_form_factor_narrows_single_rayleigh_scatter(gd):
+    # pencil beam through water, single-Rayleigh scatter only: the detector
+    # (128 mm at 500 mm behind the slab) sees scattering angles below ~7 deg;
+    # the form factor puts most Rayleigh events there, Thomson spreads them
+    # over the sphere
+    prob = inputs.uniform_slab_problem(mat_id=1, nx=16, ny=16, nz=16, nu=64, nv=64, det_px=2.0)
+    n = 4_000_000
+    _, _, st_ff, _ = _run_gpu(gd, prob, n, seed=37, rayleigh_form_factor=1, scatter_filter=2)
+    _, _, st_th, _ = _run_gpu(gd, prob, n, seed=37, scatter_filter=2)
+    assert st_th["tally_scatter"] > 100
+    assert st_ff["tally_scatter"] > 20 * st_th["tally_scatter"], (st_ff, st_th)
+
+
+def test_rayleigh_form_factor_option_checks(gd, small):
+    prob = inputs.small_problem()
+    prob.form_factor = None
+    with gd.Context(prob) as ctx:
+        with pytest.raises(gd.GdrrError):
+            gd.gdrr_set_options(ctx, rayleigh_form_factor=1)
+        x = 0.01 * np.arange(500)       # reaches 4.99 1/Angstrom; 150 keV backscatter needs 12.1
+        with pytest.raises(gd.GdrrError):
+            gd.gdrr_set_form_factor(ctx, np.stack([inputs.form_factor(m, x) for m in
+                                                   (inputs.AIR, inputs.WATER, inputs.BONE)]), 0.01)
+        gd.gdrr_set_form_factor(ctx, small.form_factor, small.ff_dx)
+        gd.gdrr_set_options(ctx, rayleigh_form_factor=1)
+        with pytest.raises(gd.GdrrError):
+            gd.gdrr_set_form_factor(ctx, None, 0.0)      # refused while the option is on
