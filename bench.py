@@ -381,7 +381,8 @@ def run_ours(args):
             variants[name] = e0.elapsed_time(e1)
         opts = gdrr.gdrr_get_options(ctx)
         for name, kw in (("mc_nearest_voxel_ms", dict(nearest_voxel=1)),
-                         ("mc_first_order_compton_ms", dict(scatter_filter=1))):
+                         ("mc_first_order_compton_ms", dict(scatter_filter=1)),
+                         ("mc_rayleigh_form_factor_ms", dict(rayleigh_form_factor=1))):
             gdrr.gdrr_set_options(ctx, **kw)
             vp, vs = gdrr.gdrr_mc_project(ctx, n_hist, seed, angle)
             torch.cuda.synchronize()
@@ -393,7 +394,19 @@ def run_ours(args):
             variants[name] = e0.elapsed_time(e1)
             gdrr.gdrr_set_options(ctx, **opts)
         variants["mc_trilinear_ms"] = statistics.mean(mc_ms)
-        del vp, vs
+        # per-column spectra behind the bowtie (energy-dependent hardening)
+        ph = inputs.torso_problem(vox=2.0, hardened_bowtie=True)
+        with gdrr.Context(ph, stream=stream) as ch:
+            gdrr.gdrr_set_options(ch, **{k: v for k, v in opts.items() if k != "rayleigh_form_factor"})
+            gdrr.gdrr_mc_project(ch, n_hist, seed, angle, prim=vp, scat=vs)
+            torch.cuda.synchronize()
+            flush.fill_(2.0)
+            e0.record(stream)
+            gdrr.gdrr_mc_project(ch, n_hist, seed, angle, prim=vp, scat=vs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            variants["mc_hardened_bowtie_ms"] = e0.elapsed_time(e1)
+        del vp, vs, ph
 
     # learned scatter estimator against the plain method: train on pairs the
     # method generates (32 torsos x 4 angles), evaluate on held-out torsos
