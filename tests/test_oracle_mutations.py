@@ -73,6 +73,16 @@ MUTATIONS = [
     ("gdrr_oracle.c", "acc += 0.5 * (f0 * f0 + f1 * f1) * (c->gd.ff_s[j] - c->gd.ff_s[j - 1]);",
      "acc += 0.5 * (f0 + f1) * (c->gd.ff_s[j] - c->gd.ff_s[j - 1]);",
      "form factor not squared in the cumulative", "test_oracle_rayleigh_ff.py"),
+    ("fdk.py", "e0, e1 = math.sin(phi), -math.cos(phi)", "e0, e1 = -math.sin(phi), math.cos(phi)",
+     "reconstruction u axis mirrored", "test_oracle_fdk.py"),
+    ("fdk.py", "out[i, r] = 0.5 * tau * full[nu - 1:2 * nu - 1]", "out[i, r] = tau * full[nu - 1:2 * nu - 1]",
+     "full-scan factor 1/2 of the filter dropped", "test_oracle_fdk.py"),
+    ("fdk.py", "f += d_beta * val / (U * U)", "f += d_beta * val",
+     "FDK distance weight dropped", "test_oracle_fdk.py"),
+    ("fdk.py", "w = sad / np.sqrt(sad * sad + a[None, :] ** 2 + b[:, None] ** 2)", "w = 1.0",
+     "FDK cosine weight dropped", "test_oracle_fdk.py"),
+    ("fdk.py", "h[odd] = -1.0 / (np.pi * k[odd] * tau) ** 2", "h[odd] = -1.0 / (np.pi * k[odd] * tau ** 2)",
+     "Ram-Lak odd taps", "test_oracle_fdk.py"),
     ("oracle.py", "sigma - (1.0 / beta) * (1.0 - s_hat / s)", "sigma - (1.0 / beta) * (1.0 - s / s_hat)",
      "denoiser fidelity term", "test_oracle_image.py"),
     ("oracle.py", "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[:-2, 1:-1]\n        s = ",
