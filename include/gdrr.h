@@ -264,6 +264,59 @@ typedef struct {
 } gdrr_form_factor;
 GDRR_API int gdrr_set_form_factor(gdrr_ctx* ctx, const gdrr_form_factor* ff);
 
+/* ---- Reconstruction of simulated scans (Section 3.5) ---------------------- */
+
+/* The unattenuated signal I0 of every pixel (an air scan): w(u) times the
+ * response-weighted spectrum sum_b phi_u(b) r(E_b), per source photon, the
+ * signal gdrr_raytrace_primary gives for an empty phantom.  FP64 device
+ * [nv][nu], caller-owned.  Asynchronous on the context stream. */
+GDRR_API int gdrr_air_scan(gdrr_ctx* ctx, double* I0_dev);
+
+/* Line integrals g = -ln(max(I, floor_rel I0) / I0) of n pixels: signal and
+ * air scan FP64 device arrays, out FP32 device; 0 < floor_rel < 1 keeps the
+ * logarithm finite where the signal is zero or negative (noise).  No
+ * context; asynchronous on cuda_stream (a cudaStream_t, NULL = legacy). */
+GDRR_API int gdrr_line_integrals(const double* signal_dev, const double* air_dev, int64_t n, double floor_rel,
+                                 float* out_dev, void* cuda_stream);
+
+/* Geometry of an FDK reconstruction: the circular orbit of Section 2.1
+ * (source at sad_mm from the isocentre, imager at sdd_mm from the source,
+ * opposite it: theta = 0), the detector grid, and the output voxel grid of
+ * nx x ny x nz voxels of dx x dy x dz mm centred on the isocentre. */
+typedef struct {
+    double sad_mm, sdd_mm;
+    int32_t nu, nv;
+    double du_mm, dv_mm;
+    int32_t nx, ny, nz;
+    double dx_mm, dy_mm, dz_mm;
+} gdrr_fdk_geometry;
+
+/* FDK step 1 (Feldkamp, Davis & Kress 1984; Kak & Slaney's equally spaced
+ * fan-beam form): on the virtual detector at the isocentre (spacing
+ * tau = du SAD / SDD), weight each line integral by SAD / sqrt(SAD^2 + a^2 +
+ * b^2) and convolve each row with the Ram-Lak kernel (h(0) = 1 / (4 tau^2),
+ * h(odd n) = -1 / (n pi tau)^2, 0 otherwise) times tau / 2, zeros outside
+ * the row.  proj_dev and filtered_dev: FP32 device [n_proj][nv][nu] (may not
+ * alias).  nu <= 4096 (GDRR_ERR_UNSUPPORTED beyond).  No context;
+ * asynchronous on cuda_stream. */
+GDRR_API int gdrr_fdk_filter(const gdrr_fdk_geometry* geometry, int32_t n_proj, const float* proj_dev,
+                             float* filtered_dev, void* cuda_stream);
+
+/* FDK step 2: voxel-driven backprojection f(x) = sum_views d_beta
+ * (SAD / (SAD + x.n))^2 Qf(a(x), b(x)) of the filtered views taken at the
+ * gantry angles angles_rad (host, n_proj values; n = (cos phi, sin phi, 0)
+ * points from the source through the isocentre), bilinear on the pixel-centre
+ * grid with zeros outside the detector.  d_beta is the angular weight of one
+ * view (2 pi / n_proj for a full scan of equally spaced views).  volume_dev:
+ * FP32 device [nz][ny][nx], attenuation in 1/mm; accumulate = 1 adds to it
+ * (so views may come in batches), 0 overwrites it.  The grid must keep every
+ * voxel between the source and the isocentre plane's far side at every angle
+ * (half-diagonal of the x-y extent < sad_mm), else GDRR_ERR_INVALID_ARG.  No
+ * context; asynchronous on cuda_stream. */
+GDRR_API int gdrr_fdk_backproject(const gdrr_fdk_geometry* geometry, int32_t n_proj, const double* angles_rad,
+                                  double d_beta, const float* filtered_dev, float* volume_dev, int32_t accumulate,
+                                  void* cuda_stream);
+
 /* Autotuner: time gdrr_mc_project of n_probe histories at angle_rad for each
  * launch configuration of a fixed grid (block size 64 / 128 / 256, batch_min
  * 8 .. 32, hist_per_thread 1 / 8 / 64), into scratch tallies, and keep the

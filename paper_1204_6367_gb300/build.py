@@ -29,6 +29,7 @@ SOURCES = {
     "image_ops.cu": [],
     "cnn_gemm.cu": [],
     "cnn.cu": [],
+    "fdk.cu": [],
 }
 HEADERS = [os.path.join(INCLUDE, "gdrr.h"), os.path.join(CSRC, "gdrr_internal.cuh")]
 

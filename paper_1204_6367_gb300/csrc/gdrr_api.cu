@@ -505,6 +505,16 @@ GDRR_API int gdrr_sync(gdrr_ctx* ctx) {
     return cuda_err(cudaStreamSynchronize(ctx->stream));
 }
 
+GDRR_API int gdrr_air_scan(gdrr_ctx* ctx, double* I0_dev) {
+    if (!ctx || !I0_dev) return GDRR_ERR_INVALID_ARG;
+    RtParams p;
+    memset(&p, 0, sizeof p);
+    p.n_bins = ctx->n_bins;
+    p.wr = ctx->d_wr; p.wr_cols = ctx->d_wr_cols; p.wnorm = ctx->d_wnorm;
+    p.nu = ctx->geo.nu; p.nv = ctx->geo.nv;
+    return cuda_err(launch_air(p, I0_dev, ctx->stream));
+}
+
 static int raytrace(gdrr_ctx* ctx, double angle_rad, double* P_dev, bool siddon) {
     if (!ctx || !P_dev || !std::isfinite(angle_rad)) return GDRR_ERR_INVALID_ARG;
     if (!geometry_ok(ctx, angle_rad)) return GDRR_ERR_INVALID_ARG;

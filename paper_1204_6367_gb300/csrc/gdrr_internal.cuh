@@ -124,6 +124,7 @@ cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cuda
 int mc_occupancy_blocks(int n_mat, int block, bool records);
 cudaError_t launch_rt(const RtParams& p, double* out, cudaStream_t s);
 cudaError_t launch_rt_siddon(const RtParams& p, double* out, cudaStream_t s);
+cudaError_t launch_air(const RtParams& p, double* out, cudaStream_t s);
 cudaError_t launch_gather_probe(const McParams& p, uint64_t n_cells, int grid, unsigned int* sink, cudaStream_t s);
 cudaError_t launch_stream_words(uint64_t seed, uint32_t angle_index, uint64_t hid0, int n_hist,
                                 int n_blocks, uint32_t* out, cudaStream_t s);

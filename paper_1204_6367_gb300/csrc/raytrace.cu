@@ -221,7 +221,25 @@ __global__ void __launch_bounds__(128) rt_siddon_kernel(const RtParams P, double
     out[j] = P.wnorm[j] * (double)sig;
 }
 
+// The unattenuated signal of each pixel: w(u) sum_b phi_u(b) r(E_b).
+__global__ void air_kernel(const RtParams P, double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.nu * P.nv) return;
+    const int iu = j % P.nu;
+    const float* w = P.wr_cols ? P.wr_cols + (size_t)iu * P.n_bins : P.wr;
+    float sig = 0.0f;
+    for (int b = 0; b < P.n_bins; ++b) sig += __ldg(w + b);
+    out[j] = P.wnorm[j] * (double)sig;
+}
+
 }  // namespace
+
+cudaError_t launch_air(const RtParams& p, double* out, cudaStream_t s) {
+    const int npix = p.nu * p.nv;
+    const int block = 128, grid = (npix + block - 1) / block;
+    air_kernel<<<grid, block, 0, s>>>(p, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rt_siddon(const RtParams& p, double* out, cudaStream_t s) {
     if (p.n_bins > RT_MAX_BINS) return cudaErrorInvalidValue;

@@ -72,6 +72,13 @@ class McOptions(ctypes.Structure):
                 ("scatter_filter", ctypes.c_int32), ("rayleigh_form_factor", ctypes.c_int32)]
 
 
+class FdkGeometry(ctypes.Structure):
+    _fields_ = [("sad_mm", ctypes.c_double), ("sdd_mm", ctypes.c_double), ("nu", ctypes.c_int32),
+                ("nv", ctypes.c_int32), ("du_mm", ctypes.c_double), ("dv_mm", ctypes.c_double),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx_mm", ctypes.c_double), ("dy_mm", ctypes.c_double), ("dz_mm", ctypes.c_double)]
+
+
 class FormFactor(ctypes.Structure):
     _fields_ = [("n_x", ctypes.c_int32), ("dx_inv_angstrom", ctypes.c_double), ("form_factor", ctypes.c_void_p)]
 
@@ -129,6 +136,10 @@ def lib():
             "gdrr_cnn_forward": [vp, i32, vp, vp],
             "gdrr_cnn_backward": [vp, vp, vp],
             "gdrr_cnn_adam_step": [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float],
+            "gdrr_air_scan": [vp, vp],
+            "gdrr_line_integrals": [vp, vp, i64, dbl, vp, vp],
+            "gdrr_fdk_filter": [vp, i32, vp, vp, vp],
+            "gdrr_fdk_backproject": [vp, i32, vp, dbl, vp, vp, i32, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -507,7 +518,7 @@ def records_array(records) -> np.ndarray:
 
 def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin_factor: int = 4,
             beta: float = 0.02, omega: float = 0.8, iters: int = 300, mas: float = 0.4,
-            zeta: float = 5.2913e9, stats=None):
+            zeta: float = 5.2913e9, stats=None, angle_index: int = 0):
     """P (ray traced), P^ and S^ (MC), S (denoised, coarse and full), N (scaled noise).
 
     Every step is a libgdrr kernel.  The denoiser runs on the bin_factor x
@@ -520,7 +531,7 @@ def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin
     if own_stats:
         stats = torch.zeros(GDRR_NSTATS, dtype=torch.int64, device="cuda")
     P = gdrr_raytrace_primary(ctx, angle_rad)
-    prim, scat = gdrr_mc_project(ctx, n_photons, seed, angle_rad, stats=stats)
+    prim, scat = gdrr_mc_project(ctx, n_photons, seed, angle_rad, angle_index, stats=stats)
     P_hat = gdrr_finalize(ctx, prim, n_photons)
     S_hat = gdrr_finalize(ctx, scat, n_photons)
     S_hat_c = gdrr_finalize(ctx, gdrr_bin_tally(ctx, scat, bin_factor), n_photons)
@@ -534,6 +545,75 @@ def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin
     N = gdrr_noise_calibrate(ctx, P_hat, P, S_hat, S, n_photons, mas, zeta)
     return dict(P=P, P_hat=P_hat, S_hat=S_hat, S_hat_coarse=S_hat_c, S_coarse=S_c, S=S, N=N,
                 prim=prim, scat=scat, stats=stats)
+
+
+# ---- reconstruction of simulated scans (Section 3.5) ----------------------
+
+def gdrr_air_scan(ctx: Context, out=None):
+    """Unattenuated signal I0 [nv, nu] FP64 of the context's source and detector."""
+    import torch
+    if out is None:
+        out = torch.empty((ctx.nv, ctx.nu), dtype=torch.float64, device="cuda")
+    _check("gdrr_air_scan", lib().gdrr_air_scan(ctx.handle, _dev_ptr(out, torch.float64, ctx.nu * ctx.nv, "I0")))
+    return out
+
+
+def gdrr_line_integrals(signal, air, floor_rel: float = 1e-6, out=None, stream=None):
+    """g = -ln(max(I, floor I0) / I0), FP32, same shape as signal."""
+    import torch
+    if out is None:
+        out = torch.empty(signal.shape, dtype=torch.float32, device="cuda")
+    h, _ = _stream_handle(stream)
+    n = signal.numel()
+    _check("gdrr_line_integrals", lib().gdrr_line_integrals(_dev_ptr(signal, torch.float64, None, "signal"),
+                                                            _dev_ptr(air, torch.float64, n, "air"), n,
+                                                            float(floor_rel), _dev_ptr(out, torch.float32, n, "out"),
+                                                            h))
+    return out
+
+
+def fdk_geometry(sad, sdd, nu, nv, du, dv, shape, voxel) -> FdkGeometry:
+    nz, ny, nx = shape
+    return FdkGeometry(float(sad), float(sdd), int(nu), int(nv), float(du), float(dv), int(nx), int(ny), int(nz),
+                       float(voxel[0]), float(voxel[1]), float(voxel[2]))
+
+
+def gdrr_fdk_filter(geo: FdkGeometry, proj, out=None, stream=None):
+    """Cosine-weighted Ram-Lak filtering of line integrals [n_proj, nv, nu] FP32."""
+    import torch
+    if out is None:
+        out = torch.empty_like(proj)
+    h, _ = _stream_handle(stream)
+    n_proj = proj.shape[0]
+    _check("gdrr_fdk_filter", lib().gdrr_fdk_filter(ctypes.byref(geo), n_proj,
+                                                    _dev_ptr(proj, torch.float32, n_proj * geo.nu * geo.nv, "proj"),
+                                                    _dev_ptr(out, torch.float32, n_proj * geo.nu * geo.nv, "out"), h))
+    return out
+
+
+def gdrr_fdk_backproject(geo: FdkGeometry, filtered, angles, d_beta=None, volume=None, accumulate=False,
+                         stream=None):
+    """Voxel-driven FDK backprojection into [nz, ny, nx] FP32 (1/mm)."""
+    import torch
+    ang = np.ascontiguousarray(angles, np.float64)
+    n_proj = ang.size
+    if d_beta is None:
+        d_beta = 2.0 * math.pi / n_proj
+    if volume is None:
+        volume = torch.empty((geo.nz, geo.ny, geo.nx), dtype=torch.float32, device="cuda")
+        accumulate = False
+    h, _ = _stream_handle(stream)
+    _check("gdrr_fdk_backproject",
+           lib().gdrr_fdk_backproject(ctypes.byref(geo), n_proj, _np_ptr(ang), float(d_beta),
+                                      _dev_ptr(filtered, torch.float32, n_proj * geo.nu * geo.nv, "filtered"),
+                                      _dev_ptr(volume, torch.float32, geo.nx * geo.ny * geo.nz, "volume"),
+                                      1 if accumulate else 0, h))
+    return volume
+
+
+def fdk(geo: FdkGeometry, proj, angles, d_beta=None, stream=None):
+    """Full FDK reconstruction of line integrals [n_proj, nv, nu] FP32."""
+    return gdrr_fdk_backproject(geo, gdrr_fdk_filter(geo, proj, stream=stream), angles, d_beta, stream=stream)
 
 
 # ---- tensor-core GEMM and the learned scatter estimator ------------------
