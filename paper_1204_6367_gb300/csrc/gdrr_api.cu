@@ -97,6 +97,71 @@ int upload(T** dst, const T* src, size_t n, cudaStream_t s) {
     return GDRR_OK;
 }
 
+// Device staging of the voxel phantom: one thread per voxel (x fastest)
+// checks its material index and density, raises the per-material maximum
+// density (float bits of non-negative values order like the values, so an
+// unsigned atomicMax is exact) and writes its 8-byte record to the bricked
+// layout.  aux[0] counts invalid voxels; aux[1 + m] holds material m's
+// maximum density bits.
+__global__ void stage_voxels_kernel(const uint8_t* __restrict__ mat, const float* __restrict__ den, int nx, int ny,
+                                    int nz, int n_mat, int bsy, int bsz, uint2* __restrict__ vox,
+                                    unsigned int* __restrict__ aux) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)nx * ny * nz;
+    if (v >= n) return;
+    const int x = (int)(v % nx);
+    const int y = (int)((v / nx) % ny);
+    const int z = (int)(v / ((int64_t)nx * ny));
+    const uint32_t m = mat[v];
+    const float d = den[v];
+    const uint32_t bits = __float_as_uint(d);
+    if (m >= (uint32_t)n_mat || !(d >= 0.0f) || !isfinite(d)) {
+        atomicAdd(aux, 1u);
+        return;
+    }
+    atomicMax(aux + 1 + m, bits);
+    vox[(size_t)brick_x(x) + brick_y(y, bsy) + brick_z(z, bsz)] = make_uint2(bits, m);
+}
+
+// Copy the host phantom to the device and stage it into ctx->d_vox (n_rec
+// bricked records, padding zero).  Returns the per-material maximum density
+// in rho_max, or GDRR_ERR_INVALID_ARG when a voxel is invalid.  Synchronises.
+int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, std::vector<double>& rho_max) {
+    const int64_t nvox = (int64_t)ph.nx * ph.ny * ph.nz;
+    cudaStream_t s = c->stream;
+    uint8_t* d_mat = nullptr;
+    float* d_den = nullptr;
+    unsigned int* d_aux = nullptr;
+    int rc = GDRR_OK;
+    std::vector<unsigned int> aux(1 + c->n_mat, 0u);
+    do {
+        if ((rc = cuda_err(cudaMalloc((void**)&c->d_vox, n_rec * sizeof(uint2))))) break;
+        if ((rc = cuda_err(cudaMemsetAsync(c->d_vox, 0, n_rec * sizeof(uint2), s)))) break;
+        if ((rc = upload(&d_mat, ph.material, (size_t)nvox, s))) break;
+        if ((rc = upload(&d_den, ph.density, (size_t)nvox, s))) break;
+        if ((rc = upload(&d_aux, aux.data(), aux.size(), s))) break;
+        const int block = 256;
+        stage_voxels_kernel<<<(unsigned)((nvox + block - 1) / block), block, 0, s>>>(
+            d_mat, d_den, ph.nx, ph.ny, ph.nz, c->n_mat, c->bsy, c->bsz, c->d_vox, d_aux);
+        if ((rc = cuda_err(cudaGetLastError()))) break;
+        if ((rc = cuda_err(cudaMemcpyAsync(aux.data(), d_aux, aux.size() * sizeof(unsigned int),
+                                           cudaMemcpyDeviceToHost, s)))) break;
+        if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
+    } while (0);
+    cudaFree(d_mat);
+    cudaFree(d_den);
+    cudaFree(d_aux);
+    if (rc) return rc;
+    if (aux[0]) return GDRR_ERR_INVALID_ARG;
+    rho_max.assign(c->n_mat, 0.0);
+    for (int m = 0; m < c->n_mat; ++m) {
+        float r;
+        memcpy(&r, &aux[1 + m], sizeof r);
+        rho_max[m] = (double)r;
+    }
+    return GDRR_OK;
+}
+
 // Inverse-CDF table of non-negative weights: running FP64 sum, divided by the
 // total (last entry exactly 1).  Empty vector on invalid weights.
 std::vector<double> build_cdf(const double* w, int n) {
@@ -264,9 +329,6 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
     const gdrr_detector& dt = *detector;
     if (dt.n_energies < 2 || !(dt.de_kev > 0) || !dt.response || !bowtie->fluence) return GDRR_ERR_INVALID_ARG;
 
-    for (int64_t v = 0; v < nvox; ++v)
-        if (ph.material[v] >= mt.n_materials || !(ph.density[v] >= 0.0f) || !std::isfinite(ph.density[v]))
-            return GDRR_ERR_INVALID_ARG;
     const int64_t nt = (int64_t)mt.n_materials * 3 * mt.n_energies;
     for (int64_t i = 0; i < nt; ++i)
         if (!(mt.mu_hat[i] >= 0.0f) || !std::isfinite(mt.mu_hat[i])) return GDRR_ERR_INVALID_ARG;
@@ -312,11 +374,15 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         // material coefficients in mm^-1 per g/cm^3 (mu_hat cm^2/g * 0.1)
         std::vector<float> tab(nt);
         for (int64_t i = 0; i < nt; ++i) tab[i] = (float)((double)mt.mu_hat[i] * 0.1);
+        // the phantom is validated, reduced and bricked on the device
+        cudaStream_t s = c->stream;
+        const int nbx = (ph.nx + 3) / 4, nby = (ph.ny + 1) / 2, nbz = (ph.nz + 1) / 2;
+        c->bsy = 16 * nbx;
+        c->bsz = 16 * nbx * nby;
+        std::vector<double> rho_max;
+        if ((rc = stage_phantom(c, ph, (size_t)16 * nbx * nby * nbz, rho_max))) break;
         // Woodcock majorant nodes: max over materials of the largest density of
         // that material times its total coefficient, with a 1e-5 margin.
-        std::vector<double> rho_max(mt.n_materials, 0.0);
-        for (int64_t v = 0; v < nvox; ++v)
-            rho_max[ph.material[v]] = std::max(rho_max[ph.material[v]], (double)ph.density[v]);
         std::vector<float> major(mt.n_energies);
         for (int e = 0; e < mt.n_energies; ++e) {
             double mx = 0.0;
@@ -380,22 +446,6 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         std::vector<double> wnorm(npix);
         for (int i = 0; i < npix; ++i) wnorm[i] = bowtie->fluence[i] / fsum;
 
-        cudaStream_t s = c->stream;
-        // bricked records: 4 x 2 x 2 voxels per 128-byte line, padding zero
-        const int nbx = (ph.nx + 3) / 4, nby = (ph.ny + 1) / 2, nbz = (ph.nz + 1) / 2;
-        c->bsy = 16 * nbx;
-        c->bsz = 16 * nbx * nby;
-        std::vector<uint2> vox((size_t)16 * nbx * nby * nbz, make_uint2(0u, 0u));
-        for (int z = 0; z < ph.nz; ++z)
-            for (int y = 0; y < ph.ny; ++y)
-                for (int x = 0; x < ph.nx; ++x) {
-                    const int64_t v = x + (int64_t)ph.nx * (y + (int64_t)ph.ny * z);
-                    uint32_t bits;
-                    memcpy(&bits, &ph.density[v], sizeof bits);
-                    vox[(size_t)brick_x(x) + brick_y(y, c->bsy) + brick_z(z, c->bsz)] =
-                        make_uint2(bits, (uint32_t)ph.material[v]);
-                }
-        if ((rc = upload(&c->d_vox, vox.data(), vox.size(), s))) break;
         if ((rc = upload(&c->d_tab, tab.data(), tab.size(), s))) break;
         if ((rc = upload(&c->d_major, major.data(), major.size(), s))) break;
         if ((rc = upload(&c->d_resp, dt.response, (size_t)dt.n_energies, s))) break;
