@@ -349,6 +349,8 @@ int orc_majorant(const orc_problem* p, float* node_out) {
 /* ------------------------------------------------------------------------ */
 /* The history, once per precision. */
 #define REAL float
+#define ORC_MAX_ATTEMPTS 1000   /* rejection-sampler attempt bound (see mc_history.inc) */
+
 #define FN(name) name##_f32
 #define GEO(x) (c->gf.x)
 #define LOGR(x) orc_logf(x)

@@ -419,3 +419,23 @@ def test_rayleigh_form_factor_option_checks(gd, small):
         gd.gdrr_set_options(ctx, rayleigh_form_factor=1)
         with pytest.raises(gd.GdrrError):
             gd.gdrr_set_form_factor(ctx, None, 0.0)      # refused while the option is on
+
+
+def test_create_rejects_bad_voxels(gd, small):
+    # voxel validation runs in the device staging kernel
+    bad_mat = small.material.copy()
+    bad_mat[0, 0, 0] = 7
+    neg = small.density.copy()
+    neg[1, 2, 3] = -1.0
+    nan = small.density.copy()
+    nan[0, 0, 1] = np.nan
+    inf = small.density.copy()
+    inf[5, 5, 5] = np.inf
+    for field, arr in (("material", bad_mat), ("density", neg), ("density", nan), ("density", inf)):
+        prob = inputs.small_problem()
+        setattr(prob, field, arr)
+        with pytest.raises(gd.GdrrError) as ei:
+            gd.Context(prob)
+        assert ei.value.code == -1
+    with gd.Context(inputs.small_problem()) as ctx:       # the device is still usable
+        assert gd.gdrr_raytrace_primary(ctx, 0.0).sum().item() > 0
