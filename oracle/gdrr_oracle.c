@@ -349,7 +349,7 @@ int orc_majorant(const orc_problem* p, float* node_out) {
 /* ------------------------------------------------------------------------ */
 /* The history, once per precision. */
 #define REAL float
-#define ORC_MAX_ATTEMPTS 1000   /* rejection-sampler attempt bound (see mc_history.inc) */
+#define ORC_MAX_BLOCKS (1u << 24)   /* Philox blocks per history after which samplers stop rejecting */
 
 #define FN(name) name##_f32
 #define GEO(x) (c->gf.x)

@@ -51,11 +51,12 @@
 namespace gdrr {
 namespace {
 
-// Rejection samplers give up after this many attempts and keep their last
-// candidate (the azimuth takes phi = 0).  Every sampler here accepts with
-// probability at least 1/2, so a legal input never gets there (odds below
-// 2^-1000); it bounds the loop for inputs that are not finite.
-constexpr int MAX_ATTEMPTS = 1000;
+// Rejection samplers stop rejecting once their history has drawn this many
+// Philox blocks and keep the candidate in hand (the azimuth takes phi = 0).
+// A legal history stays far below it (at most max_steps flights plus a few
+// tries per interaction, and every sampler accepts with probability at
+// least 1/2); it bounds the loops for inputs that are not finite.
+constexpr uint32_t MAX_BLOCKS = 1u << 24;
 
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -153,7 +154,7 @@ __device__ __forceinline__ float response(const McParams& P, float e) {
 }
 
 __device__ __forceinline__ void azimuth(Stream& rs, const RoundKeys& rk, float& cp, float& sp) {
-    for (int attempt = 1; attempt <= MAX_ATTEMPTS; ++attempt) {
+    while (rs.blk < MAX_BLOCKS) {
         const uint4 w = rs.block(rk);
         const float a = 2.0f * uniform(w.x) - 1.0f;
         const float b = 2.0f * uniform(w.y) - 1.0f;
@@ -195,7 +196,7 @@ __device__ __forceinline__ void compton(Stream& rs, const RoundKeys& rk, float e
     const float ialpha = (float)510.99895 / e;
     const float ta = 2.0f * alpha;
     float x;
-    for (int attempt = 1;; ++attempt) {
+    for (;;) {
         const uint4 w = rs.block(rk);
         const float r1 = uniform(w.x);
         const float r2 = uniform(w.y);
@@ -208,7 +209,7 @@ __device__ __forceinline__ void compton(Stream& rs, const RoundKeys& rk, float e
             const float ct = 1.0f - (x - 1.0f) * ialpha;
             if (r3 <= 0.5f * (ct * ct + 1.0f / x)) break;
         }
-        if (attempt >= MAX_ATTEMPTS) break;      // keep the last candidate
+        if (rs.blk >= MAX_BLOCKS) break;         // keep the last candidate
     }
     ct_out = 1.0f - (x - 1.0f) * ialpha;
     e_out = e / x;
@@ -234,7 +235,7 @@ __device__ __forceinline__ float rayleigh_ff(Stream& rs, const McParams& P, floa
     const float hj = sj1 - sj;
     const float tj = smax - sj;
     const float amax = __ldg(A + j) + tj * (gj + (gj1 - gj) * tj / (2.0f * hj));
-    for (int attempt = 1;; ++attempt) {
+    for (;;) {
         const uint4 w = rs.block(P.rk);
         const float target = uniform(w.x) * amax;
         int lo = 1, hi = j + 1;        // smallest k in [1, j+1] with A[k] >= target
@@ -252,17 +253,17 @@ __device__ __forceinline__ float rayleigh_ff(Stream& rs, const McParams& P, floa
         if (s > smax) s = smax;
         float ct = 1.0f - 2.0f * s / smax;
         if (!(ct >= -1.0f)) ct = -1.0f;
-        if (2.0f * uniform(w.y) <= 1.0f + ct * ct || attempt >= MAX_ATTEMPTS) return ct;
+        if (2.0f * uniform(w.y) <= 1.0f + ct * ct || rs.blk >= MAX_BLOCKS) return ct;
     }
 }
 
 __device__ __forceinline__ float rayleigh(Stream& rs, const RoundKeys& rk) {
-    for (int attempt = 1;; ++attempt) {
+    for (;;) {
         const uint4 w = rs.block(rk);
         const float a = uniform(w.x);
         const float b = uniform(w.y);
         const float mu = 2.0f * a - 1.0f;
-        if (2.0f * b <= 1.0f + mu * mu || attempt >= MAX_ATTEMPTS) return mu;
+        if (2.0f * b <= 1.0f + mu * mu || rs.blk >= MAX_BLOCKS) return mu;
     }
 }
 

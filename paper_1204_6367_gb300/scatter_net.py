@@ -55,8 +55,16 @@ def denoise(ctx, s_hat, stats, n: int, length: float = 4.0, iters: int = 800):
     return gdrr.gdrr_denoise_scatter(ctx, s_hat, count_scale, beta, 0.8, iters)
 
 
-LOW_LENGTH = 12.0      # denoiser smoothing length (pixels) for the low-photon input
-HIGH_LENGTH = 2.0      # and for the high-photon targets and the judge
+def plain_length(n: int) -> float:
+    """Smoothing length (pixels) of the plain method's denoiser at n histories:
+    12 px at 1e6 shrinking as n^-0.24 (8 px at 3e6, 7 at 1e7, 4 at 1e8), the
+    lengths that minimise the error against a 2e9-history reference on
+    held-out torsos (measured at 1e6, 3e6, 1e7 and 1e8)."""
+    return float(min(16.0, max(2.0, 12.0 * (n / 1e6) ** -0.24)))
+
+
+LOW_LENGTH = plain_length(10**6)      # the low-photon input (12 px)
+HIGH_LENGTH = plain_length(10**8)     # the high-photon targets and the judge (4.1 px)
 
 
 def low_input(ctx, n_low: int, seed: int, angle: float, angle_index: int, x_slot):

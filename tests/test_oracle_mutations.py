@@ -24,8 +24,8 @@ MUTATIONS = [
      "rotation sign", "test_oracle_sampling.py"),
     ("mc_history.inc", "*sp = RC(2) * a * b * inv;", "*sp = RC(2) * a * a * inv;",
      "azimuth sine", "test_oracle_sampling.py"),
-    ("mc_history.inc", "if (RC(2) * b <= RC(1) + mu * mu || attempt >= ORC_MAX_ATTEMPTS) return mu;",
-     "if (b <= RC(1) + mu * mu || attempt >= ORC_MAX_ATTEMPTS) return mu;",
+    ("mc_history.inc", "if (RC(2) * b <= RC(1) + mu * mu || rs->ctr[0] >= ORC_MAX_BLOCKS) return mu;",
+     "if (b <= RC(1) + mu * mu || rs->ctr[0] >= ORC_MAX_BLOCKS) return mu;",
      "Thomson acceptance", "test_oracle_sampling.py"),
     ("mc_history.inc", "w0[a] = RC(1) - t; w1[a] = t;", "w0[a] = t; w1[a] = RC(1) - t;",
      "trilinear weights swapped", "test_oracle_transport.py"),
