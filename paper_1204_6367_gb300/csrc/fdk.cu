@@ -13,7 +13,7 @@
 //     Qf(a(x), b(x)), depth = SAD + x.n, bilinear on the pixel-centre grid,
 //     zero outside the detector.
 // The filter is a short dense row convolution (nu^2 / 2 FMAs per row) done
-// in shared memory; the backprojection gathers 4 detector samples per voxel
+// in shared memory with register tiling; the backprojection gathers 4 detector samples per voxel
 // and view from L1 / L2 and keeps 8 voxels of a column in registers, so the
 // per-view geometry (depth, u, weight) is computed once per column.
 #include <cmath>
@@ -36,18 +36,29 @@ struct FilterParams {
     float scale;            // 1 / (2 tau_u)
 };
 
+// Register tiling: a thread owns FJ outputs of one parity, n_j = n0 + 2j.
+// Only sources k of the other parity contribute (odd offsets), and as k
+// advances by 2 the offsets |n_j - k| all move by 2 in the same direction, so
+// the FJ coefficients in use form a window that slides by one slot per
+// source: one shared-memory load of q(k) and one of the entering coefficient
+// serve FJ FMAs.  Sources between n_0 and n_{FJ-1} are taken directly.
+constexpr int FJ = 4;
+
 __global__ void __launch_bounds__(FILTER_BLOCK) fdk_filter_kernel(const FilterParams p, const float* __restrict__ g,
                                                                  float* __restrict__ out) {
     extern __shared__ float sm[];
     float* q = sm;                // weighted row [nu]
-    float* c = sm + p.nu;         // |d| -> kernel coefficient [nu]
+    float* c = sm + p.nu;         // offset |d| -> kernel coefficient [nu + 2 FJ]
+    const int nu = p.nu;
     const int row = blockIdx.x;
-    const size_t base = ((size_t)blockIdx.y * p.nv + row) * p.nu;
+    const size_t base = ((size_t)blockIdx.y * p.nv + row) * nu;
     const float b = ((float)row + 0.5f - 0.5f * (float)p.nv) * p.mag_dv;
     const float sad2b2 = p.sad * p.sad + b * b;
-    for (int k = threadIdx.x; k < p.nu; k += blockDim.x) {
-        const float a = ((float)k + 0.5f - 0.5f * (float)p.nu) * p.mag_du;
+    for (int k = threadIdx.x; k < nu; k += blockDim.x) {
+        const float a = ((float)k + 0.5f - 0.5f * (float)nu) * p.mag_du;
         q[k] = g[base + k] * (p.sad / sqrtf(sad2b2 + a * a));
+    }
+    for (int k = threadIdx.x; k < nu + 2 * FJ; k += blockDim.x) {
         float ck = 0.0f;
         if (k == 0) {
             ck = 0.25f;
@@ -58,12 +69,50 @@ __global__ void __launch_bounds__(FILTER_BLOCK) fdk_filter_kernel(const FilterPa
         c[k] = ck;
     }
     __syncthreads();
-    for (int n = threadIdx.x; n < p.nu; n += blockDim.x) {
-        float acc = c[0] * q[n];
-        // odd offsets below and above n
-        for (int d = 1; d <= n; d += 2) acc += c[d] * q[n - d];
-        for (int d = 1; n + d < p.nu; d += 2) acc += c[d] * q[n + d];
-        out[base + n] = p.scale * acc;
+    const int n_groups = 2 * ((nu + 2 * FJ - 1) / (2 * FJ));
+    for (int grp = threadIdx.x; grp < n_groups; grp += blockDim.x) {
+        const int par = grp & 1;
+        const int n0 = 2 * FJ * (grp >> 1) + par;
+        float acc[FJ], w[FJ];
+#pragma unroll
+        for (int j = 0; j < FJ; ++j) acc[j] = (n0 + 2 * j < nu) ? c[0] * q[n0 + 2 * j] : 0.0f;
+        // sources below n0: offsets n_j - k, shrinking by 2 per source
+        int k = 1 - par;
+        if (k < n0) {
+#pragma unroll
+            for (int j = 0; j < FJ; ++j) w[j] = c[n0 - k + 2 * j];
+            for (; k < n0; k += 2) {
+                const float qk = q[k];
+#pragma unroll
+                for (int j = 0; j < FJ; ++j) acc[j] += w[j] * qk;
+#pragma unroll
+                for (int j = FJ - 1; j > 0; --j) w[j] = w[j - 1];
+                w[0] = c[max(n0 - k - 2, 0)];
+            }
+        }
+        // sources between n_0 and n_{FJ-1}
+        for (k = n0 + 1; k < n0 + 2 * (FJ - 1) && k < nu; k += 2) {
+            const float qk = q[k];
+#pragma unroll
+            for (int j = 0; j < FJ; ++j) acc[j] += c[abs(n0 + 2 * j - k)] * qk;
+        }
+        // sources above n_{FJ-1}: offsets k - n_j, growing by 2 per source
+        k = n0 + 2 * FJ - 1;
+        if (k < nu) {
+#pragma unroll
+            for (int j = 0; j < FJ; ++j) w[j] = c[k - n0 - 2 * j];
+            for (; k < nu; k += 2) {
+                const float qk = q[k];
+#pragma unroll
+                for (int j = 0; j < FJ; ++j) acc[j] += w[j] * qk;
+#pragma unroll
+                for (int j = FJ - 1; j > 0; --j) w[j] = w[j - 1];
+                w[0] = c[min(k + 2 - n0, nu + 2 * FJ - 1)];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < FJ; ++j)
+            if (n0 + 2 * j < nu) out[base + n0 + 2 * j] = p.scale * acc[j];
     }
 }
 
@@ -177,7 +226,7 @@ extern "C" GDRR_API int gdrr_fdk_filter(const gdrr_fdk_geometry* g, int32_t n_pr
     p.sad = (float)g->sad_mm;
     p.scale = (float)(0.5 / (g->du_mm * mag));
     const dim3 grid((unsigned)g->nv, (unsigned)n_proj);
-    const size_t smem = 2 * sizeof(float) * (size_t)g->nu;
+    const size_t smem = sizeof(float) * (2 * (size_t)g->nu + 2 * gdrr::FJ);
     gdrr::fdk_filter_kernel<<<grid, gdrr::FILTER_BLOCK, smem, (cudaStream_t)cuda_stream>>>(p, proj_dev, filtered_dev);
     return cudaGetLastError() == cudaSuccess ? GDRR_OK : GDRR_ERR_CUDA;
 }
