@@ -98,29 +98,39 @@ int upload(T** dst, const T* src, size_t n, cudaStream_t s) {
 }
 
 // Device staging of the voxel phantom: one thread per voxel (x fastest)
-// checks its material index and density, raises the per-material maximum
-// density (float bits of non-negative values order like the values, so an
-// unsigned atomicMax is exact) and writes its 8-byte record to the bricked
-// layout.  aux[0] counts invalid voxels; aux[1 + m] holds material m's
+// checks its material index and density, raises its block's maximum density
+// for the material (float bits of non-negative values order like the
+// values, so an unsigned atomicMax is exact), and writes its 8-byte record to
+// the bricked layout; each block then raises the global maxima once per
+// material.  aux[0] counts invalid voxels; aux[1 + m] holds material m's
 // maximum density bits.
 __global__ void stage_voxels_kernel(const uint8_t* __restrict__ mat, const float* __restrict__ den, int nx, int ny,
                                     int nz, int n_mat, int bsy, int bsz, uint2* __restrict__ vox,
                                     unsigned int* __restrict__ aux) {
+    __shared__ unsigned int s_max[GDRR_MAX_MATERIALS];
+    __shared__ unsigned int s_bad;
+    if (threadIdx.x < GDRR_MAX_MATERIALS) s_max[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) s_bad = 0u;
+    __syncthreads();
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = (int64_t)nx * ny * nz;
-    if (v >= n) return;
-    const int x = (int)(v % nx);
-    const int y = (int)((v / nx) % ny);
-    const int z = (int)(v / ((int64_t)nx * ny));
-    const uint32_t m = mat[v];
-    const float d = den[v];
-    const uint32_t bits = __float_as_uint(d);
-    if (m >= (uint32_t)n_mat || !(d >= 0.0f) || !isfinite(d)) {
-        atomicAdd(aux, 1u);
-        return;
+    if (v < n) {
+        const int x = (int)(v % nx);
+        const int y = (int)((v / nx) % ny);
+        const int z = (int)(v / ((int64_t)nx * ny));
+        const uint32_t m = mat[v];
+        const float d = den[v];
+        const uint32_t bits = __float_as_uint(d);
+        if (m >= (uint32_t)n_mat || !(d >= 0.0f) || !isfinite(d)) {
+            atomicAdd(&s_bad, 1u);
+        } else {
+            atomicMax(&s_max[m], bits);
+            vox[(size_t)brick_x(x) + brick_y(y, bsy) + brick_z(z, bsz)] = make_uint2(bits, m);
+        }
     }
-    atomicMax(aux + 1 + m, bits);
-    vox[(size_t)brick_x(x) + brick_y(y, bsy) + brick_z(z, bsz)] = make_uint2(bits, m);
+    __syncthreads();
+    if (threadIdx.x < n_mat && s_max[threadIdx.x]) atomicMax(aux + 1 + threadIdx.x, s_max[threadIdx.x]);
+    if (threadIdx.x == 0 && s_bad) atomicAdd(aux, s_bad);
 }
 
 // Copy the host phantom to the device and stage it into ctx->d_vox (n_rec
