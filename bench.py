@@ -503,7 +503,26 @@ def run_ours(args):
         net.forward(xb)
         e1.record(stream)
         torch.cuda.synchronize()
+        # the network's building block against the measured BF16 tensor peak:
+        # one 8192^3 GEMM through the library's tcgen05 kernel
+        ga = torch.randn((8192, 8192), dtype=torch.bfloat16, device="cuda")
+        gb = torch.randn((8192, 8192), dtype=torch.bfloat16, device="cuda")
+        gc = torch.empty((8192, 8192), dtype=torch.float32, device="cuda")
+        gdrr.gdrr_gemm_bf16(ga, gb, out=gc)
+        e0.record(stream)
+        gdrr.gdrr_gemm_bf16(ga, gb, out=gc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gemm_ms = e0.elapsed_time(e1)
+        try:
+            bf16_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+        except (OSError, ValueError, KeyError):
+            bf16_peak = 1900.0
+        gemm = {"m_n_k": 8192, "ms": gemm_ms, "tflops": 2 * 8192**3 / gemm_ms / 1e9,
+                "frac_of_measured_bf16_peak": 2 * 8192**3 / gemm_ms / 1e9 / bf16_peak}
+        del ga, gb, gc
         learned = {"train_pairs": int(LX.shape[0]), "data_s": t_data, "train_steps": n_train, "train_s": t_train,
+                   "gemm_bf16": gemm,
                    "final_loss": float(np.mean(losses[-50:])),
                    "rel_l2_vs_2e9_reference": {"learned_1e6": err_net,
                                                **{f"plain_denoised_{n:.0e}": err_plain[n] for n in plain_counts}},

@@ -120,7 +120,7 @@ typedef struct {
 typedef struct {
     double e_cut_kev;          /* absorb photons below this energy [1.0]           */
     int32_t max_steps;         /* free flights per history before giving up [1e5]  */
-    int32_t block_size;        /* threads per block, multiple of 32 [256]           */
+    int32_t block_size;        /* threads per block, multiple of 32, <= 512 [256]   */
     int32_t blocks_per_sm;     /* resident blocks per SM for the persistent grid [by occupancy] */
     int32_t hist_per_thread;   /* histories a warp claims per lane at a time [8]    */
     int32_t batch_min;         /* lanes of a warp that must be waiting for an
@@ -318,7 +318,7 @@ GDRR_API int gdrr_fdk_backproject(const gdrr_fdk_geometry* geometry, int32_t n_p
                                   void* cuda_stream);
 
 /* Autotuner: time gdrr_mc_project of n_probe histories at angle_rad for each
- * launch configuration of a fixed grid (block size 64 / 128 / 256, batch_min
+ * launch configuration of a fixed grid (block size 64 / 128 / 256 / 512, batch_min
  * 8 .. 32, hist_per_thread 1 / 8 / 64), into scratch tallies, and keep the
  * fastest as the context's options (also copied to *best_out when not NULL).
  * Tallies do not depend on these options, only the speed does.  Synchronises. */

@@ -486,7 +486,7 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
     if (!ctx || !o) return GDRR_ERR_INVALID_ARG;
     gdrr_mc_options n = *o;
     set_defaults(&n);
-    if (n.block_size % 32 || n.block_size > 256 || n.block_size < 32) return GDRR_ERR_INVALID_ARG;
+    if (n.block_size % 32 || n.block_size > 512 || n.block_size < 32) return GDRR_ERR_INVALID_ARG;
     if (n.hist_per_thread > 4096 || n.batch_min > 32 || n.blocks_per_sm < 0 || n.blocks_per_sm > 64)
         return GDRR_ERR_INVALID_ARG;
     if (!(n.e_cut_kev < 1e6)) return GDRR_ERR_INVALID_ARG;
@@ -820,7 +820,7 @@ GDRR_API int gdrr_autotune(gdrr_ctx* ctx, double angle_rad, uint64_t n_probe, ui
     j.tally_s = ctx->d_tune + npix;
     const std::vector<Job> jobs(1, j);
     const gdrr_mc_options base = ctx->opt;
-    static const int blocks[] = {64, 128, 256};
+    static const int blocks[] = {64, 128, 256, 512};
     static const int batch[] = {8, 12, 16, 20, 24, 28, 32};
     static const int hpt[] = {1, 8, 64};
     cudaEvent_t e0, e1;

@@ -628,7 +628,9 @@ struct Lane {
 };
 
 template <int NM, bool REC, bool GEN>
-__global__ void __launch_bounds__(256, 4) mc_kernel(const McParams P) {
+// Up to 512 threads per block, 64 registers per thread (the same cap at 2 x 512
+// or 4 x 256 resident threads): the autotuner's block sizes 64 ... 512.
+__global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
     extern __shared__ float smem[];
     __shared__ unsigned long long cnt[GDRR_NSTATS];
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x) cnt[i] = 0ull;
@@ -733,8 +735,19 @@ __global__ void stream_words_kernel(const RoundKeys rk, uint32_t angle_index, ui
 template <int NM>
 constexpr size_t smem_bytes(int block) { return (size_t)3 * NM * block * sizeof(float); }
 
+// Per-thread coefficient tables beyond 47 KB per block (8 materials at 512
+// threads) need the kernel's dynamic shared-memory cap raised first.
+template <int NM, bool REC, bool GEN>
+cudaError_t allow_smem(int block) {
+    const size_t bytes = smem_bytes<NM>(block);
+    if (bytes <= 47 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(mc_kernel<NM, REC, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <int NM, bool REC, bool GEN>
 cudaError_t launch_t(const McParams& p, int block, int grid, cudaStream_t s) {
+    const cudaError_t e = allow_smem<NM, REC, GEN>(block);
+    if (e != cudaSuccess) return e;
     mc_kernel<NM, REC, GEN><<<grid, block, smem_bytes<NM>(block), s>>>(p);
     return cudaGetLastError();
 }
@@ -742,8 +755,9 @@ cudaError_t launch_t(const McParams& p, int block, int grid, cudaStream_t s) {
 template <int NM, bool REC, bool GEN>
 int occupancy_t(int block) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_kernel<NM, REC, GEN>, block, smem_bytes<NM>(block))
-        != cudaSuccess)
+    if (allow_smem<NM, REC, GEN>(block) != cudaSuccess
+        || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_kernel<NM, REC, GEN>, block, smem_bytes<NM>(block))
+               != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }

@@ -86,7 +86,8 @@ def test_torso_4mm_polyenergetic_bit_exact(gd):
 
 @pytest.mark.parametrize("opts", [dict(block_size=64, hist_per_thread=1, batch_min=1),
                                   dict(block_size=128, hist_per_thread=64, batch_min=32),
-                                  dict(block_size=256, hist_per_thread=3, batch_min=3, blocks_per_sm=1)])
+                                  dict(block_size=256, hist_per_thread=3, batch_min=3, blocks_per_sm=1),
+                                  dict(block_size=512, hist_per_thread=8, batch_min=20)])
 def test_launch_configuration_invariance(gd, small, opts):
     n = 200_003
     ref = _run_gpu(gd, small, n, seed=5)
@@ -439,3 +440,21 @@ def test_create_rejects_bad_voxels(gd, small):
         assert ei.value.code == -1
     with gd.Context(inputs.small_problem()) as ctx:       # the device is still usable
         assert gd.gdrr_raytrace_primary(ctx, 0.0).sum().item() > 0
+
+
+def test_eight_materials_at_512_threads(gd):
+    # 8 materials x 512 threads need 48 KB of per-thread coefficients: above the
+    # default dynamic shared-memory cap, which the launch raises
+    prob = inputs.uniform_slab_problem(mat_id=1, nx=12, ny=12, nz=12, nu=24, nv=24, det_px=3.0, pencil=False,
+                                       materials=[inputs.AIR, inputs.WATER, inputs.BONE, inputs.LUNG,
+                                                  inputs.ALUMINIUM, inputs.WATER, inputs.BONE, inputs.LUNG])
+    rng = np.random.default_rng(21)
+    prob.material[:] = rng.integers(0, 8, prob.material.shape).astype(np.uint8)
+    prob.density[:] = rng.uniform(0.1, 2.0, prob.density.shape).astype(np.float32)
+    prob.form_factor = None
+    n = 100_000
+    got = _run_gpu(gd, prob, n, seed=3, block_size=512)
+    ref = oracle.mc_run(prob, n, seed=3, threads=NTH)
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_array_equal(got[1], ref[1])
+    assert got[2] == ref[2]
