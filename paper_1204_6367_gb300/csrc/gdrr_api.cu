@@ -1,10 +1,13 @@
 // Host side of libgdrr: the C ABI declared in include/gdrr.h.
 //
-// gdrr_create validates and deep-copies the inputs of Section 2.1, builds the
-// derived tables on the host in FP64 (material coefficients in mm^-1, the
-// Woodcock majorant, inverse-CDF tables of the fluence map and spectrum, the
-// ray-tracing channel tables) and stages them in device memory.  Every other
-// call only enqueues kernels on the context stream.
+// gdrr_create validates and deep-copies the inputs of Section 2.1.  The voxel
+// phantom is copied as is and staged by one device kernel (validation, the
+// per-material maximum density, the bricked records); the derived tables are
+// built on the host in FP64 (material coefficients in mm^-1, the Woodcock
+// majorant, inverse-CDF tables of the fluence map and of the spectrum or the
+// per-column spectra, the ray-tracing channel tables).  Every other call only
+// enqueues kernels on the context stream, apart from the documented
+// synchronising ones.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
