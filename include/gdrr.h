@@ -413,7 +413,10 @@ GDRR_API int gdrr_scale_to_f64(const float* src_dev, int64_t n, double scale, do
 
 /* BF16 tensor-core GEMM (tcgen05): C[M x N] (FP32, row length ldc) = A[M x K]
  * . B[N x K]^T with A and B BF16 device matrices whose rows are K-contiguous
- * (row lengths lda, ldb, multiples of 8 elements); K a multiple of 64.  With
+ * (row lengths lda, ldb, multiples of 8 elements; A_dev and B_dev 16-byte
+ * aligned, C_dev 4-byte aligned, else GDRR_ERR_INVALID_ARG before any launch);
+ * K a multiple of 64.  Outputs wider than 64 columns take the TMA-fed
+ * pipelined kernel.  With
  * splits > 1 the K range is split across CTAs that add into C, which the
  * caller zeroes first.  Synchronises; GDRR_ERR_CUDA also reports a tensor-core
  * wait that timed out.  Not in the paper: the building block of the learned

@@ -1,5 +1,8 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) of sm_103a, for the
-// convolutions of the learned scatter estimator.
+// convolutions of the learned scatter estimator.  Two forms: the one below
+// for narrow outputs (N <= 64), whose threads stage the tiles, and a TMA-fed,
+// multi-stage, warp-specialised form for N > 64 (further down).  Both read
+// operand rows in 16-byte pieces: A and B start on 16-byte boundaries.
 //
 //   C[M x N] (FP32)  =  A[M x K] . B[N x K]^T      (A, B BF16, rows K-contiguous)
 //
@@ -17,7 +20,11 @@
 //
 // Every wait is bounded: a wait that runs out sets *err and the CTA still
 // frees its TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "gdrr_internal.cuh"
 
@@ -185,6 +192,245 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(const __nv_bflo
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"((uint32_t)BN) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// The TMA-fed, pipelined form for outputs at least 128 columns wide.
+//
+// Operand tiles (128 x 64 of A, BN x 64 of B) arrive by TMA
+// (cp.async.bulk.tensor) in the tensor core's 128-byte-swizzled K-major layout
+// (row r of 128 bytes keeps its 16-byte chunk c at c ^ (r & 7); 8-row groups
+// 1024 bytes apart) into a ring of STAGES stages.  Warp 0's elected thread
+// produces: it waits until a stage is empty, announces the stage's bytes on
+// its "full" barrier and issues the two tile loads.  Warp 1's elected thread
+// consumes: it waits until the stage is full, issues the four K16 MMAs into
+// the TMEM accumulator, and commits them to the stage's "empty" barrier, which
+// fires when the tensor core has read the stage.  A last commit signals the
+// epilogue, where all four warps read TMEM rows (warp w owns lanes 32w..32w+31)
+// and store FP32.  Waits are bounded; a wait that runs out sets *err, the
+// producer's and consumer's loops stop, and the CTA still waits (bounded) for
+// its own copies in flight, frees its TMEM and returns.
+constexpr int TMA_THREADS = 128;
+
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                       // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8-row groups 1024 bytes apart
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= (uint64_t)2 << 61;                       // layout: 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(TMA_THREADS) gemm_tma_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                              const __grid_constant__ CUtensorMap mapB,
+                                                              float* __restrict__ C, int ldc, int M, int N, int K,
+                                                              int k_split, int atomic_out, int* err) {
+    constexpr uint32_t A_BYTES = GEMM_BM * GEMM_BK * 2, B_BYTES = BN * GEMM_BK * 2;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    // 1024-byte-aligned ring: STAGES x (A tile, B tile)
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t ring = (raw + 1023u) & ~1023u;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * GEMM_BM;
+    const int n0 = blockIdx.y * BN;
+    const int k_begin = blockIdx.z * k_split;
+    const int k_end = min(K, k_begin + k_split);
+    const int n_iter = (k_end - k_begin) / GEMM_BK;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_base)), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_addr(&full_bar[s]), 1);
+            mbar_init(smem_addr(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_addr(&acc_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    int issued = 0;                                   // producer: stage loads issued
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        for (int it = 0; it < n_iter; ++it) {
+            const int s = it % STAGES;
+            if (it >= STAGES && !mbar_wait(smem_addr(&empty_bar[s]), (uint32_t)((it / STAGES - 1) & 1))) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            if (*(volatile int*)&s_fail) break;
+            const uint32_t sa = ring + (uint32_t)s * (A_BYTES + B_BYTES);
+            const uint32_t fb = smem_addr(&full_bar[s]);
+            mbar_expect_tx(fb, A_BYTES + B_BYTES);
+            const int k0 = k_begin + it * GEMM_BK;
+            tma_load_2d(sa, &mapA, k0, m0, fb);
+            tma_load_2d(sa + A_BYTES, &mapB, k0, n0, fb);
+            ++issued;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = instr_desc(GEMM_BM, BN);
+        int it = 0;
+        for (; it < n_iter; ++it) {
+            const int s = it % STAGES;
+            if (!mbar_wait(smem_addr(&full_bar[s]), (uint32_t)((it / STAGES) & 1))) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = ring + (uint32_t)s * (A_BYTES + B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < GEMM_BK / 16; ++kk) {
+                // K16 step inside the 128-byte swizzle atom: advance the start by 32 bytes
+                const uint64_t ad = smem_desc_sw128(sa + kk * 32);
+                const uint64_t bd = smem_desc_sw128(sa + A_BYTES + kk * 32);
+                const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                    :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_addr(&empty_bar[s])) : "memory");
+        }
+        // accumulator complete (or, after a failure, every issued MMA retired)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_addr(&acc_bar)) : "memory");
+    }
+    __syncwarp();
+    // everyone waits for the accumulator
+    const bool acc_ok = mbar_wait(smem_addr(&acc_bar), 0u);
+    const bool ok = __syncthreads_and((acc_ok && !*(volatile int*)&s_fail && n_iter > 0) ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                  "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+                float* dst = C + (size_t)row * ldc + n0 + c0;
+                if (!atomic_out && n0 + c0 + 16 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(dst + j) =
+                            make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                        __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (n0 + c0 + j < N) {
+                            if (atomic_out) atomicAdd(dst + j, __uint_as_float(r[j]));
+                            else dst[j] = __uint_as_float(r[j]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (!ok && threadIdx.x == 0) {
+        atomicExch(err, 1);
+        // copies still in flight land in this CTA's shared memory: wait for
+        // every issued stage to fill (bounded) before the CTA exits
+    }
+    if (!ok && warp == 0 && lane == 0) {
+        for (int it = max(0, issued - STAGES); it < issued; ++it)
+            mbar_wait(smem_addr(&full_bar[it % STAGES]), (uint32_t)((it / STAGES) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of a K-contiguous BF16 matrix [rows x K] (row length ld
+// elements) with box [box_rows x 64] and 128-byte swizzle; rows beyond
+// `rows` read as zero.
+bool make_map(CUtensorMap* map, const void* base, int rows, int K, int ld, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)GEMM_BK, (cuuint32_t)box_rows};
+    const cuuint32_t elem[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, elem,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_tma_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
+                         int M, int N, int K, int splits, int* err, cudaStream_t s) {
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, A, M, K, lda, GEMM_BM) || !make_map(&mB, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
+    const int k_slices = K / GEMM_BK;
+    splits = max(1, min(splits, k_slices));
+    const int per = (k_slices + splits - 1) / splits;
+    splits = (k_slices + per - 1) / per;
+    const size_t smem = (size_t)STAGES * (GEMM_BM + BN) * GEMM_BK * 2 + 1024;
+    cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((M + GEMM_BM - 1) / GEMM_BM, (N + BN - 1) / BN, splits);
+    gemm_tma_kernel<BN, STAGES><<<grid, TMA_THREADS, smem, s>>>(mA, mB, C, ldc, M, N, K, per * GEMM_BK,
+                                                                 splits > 1 ? 1 : 0, err);
+    return cudaGetLastError();
+}
+
 template <int BN>
 cudaError_t launch_gemm_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
                           int M, int N, int K, int splits, int* err, cudaStream_t s) {
@@ -205,10 +451,16 @@ cudaError_t launch_gemm_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* 
 cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N, int K,
                              int splits, int* err, cudaStream_t s) {
     if (M <= 0 || N <= 0 || K <= 0 || K % GEMM_BK || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
+    // both forms read operand rows in 16-byte pieces (vector loads or TMA)
+    if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) != 0) return cudaErrorInvalidValue;
     const auto* a = static_cast<const __nv_bfloat16*>(A);
     const auto* b = static_cast<const __nv_bfloat16*>(B);
     if (N <= 32) return launch_gemm_t<32>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
     if (N <= 64) return launch_gemm_t<64>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+    if (encode_fn()) {
+        if (N >= 256) return launch_tma_t<256, 4>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+        return launch_tma_t<128, 6>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+    }
     return launch_gemm_t<128>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
 }
 
@@ -218,6 +470,9 @@ extern "C" GDRR_API int gdrr_gemm_bf16(const void* A_dev, int32_t lda, const voi
                                       int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t splits, void* cuda_stream) {
     if (!A_dev || !B_dev || !C_dev || M <= 0 || N <= 0 || K <= 0 || K % 64 || lda % 8 || ldb % 8 || ldc < N ||
         lda < K || ldb < K || splits < 1)
+        return GDRR_ERR_INVALID_ARG;
+    if (((reinterpret_cast<uintptr_t>(A_dev) | reinterpret_cast<uintptr_t>(B_dev)) & 15u) != 0 ||
+        (reinterpret_cast<uintptr_t>(C_dev) & 3u) != 0)
         return GDRR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int* err = nullptr;

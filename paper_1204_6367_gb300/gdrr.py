@@ -636,17 +636,30 @@ def gdrr_scale_to_f64(src, scale: float, out, stream=None):
     return out
 
 
+def _row_major_ptr(t, dtype, name):
+    """Device pointer of a 2-D CUDA tensor whose rows are contiguous (any row stride)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.stride(1) != 1:
+        raise ValueError(f"{name} rows must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def gdrr_gemm_bf16(a, b, splits: int = 1, out=None, stream=None):
-    """C = A . B^T for BF16 CUDA tensors A [M, K], B [N, K] (K a multiple of 64)."""
+    """C = A . B^T for BF16 CUDA tensors A [M, K], B [N, K] (K a multiple of 64;
+    rows contiguous, row strides multiples of 8 elements)."""
     import torch
     M, K = a.shape
     N = b.shape[0]
     if out is None:
         out = torch.zeros((M, N), dtype=torch.float32, device="cuda")
     h, _ = _stream_handle(stream)
-    _check("gdrr_gemm_bf16", lib().gdrr_gemm_bf16(_dev_ptr(a, torch.bfloat16, None, "A"), a.stride(0),
-                                                  _dev_ptr(b, torch.bfloat16, None, "B"), b.stride(0),
-                                                  _dev_ptr(out, torch.float32, None, "C"), out.stride(0),
+    _check("gdrr_gemm_bf16", lib().gdrr_gemm_bf16(_row_major_ptr(a, torch.bfloat16, "A"), a.stride(0),
+                                                  _row_major_ptr(b, torch.bfloat16, "B"), b.stride(0),
+                                                  _row_major_ptr(out, torch.float32, "C"), out.stride(0),
                                                   M, N, K, int(splits), h))
     return out
 

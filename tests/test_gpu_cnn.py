@@ -44,6 +44,47 @@ def test_gemm_bf16(gd, M, N, K, splits):
     assert np.all(err <= bound), float((err / bound).max())
 
 
+@pytest.mark.parametrize("M, N, K, splits", [(1000, 256, 320, 1),    # TMA path, 256-wide tiles, ragged M
+                                             (130, 200, 128, 1),     # TMA path, 128-wide tiles, ragged M and N
+                                             (4096, 512, 1024, 3),   # TMA path, K split across CTAs
+                                             (300, 128, 64, 1),      # one K slice
+                                             (512, 384, 2048, 1)])   # ring wraps many times
+def test_gemm_bf16_tma_path(gd, M, N, K, splits):
+    rng = np.random.default_rng(M + 3 * N + K)
+    a = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    b = torch.from_numpy(rng.normal(size=(N, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    c = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    gd.gdrr_gemm_bf16(a, b, splits, out=c)
+    torch.cuda.synchronize()
+    ad, bd = a.double().cpu().numpy(), b.double().cpu().numpy()
+    ref = ad @ bd.T
+    bound = 2.0**-20 * (np.abs(ad) @ np.abs(bd).T) * max(1, splits)
+    err = np.abs(c.cpu().numpy() - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_gemm_bf16_strided_and_unaligned_operands(gd):
+    # row strides above K give the same products; a base off a 16-byte
+    # boundary is refused before any launch (operand rows are read in 16-byte
+    # pieces)
+    rng = np.random.default_rng(77)
+    M, N, K = 257, 192, 192
+    big_a = torch.from_numpy(rng.normal(size=(M, K + 64)).astype(np.float32)).to(torch.bfloat16).cuda()
+    big_b = torch.from_numpy(rng.normal(size=(N + 1, K + 8)).astype(np.float32)).to(torch.bfloat16).cuda()
+    a = big_a[:, :K]                      # lda = K + 64
+    b = big_b[:N, :K]                     # ldb = K + 8
+    ad, bd = a.double().cpu().numpy(), b.double().cpu().numpy()
+    c = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    gd.gdrr_gemm_bf16(a, b, 1, out=c)
+    torch.cuda.synchronize()
+    bound = 2.0**-20 * (np.abs(ad) @ np.abs(bd).T)
+    assert np.all(np.abs(c.cpu().numpy() - ad @ bd.T) <= bound)
+    b_off = big_b.reshape(-1)[4:4 + N * (K + 8)].view(N, K + 8)[:, :K]    # base 8 bytes off
+    with pytest.raises(gd.GdrrError) as ei:
+        gd.gdrr_gemm_bf16(a, b_off, 1, out=c)
+    assert ei.value.code == -1
+
+
 def test_cnn_forward_backward_against_oracle(gd):
     c, H, W, B = 32, 32, 32, 2
     rng = np.random.default_rng(9)
