@@ -509,11 +509,12 @@ def run_ours(args):
         gb = torch.randn((8192, 8192), dtype=torch.bfloat16, device="cuda")
         gc = torch.empty((8192, 8192), dtype=torch.float32, device="cuda")
         gdrr.gdrr_gemm_bf16(ga, gb, out=gc)
-        e0.record(stream)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
         gdrr.gdrr_gemm_bf16(ga, gb, out=gc)
-        e1.record(stream)
+        g1.record(stream)
         torch.cuda.synchronize()
-        gemm_ms = e0.elapsed_time(e1)
+        gemm_ms = g0.elapsed_time(g1)
         try:
             bf16_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
         except (OSError, ValueError, KeyError):
