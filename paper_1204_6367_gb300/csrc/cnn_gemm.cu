@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(const __nv_bflo
 // producer's and consumer's loops stop, and the CTA still waits (bounded) for
 // its own copies in flight, frees its TMEM and returns.
 constexpr int TMA_THREADS = 128;
+constexpr int GROUP_M = 8;
 
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     uint64_t d = 0;
@@ -250,8 +251,15 @@ __global__ void __launch_bounds__(TMA_THREADS) gemm_tma_kernel(const __grid_cons
     const uint32_t ring = (raw + 1023u) & ~1023u;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * GEMM_BM;
-    const int n0 = blockIdx.y * BN;
+    // tile order: groups of GROUP_M row tiles, walked column by column, so the
+    // CTAs resident at one time share their A and B tiles in L2
+    const int tiles_m = (M + GEMM_BM - 1) / GEMM_BM, tiles_n = (N + BN - 1) / BN;
+    const int per_group = GROUP_M * tiles_n;
+    const int grp = (int)blockIdx.x / per_group, in_grp = (int)blockIdx.x % per_group;
+    const int first_m = grp * GROUP_M;
+    const int size_m = min(GROUP_M, tiles_m - first_m);
+    const int m0 = (first_m + in_grp % size_m) * GEMM_BM;
+    const int n0 = (in_grp / size_m) * BN;
     const int k_begin = blockIdx.z * k_split;
     const int k_end = min(K, k_begin + k_split);
     const int n_iter = (k_end - k_begin) / GEMM_BK;
@@ -425,7 +433,7 @@ cudaError_t launch_tma_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
     cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((M + GEMM_BM - 1) / GEMM_BM, (N + BN - 1) / BN, splits);
+    dim3 grid((unsigned)(((M + GEMM_BM - 1) / GEMM_BM) * ((N + BN - 1) / BN)), 1, splits);
     gemm_tma_kernel<BN, STAGES><<<grid, TMA_THREADS, smem, s>>>(mA, mB, C, ldc, M, N, K, per * GEMM_BK,
                                                                  splits > 1 ? 1 : 0, err);
     return cudaGetLastError();
