@@ -108,6 +108,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_peak(key, fallback):
+    """A peak from MEASURED_PEAKS.json (measured on the GB300s),
+    else the fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except (OSError, ValueError, KeyError):
+        return fallback
+
+
 def kernel_traffic():
     """DRAM bytes per transport launch from the committed ncu summary, or None
     when the kernel source changed since those counters were taken."""
@@ -324,19 +333,30 @@ def run_ours(args):
         torch.cuda.synchronize()
         graph_s = e0.elapsed_time(e1) / 1e3
         pp, ps = gdrr.new_tallies(ctx, angles.size)
+        scan_stats = torch.zeros(gdrr.GDRR_NSTATS, dtype=torch.int64, device="cuda")
         e0.record(stream)
         for a in range(angles.size):
-            gdrr.gdrr_mc_project(ctx, int(budgets[a]), seed, float(angles[a]), a, prim=pp[a], scat=ps[a])
+            gdrr.gdrr_mc_project(ctx, int(budgets[a]), seed, float(angles[a]), a, prim=pp[a], scat=ps[a],
+                                 stats=scan_stats)
         e1.record(stream)
         torch.cuda.synchronize()
         plain_s = e0.elapsed_time(e1) / 1e3
         same = bool(torch.equal(sp, pp) and torch.equal(ss, ps))
         scan.close()
         del sp, ss, pp, ps
+        # the same histories' free flights (identical tallies, so identical
+        # flights): algorithmic bytes against the HBM peak and the gather probe
+        scan_steps = gdrr.stats_dict(scan_stats)["steps"]
+        scan_probe_s = gdrr.gdrr_gather_roofline(ctx, scan_steps)
         batched = {"angles": int(angles.size), "histories": tot_hist,
                    "graph_s": graph_s, "plain_64_launches_s": plain_s,
                    "graph_histories_per_s": tot_hist / graph_s, "plain_histories_per_s": tot_hist / plain_s,
-                   "speedup": plain_s / graph_s, "tallies_identical": same}
+                   "speedup": plain_s / graph_s, "tallies_identical": same,
+                   "woodcock_steps": scan_steps,
+                   "graph_algorithmic_gbs": scan_steps * BYTES_PER_STEP_ALGO / graph_s / 1e9,
+                   "graph_frac_of_hbm_peak": scan_steps * BYTES_PER_STEP_ALGO / graph_s / 1e9
+                   / measured_peak("hbm_gbs", 6800.0),
+                   "graph_frac_of_gather_roof": scan_probe_s / graph_s}
 
     # voxel-size sweep: the same torso at 1 mm (512x512x256, 537 MB of
     # records: beyond L2) and 4 mm (128x128x64), transport only, 1e8 histories
@@ -515,10 +535,7 @@ def run_ours(args):
         g1.record(stream)
         torch.cuda.synchronize()
         gemm_ms = g0.elapsed_time(g1)
-        try:
-            bf16_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
-        except (OSError, ValueError, KeyError):
-            bf16_peak = 1900.0
+        bf16_peak = measured_peak("bf16_tflops", 1900.0)
         gemm = {"m_n_k": 8192, "ms": gemm_ms, "tflops": 2 * 8192**3 / gemm_ms / 1e9,
                 "frac_of_measured_bf16_peak": 2 * 8192**3 / gemm_ms / 1e9 / bf16_peak}
         del ga, gb, gc
