@@ -73,7 +73,7 @@ def low_input(ctx, n_low: int, seed: int, angle: float, angle_index: int, x_slot
     x_slot [2, H, W] FP32.  Returns the denoised low-photon estimate."""
     P = gdrr.gdrr_raytrace_primary(ctx, angle)
     s_low, st = simulate(ctx, n_low, seed, angle, angle_index)
-    d_low = denoise(ctx, s_low, st, n_low, LOW_LENGTH)
+    d_low = denoise(ctx, s_low, st, n_low, plain_length(n_low))
     gdrr.gdrr_scale_to_f32(d_low, SCALE, x_slot[0])
     gdrr.gdrr_scale_to_f32(P, SCALE, x_slot[1])
     return d_low
@@ -95,7 +95,7 @@ def make_dataset(seeds, angles_per_phantom: int, n_low: int, n_high: int, rng_se
                 angle = float(rng.uniform(0.0, 2.0 * math.pi))
                 low_input(ctx, n_low, 1_000_003 + 7 * k, angle, a, X[k])
                 s_high, st = simulate(ctx, n_high, 2_000_029 + 11 * k, angle, a)
-                gdrr.gdrr_scale_to_f32(denoise(ctx, s_high, st, n_high, HIGH_LENGTH), SCALE, Y[k, 0])
+                gdrr.gdrr_scale_to_f32(denoise(ctx, s_high, st, n_high, plain_length(n_high)), SCALE, Y[k, 0])
                 k += 1
     return X, Y
 
@@ -130,3 +130,72 @@ def rel_l2(a, ref) -> float:
     a = np.asarray(a, np.float64)
     ref = np.asarray(ref, np.float64)
     return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+def evaluate(net, seeds=(900, 901, 902, 903), angles_per_seed=2, n_low=10**6, n_ref=2 * 10**9,
+             plain_counts=(10**6, 3 * 10**6, 10**7, 10**8), rng_seed=7):
+    """Held-out evaluation: relative l2 of the network's estimate and of the
+    plain method at several photon counts against a denoised n_ref-history
+    reference; the plain photon count that matches the network's error
+    (log-log interpolation)."""
+    import torch
+    rng = np.random.default_rng(rng_seed)
+    e_net, e_plain = [], {n: [] for n in plain_counts}
+    for s in seeds:
+        with gdrr.Context(coarse_problem(int(s))) as ctx:
+            for a in range(angles_per_seed):
+                ang = float(rng.uniform(0.0, 2.0 * math.pi))
+                sr, st = simulate(ctx, n_ref, 91 + 10 * s + a, ang, a)
+                ref = denoise(ctx, sr, st, n_ref, 1.5).cpu().numpy()
+                x = torch.empty((1, 2, H, W), dtype=torch.float32, device="cuda")
+                low_input(ctx, n_low, 31 + 10 * s + a, ang, a, x[0])
+                e_net.append(rel_l2(predict(net, x).cpu().numpy()[0], ref))
+                for n in plain_counts:
+                    sp, stp = simulate(ctx, n, (31 if n < 10**8 else 57) + 10 * s + a, ang, a)
+                    e_plain[n].append(rel_l2(denoise(ctx, sp, stp, n, plain_length(n)).cpu().numpy(), ref))
+    err_net = float(np.mean(e_net))
+    err_plain = {n: float(np.mean(v)) for n, v in e_plain.items()}
+    lx = np.log(np.array(plain_counts, np.float64))
+    ly = np.log(np.array([err_plain[n] for n in plain_counts]))
+    order = np.argsort(ly)
+    matched = float(np.exp(np.interp(math.log(err_net), ly[order], lx[order])))
+    return {"learned": err_net, "plain": err_plain, "plain_histories_at_learned_error": matched}
+
+
+def main(argv=None):
+    """Train and judge the estimator at a chosen scale; prints one JSON line."""
+    import argparse
+    import json
+    import time
+
+    import torch
+    ap = argparse.ArgumentParser(description="train the learned scatter estimator on method-generated pairs")
+    ap.add_argument("--phantoms", type=int, default=256, help="training torsos (one random angle each)")
+    ap.add_argument("--steps", type=int, default=4000, help="Adam steps")
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--low", type=float, default=1e6, help="histories of the network's input")
+    ap.add_argument("--high", type=float, default=1e8, help="histories of the targets")
+    args = ap.parse_args(argv)
+    gdrr.lib()
+    t0 = time.perf_counter()
+    # training torsos from seed 10000 on; the held-out torsos are 900 ... 903
+    X, Y = make_dataset(range(10000, 10000 + args.phantoms), 1, int(args.low), int(args.high), rng_seed=1)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = gdrr.Cnn(max(64, args.batch), H, W, 32, seed=1)
+    t0 = time.perf_counter()
+    losses = train(net, X, Y, args.steps, args.batch, args.lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res = evaluate(net, n_low=int(args.low))
+    res.update({"train_pairs": args.phantoms, "train_steps": args.steps, "data_s": t_data, "train_s": t_train,
+                "final_loss": float(np.mean(losses[-50:])), "input_histories": args.low,
+                "target_histories": args.high})
+    res["plain"] = {f"{n:.0e}": v for n, v in res["plain"].items()}
+    print(json.dumps(res))
+    net.close()
+
+
+if __name__ == "__main__":
+    main()
