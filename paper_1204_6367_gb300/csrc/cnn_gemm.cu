@@ -1,7 +1,8 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) of sm_103a, for the
-// convolutions of the learned scatter estimator.  Two forms: the one below
-// for narrow outputs (N <= 64), whose threads stage the tiles, and a TMA-fed,
-// multi-stage, warp-specialised form for N > 64 (further down).  Both read
+// convolutions of the learned scatter estimator.  Three forms: the one below
+// for narrow outputs (N <= 64), whose threads stage the tiles; a TMA-fed,
+// multi-stage, warp-specialised form with one tile per CTA for 64 < N < 256;
+// and its persistent form with two TMEM accumulators for N >= 256.  Both read
 // operand rows in 16-byte pieces: A and B start on 16-byte boundaries.
 //
 //   C[M x N] (FP32)  =  A[M x K] . B[N x K]^T      (A, B BF16, rows K-contiguous)
@@ -24,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "gdrr_internal.cuh"
@@ -393,6 +395,198 @@ __global__ void __launch_bounds__(TMA_THREADS) gemm_tma_kernel(const __grid_cons
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"((uint32_t)BN) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form: one CTA per SM walks the tiles (grouped order, K splits
+// included) with two TMEM accumulators of BN columns.  Warp 0's elected thread
+// keeps the operand ring full across tiles; warp 1's elected thread issues a
+// tile's MMAs into accumulator (i & 1) once the epilogue has emptied it and
+// commits it to that accumulator's "full" barrier; warps 2-5 drain it (warp w
+// reads TMEM lanes 32 (w % 4) ... + 31) and release it on its "empty" barrier
+// (one arrival per warp), so one tile's epilogue runs under the next tile's
+// MMAs.  All waits are bounded; a failure stops every role's loop.
+constexpr int PERSIST_THREADS = 192;
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(PERSIST_THREADS) gemm_persistent_kernel(
+        const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* __restrict__ C,
+        int ldc, int M, int N, int K, int k_split, int n_splits, int atomic_out, int* err) {
+    constexpr uint32_t A_BYTES = GEMM_BM * GEMM_BK * 2, B_BYTES = BN * GEMM_BK * 2;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const uint32_t ring = (smem_addr(smem_raw) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_m = (M + GEMM_BM - 1) / GEMM_BM, tiles_n = (N + BN - 1) / BN;
+    const int per_split = tiles_m * tiles_n;
+    const int n_tiles = per_split * n_splits;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_base)), "r"((uint32_t)(2 * BN)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_addr(&full_bar[s]), 1);
+            mbar_init(smem_addr(&empty_bar[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_addr(&tfull[a]), 1);
+            mbar_init(smem_addr(&tempty[a]), 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    // tile t -> (m0, n0, k range): grouped order within a split
+    auto tile_coords = [&](int t, int& m0, int& n0, int& k_begin, int& n_iter) {
+        const int split = t / per_split, r = t % per_split;
+        const int per_group = GROUP_M * tiles_n;
+        const int grp = r / per_group, in_grp = r % per_group;
+        const int first_m = grp * GROUP_M;
+        const int size_m = min(GROUP_M, tiles_m - first_m);
+        m0 = (first_m + in_grp % size_m) * GEMM_BM;
+        n0 = (in_grp / size_m) * BN;
+        k_begin = split * k_split;
+        n_iter = (min(K, k_begin + k_split) - k_begin) / GEMM_BK;
+    };
+
+    if (warp == 0 && lane == 0) {
+        // producer: the ring's stage counter runs across tiles
+        int it = 0;
+        for (int t = blockIdx.x; t < n_tiles && !*(volatile int*)&s_fail; t += gridDim.x) {
+            int m0, n0, kb, n_iter;
+            tile_coords(t, m0, n0, kb, n_iter);
+            for (int i = 0; i < n_iter; ++i, ++it) {
+                const int s = it % STAGES;
+                if (it >= STAGES && !mbar_wait(smem_addr(&empty_bar[s]), (uint32_t)((it / STAGES - 1) & 1))) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                const uint32_t sa = ring + (uint32_t)s * (A_BYTES + B_BYTES);
+                const uint32_t fb = smem_addr(&full_bar[s]);
+                mbar_expect_tx(fb, A_BYTES + B_BYTES);
+                tma_load_2d(sa, &mapA, kb + i * GEMM_BK, m0, fb);
+                tma_load_2d(sa + A_BYTES, &mapB, kb + i * GEMM_BK, n0, fb);
+            }
+        }
+        // the ring's last loads land before the CTA can leave (bounded)
+        for (int j = max(0, it - STAGES); j < it; ++j)
+            mbar_wait(smem_addr(&full_bar[j % STAGES]), (uint32_t)((j / STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = instr_desc(GEMM_BM, BN);
+        int it = 0, local = 0;
+        for (int t = blockIdx.x; t < n_tiles && !*(volatile int*)&s_fail; t += gridDim.x, ++local) {
+            int m0, n0, kb, n_iter;
+            tile_coords(t, m0, n0, kb, n_iter);
+            const int a = local & 1;
+            // the accumulator is free once the epilogue released its previous tile
+            if (!mbar_wait(smem_addr(&tempty[a]), (uint32_t)(((local >> 1) & 1) ^ 1))) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc_tmem = tmem + (uint32_t)(a * BN);
+            for (int i = 0; i < n_iter; ++i, ++it) {
+                const int s = it % STAGES;
+                if (!mbar_wait(smem_addr(&full_bar[s]), (uint32_t)((it / STAGES) & 1))) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = ring + (uint32_t)s * (A_BYTES + B_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < GEMM_BK / 16; ++kk) {
+                    const uint64_t ad = smem_desc_sw128(sa + kk * 32);
+                    const uint64_t bd = smem_desc_sw128(sa + A_BYTES + kk * 32);
+                    const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                        :: "r"(acc_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_addr(&empty_bar[s])) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_addr(&tfull[a])) : "memory");
+        }
+    } else if (warp >= 2) {
+        // epilogue
+        const int q = warp & 3;                               // TMEM lane quarter of this warp
+        int local = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++local) {
+            int m0, n0, kb, n_iter;
+            tile_coords(t, m0, n0, kb, n_iter);
+            const int a = local & 1;
+            const bool got = mbar_wait(smem_addr(&tfull[a]), (uint32_t)((local >> 1) & 1));
+            const bool good = __all_sync(0xffffffffu, got) && !*(volatile int*)&s_fail;
+            if (!good) {
+                if (lane == 0) atomicExch(&s_fail, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                    "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < M) {
+                    float* dst = C + (size_t)row * ldc + n0 + c0;
+                    if (!atomic_out && n0 + c0 + 16 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<float4*>(dst + j) =
+                                make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                            __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (n0 + c0 + j < N) {
+                                if (atomic_out) atomicAdd(dst + j, __uint_as_float(r[j]));
+                                else dst[j] = __uint_as_float(r[j]);
+                            }
+                        }
+                    }
+                }
+            }
+            // this warp's TMEM reads are done: release the accumulator
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&tempty[a])) : "memory");
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int*)&s_fail) atomicExch(err, 1);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -440,6 +634,29 @@ cudaError_t launch_tma_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
     return cudaGetLastError();
 }
 
+template <int BN, int STAGES>
+cudaError_t launch_persistent_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
+                                int M, int N, int K, int splits, int* err, cudaStream_t s) {
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, A, M, K, lda, GEMM_BM) || !make_map(&mB, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
+    const int k_slices = K / GEMM_BK;
+    splits = max(1, min(splits, k_slices));
+    const int per = (k_slices + splits - 1) / splits;
+    splits = (k_slices + per - 1) / per;
+    const size_t smem = (size_t)STAGES * (GEMM_BM + BN) * GEMM_BK * 2 + 1024;
+    cudaError_t e = cudaFuncSetAttribute(gemm_persistent_kernel<BN, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n_sm = 1;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t n_tiles = (int64_t)((M + GEMM_BM - 1) / GEMM_BM) * ((N + BN - 1) / BN) * splits;
+    const int grid = (int)std::min<int64_t>(n_tiles, n_sm);
+    gemm_persistent_kernel<BN, STAGES><<<grid, PERSIST_THREADS, smem, s>>>(mA, mB, C, ldc, M, N, K, per * GEMM_BK,
+                                                                           splits, splits > 1 ? 1 : 0, err);
+    return cudaGetLastError();
+}
+
 template <int BN>
 cudaError_t launch_gemm_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
                           int M, int N, int K, int splits, int* err, cudaStream_t s) {
@@ -466,11 +683,11 @@ cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, flo
     const auto* b = static_cast<const __nv_bfloat16*>(B);
     if (N <= 32) return launch_gemm_t<32>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
     if (N <= 64) return launch_gemm_t<64>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
-    // two CTAs per SM (97-99 KB of ring each): one CTA's epilogue overlaps the
-    // other's MMAs (measured at 8192^3: 256 x 2 stages 0.75 of peak against 0.73
-    // for one CTA with 4 stages; 128 x 3 stages 0.67 against 0.49 with 6)
+    // measured at 8192^3 (fraction of the BF16 peak): persistent 256-wide tiles
+    // with two TMEM accumulators 0.78; per-tile CTAs, two per SM, 256 x 2
+    // stages 0.74 and 128 x 3 stages 0.67 (persistent 128-wide: 0.52)
     if (encode_fn()) {
-        if (N >= 256) return launch_tma_t<256, 2>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+        if (N >= 256) return launch_persistent_t<256, 4>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
         return launch_tma_t<128, 3>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
     }
     return launch_gemm_t<128>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);

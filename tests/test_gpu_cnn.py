@@ -48,7 +48,10 @@ def test_gemm_bf16(gd, M, N, K, splits):
                                              (130, 200, 128, 1),     # TMA path, 128-wide tiles, ragged M and N
                                              (4096, 512, 1024, 3),   # TMA path, K split across CTAs
                                              (300, 128, 64, 1),      # one K slice
-                                             (512, 384, 2048, 1)])   # ring wraps many times
+                                             (512, 384, 2048, 1),    # ring wraps many times
+                                             (8192, 2048, 64, 1),    # persistent: 3-4 tiles per CTA
+                                             (4000, 1024, 384, 3),   # persistent with K splits (atomics)
+                                             (3000, 768, 128, 1)])   # persistent, fewer tiles than SMs
 def test_gemm_bf16_tma_path(gd, M, N, K, splits):
     rng = np.random.default_rng(M + 3 * N + K)
     a = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
