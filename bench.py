@@ -36,6 +36,8 @@ METRIC = "MC photon histories/s and s/projection, 2 mm torso 120 kVp; batched vs
 UNIT = "histories/s"
 WORKLOAD = "torso-256x256x128-2mm, 120kVp Kramers+2.5mmAl, Al bowtie 0-30mm, 512x384 det 0.776mm, CsI response, 1e8 histories"
 BYTES_PER_STEP_ALGO = 8 * 5          # 8 corner voxels x (1 B material + 4 B density) per Woodcock step
+RECORD_BYTES_PER_STEP = 8 * 8        # the 8 corner records the kernel loads, 8 bytes each
+FLOPS_PER_STEP_ALGO = 40             # trilinear weights, 8-corner mixture, free path: ~40 FP32 flops
 
 
 def parse():
@@ -257,6 +259,9 @@ def run_ours(args):
     # gathers at as many random cells as the projection has free flights
     gdrr.gdrr_gather_roofline(ctx, min(steps_per_proj, 10**9))
     probe_s = gdrr.gdrr_gather_roofline(ctx, steps_per_proj)
+    # machine ceilings measured on this GPU: random 8-byte L2 gathers, FP32 FMA
+    l2_probe_gbs = gdrr.gdrr_probe_l2_gather(32 << 20)
+    fp32_probe_tflops = gdrr.gdrr_probe_fp32()
     launches_per_step = 1 + 1 + 3 + 1 + (iters + 2) + 1 + 1
 
     clocks = ClockSampler(dev)
@@ -591,7 +596,17 @@ def run_ours(args):
                      "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} steps",
                      "gather_roof": {"probe_gbs": algo_bytes / probe_s / 1e9, "probe_ms": 1e3 * probe_s,
                                      "frac": achieved / (algo_bytes / probe_s / 1e9),
-                                     "what": "same 8-corner gathers, same layout, random cells, no other work"}},
+                                     "what": "same 8-corner gathers, same layout, random cells, no other work"},
+                     "l2_roof": {"probe_gbs": l2_probe_gbs,
+                                 "achieved_gbs": steps_per_proj * RECORD_BYTES_PER_STEP / mc_avg_s / 1e9,
+                                 "frac": steps_per_proj * RECORD_BYTES_PER_STEP / mc_avg_s / 1e9 / l2_probe_gbs,
+                                 "what": "random 8-byte loads over a 32 MiB L2-resident set vs the transport's "
+                                         "8 x 8-byte voxel-record loads per Woodcock step"},
+                     "fp32_roof": {"probe_tflops": fp32_probe_tflops,
+                                   "achieved_tflops": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12,
+                                   "frac": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12 / fp32_probe_tflops,
+                                   "what": f"{FLOPS_PER_STEP_ALGO} FP32 flops per Woodcock step (trilinear weights, "
+                                           "mixture, free path) vs an FMA-chain probe"}},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,

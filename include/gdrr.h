@@ -317,6 +317,16 @@ GDRR_API int gdrr_fdk_backproject(const gdrr_fdk_geometry* geometry, int32_t n_p
                                   double d_beta, const float* filtered_dev, float* volume_dev, int32_t accumulate,
                                   void* cuda_stream);
 
+/* Roofline probes (machine ceilings, not part of the method).
+ * gdrr_probe_l2_gather: 8-byte loads at pseudo-random indices over a
+ * working set of the largest power of two <= working_set_bytes (1 MiB ...
+ * 4 GiB; 32 MiB fits in L2), *gbs_out = GB/s of 8-byte words.
+ * gdrr_probe_fp32: independent FMA chains, *tflops_out = FP32 TFLOP/s (two
+ * flops per FMA).  Both allocate their buffers, run one warm-up and one timed
+ * launch on cuda_stream, and synchronise. */
+GDRR_API int gdrr_probe_l2_gather(int64_t working_set_bytes, double* gbs_out, void* cuda_stream);
+GDRR_API int gdrr_probe_fp32(double* tflops_out, void* cuda_stream);
+
 /* Autotuner: time gdrr_mc_project of n_probe histories at angle_rad for each
  * launch configuration of a fixed grid (block size 64 / 128 / 256 / 512, batch_min
  * 8 .. 32, hist_per_thread 1 / 8 / 64), into scratch tallies, and keep the

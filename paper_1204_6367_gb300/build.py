@@ -30,6 +30,7 @@ SOURCES = {
     "cnn_gemm.cu": [],
     "cnn.cu": [],
     "fdk.cu": [],
+    "probes.cu": [],
 }
 HEADERS = [os.path.join(INCLUDE, "gdrr.h"), os.path.join(CSRC, "gdrr_internal.cuh")]
 

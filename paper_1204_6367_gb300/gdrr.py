@@ -137,6 +137,8 @@ def lib():
             "gdrr_cnn_backward": [vp, vp, vp],
             "gdrr_cnn_adam_step": [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float],
             "gdrr_air_scan": [vp, vp],
+            "gdrr_probe_l2_gather": [i64, vp, vp],
+            "gdrr_probe_fp32": [vp, vp],
             "gdrr_line_integrals": [vp, vp, i64, dbl, vp, vp],
             "gdrr_fdk_filter": [vp, i32, vp, vp, vp],
             "gdrr_fdk_backproject": [vp, i32, vp, dbl, vp, vp, i32, vp],
@@ -503,6 +505,22 @@ def gdrr_gather_roofline(ctx: Context, n_cells: int) -> float:
     sec = ctypes.c_double()
     _check("gdrr_gather_roofline", lib().gdrr_gather_roofline(ctx.handle, int(n_cells), ctypes.byref(sec)))
     return sec.value
+
+
+def gdrr_probe_l2_gather(working_set_bytes: int = 32 << 20, stream=None) -> float:
+    """GB/s of random 8-byte loads over an L2-resident working set."""
+    h, _ = _stream_handle(stream)
+    out = ctypes.c_double()
+    _check("gdrr_probe_l2_gather", lib().gdrr_probe_l2_gather(int(working_set_bytes), ctypes.byref(out), h))
+    return out.value
+
+
+def gdrr_probe_fp32(stream=None) -> float:
+    """FP32 FMA throughput in TFLOP/s."""
+    h, _ = _stream_handle(stream)
+    out = ctypes.c_double()
+    _check("gdrr_probe_fp32", lib().gdrr_probe_fp32(ctypes.byref(out), h))
+    return out.value
 
 
 def stats_dict(stats) -> dict:
