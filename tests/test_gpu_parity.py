@@ -458,3 +458,13 @@ def test_eight_materials_at_512_threads(gd):
     np.testing.assert_array_equal(got[0], ref[0])
     np.testing.assert_array_equal(got[1], ref[1])
     assert got[2] == ref[2]
+
+
+def test_roofline_probes(gd):
+    # the machine ceilings the bench reports the transport against
+    l2 = gd.gdrr_probe_l2_gather(32 << 20)
+    fp32 = gd.gdrr_probe_fp32()
+    assert 100.0 < l2 < 50_000.0          # GB/s of 8-byte words
+    assert 5.0 < fp32 < 500.0             # TFLOP/s
+    with pytest.raises(gd.GdrrError):
+        gd.gdrr_probe_l2_gather(1 << 10)  # below the 1 MiB minimum
