@@ -60,15 +60,18 @@ extern "C" GDRR_API int gdrr_probe_l2_gather(int64_t working_set_bytes, double* 
         if (cudaMalloc((void**)&sink, sizeof(unsigned int)) != cudaSuccess) { rc = GDRR_ERR_OOM; break; }
         if (cudaMemsetAsync(buf, 0x5A, (size_t)n_words * 8, s) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
         int dev = 0, n_sm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            rc = GDRR_ERR_CUDA;
+            break;
+        }
         const int grid = n_sm * 8, loads = 4096;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
         gdrr::l2_gather_kernel<<<grid, gdrr::PROBE_BLOCK, 0, s>>>(buf, n_words - 1u, loads, sink);   // warm the L2
         cudaEventRecord(e0, s);
         gdrr::l2_gather_kernel<<<grid, gdrr::PROBE_BLOCK, 0, s>>>(buf, n_words - 1u, loads, sink);
         cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         *gbs_out = (double)grid * gdrr::PROBE_BLOCK * loads * 8.0 / (ms * 1e-3) / 1e9;
@@ -89,15 +92,18 @@ extern "C" GDRR_API int gdrr_probe_fp32(double* tflops_out, void* cuda_stream) {
     do {
         if (cudaMalloc((void**)&sink, sizeof(float)) != cudaSuccess) { rc = GDRR_ERR_OOM; break; }
         int dev = 0, n_sm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            rc = GDRR_ERR_CUDA;
+            break;
+        }
         const int grid = n_sm * 8, iters = 1 << 14;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
         gdrr::fp32_fma_kernel<<<grid, gdrr::PROBE_BLOCK, 0, s>>>(1.0f, iters, sink);
         cudaEventRecord(e0, s);
         gdrr::fp32_fma_kernel<<<grid, gdrr::PROBE_BLOCK, 0, s>>>(1.0f, iters, sink);
         cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         *tflops_out = (double)grid * gdrr::PROBE_BLOCK * iters * 8.0 * 2.0 / (ms * 1e-3) / 1e12;
