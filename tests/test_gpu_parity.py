@@ -468,3 +468,32 @@ def test_roofline_probes(gd):
     assert 5.0 < fp32 < 500.0             # TFLOP/s
     with pytest.raises(gd.GdrrError):
         gd.gdrr_probe_l2_gather(1 << 10)  # below the 1 MiB minimum
+
+
+def test_maximum_bins_and_materials(gd):
+    # 512 spectrum channels (the library's limit) with 8 materials: transport
+    # bit-exact, both ray tracers within tolerance
+    mats = [inputs.AIR, inputs.WATER, inputs.BONE, inputs.LUNG, inputs.ALUMINIUM,
+            inputs.WATER, inputs.BONE, inputs.LUNG]
+    prob = inputs.uniform_slab_problem(nx=10, ny=9, nz=8, nu=12, nv=10, det_px=3.0, materials=mats, pencil=False)
+    rng = np.random.default_rng(5)
+    prob.material[:] = rng.integers(0, 8, prob.material.shape).astype(np.uint8)
+    prob.density[:] = rng.uniform(0.05, 2.5, prob.density.shape).astype(np.float32)
+    prob.spec_e = np.linspace(10.25, 139.75, 512)
+    prob.spec_w = rng.uniform(0.1, 1.0, 512)
+    prob.form_factor = None
+    tp, ts, st, _ = _run_gpu(gd, prob, 100_000, seed=8, phi=2.0)
+    otp, ots, ost, _ = oracle.mc_run(prob, 100_000, seed=8, phi=2.0, threads=NTH)
+    assert st == ost
+    np.testing.assert_array_equal(tp, otp)
+    np.testing.assert_array_equal(ts, ots)
+    with gd.Context(prob) as ctx:
+        P = gd.gdrr_raytrace_primary(ctx, 2.0).cpu().numpy()
+        Ps = gd.gdrr_raytrace_primary_siddon(ctx, 2.0).cpu().numpy()
+    np.testing.assert_allclose(P, oracle.rt_primary(prob, phi=2.0), rtol=RT_RTOL)
+    np.testing.assert_allclose(Ps, oracle.rt_primary_siddon(prob, phi=2.0), rtol=RT_RTOL)
+    prob.spec_e = np.linspace(10.25, 139.75, 513)
+    prob.spec_w = np.ones(513)
+    with pytest.raises(gd.GdrrError) as ei:
+        gd.Context(prob)
+    assert ei.value.code == -6
