@@ -33,7 +33,8 @@
 namespace gdrr {
 
 cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N, int K,
-                             int splits, int* err, cudaStream_t s);
+                             int splits, int* err, cudaStream_t s, int64_t partial_stride = 0,
+                             int* splits_used = nullptr);
 
 namespace {
 
@@ -267,6 +268,22 @@ struct Conv {
     bf16* wt16 = nullptr;  // [K9p][Cop]
 };
 
+// K splits of a weight-gradient product over P pixels (a function of P alone,
+// so the workspace for the largest batch bounds every call).
+int wgrad_splits(int64_t P) {
+    const int Pp = pad64(P);
+    return std::max(1, std::min(Pp / 64, (int)(P / 4096) + 1));
+}
+
+// out[i] = sum over z of p[z * stride + i], in the order z = 0, 1, ...
+__global__ void splits_sum_kernel(const float* __restrict__ p, int n_splits, int64_t stride, float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= stride) return;
+    float s = 0.0f;
+    for (int z = 0; z < n_splits; ++z) s += p[(int64_t)z * stride + i];
+    out[i] = s;
+}
+
 }  // namespace
 }  // namespace gdrr
 
@@ -294,6 +311,7 @@ struct gdrr_cnn {
     // workspaces
     bf16* cols = nullptr;      // im2col, either layout
     float* gemm = nullptr;     // GEMM output
+    float* partials = nullptr; // per-split partial products of the weight gradients
     bf16* dz_pc = nullptr;
     bf16* dz_cp = nullptr;
     float* dz_f = nullptr;
@@ -375,9 +393,19 @@ cudaError_t conv_backward(gdrr_cnn* n, const Conv& L, int B, const float* dy, co
     // weight gradient: dW[co][k] = sum_p dZ[p][co] cols[p][k]
     im2col_kernel<<<nblk((int64_t)Pp * L.K9p), TB, 0, n->stream>>>(x, B, L.ci, L.H, L.W, L.ks, L.K9p, Pp, 1, n->cols);
     CK(cudaGetLastError());
-    const int splits = std::max(1, std::min(Pp / 64, (int)(P / 4096) + 1));
-    CK(cudaMemsetAsync(n->gemm, 0, (size_t)L.co * L.K9p * sizeof(float), n->stream));
-    CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->gemm, L.K9p, L.co, L.K9p, Pp, splits, n->err, n->stream));
+    // the pixel sum is split across CTAs; each split writes its own partial
+    // product and one ordered pass adds them, so training is bit-reproducible
+    const int splits = wgrad_splits(P);
+    if (splits > 1) {
+        const int64_t slice = (int64_t)L.co * L.K9p;
+        int used = 1;
+        CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->partials, L.K9p, L.co, L.K9p, Pp, splits, n->err, n->stream,
+                            slice, &used));
+        splits_sum_kernel<<<nblk(slice), TB, 0, n->stream>>>(n->partials, used, slice, n->gemm);
+        CK(cudaGetLastError());
+    } else {
+        CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->gemm, L.K9p, L.co, L.K9p, Pp, 1, n->err, n->stream));
+    }
     unpad_kernel<<<nblk((int64_t)L.co * L.K9), TB, 0, n->stream>>>(n->gemm, L.co, L.K9, L.K9p, n->grads + L.w_off);
     CK(cudaGetLastError());
     if (dx) {
@@ -427,12 +455,13 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
     }
     n->n_params = off;
     const int64_t B = max_batch, HW = (int64_t)H * W;
-    int64_t max_cols = 0, max_gemm = 0, max_dz = 0;
+    int64_t max_cols = 0, max_gemm = 0, max_dz = 0, max_part = 0;
     for (const Conv& L : n->conv) {
         const int64_t P = B * L.H * L.W, Pp = pad64(P);
         max_cols = std::max(max_cols, Pp * L.K9p);
         max_gemm = std::max({max_gemm, P * L.K9p, (int64_t)L.co * L.K9p, P * L.co});
         max_dz = std::max({max_dz, P * L.Cop, (int64_t)L.co * Pp});
+        max_part = std::max(max_part, (int64_t)wgrad_splits(P) * L.co * L.K9p);
     }
     cudaError_t e = cudaSuccess;
     do {
@@ -465,7 +494,8 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
             break;
         if ((e = dalloc(n, &n->cols, max_cols)) || (e = dalloc(n, &n->gemm, max_gemm)) ||
             (e = dalloc(n, &n->dz_pc, max_dz)) || (e = dalloc(n, &n->dz_cp, max_dz)) ||
-            (e = dalloc(n, &n->dz_f, max_dz)) || (e = dalloc(n, &n->err, 1)))
+            (e = dalloc(n, &n->dz_f, max_dz)) || (e = dalloc(n, &n->partials, max_part)) ||
+            (e = dalloc(n, &n->err, 1)))
             break;
         // He-normal initial weights, zero biases
         std::vector<float> h(off, 0.0f);

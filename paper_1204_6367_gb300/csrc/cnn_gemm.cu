@@ -97,8 +97,10 @@ template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
                                                                 const __nv_bfloat16* __restrict__ B, int ldb,
                                                                 float* __restrict__ C, int ldc, int M, int N, int K,
-                                                                int k_split, int atomic_out, int* err) {
+                                                                int k_split, int atomic_out, int64_t partial_stride,
+                                                                int* err) {
     __shared__ __align__(1024) __nv_bfloat16 sA[GEMM_BM * GEMM_BK];
+    if (partial_stride) C += (int64_t)blockIdx.z * partial_stride;     // this split's own slice
     __shared__ __align__(1024) __nv_bfloat16 sB[BN * GEMM_BK];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
@@ -243,10 +245,12 @@ template <int BN, int STAGES>
 __global__ void __launch_bounds__(TMA_THREADS) gemm_tma_kernel(const __grid_constant__ CUtensorMap mapA,
                                                               const __grid_constant__ CUtensorMap mapB,
                                                               float* __restrict__ C, int ldc, int M, int N, int K,
-                                                              int k_split, int atomic_out, int* err) {
+                                                              int k_split, int atomic_out, int64_t partial_stride,
+                                                              int* err) {
     constexpr uint32_t A_BYTES = GEMM_BM * GEMM_BK * 2, B_BYTES = BN * GEMM_BK * 2;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+    if (partial_stride) C += (int64_t)blockIdx.z * partial_stride;     // this split's own slice
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     // 1024-byte-aligned ring: STAGES x (A tile, B tile)
@@ -409,7 +413,7 @@ constexpr int PERSIST_THREADS = 192;
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(PERSIST_THREADS) gemm_persistent_kernel(
         const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* __restrict__ C,
-        int ldc, int M, int N, int K, int k_split, int n_splits, int atomic_out, int* err) {
+        int ldc, int M, int N, int K, int k_split, int n_splits, int atomic_out, int64_t partial_stride, int* err) {
     constexpr uint32_t A_BYTES = GEMM_BM * GEMM_BK * 2, B_BYTES = BN * GEMM_BK * 2;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2];
@@ -539,6 +543,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS) gemm_persistent_kernel(
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = m0 + q * 32 + lane;
+            float* Ct = partial_stride ? C + (int64_t)(t / per_split) * partial_stride : C;   // split's slice
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 uint32_t r[16];
@@ -553,7 +558,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS) gemm_persistent_kernel(
                     : "memory");
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (row < M) {
-                    float* dst = C + (size_t)row * ldc + n0 + c0;
+                    float* dst = Ct + (size_t)row * ldc + n0 + c0;
                     if (!atomic_out && n0 + c0 + 16 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
 #pragma unroll
                         for (int j = 0; j < 16; j += 4)
@@ -617,7 +622,7 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int K, int ld, int b
 
 template <int BN, int STAGES>
 cudaError_t launch_tma_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
-                         int M, int N, int K, int splits, int* err, cudaStream_t s) {
+                         int M, int N, int K, int splits, int64_t partial_stride, int* err, cudaStream_t s) {
     CUtensorMap mA, mB;
     if (!make_map(&mA, A, M, K, lda, GEMM_BM) || !make_map(&mB, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
     const int k_slices = K / GEMM_BK;
@@ -630,13 +635,14 @@ cudaError_t launch_tma_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(((M + GEMM_BM - 1) / GEMM_BM) * ((N + BN - 1) / BN)), 1, splits);
     gemm_tma_kernel<BN, STAGES><<<grid, TMA_THREADS, smem, s>>>(mA, mB, C, ldc, M, N, K, per * GEMM_BK,
-                                                                 splits > 1 ? 1 : 0, err);
+                                                                 (splits > 1 && !partial_stride) ? 1 : 0,
+                                                                 partial_stride, err);
     return cudaGetLastError();
 }
 
 template <int BN, int STAGES>
 cudaError_t launch_persistent_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
-                                int M, int N, int K, int splits, int* err, cudaStream_t s) {
+                                int M, int N, int K, int splits, int64_t partial_stride, int* err, cudaStream_t s) {
     CUtensorMap mA, mB;
     if (!make_map(&mA, A, M, K, lda, GEMM_BM) || !make_map(&mB, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
     const int k_slices = K / GEMM_BK;
@@ -652,45 +658,56 @@ cudaError_t launch_persistent_t(const __nv_bfloat16* A, int lda, const __nv_bflo
     if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int64_t n_tiles = (int64_t)((M + GEMM_BM - 1) / GEMM_BM) * ((N + BN - 1) / BN) * splits;
     const int grid = (int)std::min<int64_t>(n_tiles, n_sm);
-    gemm_persistent_kernel<BN, STAGES><<<grid, PERSIST_THREADS, smem, s>>>(mA, mB, C, ldc, M, N, K, per * GEMM_BK,
-                                                                           splits, splits > 1 ? 1 : 0, err);
+    gemm_persistent_kernel<BN, STAGES><<<grid, PERSIST_THREADS, smem, s>>>(
+        mA, mB, C, ldc, M, N, K, per * GEMM_BK, splits, (splits > 1 && !partial_stride) ? 1 : 0, partial_stride, err);
     return cudaGetLastError();
 }
 
 template <int BN>
 cudaError_t launch_gemm_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
-                          int M, int N, int K, int splits, int* err, cudaStream_t s) {
+                          int M, int N, int K, int splits, int64_t partial_stride, int* err, cudaStream_t s) {
     const int k_slices = K / GEMM_BK;
     splits = max(1, min(splits, k_slices));
     const int per = (k_slices + splits - 1) / splits;
     splits = (k_slices + per - 1) / per;
     dim3 grid((M + GEMM_BM - 1) / GEMM_BM, (N + BN - 1) / BN, splits);
     gemm_bf16_kernel<BN><<<grid, GEMM_THREADS, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, per * GEMM_BK,
-                                                        splits > 1 ? 1 : 0, err);
+                                                        (splits > 1 && !partial_stride) ? 1 : 0, partial_stride, err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// C = A . B^T; K a multiple of 64; lda, ldb multiples of 8 (16-byte rows);
-// with splits > 1 the caller zeroes C first (partial products are added).
+// C = A . B^T; K a multiple of 64; lda, ldb multiples of 8 (16-byte rows).
+// With splits > 1 and partial_stride == 0 the caller zeroes C first and the
+// splits add into it (atomics: the summation order varies); with
+// partial_stride > 0 split z writes its own partial product to C + z *
+// partial_stride, for an ordered sum by the caller.  Returns the number of
+// splits used through *splits_used when not NULL.
 cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N, int K,
-                             int splits, int* err, cudaStream_t s) {
+                             int splits, int* err, cudaStream_t s, int64_t partial_stride, int* splits_used) {
     if (M <= 0 || N <= 0 || K <= 0 || K % GEMM_BK || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
     // both forms read operand rows in 16-byte pieces (vector loads or TMA)
     if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) != 0) return cudaErrorInvalidValue;
     const auto* a = static_cast<const __nv_bfloat16*>(A);
     const auto* b = static_cast<const __nv_bfloat16*>(B);
-    if (N <= 32) return launch_gemm_t<32>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
-    if (N <= 64) return launch_gemm_t<64>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+    if (splits_used) {
+        const int k_slices = K / GEMM_BK;
+        const int sp = max(1, min(splits, k_slices));
+        const int per = (k_slices + sp - 1) / sp;
+        *splits_used = (k_slices + per - 1) / per;
+    }
+    if (N <= 32) return launch_gemm_t<32>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
+    if (N <= 64) return launch_gemm_t<64>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
     // measured at 8192^3 (fraction of the BF16 peak): persistent 256-wide tiles
     // with two TMEM accumulators 0.78; per-tile CTAs, two per SM, 256 x 2
     // stages 0.74 and 128 x 3 stages 0.67 (persistent 128-wide: 0.52)
     if (encode_fn()) {
-        if (N >= 256) return launch_persistent_t<256, 4>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
-        return launch_tma_t<128, 3>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+        if (N >= 256)
+            return launch_persistent_t<256, 4>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
+        return launch_tma_t<128, 3>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
     }
-    return launch_gemm_t<128>(a, lda, b, ldb, C, ldc, M, N, K, splits, err, s);
+    return launch_gemm_t<128>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
 }
 
 }  // namespace gdrr
@@ -708,7 +725,7 @@ extern "C" GDRR_API int gdrr_gemm_bf16(const void* A_dev, int32_t lda, const voi
     // a 4-byte wait-timeout flag; allocated per call (this entry point is a test and utility hook)
     if (cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess) return GDRR_ERR_OOM;
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = gdrr::launch_gemm_bf16(A_dev, lda, B_dev, ldb, C_dev, ldc, M, N, K, splits, err, s);
+    if (e == cudaSuccess) e = gdrr::launch_gemm_bf16(A_dev, lda, B_dev, ldb, C_dev, ldc, M, N, K, splits, err, s, 0, nullptr);
     int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -132,3 +132,23 @@ def test_cnn_training_reduces_loss(gd):
         net.adam_step(1e-3)
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
     net.close()
+
+
+def test_training_is_bit_reproducible(gd):
+    # at the estimator's size the first layers split their weight-gradient pixel
+    # sums across CTAs; the partial products are added in a fixed order, so
+    # two trainings from the same start end bit-identical
+    rng = np.random.default_rng(3)
+    H, W, B, c = 96, 128, 16, 32
+    x = torch.from_numpy(rng.normal(size=(B, 2, H, W)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(B, 1, H, W)).astype(np.float32)).cuda()
+    params = []
+    for _ in range(2):
+        net = gd.Cnn(B, H, W, c, seed=4)
+        for _ in range(5):
+            net.forward(x)
+            net.backward(t)
+            net.adam_step(1e-3)
+        params.append(net.get_params())
+        net.close()
+    np.testing.assert_array_equal(params[0], params[1])
