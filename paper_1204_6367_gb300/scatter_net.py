@@ -176,6 +176,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--low", type=float, default=1e6, help="histories of the network's input")
     ap.add_argument("--high", type=float, default=1e8, help="histories of the targets")
+    ap.add_argument("--channels", type=int, default=32, help="base channels of the network (<= 64)")
     args = ap.parse_args(argv)
     gdrr.lib()
     t0 = time.perf_counter()
@@ -183,13 +184,14 @@ def main(argv=None):
     X, Y = make_dataset(range(10000, 10000 + args.phantoms), 1, int(args.low), int(args.high), rng_seed=1)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
-    net = gdrr.Cnn(max(64, args.batch), H, W, 32, seed=1)
+    net = gdrr.Cnn(max(64, args.batch), H, W, args.channels, seed=1)
     t0 = time.perf_counter()
     losses = train(net, X, Y, args.steps, args.batch, args.lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     res = evaluate(net, n_low=int(args.low))
-    res.update({"train_pairs": args.phantoms, "train_steps": args.steps, "data_s": t_data, "train_s": t_train,
+    res.update({"train_pairs": args.phantoms, "train_steps": args.steps, "channels": args.channels,
+                "data_s": t_data, "train_s": t_train,
                 "final_loss": float(np.mean(losses[-50:])), "input_histories": args.low,
                 "target_histories": args.high})
     res["plain"] = {f"{n:.0e}": v for n, v in res["plain"].items()}
