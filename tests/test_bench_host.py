@@ -1,0 +1,57 @@
+"""Host-side logic of the benchmark (no GPU): the DRAM-traffic record is tied
+to the transport kernel's source, the peaks come from the measured file or
+the stated fallback, and the reference leg prints one JSON line with the
+contract's keys."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_traffic_record_matches_the_kernel_source():
+    # the committed ncu record belongs to the committed transport source
+    t = bench.kernel_traffic()
+    assert isinstance(t, int) and 5e8 < t < 5e9
+
+
+def test_traffic_record_is_dropped_for_another_source(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_1204_6367_gb300" / "csrc").mkdir(parents=True)
+    src = open(os.path.join(ROOT, "profiles", "mc_kernel_torso2mm_traffic.txt")).read()
+    (tmp_path / "profiles" / "mc_kernel_torso2mm_traffic.txt").write_text(src)
+    kernel = open(os.path.join(ROOT, "paper_1204_6367_gb300", "csrc", "mc_transport.cu")).read()
+    (tmp_path / "paper_1204_6367_gb300" / "csrc" / "mc_transport.cu").write_text(kernel + "\n// edited\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic() is None
+    (tmp_path / "paper_1204_6367_gb300" / "csrc" / "mc_transport.cu").write_text(kernel)
+    assert bench.kernel_traffic() == int(dict(l.split() for l in src.splitlines()
+                                              if l.strip() and not l.startswith("#"))["bytes_per_launch"])
+
+
+def test_measured_peak_and_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peak("hbm_gbs", 6800.0) == 6800.0          # no file: the stated fallback
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6790.3}))
+    assert bench.measured_peak("hbm_gbs", 6800.0) == pytest.approx(6790.3)
+    assert bench.measured_peak("bf16_tflops", 1900.0) == 1900.0      # missing key: the fallback
+
+
+def test_reference_leg_prints_the_contract_line():
+    # a tiny run of the CPU reference arm (the oracle on host cores)
+    env = dict(os.environ, PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"],
+                         capture_output=True, text=True, timeout=900, env=env, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
