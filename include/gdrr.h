@@ -360,8 +360,12 @@ GDRR_API int gdrr_upsample(gdrr_ctx* ctx, const double* coarse_dev, int32_t cu, 
  * iterate, replicate edges, S kept >= eps = 1e-3 counts.  The iteration runs
  * on the count scale: S^ / count_scale (count_scale > 0 is the signal of one
  * detected photon); the result is returned on the input scale.  The paper uses
- * omega = 0.8.  It is stable while beta * S > omega / (4 (2 - omega)) in
- * counts.  S_hat_dev, S_dev: caller-owned device double[nv*nu]. */
+ * omega = 0.8.  Linearised at its fixed point the iteration converges while
+ * beta * S > omega / (8 (1 - omega)) in counts (0.5 at omega = 0.8; a
+ * checkerboard is the first pattern to grow below it), and for no beta when
+ * omega >= 1.  Below that floor the result oscillates and is not the Eq. 4
+ * solution; no error is returned.  S_hat_dev, S_dev: caller-owned device
+ * double[nv*nu]. */
 GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double* S_dev,
                                   int32_t nu, int32_t nv, double count_scale, double beta,
                                   double omega, int32_t iters);

@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import warnings
 
 import numpy as np
 
@@ -534,15 +535,34 @@ def records_array(records) -> np.ndarray:
 
 # ---- one full projection: Steps 1-4 of Section 2.2 ------------------------
 
+def denoise_stability_floor(omega: float = 0.8) -> float:
+    """Smallest beta * S (S in counts) at which the Eq. 5 iteration converges.
+
+    Linearised at its fixed point, Eq. 5 multiplies a perturbation along an
+    eigenvector of the neighbour sum (eigenvalue lam in (-4, 4]) by
+    1 - omega + (omega / 4) (lam - 1 / (beta S)) per iteration.  The
+    checkerboard (lam -> -4) bounds it: |.| < 1 needs beta S > omega / (8 (1 - omega)),
+    0.5 at omega = 0.8; for omega >= 1 no beta converges."""
+    if not 0.0 < omega < 1.0:
+        return math.inf
+    return omega / (8.0 * (1.0 - omega))
+
+
 def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin_factor: int = 4,
             beta: float = 0.02, omega: float = 0.8, iters: int = 300, mas: float = 0.4,
-            zeta: float = 5.2913e9, stats=None, angle_index: int = 0):
+            zeta: float = 5.2913e9, stats=None, angle_index: int = 0, smoothing_px: float | None = None):
     """P (ray traced), P^ and S^ (MC), S (denoised, coarse and full), N (scaled noise).
 
     Every step is a libgdrr kernel.  The denoiser runs on the bin_factor x
     bin_factor coarse scatter grid on the count scale: one detected scattered
     photon deposits on average (scatter tally sum) / (scattered photons
     tallied), the count_scale.
+
+    beta is in counts^-1, so a fixed beta smooths less as n_photons grows and
+    the iteration diverges once beta times the counts of most coarse pixels
+    falls below denoise_stability_floor(omega) (a warning says so).
+    smoothing_px, when given, replaces beta by smoothing_px^2 / (mean coarse
+    count): a smoothing length in coarse pixels, the same at any photon count.
     """
     import torch
     own_stats = stats is None
@@ -558,11 +578,18 @@ def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin
     count_scale = float(S_hat.sum().item()) / n_det if n_det else 1.0
     if not count_scale > 0:
         count_scale = 1.0 / n_photons
+    mean_count = n_det / S_hat_c.numel()
+    if smoothing_px is not None:
+        beta = smoothing_px * smoothing_px / max(mean_count, 1e-6)
+    elif beta * mean_count < denoise_stability_floor(omega):
+        warnings.warn(f"beta * mean scatter count = {beta * mean_count:.3g} is below "
+                      f"{denoise_stability_floor(omega):.3g}: the Eq. 5 iteration diverges on most of the image "
+                      "(raise beta, n_photons or bin_factor, or pass smoothing_px)", RuntimeWarning, stacklevel=2)
     S_c = gdrr_denoise_scatter(ctx, S_hat_c, count_scale, beta, omega, iters)
     S = gdrr_upsample(ctx, S_c, bin_factor)
     N = gdrr_noise_calibrate(ctx, P_hat, P, S_hat, S, n_photons, mas, zeta)
     return dict(P=P, P_hat=P_hat, S_hat=S_hat, S_hat_coarse=S_hat_c, S_coarse=S_c, S=S, N=N,
-                prim=prim, scat=scat, stats=stats)
+                prim=prim, scat=scat, stats=stats, count_scale=count_scale, beta=beta)
 
 
 # ---- reconstruction of simulated scans (Section 3.5) ----------------------

@@ -29,8 +29,12 @@ def full_orbit(n_views: int):
 
 
 def scan(ctx, n_views: int, components: str = "P", n_photons: int = 1_000_000, seed: int = 1,
-         mas: float = 0.4, zeta: float = 5.2913e9, bin_factor: int = 4, beta: float = 0.02, iters: int = 300):
-    """Signals [n_views, nv, nu] FP64 (per source photon) of a full orbit."""
+         mas: float = 0.4, zeta: float = 5.2913e9, bin_factor: int = 4, beta: float = 0.02, iters: int = 300,
+         smoothing_px: float | None = None):
+    """Signals [n_views, nv, nu] FP64 (per source photon) of a full orbit.
+
+    beta / smoothing_px set the scatter denoiser of each view as in
+    gdrr.project (smoothing_px: beta from the view's mean scatter count)."""
     import torch
     if components not in ("P", "PS", "PSN"):
         raise ValueError("components must be 'P', 'PS' or 'PSN'")
@@ -43,7 +47,7 @@ def scan(ctx, n_views: int, components: str = "P", n_photons: int = 1_000_000, s
             gdrr.gdrr_raytrace_primary(ctx, float(a), out=sig[i])
             continue
         r = gdrr.project(ctx, n_photons, seed, float(a), bin_factor=bin_factor, beta=beta, iters=iters, mas=mas,
-                         zeta=zeta, angle_index=i)
+                         zeta=zeta, angle_index=i, smoothing_px=smoothing_px)
         s = r["P"] + r["S"]
         if components == "PSN":
             s = s + r["N"]

@@ -9,8 +9,10 @@ to ~1e-5 pixel), so 1e-4 of the volume's largest magnitude bounds it.
 The scan tests reproduce the paper's demonstrations on a synthetic water
 cylinder with a bone rod: no cupping with a mono-energetic source, a cupping
 artifact with a poly-energetic one (beam hardening, Fig. 9(a)-(b)), a lower
-reconstruction when scatter enters (Fig. 9(c)), and noise that scales as
-1/sqrt(mAs) (Fig. 10).
+reconstruction when scatter enters (Fig. 9(c)), the ring shadow of scatter
+behind a bowtie (Fig. 9(d)), and noise that scales as 1/sqrt(mAs) (Fig. 10).
+Every view's scatter denoiser runs with a 4-pixel smoothing length (beta
+from the view's mean count), inside the range where Eq. 5 converges.
 """
 import math
 
@@ -23,7 +25,7 @@ pytestmark = pytest.mark.gpu
 import oracle  # noqa: E402
 from oracle import fdk as ofdk  # noqa: E402
 from paper_1204_6367_gb300 import inputs  # noqa: E402
-from test_oracle_fdk import _ball_projections  # noqa: E402
+from test_oracle_fdk import SHADOW_EDGES, _ball_projections, radial_means, water_cylinder  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -133,7 +135,8 @@ def test_scan_beam_hardening_and_scatter(gd):
     for name, poly, comp in (("mono", False, "P"), ("poly", True, "P"), ("poly_ps", True, "PS")):
         prob = _cylinder(poly)
         with gd.Context(prob) as ctx:
-            angles, sig = scan.scan(ctx, 90, comp, n_photons=1_000_000, seed=5, bin_factor=4, beta=0.02, iters=300)
+            angles, sig = scan.scan(ctx, 90, comp, n_photons=2_000_000, seed=5, bin_factor=4, iters=1000,
+                                    smoothing_px=4.0)
             vol = scan.reconstruct(ctx, angles, sig, prob.material.shape, prob.voxel).cpu().numpy()
         mid = vol[vol.shape[0] // 2]
         out[name] = (mid[centre].mean(), mid[periphery].mean())
@@ -155,9 +158,10 @@ def test_scan_noise_scales_with_mas(gd):
         # 0.019 at 0.1 mAs: noise of about 2 % of the signal, where -ln is close
         # to linear
         for mas in (0.1, 1.0):
-            angles, s = scan.scan(ctx, 60, "PSN", n_photons=200_000, seed=9, mas=mas, zeta=5.2913e9)
+            angles, s = scan.scan(ctx, 60, "PSN", n_photons=200_000, seed=9, mas=mas, zeta=5.2913e9, iters=1000,
+                                  smoothing_px=4.0)
             sig[mas] = s
-        _, s_ps = scan.scan(ctx, 60, "PS", n_photons=200_000, seed=9)
+        _, s_ps = scan.scan(ctx, 60, "PS", n_photons=200_000, seed=9, iters=1000, smoothing_px=4.0)
         vols = {k: scan.reconstruct(ctx, angles, v, prob.material.shape, prob.voxel).cpu().numpy() for k, v in
                 sig.items()}
         v_ps = scan.reconstruct(ctx, angles, s_ps, prob.material.shape, prob.voxel).cpu().numpy()
@@ -165,3 +169,36 @@ def test_scan_noise_scales_with_mas(gd):
     sd = {k: float((v[z] - v_ps[z])[centre].std()) for k, v in vols.items()}
     # the noise image scales as 1 / sqrt(mAs) (Section 2.6, Fig. 10)
     assert sd[0.1] / sd[1.0] == pytest.approx(math.sqrt(10.0), rel=0.05)
+
+
+def test_denoised_view_converges_and_low_counts_warn(gd):
+    prob = _cylinder(True)
+    with gd.Context(prob) as ctx:
+        r = gd.project(ctx, 2_000_000, 5, 0.3, iters=1000, smoothing_px=4.0)
+        cs, beta = r["count_scale"], r["beta"]
+        res = oracle.optimality_residual(r["S_coarse"].cpu().numpy() / cs, r["S_hat_coarse"].cpu().numpy() / cs, beta)
+        assert np.abs(res).max() < 1e-6                     # Eq. 4 holds: the iteration converged
+        # a fixed beta at a low count: beta * mean count far below the
+        # stability floor omega / (8 (1 - omega)) = 0.5
+        assert gd.denoise_stability_floor(0.8) == pytest.approx(0.5)
+        with pytest.warns(RuntimeWarning, match="diverges"):
+            gd.project(ctx, 200_000, 5, 0.3, beta=0.02, iters=50)
+
+
+def test_scan_scatter_shadow_follows_the_bowtie(gd):
+    # the full orbit through the library (independent streams per view)
+    from paper_1204_6367_gb300 import scan
+    deficit = {}
+    for bowtie in (0.0, 30.0):
+        prob = water_cylinder(bowtie)
+        with gd.Context(prob) as ctx:
+            vol = {}
+            for comp in ("P", "PS"):
+                angles, sig = scan.scan(ctx, 90, comp, n_photons=2_000_000, seed=3, iters=1500, smoothing_px=4.0)
+                v = scan.reconstruct(ctx, angles, sig, prob.material.shape, prob.voxel).cpu().numpy()
+                vol[comp] = radial_means(v[v.shape[0] // 2], 2.0, 64, SHADOW_EDGES)
+        deficit[bowtie] = vol["P"] - vol["PS"]
+    centre, middle, ring = deficit[0.0]
+    assert centre > 1.1 * middle > 1.2 * ring > 0                 # no bowtie: cupping, deepest at the centre
+    centre, middle, ring = deficit[30.0]
+    assert ring > 1.3 * middle and ring > 2.5 * abs(centre)       # bowtie: the shadow is a ring (Fig. 9(d))

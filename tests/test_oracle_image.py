@@ -3,7 +3,9 @@
 Step 3 (Section 2.5): the Eq. 5 iteration must converge to the minimiser of
 the convex energy of Eq. 2, i.e. to a zero of the discrete optimality
 condition Eq. 4, independently of the start (convexity), leave a constant
-image unchanged, and reduce to the data as beta -> 0.
+image unchanged, and reduce to the data as beta -> 0.  Linearised, it must
+multiply each cosine mode of a flat image by the closed-form growth factor,
+which puts its convergence floor at beta S = omega / (8 (1 - omega)).
 Step 4 (Section 2.6): the printed calibration example, the 1/sqrt(n) noise
 law, and recovery of a known zeta.
 """
@@ -66,12 +68,56 @@ def test_denoise_independent_of_start():
     np.testing.assert_allclose(a, b, rtol=1e-8)
 
 
+def _cosine_mode(nv, nu, kv, ku):
+    # eigenvectors of the neighbour sum with replicate edges: along an axis of
+    # n pixels cos(pi k (i + 1/2) / n) has eigenvalue 2 cos(pi k / n)
+    j, i = np.indices((nv, nu))
+    v = np.cos(math.pi * ku * (i + 0.5) / nu) * np.cos(math.pi * kv * (j + 0.5) / nv)
+    return v, 2.0 * math.cos(math.pi * ku / nu) + 2.0 * math.cos(math.pi * kv / nv)
+
+
+@pytest.mark.parametrize("omega", [0.8, 0.5])
+@pytest.mark.parametrize("mode", ["checkerboard", "smooth"])
+@pytest.mark.parametrize("beta_c", [0.45, 0.55, 1.0, 3.0])
+def test_denoise_linear_growth_factor(omega, mode, beta_c):
+    # Linearising Eq. 5 at the fixed point S = S^ = c of a flat image: a
+    # perturbation along an eigenvector of the neighbour sum (eigenvalue lam)
+    # is multiplied every iteration by
+    #     g = 1 - omega + (omega / 4) (lam - 1 / (beta c)),
+    # since d/dS (S^ / S) = -S^ / S^2 = -1 / c there.  A wrong relaxation
+    # weight, neighbour sum or sign of the data term changes g.
+    nv, nu, c = 24, 30, 50.0
+    v, lam = _cosine_mode(nv, nu, *((nv - 1, nu - 1) if mode == "checkerboard" else (1, 2)))
+    g = 1.0 - omega + omega / 4.0 * (lam - 1.0 / beta_c)
+    # as many iterations (2 .. 12) as keep the perturbation above 1e-3 of its start
+    k = 12 if abs(g) ** 12 >= 1e-3 else max(2, int(math.log(1e-3) / math.log(abs(g))))
+    eps = 1e-6
+    beta = beta_c / c
+    s = oracle.denoise(np.full((nv, nu), c), beta, omega=omega, iters=k, s0=c + eps * v)
+    amp = float(((s - c) * v).sum() / (v * v).sum()) / eps
+    assert amp == pytest.approx(g**k, rel=1e-5)
+
+
+def test_denoise_stability_bound():
+    # The checkerboard (lam -> -4) limits the iteration: |g| < 1 needs
+    # beta S > omega / (8 (1 - omega)) counts (0.5 at the paper's omega = 0.8),
+    # and no beta makes it stable for omega >= 1.  On a flat image at
+    # beta S = 0.45 a tiny checkerboard grows; at 0.55 it dies out.
+    c, shape = 40.0, (32, 40)
+    v, _ = _cosine_mode(*shape, shape[0] - 1, shape[1] - 1)
+    amp = {}
+    for beta_c in (0.45, 0.55):
+        s = oracle.denoise(np.full(shape, c), beta_c / c, omega=0.8, iters=400, s0=c + 1e-6 * v)
+        amp[beta_c] = np.abs(s - c).max()
+    assert amp[0.45] > 1e-3 and amp[0.55] < 1e-9
+
+
 def test_denoise_constant_and_small_beta():
     c = np.full((16, 20), 123.0)
     np.testing.assert_allclose(oracle.denoise(c, 0.3, iters=50), c, rtol=1e-14)
     # beta -> 0 leaves the data term alone: S -> S^.  The Eq. 5 iteration is
-    # stable only while beta * S > omega / (4 (2 - omega)) (linearisation at
-    # the fixed point), so shrink beta within that range.
+    # stable only while beta * S > omega / (8 (1 - omega)) counts (the
+    # checkerboard bound above), so shrink beta within that range.
     _, s_hat = _smooth_poisson(seed=2)
     dist = [np.linalg.norm(oracle.denoise(s_hat, b, iters=4000) - s_hat) / np.linalg.norm(s_hat)
             for b in (0.05, 0.02, 0.008)]
