@@ -174,7 +174,7 @@ def test_scan_noise_scales_with_mas(gd):
 def test_denoised_view_converges_and_low_counts_warn(gd):
     prob = _cylinder(True)
     with gd.Context(prob) as ctx:
-        r = gd.project(ctx, 2_000_000, 5, 0.3, iters=1000, smoothing_px=4.0)
+        r = gd.project(ctx, 2_000_000, 5, 0.3, iters=2000, smoothing_px=4.0)
         cs, beta = r["count_scale"], r["beta"]
         res = oracle.optimality_residual(r["S_coarse"].cpu().numpy() / cs, r["S_hat_coarse"].cpu().numpy() / cs, beta)
         assert np.abs(res).max() < 1e-6                     # Eq. 4 holds: the iteration converged
