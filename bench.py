@@ -119,11 +119,12 @@ def measured_peak(key, fallback):
         return fallback
 
 
-def kernel_traffic():
-    """DRAM bytes per transport launch from the committed ncu summary, or None
-    when the kernel source changed since those counters were taken."""
+def profile_record(name):
+    """Key/value counters of the transport kernel from a committed ncu summary
+    (profiles/<name>), or None when the kernel source changed since those
+    counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "mc_kernel_torso2mm_traffic.txt")
+    path = os.path.join(ROOT, "profiles", name)
     try:
         vals = dict(l.split() for l in open(path) if l.strip() and not l.startswith("#"))
     except (OSError, ValueError):
@@ -132,7 +133,21 @@ def kernel_traffic():
     h.update(open(os.path.join(ROOT, "paper_1204_6367_gb300", "csrc", "mc_transport.cu"), "rb").read())
     if h.hexdigest()[:16] != vals.get("source_sha256_16"):
         return None
-    return int(vals["bytes_per_launch"])
+    return vals
+
+
+def kernel_traffic():
+    """DRAM bytes per transport launch (ncu), or None for another kernel source."""
+    v = profile_record("mc_kernel_torso2mm_traffic.txt")
+    return int(v["bytes_per_launch"]) if v else None
+
+
+def kernel_inst_per_step():
+    """Thread instructions the transport executes per Woodcock free flight
+    (ncu smsp__thread_inst_executed.sum / free flights of the same launch), or
+    None for another kernel source."""
+    v = profile_record("mc_kernel_torso2mm_issue.txt")
+    return float(v["thread_inst_per_step"]) if v else None
 
 
 def dist_env():
@@ -237,6 +252,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     st = gdrr.stats_dict(stats)
     steps_per_proj = st["steps"]
+    skips_per_proj = gdrr.cell_skips(stats)            # virtual collisions decided without corner gathers
+    gathers_per_proj = steps_per_proj - skips_per_proj
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     ev_mc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -256,9 +273,10 @@ def run_ours(args):
 
     count_scale = float(out["S_hat"].sum().item()) / max(1, st["tally_scatter"])
     # memory ceiling for the transport's access pattern: the same corner
-    # gathers at as many random cells as the projection has free flights
-    gdrr.gdrr_gather_roofline(ctx, min(steps_per_proj, 10**9))
-    probe_s = gdrr.gdrr_gather_roofline(ctx, steps_per_proj)
+    # gathers at as many random cells as the projection gathers (free flights
+    # less those the macro-cell bound decided)
+    gdrr.gdrr_gather_roofline(ctx, min(gathers_per_proj, 10**9))
+    probe_s = gdrr.gdrr_gather_roofline(ctx, gathers_per_proj)
     # machine ceilings measured on this GPU: random 8-byte L2 gathers, FP32 FMA
     l2_probe_gbs = gdrr.gdrr_probe_l2_gather(32 << 20)
     fp32_probe_tflops = gdrr.gdrr_probe_fp32()
@@ -352,7 +370,7 @@ def run_ours(args):
         # the same histories' free flights (identical tallies, so identical
         # flights): algorithmic bytes against the HBM peak and the gather probe
         scan_steps = gdrr.stats_dict(scan_stats)["steps"]
-        scan_probe_s = gdrr.gdrr_gather_roofline(ctx, scan_steps)
+        scan_probe_s = gdrr.gdrr_gather_roofline(ctx, scan_steps - gdrr.cell_skips(scan_stats))
         batched = {"angles": int(angles.size), "histories": tot_hist,
                    "graph_s": graph_s, "plain_64_launches_s": plain_s,
                    "graph_histories_per_s": tot_hist / graph_s, "plain_histories_per_s": tot_hist / plain_s,
@@ -383,7 +401,7 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 ms_v = e0.elapsed_time(e1)
                 sv = gdrr.stats_dict(vstats)
-                probe_v = gdrr.gdrr_gather_roofline(cv, sv["steps"])
+                probe_v = gdrr.gdrr_gather_roofline(cv, sv["steps"] - gdrr.cell_skips(vstats))
                 voxel_sweep[f"{vox:g}mm"] = {
                     "shape_zyx": list(pv.material.shape), "mc_ms": ms_v, "histories_per_s": n_hist / ms_v * 1e3,
                     "free_flights": sv["steps"], "algorithmic_gbs": sv["steps"] * BYTES_PER_STEP_ALGO / ms_v / 1e6,
@@ -408,7 +426,12 @@ def run_ours(args):
         opts = gdrr.gdrr_get_options(ctx)
         for name, kw in (("mc_nearest_voxel_ms", dict(nearest_voxel=1)),
                          ("mc_first_order_compton_ms", dict(scatter_filter=1)),
-                         ("mc_rayleigh_form_factor_ms", dict(rayleigh_form_factor=1))):
+                         ("mc_rayleigh_form_factor_ms", dict(rayleigh_form_factor=1)),
+                         # the macro-cell test of virtual collisions: off, and cells of 4 and 16 voxels
+                         # (the default is 8); tallies are identical in every case
+                         ("mc_no_cell_bound_ms", dict(cell_shift=-1)),
+                         ("mc_cells_4_ms", dict(cell_shift=2)),
+                         ("mc_cells_16_ms", dict(cell_shift=4))):
             gdrr.gdrr_set_options(ctx, **kw)
             vp, vs = gdrr.gdrr_mc_project(ctx, n_hist, seed, angle)
             torch.cuda.synchronize()
@@ -565,6 +588,9 @@ def run_ours(args):
 
     mc_avg_s = statistics.mean(mc_ms) / 1e3
     algo_bytes = steps_per_proj * BYTES_PER_STEP_ALGO
+    n_mat = prob.mu_hat.shape[0]
+    cell_bytes = 4 * (2 if n_mat <= 2 else (4 if n_mat <= 4 else 8))
+    loaded_bytes = gathers_per_proj * RECORD_BYTES_PER_STEP + steps_per_proj * cell_bytes
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -574,6 +600,51 @@ def run_ours(args):
     achieved = algo_bytes / mc_avg_s / 1e9
     value = n_hist * world * args.steps / (tot_ms / 1e3)
     traffic = kernel_traffic()
+
+    # The transport is bound by instruction issue (ncu: issue slots busy,
+    # "not selected" the first stall), not by memory: most tentative collisions
+    # skip the corner gathers, and the phantom is L2-resident.  Its roofline is
+    # the issue rate: thread instructions per free flight (ncu, this kernel
+    # source) x the free flights counted live, over the measured launch time,
+    # against SMs x 4 schedulers x 32 lanes x the maximum SM clock.  The
+    # memory ceilings follow as context.
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    issue_peak = n_sm * 4 * 32 * sm_max_mhz * 1e6 / 1e12
+    inst_per_step = kernel_inst_per_step()
+    memory = {
+        "hbm_roof": {"achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
+                     "what": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} steps "
+                             "(algorithmic) vs MEASURED_PEAKS.json hbm_gbs"},
+        "cell_skips_per_projection": skips_per_proj,
+        "gather_roof": {"probe_ms": 1e3 * probe_s, "frac": probe_s / mc_avg_s,
+                        "what": f"the kernel's own corner gathers alone ({gathers_per_proj} cells: same 8 corners, "
+                                "same layout, random cells, no other work) vs the kernel"},
+        "l2_roof": {"probe_gbs": l2_probe_gbs, "achieved_gbs": loaded_bytes / mc_avg_s / 1e9,
+                    "frac": loaded_bytes / mc_avg_s / 1e9 / l2_probe_gbs,
+                    "what": "random 8-byte loads over a 32 MiB L2-resident set vs the bytes the transport loads: "
+                            f"8 x 8-byte voxel records per gathering flight, one {cell_bytes}-byte macro-cell "
+                            "record per flight"},
+        "fp32_roof": {"probe_tflops": fp32_probe_tflops,
+                      "achieved_tflops": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12,
+                      "frac": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12 / fp32_probe_tflops,
+                      "what": f"{FLOPS_PER_STEP_ALGO} FP32 flops per Woodcock step (trilinear weights, mixture, "
+                              "free path) vs an FMA-chain probe"}}
+    if inst_per_step:
+        issue = inst_per_step * steps_per_proj / mc_avg_s / 1e12
+        roofline = {"bound": "alu", "achieved": issue, "peak": issue_peak, "unit": "Tinst/s",
+                    "frac": issue / issue_peak, "traffic": traffic, "kernel": "mc_kernel",
+                    "peak_source": f"{n_sm} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:g} MHz (one warp "
+                                   "instruction per scheduler per cycle)",
+                    "algorithmic": f"{inst_per_step:.1f} thread instructions per Woodcock step (ncu, this kernel "
+                                   f"source) x {steps_per_proj} steps",
+                    "mc_ms": statistics.mean(mc_ms), **memory}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "mc_kernel",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
+                    "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} "
+                                   "steps", "mc_ms": statistics.mean(mc_ms), **memory}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -589,24 +660,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "histories_per_projection": n_hist, "angle_rad": angle,
                    "woodcock_steps_per_projection": steps_per_proj, "l2": "256 MB buffer written between timed steps",
                    "parallelism": f"one projection angle per GPU x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "mc_kernel",
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
-                     "mc_ms": statistics.mean(mc_ms),
-                     "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} steps",
-                     "gather_roof": {"probe_gbs": algo_bytes / probe_s / 1e9, "probe_ms": 1e3 * probe_s,
-                                     "frac": achieved / (algo_bytes / probe_s / 1e9),
-                                     "what": "same 8-corner gathers, same layout, random cells, no other work"},
-                     "l2_roof": {"probe_gbs": l2_probe_gbs,
-                                 "achieved_gbs": steps_per_proj * RECORD_BYTES_PER_STEP / mc_avg_s / 1e9,
-                                 "frac": steps_per_proj * RECORD_BYTES_PER_STEP / mc_avg_s / 1e9 / l2_probe_gbs,
-                                 "what": "random 8-byte loads over a 32 MiB L2-resident set vs the transport's "
-                                         "8 x 8-byte voxel-record loads per Woodcock step"},
-                     "fp32_roof": {"probe_tflops": fp32_probe_tflops,
-                                   "achieved_tflops": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12,
-                                   "frac": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12 / fp32_probe_tflops,
-                                   "what": f"{FLOPS_PER_STEP_ALGO} FP32 flops per Woodcock step (trilinear weights, "
-                                           "mixture, free path) vs an FMA-chain probe"}},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,

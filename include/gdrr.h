@@ -140,14 +140,29 @@ typedef struct {
                                   corner voxels in proportion to their Rayleigh
                                   coefficient); 0: Thomson (1 + cos^2), the paper's
                                   default reading [0]                                 */
+    int32_t cell_shift;        /* macro cells of 2^cell_shift voxels per edge, 1..6 [3];
+                                  -1: none.  Before gathering the eight corner voxels of
+                                  a tentative collision, the transport compares it with
+                                  a bound on mu over the macro cell that holds the
+                                  corners (the largest density of each material there
+                                  times the material's coefficient, raised by 2^-10
+                                  against rounding); a tentative collision above it is
+                                  virtual without the gathers.  The bound is never below
+                                  the mu the gathers would give, so tallies, counters and
+                                  records are the same for every cell_shift; only
+                                  GDRR_ST_CELL_SKIPS and the time change.  Changing it
+                                  rebuilds the cell table (not while a scan exists).   */
 } gdrr_mc_options;
 
 /* Transport counters, accumulated by every gdrr_mc_project* call (device
- * array of GDRR_NSTATS uint64 in this order). */
+ * array of GDRR_NSTATS uint64 in this order).  The first eleven count events
+ * of the method; GDRR_ST_CELL_SKIPS counts the virtual collisions (included
+ * in GDRR_ST_VIRTUAL) that the macro-cell bound decided without gathering
+ * corner voxels (see gdrr_mc_options.cell_shift). */
 enum {
     GDRR_ST_HISTORIES = 0, GDRR_ST_STEPS, GDRR_ST_VIRTUAL, GDRR_ST_RAYLEIGH, GDRR_ST_COMPTON,
     GDRR_ST_PHOTO, GDRR_ST_TALLY_PRIMARY, GDRR_ST_TALLY_SCATTER, GDRR_ST_MISS, GDRR_ST_CUTOFF,
-    GDRR_ST_STEP_LIMIT, GDRR_NSTATS
+    GDRR_ST_STEP_LIMIT, GDRR_ST_CELL_SKIPS, GDRR_NSTATS
 };
 
 /* Per-history event record (tiny parity runs only). outcome: 0 primary tally,

@@ -51,6 +51,9 @@ struct gdrr_ctx {
     float* d_ff_g = nullptr;
     int n_ff = 0;
     float ff_idx = 0.0f;
+    // macro-cell table of the early virtual-collision test (NULL: none)
+    float* d_cells = nullptr;
+    int cell_shift = -1, ncx = 0, ncy = 0, ncz = 0;
     int n_scans = 0;              // live scans, which captured the table pointers
     int e_col = 0;                // 1: energy CDFs hold one row per detector column
     int n_guide_pix = 0, n_guide_e = 0;
@@ -123,7 +126,8 @@ __global__ void stage_voxels_kernel(const uint8_t* __restrict__ mat, const float
         const int z = (int)(v / ((int64_t)nx * ny));
         const uint32_t m = mat[v];
         const float d = den[v];
-        const uint32_t bits = __float_as_uint(d);
+        // -0 is stored as +0 so that the float bits order like the values
+        const uint32_t bits = d == 0.0f ? 0u : __float_as_uint(d);
         if (m >= (uint32_t)n_mat || !(d >= 0.0f) || !isfinite(d)) {
             atomicAdd(&s_bad, 1u);
         } else {
@@ -134,6 +138,68 @@ __global__ void stage_voxels_kernel(const uint8_t* __restrict__ mat, const float
     __syncthreads();
     if (threadIdx.x < n_mat && s_max[threadIdx.x]) atomicMax(aux + 1 + threadIdx.x, s_max[threadIdx.x]);
     if (threadIdx.x == 0 && s_bad) atomicAdd(aux, s_bad);
+}
+
+// Macro-cell table of the early virtual-collision test.  Cell c of an axis
+// covers voxels [c 2^shift, (c + 1) 2^shift] (its own and the next one): the
+// corners a point can touch whose lower corner lies in the cell.  Each voxel
+// raises its material's entry in every cell that covers it (at most two per
+// axis); float bits of non-negative densities order like the values, so an
+// unsigned atomicMax is exact.  cells: zeroed [cell][slots] words.
+__global__ void build_cells_kernel(const uint2* __restrict__ vox, int nx, int ny, int nz, int bsy, int bsz, int shift,
+                                   int ncx, int ncy, int slots, unsigned int* __restrict__ cells) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= (int64_t)nx * ny * nz) return;
+    const int x = (int)(v % nx);
+    const int y = (int)((v / nx) % ny);
+    const int z = (int)(v / ((int64_t)nx * ny));
+    const uint2 r = vox[(size_t)brick_x(x) + brick_y(y, bsy) + brick_z(z, bsz)];
+    if (r.x == 0u) return;                       // zero density raises nothing
+    const int mask = (1 << shift) - 1;
+    const int cx1 = x >> shift, cy1 = y >> shift, cz1 = z >> shift;
+    const int cx0 = (x > 0 && (x & mask) == 0) ? cx1 - 1 : cx1;
+    const int cy0 = (y > 0 && (y & mask) == 0) ? cy1 - 1 : cy1;
+    const int cz0 = (z > 0 && (z & mask) == 0) ? cz1 - 1 : cz1;
+    for (int cz = cz0; cz <= cz1; ++cz)
+        for (int cy = cy0; cy <= cy1; ++cy)
+            for (int cx = cx0; cx <= cx1; ++cx)
+                atomicMax(cells + ((size_t)(cz * ncy + cy) * ncx + cx) * slots + r.y, r.x);
+}
+
+// (Re)build the macro-cell table for cells of 2^shift voxels per edge, or
+// drop it (shift < 0).  Synchronises the context stream.
+int build_cells(gdrr_ctx* c, int shift) {
+    cudaStream_t s = c->stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GDRR_ERR_CUDA;
+    cudaFree(c->d_cells);
+    c->d_cells = nullptr;
+    c->cell_shift = -1;
+    if (shift < 0) return GDRR_OK;
+    const int ncx = ((c->nx - 1) >> shift) + 1, ncy = ((c->ny - 1) >> shift) + 1, ncz = ((c->nz - 1) >> shift) + 1;
+    const int slots = material_slots(c->n_mat);
+    const size_t bytes = (size_t)ncx * ncy * ncz * slots * sizeof(float);
+    if (cudaMalloc((void**)&c->d_cells, bytes) != cudaSuccess) {
+        c->d_cells = nullptr;
+        return GDRR_ERR_OOM;
+    }
+    int rc = cuda_err(cudaMemsetAsync(c->d_cells, 0, bytes, s));
+    if (!rc) {
+        const int64_t nvox = (int64_t)c->nx * c->ny * c->nz;
+        const int block = 256;
+        build_cells_kernel<<<(unsigned)((nvox + block - 1) / block), block, 0, s>>>(
+            c->d_vox, c->nx, c->ny, c->nz, c->bsy, c->bsz, shift, ncx, ncy, slots,
+            reinterpret_cast<unsigned int*>(c->d_cells));
+        rc = cuda_err(cudaGetLastError());
+    }
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+    if (rc) {
+        cudaFree(c->d_cells);
+        c->d_cells = nullptr;
+        return rc;
+    }
+    c->cell_shift = shift;
+    c->ncx = ncx; c->ncy = ncy; c->ncz = ncz;
+    return GDRR_OK;
 }
 
 // Copy the host phantom to the device and stage it into ctx->d_vox (n_rec
@@ -283,6 +349,7 @@ void set_defaults(gdrr_mc_options* o) {
     if (o->block_size <= 0) o->block_size = 256;
     if (o->hist_per_thread <= 0) o->hist_per_thread = 8;
     if (o->batch_min <= 0) o->batch_min = 16;
+    if (o->cell_shift == 0) o->cell_shift = 3;
 }
 
 int free_ctx(gdrr_ctx* c) {
@@ -291,7 +358,7 @@ int free_ctx(gdrr_ctx* c) {
     void* bufs[] = {c->d_vox, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_kcdf_pix,
                     c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr, c->d_wr_cols,
                     c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise, c->d_tune,
-                    c->d_ff_s, c->d_ff_a, c->d_ff_g};
+                    c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -394,6 +461,7 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         c->bsz = 16 * nbx * nby;
         std::vector<double> rho_max;
         if ((rc = stage_phantom(c, ph, (size_t)16 * nbx * nby * nbz, rho_max))) break;
+        if ((rc = build_cells(c, c->opt.cell_shift))) break;
         // Woodcock majorant nodes: max over materials of the largest density of
         // that material times its total coefficient, with a 1e-5 margin.
         std::vector<float> major(mt.n_energies);
@@ -497,6 +565,12 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
         return GDRR_ERR_INVALID_ARG;
     if (n.rayleigh_form_factor < 0 || n.rayleigh_form_factor > 1 || (n.rayleigh_form_factor && !ctx->n_ff))
         return GDRR_ERR_INVALID_ARG;
+    if (n.cell_shift < -1 || n.cell_shift > 6) return GDRR_ERR_INVALID_ARG;
+    if (n.cell_shift != ctx->cell_shift) {
+        if (ctx->n_scans > 0) return GDRR_ERR_INVALID_ARG;     // scans hold the old table pointer
+        const int rc = build_cells(ctx, n.cell_shift);
+        if (rc) return rc;
+    }
     ctx->opt = n;
     return GDRR_OK;
 }
@@ -638,6 +712,8 @@ static McParams static_mc_params(const gdrr_ctx* ctx) {
     p.n_ff = ctx->n_ff;
     p.ff_s = ctx->d_ff_s; p.ff_a = ctx->d_ff_a; p.ff_g = ctx->d_ff_g;
     p.inv_hc = (float)(1.0 / 12.398419843320026);
+    p.cells = ctx->d_cells;
+    p.cshift = ctx->cell_shift; p.ncx = ctx->ncx; p.ncy = ctx->ncy;
     p.ff_idx = ctx->ff_idx;
     return p;
 }

@@ -101,7 +101,17 @@ struct McParams {
     const float* ff_a;
     const float* ff_g;
     float inv_hc, ff_idx;
+    // macro cells of 2^cshift voxels per edge: per cell and material the
+    // largest density over the voxels [c 2^s, (c + 1) 2^s] of each axis (the
+    // cell and the next voxel), [cell][NM] with NM the kernel's material
+    // slots; NULL disables the early virtual-collision test
+    const float* cells;
+    int cshift, ncx, ncy;
 };
+
+// Material slots of the transport kernel (and of a macro-cell record) for
+// n_mat materials: 2, 4 or 8.
+__host__ __device__ __forceinline__ int material_slots(int n_mat) { return n_mat <= 2 ? 2 : (n_mat <= 4 ? 4 : 8); }
 
 // Ray-tracing parameters.
 struct RtParams {

@@ -19,6 +19,15 @@
 // the per-lane energy-dependent coefficients live in shared memory, indexed
 // by material, one column per thread.
 //
+// Most tentative collisions of Woodcock tracking are virtual (over 90 % in a
+// torso, whose majorant is set by dense bone).  Before the eight corner
+// gathers, a tentative collision is compared with a bound on mu over the
+// macro cell that holds the corners (a small table: the largest density of
+// each material per cell); above it the collision is virtual whatever the
+// corners hold, and the gathers are skipped.  The bound never falls below the
+// mu the gathers give, so every decision, draw and tally is the one plain
+// Woodcock tracking makes.
+//
 // Arithmetic contract.  This file is compiled with -fmad=false: every FP32
 // operation below is one IEEE-rounded operation, evaluated in the order
 // written (divide and square root are the correctly rounded ones).  The only
@@ -50,6 +59,11 @@
 
 namespace gdrr {
 namespace {
+
+// The macro-cell bound is raised by 2^-10, far above the rounding of the
+// eight-corner mixture (eleven FP32 operations on the way to mu, each within
+// 2^-24 relative), so mu as the kernel computes it never exceeds it.
+constexpr float CELL_MARGIN = 1.0009765625f;
 
 // Rejection samplers stop rejecting once their history has drawn this many
 // Philox blocks and keep the candidate in hand (the azimuth takes phi = 0).
@@ -301,6 +315,28 @@ struct Lane {
 
     __device__ __forceinline__ float& cf(int k, int m) { return coef[(k * NM + m) * stride]; }
 
+    // Largest total mu at the lane's energy over a macro cell's voxels: the
+    // cell's per-material maximum densities times the lane's coefficients.
+    // Every corner's term rho_c mu_m(E) is at most this, and the trilinear
+    // weights sum to one, so the mixture mu is at most it too.
+    __device__ __forceinline__ float cell_bound(const McParams& P, int cell) {
+        const float* r = P.cells + (size_t)cell * NM;
+        float b;
+        if constexpr (NM == 2) {
+            const float2 v = __ldg(reinterpret_cast<const float2*>(r));
+            b = fmaxf(v.x * cf(0, 0), v.y * cf(0, 1));
+        } else {
+            b = 0.0f;
+#pragma unroll
+            for (int q = 0; q < NM; q += 4) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(r + q));
+                b = fmaxf(b, fmaxf(fmaxf(v.x * cf(0, q), v.y * cf(0, q + 1)),
+                                   fmaxf(v.z * cf(0, q + 2), v.w * cf(0, q + 3))));
+            }
+        }
+        return b * CELL_MARGIN;
+    }
+
     __device__ __forceinline__ void set_energy(const McParams& P, float en) {
         e = en;
         int ie; float f;
@@ -473,7 +509,7 @@ struct Lane {
     }
 
     // One Woodcock free flight and the real/virtual decision at its end.
-    __device__ __forceinline__ void step(const McParams& P, uint32_t& c_steps, uint32_t& c_virt,
+    __device__ __forceinline__ void step(const McParams& P, uint32_t& c_steps, uint32_t& c_virt, uint32_t& c_skip,
                                          unsigned long long* cnt) {
         if ((int)nsteps >= P.max_steps) {
             count(cnt, GDRR_ST_STEP_LIMIT);
@@ -525,6 +561,18 @@ struct Lane {
         const int x0 = max(gx, 0), x1 = min(gx + 1, P.nx - 1);
         const int y0 = max(gy, 0), y1 = min(gy + 1, P.ny - 1);
         const int z0 = max(gz, 0), z1 = min(gz + 1, P.nz - 1);
+        const float t = uniform(wf.y) * mumax;
+        if (P.cells) {
+            // the corners lie in [x0, x0 + 1] etc., inside the cover of x0's cell:
+            // above the cell's bound the collision is virtual whatever they hold
+            const int cell = (x0 >> P.cshift) + P.ncx * ((y0 >> P.cshift) + P.ncy * (z0 >> P.cshift));
+            if (t > cell_bound(P, cell)) {
+                ++c_virt;
+                ++c_skip;
+                if (REC) ++r_virt;
+                return;
+            }
+        }
         const float wx0 = 1.0f - tx, wy0 = 1.0f - ty, wz0 = 1.0f - tz;
         const float wxy[4] = {wx0 * wy0, tx * wy0, wx0 * ty, tx * ty};
         const int bx[2] = {brick_x(x0), brick_x(x1)};
@@ -543,7 +591,6 @@ struct Lane {
         float muT = a[0] * cf(0, mc[0]);
 #pragma unroll
         for (int c = 1; c < 8; ++c) muT = muT + a[c] * cf(0, mc[c]);
-        const float t = uniform(wf.y) * mumax;
         if (t > muT) {
             ++c_virt;
             if (REC) ++r_virt;
@@ -641,7 +688,7 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
     L.coef = smem + threadIdx.x;
     L.stride = blockDim.x;
     L.state = S_DEAD;
-    uint32_t c_steps = 0, c_virt = 0;
+    uint32_t c_steps = 0, c_virt = 0, c_skip = 0;
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
 
@@ -674,11 +721,12 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
             }
             if (exhausted && !__any_sync(FULL, L.state != S_DEAD)) break;
         }
-        if (L.state == S_FLY) L.step(P, c_steps, c_virt, cnt);
+        if (L.state == S_FLY) L.step(P, c_steps, c_virt, c_skip, cnt);
     }
 
     atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)c_steps);
     atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)c_virt);
+    atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)c_skip);
     __syncthreads();
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
         if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);

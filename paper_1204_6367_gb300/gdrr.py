@@ -18,9 +18,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgdrr.so")
 
-GDRR_NSTATS = 11
+GDRR_NSTATS = 12
+# the method's event counters; slot 11 (cell_skips) is the kernel's own count
+# of virtual collisions the macro-cell bound decided without corner gathers
 STAT_NAMES = ("histories", "steps", "virtual", "rayleigh", "compton", "photo",
               "tally_primary", "tally_scatter", "miss", "cutoff", "step_limit")
+ST_CELL_SKIPS = 11
 TALLY_BITS = 24
 RECORD_DTYPE = np.dtype([
     ("n_steps", "<u4"), ("n_virtual", "<u4"), ("n_rayleigh", "<u4"), ("n_compton", "<u4"),
@@ -70,7 +73,8 @@ class McOptions(ctypes.Structure):
     _fields_ = [("e_cut_kev", ctypes.c_double), ("max_steps", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("hist_per_thread", ctypes.c_int32),
                 ("batch_min", ctypes.c_int32), ("nearest_voxel", ctypes.c_int32),
-                ("scatter_filter", ctypes.c_int32), ("rayleigh_form_factor", ctypes.c_int32)]
+                ("scatter_filter", ctypes.c_int32), ("rayleigh_form_factor", ctypes.c_int32),
+                ("cell_shift", ctypes.c_int32)]
 
 
 class FdkGeometry(ctypes.Structure):
@@ -525,8 +529,14 @@ def gdrr_probe_fp32(stream=None) -> float:
 
 
 def stats_dict(stats) -> dict:
+    """The method's event counters (the oracle counts the same ones)."""
     v = stats.cpu().numpy().view(np.uint64)
     return dict(zip(STAT_NAMES, (int(x) for x in v)))
+
+
+def cell_skips(stats) -> int:
+    """Virtual collisions the macro-cell bound decided without corner gathers."""
+    return int(stats.cpu().numpy().view(np.uint64)[ST_CELL_SKIPS])
 
 
 def records_array(records) -> np.ndarray:

@@ -17,7 +17,7 @@ import bench  # noqa: E402
 def test_traffic_record_matches_the_kernel_source():
     # the committed ncu record belongs to the committed transport source
     t = bench.kernel_traffic()
-    assert isinstance(t, int) and 5e8 < t < 5e9
+    assert isinstance(t, int) and 1e7 < t < 5e9
 
 
 def test_traffic_record_is_dropped_for_another_source(tmp_path, monkeypatch):
@@ -32,6 +32,13 @@ def test_traffic_record_is_dropped_for_another_source(tmp_path, monkeypatch):
     (tmp_path / "paper_1204_6367_gb300" / "csrc" / "mc_transport.cu").write_text(kernel)
     assert bench.kernel_traffic() == int(dict(l.split() for l in src.splitlines()
                                               if l.strip() and not l.startswith("#"))["bytes_per_launch"])
+
+
+def test_instruction_record_matches_the_kernel_source(tmp_path, monkeypatch):
+    ipp = bench.kernel_inst_per_step()
+    assert ipp is not None and 50.0 < ipp < 2000.0
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))           # no record there
+    assert bench.kernel_inst_per_step() is None
 
 
 def test_measured_peak_and_fallback(tmp_path, monkeypatch):

@@ -497,3 +497,101 @@ def test_maximum_bins_and_materials(gd):
     with pytest.raises(gd.GdrrError) as ei:
         gd.Context(prob)
     assert ei.value.code == -6
+
+
+def _run_cells(gd, prob, n, seed, phi, shift, records=False):
+    with gd.Context(prob) as ctx:
+        gd.gdrr_set_options(ctx, cell_shift=shift)
+        assert gd.gdrr_get_options(ctx)["cell_shift"] == shift
+        stats = torch.zeros(gd.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+        rec = torch.zeros(n * gd.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda") if records else None
+        prim, scat = gd.gdrr_mc_project(ctx, n, seed, phi, 0, 0, stats=stats, records=rec)
+        gd.gdrr_sync(ctx)
+        return (prim.cpu().numpy(), scat.cpu().numpy(), gd.stats_dict(stats), gd.cell_skips(stats),
+                gd.records_array(rec) if records else None)
+
+
+def _cell_problem(which):
+    if which == "torso":                                   # 4 material slots
+        return inputs.torso_problem(vox=4.0, nu=128, nv=96, det_px=0.776 * 4)
+    rng = np.random.default_rng(17)
+    if which == "two":                                     # 2 slots: a bone block in air
+        prob = inputs.uniform_slab_problem(nx=20, ny=18, nz=17, nu=16, nv=16, det_px=3.0, pencil=False, mat_id=0,
+                                           density=0.0012, materials=[inputs.AIR, inputs.BONE])
+        prob.material[4:12, 3:15, 9:19] = 1
+        prob.density[4:12, 3:15, 9:19] = rng.uniform(1.2, 1.9, (8, 12, 10)).astype(np.float32)
+    else:                                                  # 8 slots: slabs of eight materials
+        mats = [inputs.AIR, inputs.WATER, inputs.BONE, inputs.LUNG, inputs.ALUMINIUM,
+                inputs.WATER, inputs.BONE, inputs.LUNG]
+        prob = inputs.uniform_slab_problem(nx=16, ny=15, nz=19, nu=16, nv=16, det_px=3.0, pencil=False,
+                                           materials=mats)
+        prob.material[:] = ((np.arange(19) // 3) % 8).astype(np.uint8)[:, None, None]
+        prob.density[:] = rng.uniform(0.0, 2.6, prob.density.shape).astype(np.float32)
+    prob.form_factor = None
+    return prob
+
+
+@pytest.mark.parametrize("which", ["two", "torso", "eight"])
+def test_cell_bound_changes_no_decision(gd, which):
+    # the macro-cell test skips the corner gathers only of collisions that
+    # are virtual anyway: every event record, counter and tally is the same
+    # with cells of 2, 8 or 64 voxels and without the test, and the oracle's
+    prob = _cell_problem(which)
+    n, seed, phi = 1500, 21, 0.7
+    base = _run_cells(gd, prob, n, seed, phi, -1, records=True)
+    assert base[3] == 0
+    otp, ots, ost, orec = oracle.mc_run(prob, n, seed=seed, phi=phi, records=True)
+    for f in oracle.RECORD_DTYPE.names:
+        np.testing.assert_array_equal(base[4][f], orec[f], err_msg=f)
+    assert base[2] == ost
+    np.testing.assert_array_equal(base[0], otp)
+    np.testing.assert_array_equal(base[1], ots)
+    for shift in (1, 3, 6):
+        got = _run_cells(gd, prob, n, seed, phi, shift, records=True)
+        for f in gd.RECORD_DTYPE.names:
+            np.testing.assert_array_equal(got[4][f], base[4][f], err_msg=f"{f} at cell_shift {shift}")
+        assert got[2] == base[2]
+        np.testing.assert_array_equal(got[0], base[0])
+        np.testing.assert_array_equal(got[1], base[1])
+    off = _run_cells(gd, prob, 200_000, 5, 2.1, -1)
+    on = _run_cells(gd, prob, 200_000, 5, 2.1, 3)
+    np.testing.assert_array_equal(on[0], off[0])
+    np.testing.assert_array_equal(on[1], off[1])
+    assert on[2] == off[2] and off[3] == 0
+    assert 0 < on[3] <= on[2]["virtual"]
+
+
+def test_cell_bound_skips_most_virtual_collisions_in_the_torso(gd):
+    # the torso's majorant is set by dense bone; in air, lung and soft-tissue
+    # cells most tentative collisions lie above the cell's bound
+    prob = inputs.torso_problem(vox=4.0, nu=128, nv=96, det_px=0.776 * 4)
+    _, _, st, skips, _ = _run_cells(gd, prob, 300_000, 9, 0.2, 3)
+    assert skips > 0.6 * st["virtual"]
+
+
+def test_cell_shift_option_checks(gd, small):
+    with gd.Context(small) as ctx:
+        assert gd.gdrr_get_options(ctx)["cell_shift"] == 3          # the default
+        for bad in (-2, 7):
+            with pytest.raises(gd.GdrrError):
+                gd.gdrr_set_options(ctx, cell_shift=bad)
+        gd.gdrr_set_options(ctx, cell_shift=0)                     # zero: the default
+        assert gd.gdrr_get_options(ctx)["cell_shift"] == 3
+
+
+def test_negative_zero_density_is_zero(gd):
+    # a density of -0 is a density of zero: staged as +0, it neither lowers a
+    # material's largest density (the majorant) nor the cell table
+    prob = _cell_problem("two")
+    prob.density[5, 5, 10] = 0.0                                   # a bone voxel
+    neg = _cell_problem("two")
+    neg.density[5, 5, 10] = -0.0
+    assert np.signbit(neg.density[5, 5, 10])
+    n = 100_000
+    a = _run_cells(gd, prob, n, 3, 0.4, 3)
+    b = _run_cells(gd, neg, n, 3, 0.4, 3)
+    otp, ots, ost, _ = oracle.mc_run(neg, n, seed=3, phi=0.4, threads=NTH)
+    for got in (a, b):
+        assert got[2] == ost
+        np.testing.assert_array_equal(got[0], otp)
+        np.testing.assert_array_equal(got[1], ots)
