@@ -119,10 +119,11 @@ def measured_peak(key, fallback):
         return fallback
 
 
-def profile_record(name):
+def profile_record(name, cell_shift=None):
     """Key/value counters of the transport kernel from a committed ncu summary
     (profiles/<name>), or None when the kernel source changed since those
-    counters were taken."""
+    counters were taken, or (cell_shift given) they were taken with other
+    macro cells."""
     import hashlib
     path = os.path.join(ROOT, "profiles", name)
     try:
@@ -133,20 +134,23 @@ def profile_record(name):
     h.update(open(os.path.join(ROOT, "paper_1204_6367_gb300", "csrc", "mc_transport.cu"), "rb").read())
     if h.hexdigest()[:16] != vals.get("source_sha256_16"):
         return None
+    if cell_shift is not None and str(cell_shift) != vals.get("cell_shift"):
+        return None
     return vals
 
 
-def kernel_traffic():
-    """DRAM bytes per transport launch (ncu), or None for another kernel source."""
-    v = profile_record("mc_kernel_torso2mm_traffic.txt")
+def kernel_traffic(cell_shift=None):
+    """DRAM bytes per transport launch (ncu), or None for another kernel source
+    or other macro cells."""
+    v = profile_record("mc_kernel_torso2mm_traffic.txt", cell_shift)
     return int(v["bytes_per_launch"]) if v else None
 
 
-def kernel_inst_per_step():
+def kernel_inst_per_step(cell_shift=None):
     """Thread instructions the transport executes per Woodcock free flight
     (ncu smsp__thread_inst_executed.sum / free flights of the same launch), or
-    None for another kernel source."""
-    v = profile_record("mc_kernel_torso2mm_issue.txt")
+    None for another kernel source or other macro cells."""
+    v = profile_record("mc_kernel_torso2mm_issue.txt", cell_shift)
     return float(v["thread_inst_per_step"]) if v else None
 
 
@@ -599,7 +603,7 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = algo_bytes / mc_avg_s / 1e9
     value = n_hist * world * args.steps / (tot_ms / 1e3)
-    traffic = kernel_traffic()
+    traffic = kernel_traffic(tuned["cell_shift"])
 
     # The transport is bound by instruction issue (ncu: issue slots busy,
     # "not selected" the first stall), not by memory: most tentative collisions
@@ -611,7 +615,7 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     issue_peak = n_sm * 4 * 32 * sm_max_mhz * 1e6 / 1e12
-    inst_per_step = kernel_inst_per_step()
+    inst_per_step = kernel_inst_per_step(tuned["cell_shift"])
     memory = {
         "hbm_roof": {"achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
                      "what": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} steps "

@@ -140,8 +140,10 @@ typedef struct {
                                   corner voxels in proportion to their Rayleigh
                                   coefficient); 0: Thomson (1 + cos^2), the paper's
                                   default reading [0]                                 */
-    int32_t cell_shift;        /* macro cells of 2^cell_shift voxels per edge, 1..6 [3];
-                                  -1: none.  Before gathering the eight corner voxels of
+    int32_t cell_shift;        /* macro cells of 2^cell_shift voxels per edge, 1..6;
+                                  -1: none; [0: cells of about 8 mm, cell_shift =
+                                  round(log2(8 mm / smallest voxel edge)) in 1..6].
+                                  Before gathering the eight corner voxels of
                                   a tentative collision, the transport compares it with
                                   a bound on mu over the macro cell that holds the
                                   corners (the largest density of each material there

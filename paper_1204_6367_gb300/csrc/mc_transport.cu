@@ -26,7 +26,9 @@
 // each material per cell); above it the collision is virtual whatever the
 // corners hold, and the gathers are skipped.  The bound never falls below the
 // mu the gathers give, so every decision, draw and tally is the one plain
-// Woodcock tracking makes.
+// Woodcock tracking makes.  A flight that passes the test waits, like the rare
+// events, for the warp's service batch, where its gathers run together with
+// those of the warp's other waiting lanes.
 //
 // Arithmetic contract.  This file is compiled with -fmad=false: every FP32
 // operation below is one IEEE-rounded operation, evaluated in the order
@@ -287,7 +289,7 @@ enum : uint32_t { OUT_PRIMARY = 0, OUT_SCATTER = 1, OUT_PHOTO = 2, OUT_CUTOFF = 
 // history waits in one of the non-FLY states until enough lanes of its warp
 // wait too; the warp then serves them together, which keeps the expensive
 // rare branches from running with one or two active lanes.
-enum : int { S_DEAD = 0, S_FLY = 1, S_RAY = 2, S_COMP = 3, S_ESC = 4 };
+enum : int { S_DEAD = 0, S_FLY = 1, S_RAY = 2, S_COMP = 3, S_ESC = 4, S_GATHER = 5 };
 
 // Block-shared counters (GDRR_NSTATS), flushed to the stats array at exit.
 __device__ __forceinline__ void count(unsigned long long* c, int k) { atomicAdd(c + k, 1ull); }
@@ -302,6 +304,8 @@ struct Lane {
     uint32_t nsteps;
     uint32_t n_int;      // Compton interactions (low 16 bits) and Rayleigh (high 16 bits)
     int m_ray;           // material of the pending form-factor Rayleigh event (GEN)
+    float tg;            // t = xi mu_max of a flight waiting for its corner gathers
+    uint32_t wz;         // that flight block's third word (GEN: form-factor material pick)
     Stream rs;
     // per-thread coefficient tables in shared memory: coef[k][m][tid],
     // k = 0 total, 1 Rayleigh, 2 Compton (photoelectric is the remainder)
@@ -550,17 +554,11 @@ struct Lane {
             return;
         }
 
-        // trilinear corner weights (w_x w_y) w_z and clamped corner indices
-        const float fx = (px - P.lo[0]) * P.ivox[0] - 0.5f;
-        const float fy = (py - P.lo[1]) * P.ivox[1] - 0.5f;
-        const float fz = (pz - P.lo[2]) * P.ivox[2] - 0.5f;
-        const int gx = (int)floorf(fx), gy = (int)floorf(fy), gz = (int)floorf(fz);
-        const float tx = fx - (float)gx, ty = fy - (float)gy, tz = fz - (float)gz;
-        // inside the box f lies in [-1/2, n - 1/2], so g in [-1, n - 1]: the
-        // lower corner clamps only from below, the upper only from above
-        const int x0 = max(gx, 0), x1 = min(gx + 1, P.nx - 1);
-        const int y0 = max(gy, 0), y1 = min(gy + 1, P.ny - 1);
-        const int z0 = max(gz, 0), z1 = min(gz + 1, P.nz - 1);
+        // the lower trilinear corner, computed as gather() computes it,
+        // locates the macro cell
+        const int x0 = max((int)floorf((px - P.lo[0]) * P.ivox[0] - 0.5f), 0);
+        const int y0 = max((int)floorf((py - P.lo[1]) * P.ivox[1] - 0.5f), 0);
+        const int z0 = max((int)floorf((pz - P.lo[2]) * P.ivox[2] - 0.5f), 0);
         const float t = uniform(wf.y) * mumax;
         if (P.cells) {
             // the corners lie in [x0, x0 + 1] etc., inside the cover of x0's cell:
@@ -573,6 +571,29 @@ struct Lane {
                 return;
             }
         }
+        // the corner gathers wait for the warp's service batch
+        tg = t;
+        if (GEN) wz = wf.z;
+        state = S_GATHER;
+    }
+
+    // The deferred part of a free flight that passed the macro-cell test:
+    // the eight-corner mixture at the lane's position and the real/virtual
+    // decision for its t.  The warp serves its waiting lanes together, so the
+    // gathers run on many lanes at once instead of on the few whose flights
+    // passed the test in one iteration.
+    __device__ __forceinline__ void gather(const McParams& P, uint32_t& c_virt, unsigned long long* cnt) {
+        const float t = tg;
+        const float fx = (px - P.lo[0]) * P.ivox[0] - 0.5f;
+        const float fy = (py - P.lo[1]) * P.ivox[1] - 0.5f;
+        const float fz = (pz - P.lo[2]) * P.ivox[2] - 0.5f;
+        const int gx = (int)floorf(fx), gy = (int)floorf(fy), gz = (int)floorf(fz);
+        const float tx = fx - (float)gx, ty = fy - (float)gy, tz = fz - (float)gz;
+        // inside the box f lies in [-1/2, n - 1/2], so g in [-1, n - 1]: the
+        // lower corner clamps only from below, the upper only from above
+        const int x0 = max(gx, 0), x1 = min(gx + 1, P.nx - 1);
+        const int y0 = max(gy, 0), y1 = min(gy + 1, P.ny - 1);
+        const int z0 = max(gz, 0), z1 = min(gz + 1, P.nz - 1);
         const float wx0 = 1.0f - tx, wy0 = 1.0f - ty, wz0 = 1.0f - tz;
         const float wxy[4] = {wx0 * wy0, tx * wy0, wx0 * ty, tx * ty};
         const int bx[2] = {brick_x(x0), brick_x(x1)};
@@ -594,6 +615,7 @@ struct Lane {
         if (t > muT) {
             ++c_virt;
             if (REC) ++r_virt;
+            state = S_FLY;
             return;
         }
         float muR = a[0] * cf(1, mc[0]);
@@ -605,7 +627,7 @@ struct Lane {
         if (GEN && P.ray_ff && t <= muR) {
             // the form factor's material: the corner whose Rayleigh share of
             // mu_R holds xi mu_R, xi the flight block's third word
-            const float target = uniform(wf.z) * muR;
+            const float target = uniform(wz) * muR;
             float acc = 0.0f;
             m_ray = mc[7];
 #pragma unroll
@@ -695,7 +717,9 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
     for (;;) {
         const unsigned fly = __ballot_sync(FULL, L.state == S_FLY);
         if (32 - __popc(fly) >= P.batch_min || fly == 0u) {
-            // serve waiting lanes together: interactions, tallies, new histories
+            // serve waiting lanes together: corner gathers, interactions,
+            // tallies, new histories
+            if (L.state == S_GATHER) L.gather(P, c_virt, cnt);
             if (L.state == S_RAY || L.state == S_COMP) L.interact(P, cnt);
             if (L.state == S_ESC) L.escape(P, cnt, true);
             if (!exhausted) {

@@ -37,6 +37,10 @@ def test_traffic_record_is_dropped_for_another_source(tmp_path, monkeypatch):
 def test_instruction_record_matches_the_kernel_source(tmp_path, monkeypatch):
     ipp = bench.kernel_inst_per_step()
     assert ipp is not None and 50.0 < ipp < 2000.0
+    # the records name the macro cells they were taken with
+    shift = int(bench.profile_record("mc_kernel_torso2mm_issue.txt")["cell_shift"])
+    assert bench.kernel_inst_per_step(shift) == ipp and bench.kernel_inst_per_step(shift + 1) is None
+    assert bench.kernel_traffic(shift) is not None and bench.kernel_traffic(shift + 1) is None
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))           # no record there
     assert bench.kernel_inst_per_step() is None
 

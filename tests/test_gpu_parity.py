@@ -570,13 +570,18 @@ def test_cell_bound_skips_most_virtual_collisions_in_the_torso(gd):
 
 
 def test_cell_shift_option_checks(gd, small):
+    # the default cells are about 8 mm: 2 voxels of 4 mm, 4 of 2 mm, 8 of 1 mm
+    for vox, shift in ((4.0, 1), (2.0, 2), (1.0, 3), (0.5, 4)):
+        prob = inputs.uniform_slab_problem(nx=8, ny=8, nz=8, vox=vox)
+        with gd.Context(prob) as ctx:
+            assert gd.gdrr_get_options(ctx)["cell_shift"] == shift
     with gd.Context(small) as ctx:
-        assert gd.gdrr_get_options(ctx)["cell_shift"] == 3          # the default
         for bad in (-2, 7):
             with pytest.raises(gd.GdrrError):
                 gd.gdrr_set_options(ctx, cell_shift=bad)
+        gd.gdrr_set_options(ctx, cell_shift=5)
         gd.gdrr_set_options(ctx, cell_shift=0)                     # zero: the default
-        assert gd.gdrr_get_options(ctx)["cell_shift"] == 3
+        assert gd.gdrr_get_options(ctx)["cell_shift"] == 1
 
 
 def test_negative_zero_density_is_zero(gd):
