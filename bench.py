@@ -154,6 +154,30 @@ def kernel_inst_per_step(cell_shift=None):
     return float(v["thread_inst_per_step"]) if v else None
 
 
+def transport_roofline(inst_per_step, steps, mc_s, n_sm, sm_max_mhz, traffic, memory, hbm_peak):
+    """The transport's roofline entry.  With an instruction record for this
+    kernel source: the issue rate (thread instructions per free flight x free
+    flights / launch time) against SMs x 4 schedulers x 32 lanes x the
+    maximum SM clock.  Without one: algorithmic voxel bytes against the HBM
+    copy peak.  The memory ceilings ride along as context."""
+    peak = n_sm * 4 * 32 * sm_max_mhz * 1e6 / 1e12
+    if inst_per_step:
+        issue = inst_per_step * steps / mc_s / 1e12
+        return {"bound": "alu", "achieved": issue, "peak": peak, "unit": "Tinst/s", "frac": issue / peak,
+                "traffic": traffic, "kernel": "mc_kernel",
+                "peak_source": f"{n_sm} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:g} MHz (one warp "
+                               "instruction per scheduler per cycle)",
+                "algorithmic": f"{inst_per_step:.1f} thread instructions per Woodcock step (ncu, this kernel "
+                               f"source) x {steps} steps",
+                "mc_ms": 1e3 * mc_s, **memory}
+    achieved = steps * BYTES_PER_STEP_ALGO / mc_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": traffic, "kernel": "mc_kernel",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
+            "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps} steps",
+            "mc_ms": 1e3 * mc_s, **memory}
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -614,7 +638,6 @@ def run_ours(args):
     # memory ceilings follow as context.
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    issue_peak = n_sm * 4 * 32 * sm_max_mhz * 1e6 / 1e12
     inst_per_step = kernel_inst_per_step(tuned["cell_shift"])
     memory = {
         "hbm_roof": {"achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
@@ -634,21 +657,8 @@ def run_ours(args):
                       "frac": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12 / fp32_probe_tflops,
                       "what": f"{FLOPS_PER_STEP_ALGO} FP32 flops per Woodcock step (trilinear weights, mixture, "
                               "free path) vs an FMA-chain probe"}}
-    if inst_per_step:
-        issue = inst_per_step * steps_per_proj / mc_avg_s / 1e12
-        roofline = {"bound": "alu", "achieved": issue, "peak": issue_peak, "unit": "Tinst/s",
-                    "frac": issue / issue_peak, "traffic": traffic, "kernel": "mc_kernel",
-                    "peak_source": f"{n_sm} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:g} MHz (one warp "
-                                   "instruction per scheduler per cycle)",
-                    "algorithmic": f"{inst_per_step:.1f} thread instructions per Woodcock step (ncu, this kernel "
-                                   f"source) x {steps_per_proj} steps",
-                    "mc_ms": statistics.mean(mc_ms), **memory}
-    else:
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "mc_kernel",
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
-                    "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} "
-                                   "steps", "mc_ms": statistics.mean(mc_ms), **memory}
+    roofline = transport_roofline(inst_per_step, steps_per_proj, mc_avg_s, n_sm, sm_max_mhz, traffic, memory,
+                                  hbm_peak)
 
     cpu = None
     if not args.no_cpu_baseline:

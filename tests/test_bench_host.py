@@ -66,3 +66,17 @@ def test_reference_leg_prints_the_contract_line():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_transport_roofline_entry():
+    # with an instruction record: the issue rate against 152 x 4 x 32 lanes x 2.07 GHz
+    mem = {"hbm_roof": {"frac": 0.27}}
+    r = bench.transport_roofline(275.3, 4.593e9, 0.0988, 152, 2070.0, 51540736, mem, 6790.3)
+    assert r["bound"] == "alu" and r["unit"] == "Tinst/s"
+    assert r["peak"] == pytest.approx(40.28, rel=1e-3) and r["frac"] == pytest.approx(0.3177, rel=1e-3)
+    assert r["traffic"] == 51540736 and r["hbm_roof"] == {"frac": 0.27} and r["mc_ms"] == pytest.approx(98.8)
+    json.dumps(r)
+    # without one: algorithmic voxel bytes against the HBM copy peak
+    h = bench.transport_roofline(None, 4.593e9, 0.0988, 152, 2070.0, None, mem, 6790.3)
+    assert h["bound"] == "hbm" and h["unit"] == "GB/s" and h["traffic"] is None
+    assert h["frac"] == pytest.approx(40 * 4.593e9 / 0.0988 / 1e9 / 6790.3)
