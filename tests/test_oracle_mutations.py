@@ -89,6 +89,10 @@ MUTATIONS = [
     ("oracle.py", "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[:-2, 1:-1]\n        s = ",
      "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[1:-1, 1:-1]\n        s = ",
      "denoiser stencil", "test_oracle_image.py"),
+    ("oracle.py", "s = (1.0 - omega) * s + (omega / 4.0) * (sigma", "s = (1.0 - omega) * s + (omega / 2.0) * (sigma",
+     "denoiser relaxation weight", "test_oracle_image.py"),
+    ("oracle.py", "        p = np.pad(s, 1, mode=\"edge\")\n        sigma", "        p = np.pad(s, 1, mode=\"wrap\")\n        sigma",
+     "denoiser edges wrap around instead of replicating", "test_oracle_image.py"),
     ("oracle.py", "return n_hat * np.sqrt(float(n_sim) / (zeta * mas))", "return n_hat * np.sqrt(float(n_sim) * (zeta * mas))",
      "noise scaling", "test_oracle_image.py"),
 ]
