@@ -581,7 +581,10 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
     if (n.cell_shift != ctx->cell_shift) {
         if (ctx->n_scans > 0) return GDRR_ERR_INVALID_ARG;     // scans hold the old table pointer
         const int rc = build_cells(ctx, n.cell_shift);
-        if (rc) return rc;
+        if (rc) {
+            ctx->opt.cell_shift = ctx->cell_shift;              // -1: the table is gone
+            return rc;
+        }
     }
     ctx->opt = n;
     return GDRR_OK;
