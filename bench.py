@@ -553,13 +553,13 @@ def run_ours(args):
                     pred = sn.predict(net, xl)
                     e1.record(stream)
                     s8, st8 = sn.simulate(cl, 10**8, 57 + 10 * sd + a, ang, a)
-                    judge = sn.denoise(cl, s8, st8, 10**8, sn.HIGH_LENGTH)
+                    plain8 = sn.denoise(cl, s8, st8, 10**8, sn.HIGH_LENGTH)
                     e2.record(stream)
                     torch.cuda.synchronize()
                     cost.setdefault("learned_ms", []).append(e0.elapsed_time(e1))
                     cost.setdefault("plain_1e8_ms", []).append(e1.elapsed_time(e2))
                     e_net.append(sn.rel_l2(pred.cpu().numpy()[0], ref))
-                    e_plain[10**8].append(sn.rel_l2(judge.cpu().numpy(), ref))
+                    e_plain[10**8].append(sn.rel_l2(plain8.cpu().numpy(), ref))
                     for n in plain_counts[:-1]:
                         sp_, stp = sn.simulate(cl, n, 31 + 10 * sd + a, ang, a)
                         e_plain[n].append(sn.rel_l2(sn.denoise(cl, sp_, stp, n, sn.plain_length(n)).cpu().numpy(),

@@ -5,7 +5,7 @@ The plain method (Section 2.4 Monte Carlo + the Poisson denoiser of Section
 library's convolutional encoder-decoder (gdrr_cnn_*) to map a cheap,
 low-photon Monte Carlo scatter image plus the ray-traced primary to the
 scatter image of a high-photon run, on pairs the method itself generates;
-the plain method stays the reference and the judge of the error.
+the plain method stays the reference the error is measured against.
 
 Everything that computes runs in libgdrr kernels: Monte Carlo, ray tracing,
 finalisation, denoising, scaling into the network's FP32 input, and the
@@ -64,7 +64,7 @@ def plain_length(n: int) -> float:
 
 
 LOW_LENGTH = plain_length(10**6)      # the low-photon input (12 px)
-HIGH_LENGTH = plain_length(10**8)     # the high-photon targets and the judge (4.1 px)
+HIGH_LENGTH = plain_length(10**8)     # the high-photon targets and the 1e8 comparison (4.1 px)
 
 
 def low_input(ctx, n_low: int, seed: int, angle: float, angle_index: int, x_slot):
@@ -163,7 +163,7 @@ def evaluate(net, seeds=(900, 901, 902, 903), angles_per_seed=2, n_low=10**6, n_
 
 
 def main(argv=None):
-    """Train and judge the estimator at a chosen scale; prints one JSON line."""
+    """Train and evaluate the estimator at a chosen scale; prints one JSON line."""
     import argparse
     import json
     import time

@@ -97,7 +97,7 @@ def test_mc_primary_matches_rt(small):
     assert abs(np.mean((p_mc[m] - p_rt[m]) / p_rt[m])) < 0.01
     # per-pixel: counts are ~binomial; in-pixel variation of the path length
     # gives the MC pixel a slightly different mean than the centre ray, so
-    # judge the bulk, not the tail.
+    # assess the bulk, not the tail.
     counts = tp[m] / (60.0 * 2**24)
     mean = p_rt[m] / 60.0 * n
     z = (counts - mean) / np.sqrt(mean)
