@@ -89,6 +89,11 @@ MUTATIONS = [
     ("oracle.py", "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[:-2, 1:-1]\n        s = ",
      "sigma = ((p[1:-1, 2:] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[1:-1, 1:-1]\n        s = ",
      "denoiser stencil", "test_oracle_image.py"),
+    ("mc_history.inc", "*e_out = e / x;", "*e_out = e;",
+     "Compton-scattered photon keeps its energy", "test_oracle_scatter_geometry.py"),
+    ("mc_history.inc", "int64_t q = (int64_t)LLRINTR(FN(response)(c, e) * RC(16777216.0));",
+     "int64_t q = (int64_t)LLRINTR(FN(response)(c, (REAL)r.e_source) * RC(16777216.0));",
+     "detector response at the source energy", "test_oracle_scatter_geometry.py"),
     ("oracle.py", "s = (1.0 - omega) * s + (omega / 4.0) * (sigma", "s = (1.0 - omega) * s + (omega / 2.0) * (sigma",
      "denoiser relaxation weight", "test_oracle_image.py"),
     ("oracle.py", "        p = np.pad(s, 1, mode=\"edge\")\n        sigma", "        p = np.pad(s, 1, mode=\"wrap\")\n        sigma",
