@@ -573,6 +573,8 @@ def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin
     falls below denoise_stability_floor(omega) (a warning says so).
     smoothing_px, when given, replaces beta by smoothing_px^2 / (mean coarse
     count): a smoothing length in coarse pixels, the same at any photon count.
+    stats, when given, is a device GDRR_NSTATS counter array that must be zero
+    on entry: its scatter count sets the count scale.
     """
     import torch
     own_stats = stats is None
@@ -584,14 +586,15 @@ def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin
     S_hat = gdrr_finalize(ctx, scat, n_photons)
     S_hat_c = gdrr_finalize(ctx, gdrr_bin_tally(ctx, scat, bin_factor), n_photons)
     st = stats_dict(stats) if own_stats else None
-    n_det = max(1, (st or stats_dict(stats))["tally_scatter"])
-    count_scale = float(S_hat.sum().item()) / n_det if n_det else 1.0
+    n_scat = (st or stats_dict(stats))["tally_scatter"]
+    n_det = max(1, n_scat)
+    count_scale = float(S_hat.sum().item()) / n_det
     if not count_scale > 0:
         count_scale = 1.0 / n_photons
     mean_count = n_det / S_hat_c.numel()
     if smoothing_px is not None:
         beta = smoothing_px * smoothing_px / max(mean_count, 1e-6)
-    elif beta * mean_count < denoise_stability_floor(omega):
+    elif n_scat > 0 and beta * mean_count < denoise_stability_floor(omega):
         warnings.warn(f"beta * mean scatter count = {beta * mean_count:.3g} is below "
                       f"{denoise_stability_floor(omega):.3g}: the Eq. 5 iteration diverges on most of the image "
                       "(raise beta, n_photons or bin_factor, or pass smoothing_px)", RuntimeWarning, stacklevel=2)
