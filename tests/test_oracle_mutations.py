@@ -91,6 +91,11 @@ MUTATIONS = [
      "denoiser stencil", "test_oracle_image.py"),
     ("mc_history.inc", "*e_out = e / x;", "*e_out = e;",
      "Compton-scattered photon keeps its energy", "test_oracle_scatter_geometry.py"),
+    ("mc_history.inc", "nw_ = w * ct - st * t * cp;", "nw_ = w * ct + st * t * cp;",
+     "rotation sign, seen through multiple scattering", "test_oracle_analog.py"),
+    ("mc_history.inc", "channel = t <= muR ? 1 : (t <= muR + muC ? 2 : 3);",
+     "channel = t <= muR ? 1 : (t <= muR + muR ? 2 : 3);",
+     "interaction channels, seen in the scatter image", "test_oracle_analog.py"),
     ("mc_history.inc", "int64_t q = (int64_t)LLRINTR(FN(response)(c, e) * RC(16777216.0));",
      "int64_t q = (int64_t)LLRINTR(FN(response)(c, (REAL)r.e_source) * RC(16777216.0));",
      "detector response at the source energy", "test_oracle_scatter_geometry.py"),
