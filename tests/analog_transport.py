@@ -1,14 +1,17 @@
-"""An independent analog photon transport for a homogeneous cube, for
-testing the oracle by brute force.
+"""An independent analog photon transport for a phantom that varies along x
+only (layers of voxels), for testing the oracle by brute force.
 
-It shares nothing with the oracle's transport but the problem's tables: free
-paths are drawn from the exponential law of the local total coefficient (no
-Woodcock tracking), Klein-Nishina angles by rejection from the uniform law of
-cos theta, Thomson angles by inverting their cumulative (Cardano's formula),
-azimuths as uniform angles, and new directions from an explicit orthonormal
-frame.  Random numbers come from numpy's generator.  Photons are transported
-in vectorised rounds: each round moves every live photon to its next
-interaction or out of the cube.
+It shares nothing with the oracle's transport but the problem's tables.  The
+method's trilinear field of such a phantom is linear in x between voxel
+centres and constant beyond the outer centres (clamp to edge), so the
+optical depth along a ray is a piecewise-quadratic function of x: free paths
+are drawn by inverting it exactly for an exponential optical depth (no
+Woodcock tracking).  Klein-Nishina angles come by rejection from the uniform
+law of cos theta, Thomson angles by inverting their cumulative (Cardano's
+formula), azimuths as uniform angles, new directions from an explicit
+orthonormal frame, random numbers from numpy's generator.  Photons are
+transported in vectorised rounds: each round moves every live photon to its
+next interaction or out of the box.
 """
 import math
 
@@ -17,16 +20,77 @@ import numpy as np
 MEC2 = 510.99895
 
 
-def _coeffs(prob, e):
-    """mu_R, mu_C, mu_P in 1/mm of the cube's material at energies e (linear
-    between the table's 1 keV nodes)."""
-    m = int(prob.material.flat[0])
-    rho = float(prob.density.flat[0])
-    tab = prob.mu_hat[m].astype(np.float64)
-    x = (e - prob.e0) / prob.de
-    i = np.clip(np.floor(x).astype(int), 0, tab.shape[1] - 2)
-    f = x - i
-    return [(tab[k, i] + f * (tab[k, i + 1] - tab[k, i])) * 0.1 * rho for k in range(3)]
+class _Layers:
+    """Coefficients of a phantom whose voxels vary along x only."""
+
+    def __init__(self, prob):
+        mat, den = prob.material, prob.density
+        if not ((mat == mat[:1, :1, :]).all() and (den == den[:1, :1, :]).all()):
+            raise ValueError("the analog transport needs a phantom that varies along x only")
+        nx = mat.shape[2]
+        vox = float(prob.voxel[0])
+        self.half = 0.5 * nx * vox
+        self.m = mat[0, 0, :].astype(np.int64)
+        self.rho = den[0, 0, :].astype(np.float64)
+        centres = (np.arange(nx) + 0.5) * vox - self.half
+        self.knots = np.concatenate([[-self.half], centres, [self.half]])
+        self.tab = prob.mu_hat.astype(np.float64) * 0.1           # 1/mm per g/cm^3, [m, k, e]
+        self.e0, self.de = prob.e0, prob.de
+
+    def knot_mu(self, e):
+        """mu_k at the knots for energies e: [N, knots, 3] (linear in E between
+        the table's nodes; the end knots repeat the outer centres)."""
+        x = (e - self.e0) / self.de
+        i = np.clip(np.floor(x).astype(np.int64), 0, self.tab.shape[2] - 2)
+        f = (x - i)[:, None, None]
+        t = self.tab[:, :, i] + f.transpose(1, 2, 0) * (self.tab[:, :, i + 1] - self.tab[:, :, i])   # [M, 3, N]
+        cen = self.rho[None, :, None] * t[self.m].transpose(2, 0, 1)                           # [N, nx, 3]
+        return np.concatenate([cen[:, :1], cen, cen[:, -1:]], axis=1)
+
+    def coeffs(self, x, e):
+        """mu_R, mu_C, mu_P at positions x (the x coordinate) for energies e."""
+        mu = self.knot_mu(e)
+        j = np.clip(np.searchsorted(self.knots, x, side="right") - 1, 0, len(self.knots) - 2)
+        f = np.clip((x - self.knots[j]) / (self.knots[j + 1] - self.knots[j]), 0.0, 1.0)
+        r = np.arange(len(x))
+        v = mu[r, j] + f[:, None] * (mu[r, j + 1] - mu[r, j])
+        return v[:, 0], v[:, 1], v[:, 2]
+
+    def free_path(self, x0, dx, e, tau):
+        """Distance along rays (x coordinate x0, direction cosine dx) at which
+        the optical depth of mu_T reaches tau; inf when it is not reached
+        before the last knot."""
+        mu = self.knot_mu(e).sum(axis=2)                                        # [N, K]
+        K = self.knots
+        h = np.diff(K)
+        seg = 0.5 * (mu[:, 1:] + mu[:, :-1]) * h[None, :]
+        C = np.concatenate([np.zeros((len(x0), 1)), np.cumsum(seg, axis=1)], axis=1)
+
+        def F(x):                                                               # integral of mu_T from -half
+            j = np.clip(np.searchsorted(K, x, side="right") - 1, 0, len(K) - 2)
+            r = np.arange(len(x))
+            slope = (mu[r, j + 1] - mu[r, j]) / h[j]
+            dxk = x - K[j]
+            return C[r, j] + dxk * mu[r, j] + 0.5 * slope * dxk * dxk
+
+        s = np.full(len(x0), np.inf)
+        flat = np.abs(dx) < 1e-12
+        if flat.any():                                                          # parallel to the layers
+            mT = sum(self.coeffs(x0[flat], e[flat]))
+            s[flat] = tau[flat] / mT
+        ok = ~flat
+        if ok.any():
+            r = np.nonzero(ok)[0]
+            T = F(x0[r]) + np.sign(dx[r]) * tau[r] * np.abs(dx[r])
+            inside = (T >= 0.0) & (T <= C[r, -1])
+            r, T = r[inside], T[inside]
+            j = np.clip((C[r] <= T[:, None]).sum(axis=1) - 1, 0, len(K) - 2)
+            m0 = mu[r, j]
+            slope = (mu[r, j + 1] - m0) / h[j]
+            q = T - C[r, j]
+            delta = 2.0 * q / (m0 + np.sqrt(np.maximum(m0 * m0 + 2.0 * slope * q, 0.0)))
+            s[r] = (K[j] + delta - x0[r]) / dx[r]
+        return s
 
 
 def _frame_rotate(d, ct, phi):
@@ -70,6 +134,7 @@ def transport(prob, n, seed, half):
     [-half, half]^3, imager at angle 0 (source on -x, imager plane x = sdd -
     sad, u along -y, v along z), ideal response r(E) = E."""
     rng = np.random.default_rng(seed)
+    med = _Layers(prob)
     sad, sdd, nu, nv, du, dv = prob.sad, prob.sdd, prob.nu, prob.nv, prob.du, prob.dv
     jv, ju = np.unravel_index(int(np.argmax(prob.fluence)), prob.fluence.shape)
     E0 = float(prob.spec_e[0])
@@ -94,9 +159,7 @@ def transport(prob, n, seed, half):
     live = np.arange(n)
     while live.size:
         xl, dl, el = x[live], d[live], e[live]
-        muR, muC, muP = _coeffs(prob, el)
-        muT = muR + muC + muP
-        s = -np.log(1.0 - rng.random(live.size)) / muT
+        s = med.free_path(xl[:, 0], dl[:, 0], el, -np.log(1.0 - rng.random(live.size)))
         with np.errstate(divide="ignore", invalid="ignore"):
             te = np.where(dl > 0, (half - xl) / dl, np.where(dl < 0, (-half - xl) / dl, np.inf))
         d_exit = np.maximum(te.min(axis=1), 0.0)
@@ -120,9 +183,10 @@ def transport(prob, n, seed, half):
         stay = ~out
         idx = live[stay]
         x[idx] = xl[stay] + s[stay, None] * dl[stay]
-        u = rng.random(idx.size) * muT[stay]
-        ray = u < muR[stay]
-        comp = ~ray & (u < muR[stay] + muC[stay])
+        muR, muC, muP = med.coeffs(x[idx, 0], e[idx])
+        u = rng.random(idx.size) * (muR + muC + muP)
+        ray = u < muR
+        comp = ~ray & (u < muR + muC)
         # photoelectric: absorbed
         r_idx = idx[ray]
         if r_idx.size:
