@@ -119,11 +119,12 @@ def measured_peak(key, fallback):
         return fallback
 
 
-def profile_record(name, cell_shift=None):
+def profile_record(name, cell_shift=None, config=None):
     """Key/value counters of the transport kernel from a committed ncu summary
     (profiles/<name>), or None when the kernel source changed since those
-    counters were taken, or (cell_shift given) they were taken with other
-    macro cells."""
+    counters were taken, or they were taken with other macro cells
+    (cell_shift given) or another launch configuration (config given: the
+    record's block_size, batch_min and hist_per_thread must match)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", name)
     try:
@@ -136,6 +137,10 @@ def profile_record(name, cell_shift=None):
         return None
     if cell_shift is not None and str(cell_shift) != vals.get("cell_shift"):
         return None
+    if config is not None:
+        for k in ("block_size", "batch_min", "hist_per_thread"):
+            if str(config.get(k)) != vals.get(k):
+                return None
     return vals
 
 
@@ -146,36 +151,39 @@ def kernel_traffic(cell_shift=None):
     return int(v["bytes_per_launch"]) if v else None
 
 
-def kernel_inst_per_step(cell_shift=None):
+def kernel_inst_per_step(cell_shift=None, config=None):
     """Thread instructions the transport executes per Woodcock free flight
     (ncu smsp__thread_inst_executed.sum / free flights of the same launch), or
-    None for another kernel source or other macro cells."""
-    v = profile_record("mc_kernel_torso2mm_issue.txt", cell_shift)
+    None for another kernel source, other macro cells or another launch
+    configuration."""
+    v = profile_record("mc_kernel_torso2mm_issue.txt", cell_shift, config)
     return float(v["thread_inst_per_step"]) if v else None
 
 
-def transport_roofline(inst_per_step, steps, mc_s, n_sm, sm_max_mhz, traffic, memory, hbm_peak):
-    """The transport's roofline entry.  With an instruction record for this
-    kernel source: the issue rate (thread instructions per free flight x free
-    flights / launch time) against SMs x 4 schedulers x 32 lanes x the
-    maximum SM clock.  Without one: algorithmic voxel bytes against the HBM
-    copy peak.  The memory ceilings ride along as context."""
-    peak = n_sm * 4 * 32 * sm_max_mhz * 1e6 / 1e12
+def transport_roofline(steps, mc_s, hbm_peak, traffic, inst_per_step=None, n_sm=152, sm_max_mhz=2070.0,
+                       context=None):
+    """The transport's roofline entry on its algorithmic unit: 40 B of voxel
+    data (8 corners x (1 B material + 4 B density)) per Woodcock free flight x
+    the free flights counted live in the timed launches, over their mean
+    CUDA-event time, against the measured HBM copy peak.  The issue rate
+    (thread instructions per flight from an ncu record of this kernel source
+    and launch configuration, against SMs x 4 schedulers x 32 lanes x the
+    maximum SM clock) and the other ceilings ride along as context."""
+    achieved = steps * BYTES_PER_STEP_ALGO / mc_s / 1e9
+    r = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+         "traffic": traffic, "kernel": "mc_kernel",
+         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
+         "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps} steps per launch",
+         "mc_ms": 1e3 * mc_s, "woodcock_steps": steps}
+    issue_peak = n_sm * 4 * 32 * sm_max_mhz * 1e6 / 1e12
     if inst_per_step:
         issue = inst_per_step * steps / mc_s / 1e12
-        return {"bound": "alu", "achieved": issue, "peak": peak, "unit": "Tinst/s", "frac": issue / peak,
-                "traffic": traffic, "kernel": "mc_kernel",
-                "peak_source": f"{n_sm} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:g} MHz (one warp "
-                               "instruction per scheduler per cycle)",
-                "algorithmic": f"{inst_per_step:.1f} thread instructions per Woodcock step (ncu, this kernel "
-                               f"source) x {steps} steps",
-                "mc_ms": 1e3 * mc_s, **memory}
-    achieved = steps * BYTES_PER_STEP_ALGO / mc_s / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": traffic, "kernel": "mc_kernel",
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
-            "algorithmic": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps} steps",
-            "mc_ms": 1e3 * mc_s, **memory}
+        r.update(issue_tinst_s=issue, issue_peak_tinst_s=issue_peak, issue_frac=issue / issue_peak,
+                 inst_per_step=inst_per_step)
+    else:
+        r.update(issue_frac=None, inst_per_step=None)
+    r.update(context or {})
+    return r
 
 
 def dist_env():
@@ -185,12 +193,12 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_oracle_rate(prob, target_s, threads, seed=1):
+def cpu_oracle_rate(prob, target_s, threads, seed=1, first=400000):
     """Histories/s of the CPU oracle (FP32 transport, the parity reference) on
     a bounded sample of the same workload: first history ids of the stream."""
     import oracle
     oracle.build()
-    n = 400000
+    n = first
     t0 = time.perf_counter()
     oracle.mc_run(prob, n, seed=seed, threads=threads)
     dt = time.perf_counter() - t0
@@ -265,41 +273,28 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
     stats = torch.zeros(gdrr.GDRR_NSTATS, dtype=torch.int64, device="cuda")
 
-    def step(stats_buf):
-        return gdrr.project(ctx, n_hist, seed, angle, bin_factor=4, beta=0.02, iters=iters, stats=stats_buf)
+    # one step = one gdrr_project call (Steps 1-4, every scalar on the device)
+    # into preallocated outputs; the library times the transport launch with
+    # CUDA events on the stream it runs on
+    out = {}
+
+    def step():
+        return gdrr.project(ctx, n_hist, seed, angle, bin_factor=4, beta=0.02, iters=iters, stats=stats, out=out)
 
     # launch configuration from the project's autotuner (tallies do not
     # depend on it)
     tuned = gdrr.gdrr_autotune(ctx, angle, 20_000_000, seed)
 
-    # count scale needs one host read of the scatter photon count; take it from
-    # a warm-up projection so the timed step stays asynchronous
     for _ in range(max(args.warmup, 3)):
-        stats.zero_()
-        out = step(stats)
+        res = step()
     torch.cuda.synchronize()
     st = gdrr.stats_dict(stats)
     steps_per_proj = st["steps"]
     skips_per_proj = gdrr.cell_skips(stats)            # virtual collisions decided without corner gathers
     gathers_per_proj = steps_per_proj - skips_per_proj
-
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    ev_mc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    mc_ms, dn_ms = [], []
 
-    def timed_step(k):
-        # the whole hot path, Steps 1-4, with the MC launch bracketed separately
-        P = gdrr.gdrr_raytrace_primary(ctx, angle)
-        ev_mc[k][0].record(stream)
-        prim, scat = gdrr.gdrr_mc_project(ctx, n_hist, seed, angle, stats=stats)
-        ev_mc[k][1].record(stream)
-        P_hat = gdrr.gdrr_finalize(ctx, prim, n_hist)
-        S_hat = gdrr.gdrr_finalize(ctx, scat, n_hist)
-        S_hat_c = gdrr.gdrr_finalize(ctx, gdrr.gdrr_bin_tally(ctx, scat, 4), n_hist)
-        S_c = gdrr.gdrr_denoise_scatter(ctx, S_hat_c, count_scale, 0.02, 0.8, iters)
-        S = gdrr.gdrr_upsample(ctx, S_c, 4)
-        return gdrr.gdrr_noise_calibrate(ctx, P_hat, P, S_hat, S, n_hist, 0.4, 5.2913e9)
-
-    count_scale = float(out["S_hat"].sum().item()) / max(1, st["tally_scatter"])
     # memory ceiling for the transport's access pattern: the same corner
     # gathers at as many random cells as the projection gathers (free flights
     # less those the macro-cell bound decided)
@@ -308,7 +303,10 @@ def run_ours(args):
     # machine ceilings measured on this GPU: random 8-byte L2 gathers, FP32 FMA
     l2_probe_gbs = gdrr.gdrr_probe_l2_gather(32 << 20)
     fp32_probe_tflops = gdrr.gdrr_probe_fp32()
-    launches_per_step = 1 + 1 + 3 + 1 + (iters + 2) + 1 + 1
+    # kernels per step: ray trace, transport, 3 finalisations, binning, the
+    # scalars, the denoiser (one cooperative launch, else one per iteration +
+    # 2), upsampling, noise
+    launches_per_step = 9 + (1 if res["denoise_fused"] else iters + 2)
 
     clocks = ClockSampler(dev)
     if world > 1:
@@ -320,13 +318,14 @@ def run_ours(args):
     for k in range(args.steps):
         flush.fill_(float(k))                     # evict L2 between timed iterations
         ev[k][0].record(stream)
-        timed_step(k)
+        r = step()
         ev[k][1].record(stream)
+        mc_ms.append(r["transport_ms"])
+        dn_ms.append(r["denoise_ms"])
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    mc_ms = [a.elapsed_time(b) for a, b in ev_mc]
     tot_ms = sum(step_ms)
     t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -357,6 +356,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             with gdrr.Context(hp, stream) as c2:
+                gdrr.gdrr_set_options(c2, **tuned)
                 o = gdrr.project(c2, n_hist, seed, angle, beta=0.02, iters=iters)
                 for h, key in zip(host_out, ("P", "P_hat", "S_hat", "S", "N")):
                     h.copy_(o[key], non_blocking=True)
@@ -544,16 +544,14 @@ def run_ours(args):
             with gdrr.Context(sn.coarse_problem(sd)) as cl:
                 for a in range(2):
                     ang = float(rng_l.uniform(0, 2 * math.pi))
-                    sr, str_ = sn.simulate(cl, 2 * 10**9, 91 + 10 * sd + a, ang, a)
-                    ref = sn.denoise(cl, sr, str_, 2 * 10**9, 1.5).cpu().numpy()
+                    ref = sn.estimate(cl, 2 * 10**9, 91 + 10 * sd + a, ang, a, 1.5)[0].cpu().numpy()
                     xl = torch.empty((1, 2, sn.H, sn.W), dtype=torch.float32, device="cuda")
                     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                     e0.record(stream)
                     sn.low_input(cl, 10**6, 31 + 10 * sd + a, ang, a, xl[0])
                     pred = sn.predict(net, xl)
                     e1.record(stream)
-                    s8, st8 = sn.simulate(cl, 10**8, 57 + 10 * sd + a, ang, a)
-                    plain8 = sn.denoise(cl, s8, st8, 10**8, sn.HIGH_LENGTH)
+                    plain8, _ = sn.estimate(cl, 10**8, 57 + 10 * sd + a, ang, a, sn.HIGH_LENGTH)
                     e2.record(stream)
                     torch.cuda.synchronize()
                     cost.setdefault("learned_ms", []).append(e0.elapsed_time(e1))
@@ -561,9 +559,8 @@ def run_ours(args):
                     e_net.append(sn.rel_l2(pred.cpu().numpy()[0], ref))
                     e_plain[10**8].append(sn.rel_l2(plain8.cpu().numpy(), ref))
                     for n in plain_counts[:-1]:
-                        sp_, stp = sn.simulate(cl, n, 31 + 10 * sd + a, ang, a)
-                        e_plain[n].append(sn.rel_l2(sn.denoise(cl, sp_, stp, n, sn.plain_length(n)).cpu().numpy(),
-                                                    ref))
+                        sp_, _ = sn.estimate(cl, n, 31 + 10 * sd + a, ang, a, sn.plain_length(n))
+                        e_plain[n].append(sn.rel_l2(sp_.cpu().numpy(), ref))
         err_plain = {n: float(np.mean(v)) for n, v in e_plain.items()}
         err_net = float(np.mean(e_net))
         # photons the plain method needs for the learned error (log-log interpolation)
@@ -595,8 +592,21 @@ def run_ours(args):
         gemm = {"m_n_k": 8192, "ms": gemm_ms, "tflops": 2 * 8192**3 / gemm_ms / 1e9,
                 "frac_of_measured_bf16_peak": 2 * 8192**3 / gemm_ms / 1e9 / bf16_peak}
         del ga, gb, gc
+        # the network's own convolution flops (2 x pixels x Cin x Cout x taps
+        # per layer) against the measured BF16 peak
+        fwd_flops = sn.network_flops(32)
+        inf_ms = e0.elapsed_time(e1)
+        inf_tflops = 64 * fwd_flops / inf_ms / 1e9
+        train_tflops = n_train * 16 * 3 * fwd_flops / t_train / 1e12
+        net_roof = {"bound": "tensor", "achieved": inf_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                    "frac": inf_tflops / bf16_peak, "kernel": "network forward, batch 64",
+                    "algorithmic": f"{fwd_flops / 1e9:.3f} GFLOP per 96x128 image (conv layers) x 64",
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
+                    "training_tflops": train_tflops, "training_frac": train_tflops / bf16_peak,
+                    "training_what": "3 x forward flops per image (forward, data and weight gradients) x 16 x steps "
+                                     "over the training wall time"}
         learned = {"train_pairs": int(LX.shape[0]), "data_s": t_data, "train_steps": n_train, "train_s": t_train,
-                   "gemm_bf16": gemm,
+                   "gemm_bf16": gemm, "roofline": net_roof,
                    "final_loss": float(np.mean(losses[-50:])),
                    "rel_l2_vs_2e9_reference": {"learned_1e6": err_net,
                                                **{f"plain_denoised_{n:.0e}": err_plain[n] for n in plain_counts}},
@@ -604,7 +614,7 @@ def run_ours(args):
                    "photon_saving_at_matched_error": matched / 1e6,
                    "ms_per_projection": {"learned_1e6_plus_inference": float(np.mean(cost["learned_ms"])),
                                          "plain_1e8_plus_denoise": float(np.mean(cost["plain_1e8_ms"]))},
-                   "inference_batch64_ms": e0.elapsed_time(e1)}
+                   "inference_batch64_ms": inf_ms}
         net.close()
         del LX, LY
 
@@ -615,7 +625,6 @@ def run_ours(args):
         return 0
 
     mc_avg_s = statistics.mean(mc_ms) / 1e3
-    algo_bytes = steps_per_proj * BYTES_PER_STEP_ALGO
     n_mat = prob.mu_hat.shape[0]
     cell_bytes = 4 * (2 if n_mat <= 2 else (4 if n_mat <= 4 else 8))
     loaded_bytes = gathers_per_proj * RECORD_BYTES_PER_STEP + steps_per_proj * cell_bytes
@@ -625,47 +634,41 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = algo_bytes / mc_avg_s / 1e9
     value = n_hist * world * args.steps / (tot_ms / 1e3)
     traffic = kernel_traffic(tuned["cell_shift"])
 
-    # The transport is bound by instruction issue (ncu: issue slots busy,
-    # "not selected" the first stall), not by memory: most tentative collisions
-    # skip the corner gathers, and the phantom is L2-resident.  Its roofline is
-    # the issue rate: thread instructions per free flight (ncu, this kernel
-    # source) x the free flights counted live, over the measured launch time,
-    # against SMs x 4 schedulers x 32 lanes x the maximum SM clock.  The
-    # memory ceilings follow as context.
+    # The transport on its algorithmic unit (40 B of voxel data per free
+    # flight) against the HBM copy peak; the phantom is L2-resident and most
+    # flights skip the gathers, so the issue rate and the L2 gather probe are
+    # the binding ceilings, reported beside it.
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    inst_per_step = kernel_inst_per_step(tuned["cell_shift"])
-    memory = {
-        "hbm_roof": {"achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
-                     "what": f"{BYTES_PER_STEP_ALGO} B of voxel data per Woodcock step x {steps_per_proj} steps "
-                             "(algorithmic) vs MEASURED_PEAKS.json hbm_gbs"},
+    inst_per_step = kernel_inst_per_step(tuned["cell_shift"], tuned)
+    l2_achieved = loaded_bytes / mc_avg_s / 1e9
+    context = {
+        "l2_gather_probe_gbs": l2_probe_gbs, "l2_gather_achieved_gbs": l2_achieved,
+        "l2_gather_frac": l2_achieved / l2_probe_gbs,
+        "l2_gather_what": "random 8-byte loads over a 32 MiB L2-resident set vs the bytes the transport loads: "
+                          f"8 x 8-byte voxel records per gathering flight, one {cell_bytes}-byte macro-cell record "
+                          "per flight",
+        "gather_probe_ms": 1e3 * probe_s, "gather_probe_frac": probe_s / mc_avg_s,
+        "fp32_probe_tflops": fp32_probe_tflops,
+        "fp32_frac": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12 / fp32_probe_tflops,
         "cell_skips_per_projection": skips_per_proj,
-        "gather_roof": {"probe_ms": 1e3 * probe_s, "frac": probe_s / mc_avg_s,
-                        "what": f"the kernel's own corner gathers alone ({gathers_per_proj} cells: same 8 corners, "
-                                "same layout, random cells, no other work) vs the kernel"},
-        "l2_roof": {"probe_gbs": l2_probe_gbs, "achieved_gbs": loaded_bytes / mc_avg_s / 1e9,
-                    "frac": loaded_bytes / mc_avg_s / 1e9 / l2_probe_gbs,
-                    "what": "random 8-byte loads over a 32 MiB L2-resident set vs the bytes the transport loads: "
-                            f"8 x 8-byte voxel records per gathering flight, one {cell_bytes}-byte macro-cell "
-                            "record per flight"},
-        "fp32_roof": {"probe_tflops": fp32_probe_tflops,
-                      "achieved_tflops": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12,
-                      "frac": steps_per_proj * FLOPS_PER_STEP_ALGO / mc_avg_s / 1e12 / fp32_probe_tflops,
-                      "what": f"{FLOPS_PER_STEP_ALGO} FP32 flops per Woodcock step (trilinear weights, mixture, "
-                              "free path) vs an FMA-chain probe"}}
-    roofline = transport_roofline(inst_per_step, steps_per_proj, mc_avg_s, n_sm, sm_max_mhz, traffic, memory,
-                                  hbm_peak)
+        "denoise_ms": statistics.mean(dn_ms), "denoise_fused": bool(res["denoise_fused"]),
+    }
+    roofline = transport_roofline(steps_per_proj, mc_avg_s, hbm_peak, traffic, inst_per_step, n_sm, sm_max_mhz,
+                                  context)
 
     cpu = None
     if not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         rate, n_s, dt = cpu_oracle_rate(prob, args.cpu_seconds, threads)
+        rate1, n_1, dt1 = cpu_oracle_rate(prob, args.cpu_seconds / 2, 1, first=20000)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {n_s} histories of the 1e8-history projection, FP32 oracle, {dt:.1f} s"}
+               "sample": f"first {n_s} histories of the 1e8-history projection, FP32 oracle, {dt:.1f} s on "
+                         f"{threads} threads; single thread: first {n_1} histories, {dt1:.1f} s",
+               "single_thread_value": rate1}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

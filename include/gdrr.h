@@ -45,8 +45,24 @@ enum {
     GDRR_ERR_OOM = -3,           /* device allocation failed                       */
     GDRR_ERR_TALLY_OVERFLOW = -4,/* an int64 tally would exceed its headroom       */
     GDRR_ERR_STEP_LIMIT = -5,    /* histories hit the free-flight limit            */
-    GDRR_ERR_UNSUPPORTED = -6    /* valid input this build does not handle         */
+    GDRR_ERR_UNSUPPORTED = -6,   /* valid input this build does not handle         */
+    GDRR_ERR_TIMEOUT = -7        /* a bounded device-side wait gave up             */
 };
+
+/* How the two run-time conditions reach the caller.
+ *  - GDRR_ERR_STEP_LIMIT: a history that reaches gdrr_mc_options.max_steps
+ *    free flights is dropped and counted in stats[GDRR_ST_STEP_LIMIT].  The
+ *    asynchronous transport calls (gdrr_mc_project, _batched, scans) return
+ *    before the kernel runs, so they report it only through that counter;
+ *    gdrr_project, which synchronises, returns GDRR_ERR_STEP_LIMIT when the
+ *    counter of its projection is non-zero (its outputs are still written).
+ *  - GDRR_ERR_TIMEOUT: kernels that wait on other CTAs or on the tensor-core
+ *    pipeline bound every wait (about a second) and then record a timeout
+ *    instead of spinning on.  Synchronising calls (gdrr_project,
+ *    gdrr_gemm_bf16, the learned estimator's backward) return it directly;
+ *    for asynchronous calls on a context the next gdrr_sync returns it (and
+ *    clears the record).  The context stays usable; the outputs of the call
+ *    that timed out are not defined. */
 
 /* Maximum number of materials the transport kernels handle. */
 #define GDRR_MAX_MATERIALS 8
@@ -203,7 +219,9 @@ GDRR_API const char* gdrr_error_string(int code);
 GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* options);
 GDRR_API int gdrr_get_options(const gdrr_ctx* ctx, gdrr_mc_options* options);
 
-/* Synchronise the context stream; returns GDRR_ERR_CUDA on a kernel fault. */
+/* Synchronise the context stream; returns GDRR_ERR_CUDA on a kernel fault,
+ * GDRR_ERR_TIMEOUT when a bounded device-side wait of an earlier call on the
+ * context gave up since the last gdrr_sync. */
 GDRR_API int gdrr_sync(gdrr_ctx* ctx);
 
 /* Step 1, Section 2.3, Eq. 1: P(u) = w(u) sum_E phi(E) r(E) exp(-int mu dl)
@@ -344,6 +362,13 @@ GDRR_API int gdrr_fdk_backproject(const gdrr_fdk_geometry* geometry, int32_t n_p
 GDRR_API int gdrr_probe_l2_gather(int64_t working_set_bytes, double* gbs_out, void* cuda_stream);
 GDRR_API int gdrr_probe_fp32(double* tflops_out, void* cuda_stream);
 
+/* Check of the bounded device-side wait (not part of the method): one CTA
+ * waits, with the same bounded wait the denoiser's row bands use, for a flag
+ * that nothing sets.  The wait gives up after limit_ns nanoseconds (1 ..
+ * 2e9) and the call returns GDRR_ERR_TIMEOUT; GDRR_OK would mean the flag was
+ * seen.  Allocates 16 bytes, runs on cuda_stream, synchronises. */
+GDRR_API int gdrr_probe_bounded_wait(uint64_t limit_ns, void* cuda_stream);
+
 /* Autotuner: time gdrr_mc_project of n_probe histories at angle_rad for each
  * launch configuration of a fixed grid (block size 64 / 128 / 256 / 512, batch_min
  * 8 .. 32, hist_per_thread 1 / 8 / 64), into scratch tallies, and keep the
@@ -402,7 +427,10 @@ GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double
  *    GDRR_ERR_INVALID_ARG.
  *  - The first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any
- *    stream capture.
+ *    stream capture.  The address is kept for the life of the process: after
+ *    cudaDeviceReset on a device (or a release and re-creation of its primary
+ *    context) the array may move, so do not call this entry point on that
+ *    device again in the same process.
  *  - Every call on a device shares the one array, and the array keeps the
  *    last call's contents (each call writes every element it reads before
  *    reading it, so nothing needs clearing).  Calls that overlap on the GPU
@@ -414,6 +442,88 @@ GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double
 GDRR_API int gdrr_denoise_scatter_static(const double* S_hat_dev, double* S_dev, int32_t nu, int32_t nv,
                                          double count_scale, double beta, double omega, int32_t iters,
                                          void* cuda_stream);
+
+/* ---- One whole projection: Steps 1-4 of Section 2.2 / Fig. 3 -------------- */
+
+/* What gdrr_project simulates.  beta and smoothing_px choose the Eq. 2
+ * regularisation weight: with smoothing_px > 0, beta = smoothing_px^2 /
+ * (mean scatter count per coarse pixel), a smoothing length in coarse pixels
+ * that keeps the Eq. 5 iteration convergent at any photon count (see
+ * gdrr_denoise_scatter); otherwise beta (counts^-1) is used as given. */
+typedef struct {
+    double angle_rad;        /* gantry angle phi                                   */
+    uint32_t angle_index;    /* Philox counter word of this projection's streams   */
+    uint64_t n_photons;      /* source photons n_sim, > 0                          */
+    uint64_t seed;           /* Philox key                                         */
+    int32_t bin_factor;      /* coarse scatter grid of bin_factor^2 pixels; nu and
+                                nv multiples of it                                  */
+    double beta;             /* Eq. 2 weight in counts^-1 when smoothing_px <= 0   */
+    double smoothing_px;     /* > 0: beta from the mean coarse count (see above)   */
+    double omega;            /* Eq. 5 relaxation, 0 < omega < 2 (paper: 0.8)       */
+    int32_t iters;           /* Eq. 5 iterations, >= 0                             */
+    double mAs;              /* exposure I of the noise scaling, > 0               */
+    double zeta;             /* photons per mAs of the noise scaling, > 0          */
+} gdrr_projection;
+
+/* Caller-owned device outputs of gdrr_project, all overwritten.  Required:
+ * P, P_hat, S_hat, S, N (FP64 [nv][nu]).  Optional (NULL: not returned; the
+ * context keeps its own scratch instead): S_hat_coarse and S_coarse (FP64
+ * [nv/f][nu/f], f = bin_factor), prim_tally and scat_tally (int64 [nv][nu],
+ * the projection's fixed-point tallies), stats (uint64[GDRR_NSTATS], this
+ * projection's counters; zeroed by the call, not accumulated). */
+typedef struct {
+    double* P;
+    double* P_hat;
+    double* S_hat;
+    double* S;
+    double* N;
+    double* S_hat_coarse;
+    double* S_coarse;
+    int64_t* prim_tally;
+    int64_t* scat_tally;
+    uint64_t* stats;
+} gdrr_projection_out;
+
+/* Scalars gdrr_project derived on the device, copied to the host at its end. */
+typedef struct {
+    double count_scale;      /* signal of one detected scattered photon: scatter
+                                tally sum / scattered photons tallied (1/n_photons
+                                when none was tallied)                              */
+    double beta;             /* the Eq. 2 weight the denoiser used                 */
+    double mean_count;       /* scattered photons tallied per coarse pixel (>= 1
+                                photon in total)                                    */
+    uint64_t tally_scatter;  /* scattered photons tallied                          */
+    uint64_t step_limit;     /* histories dropped at max_steps                     */
+    int32_t below_floor;     /* 1: beta * mean_count < omega / (8 (1 - omega)), the
+                                Eq. 5 iteration diverges on most of the image      */
+    int32_t denoise_fused;   /* 1: the denoiser ran as one launch (else one launch
+                                per iteration)                                     */
+    float transport_ms;      /* CUDA-event time of the transport launch (Step 2)   */
+    float denoise_ms;        /* CUDA-event time of the Eq. 5 iteration             */
+    float total_ms;          /* CUDA-event time of the whole call's device work    */
+} gdrr_projection_info;
+
+/* Steps 1-4 of Section 2.2 in one call, every step a kernel on the context
+ * stream and every scalar computed on the device:
+ *   1  P = ray-traced primary (gdrr_raytrace_primary);
+ *   2  fixed-point tallies of n_photons histories (gdrr_mc_project with
+ *      history_offset 0, into zeroed tallies), P^ and S^ per source photon
+ *      (gdrr_finalize);
+ *   3  S^ binned to the coarse grid (gdrr_bin_tally + gdrr_finalize), the count
+ *      scale and beta (gdrr_projection_info), the Eq. 5 denoiser on the count
+ *      scale (gdrr_denoise_scatter), S = its bilinear upsampling
+ *      (gdrr_upsample);
+ *   4  N = ((P^ - P) + (S^ - S)) sqrt(n_photons / (zeta mAs))
+ *      (gdrr_noise_calibrate).
+ * Each output equals what that sequence of calls gives.  The call
+ * synchronises the stream once, at its end, to read the scalars back:
+ * GDRR_ERR_STEP_LIMIT when histories hit max_steps, GDRR_ERR_TALLY_OVERFLOW
+ * when a tally wrapped, GDRR_ERR_TIMEOUT when the denoiser's bounded wait gave
+ * up; info (host, may be NULL) is filled in every one of these cases.  The
+ * first call on a context allocates its scratch (tallies, coarse images,
+ * scalars): about 2 nu nv (8 + 0.3) bytes. */
+GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* proj, const gdrr_projection_out* out,
+                          gdrr_projection_info* info);
 
 /* Step 4, Section 2.6, Eq. 4 and the scaling equation that follows it:
  * N = ((P^ - P) + (S^ - S)) sqrt(n_sim / (zeta * mAs)), element-wise over n
@@ -449,8 +559,8 @@ GDRR_API int gdrr_scale_to_f64(const float* src_dev, int64_t n, double scale, do
  * K a multiple of 64.  Outputs wider than 64 columns take the TMA-fed
  * pipelined kernel.  With
  * splits > 1 the K range is split across CTAs that add into C, which the
- * caller zeroes first.  Synchronises; GDRR_ERR_CUDA also reports a tensor-core
- * wait that timed out.  Not in the paper: the building block of the learned
+ * caller zeroes first.  Synchronises; GDRR_ERR_TIMEOUT reports a tensor-core
+ * pipeline wait that gave up.  Not in the paper: the building block of the learned
  * scatter estimator's convolutions. */
 GDRR_API int gdrr_gemm_bf16(const void* A_dev, int32_t lda, const void* B_dev, int32_t ldb, float* C_dev, int32_t ldc,
                             int32_t M, int32_t N, int32_t K, int32_t splits, void* cuda_stream);
@@ -481,7 +591,8 @@ GDRR_API int gdrr_cnn_get_grads(gdrr_cnn* net, float* host);
 GDRR_API int gdrr_cnn_forward(gdrr_cnn* net, int32_t batch, const float* in_dev, float* out_dev);
 /* Mean-squared-error loss against target_dev and the gradients of every
  * parameter for the last forward pass (overwritten, not accumulated);
- * *loss_out (host) receives the loss.  Synchronises. */
+ * *loss_out (host) receives the loss.  Synchronises; GDRR_ERR_TIMEOUT
+ * reports a tensor-core pipeline wait that gave up. */
 GDRR_API int gdrr_cnn_backward(gdrr_cnn* net, const float* target_dev, double* loss_out);
 /* One Adam update of every parameter from the last gradients. */
 GDRR_API int gdrr_cnn_adam_step(gdrr_cnn* net, float lr, float beta1, float beta2, float eps);

@@ -326,6 +326,47 @@ def denoise(s_hat, beta, omega=0.8, iters=500, eps=1e-3, s0=None):
     return s
 
 
+def count_scale(scat_tally, n_photons, n_scat):
+    """The count scale of Step 3 (Section 2.5 needs counts for the Poisson
+    fidelity of Eq. 2; reading: the mean signal one detected scattered
+    photon leaves): the scatter image per source photon, summed, over the
+    number of scattered photons tallied.  With none tallied the scale is one
+    photon's share, 1 / n_photons."""
+    total = float(np.sum(finalize(scat_tally, n_photons)))
+    scale = total / max(1, int(n_scat))
+    return scale if scale > 0 else 1.0 / n_photons
+
+
+def mean_coarse_count(n_scat, n_coarse):
+    """Scattered photons tallied per coarse pixel (at least one photon in all)."""
+    return max(1, int(n_scat)) / n_coarse
+
+
+def smoothing_beta(smoothing_px, n_scat, n_coarse):
+    """beta of Eq. 2 for a smoothing length in coarse pixels: the Laplacian term
+    of Eq. 4 balances the fidelity term over a length L where beta S ~ L^2,
+    so beta = L^2 / (mean count per coarse pixel)."""
+    return smoothing_px * smoothing_px / max(mean_coarse_count(n_scat, n_coarse), 1e-6)
+
+
+def project_chain(P, prim_tally, scat_tally, n_photons, n_scat, bin_factor=4, beta=0.02, smoothing_px=None,
+                  omega=0.8, iters=300, mas=0.4, zeta=5.2913e9):
+    """Steps 2-4 of Section 2.2 after the transport, in the paper's order, from
+    the int64 tallies and the ray-traced primary P: signals per source photon
+    (Section 2.6), the coarse scatter grid, Eq. 5 on the count scale, bilinear
+    upsampling, and the scaled noise N."""
+    P_hat = finalize(prim_tally, n_photons)
+    S_hat = finalize(scat_tally, n_photons)
+    S_hat_c = finalize(bin_tally(scat_tally, bin_factor), n_photons)
+    cs = count_scale(scat_tally, n_photons, n_scat)
+    if smoothing_px is not None and smoothing_px > 0:
+        beta = smoothing_beta(smoothing_px, n_scat, S_hat_c.size)
+    S_c = denoise(S_hat_c / cs, beta, omega, iters) * cs
+    S = upsample(S_c, bin_factor)
+    N = noise_scale(P_hat, P, S_hat, S, n_photons, mas, zeta)
+    return dict(P_hat=P_hat, S_hat=S_hat, S_hat_coarse=S_hat_c, S_coarse=S_c, S=S, N=N, count_scale=cs, beta=beta)
+
+
 def optimality_residual(s, s_hat, beta):
     """Eq. 4: (1 - S^/S) - beta (Sigma S - 4 S), per pixel, replicate edges."""
     p = np.pad(s, 1, mode="edge")

@@ -2,7 +2,8 @@
 
 Each translation unit compiles in parallel; the transport kernel is compiled
 with -fmad=false so that every FP32 operation is a single IEEE-rounded one
-(the arithmetic contract of mc_transport.cu).
+(the arithmetic contract of mc_transport.cu), and so are the FP64 image steps
+(so the one-launch and per-iteration denoisers round alike).
 """
 from __future__ import annotations
 
@@ -26,7 +27,7 @@ SOURCES = {
     "gdrr_api.cu": [],
     "mc_transport.cu": ["-fmad=false"],
     "raytrace.cu": [],
-    "image_ops.cu": [],
+    "image_ops.cu": ["-fmad=false"],
     "cnn_gemm.cu": [],
     "cnn.cu": [],
     "fdk.cu": [],

@@ -632,7 +632,7 @@ GDRR_API int gdrr_cnn_backward(gdrr_cnn* n, const float* target_dev, double* los
         int bad = 0;
         if ((e = cudaMemcpyAsync(&bad, n->err, sizeof(int), cudaMemcpyDeviceToHost, st))) break;
         if ((e = cudaStreamSynchronize(st))) break;
-        if (bad) return GDRR_ERR_CUDA;
+        if (bad) return GDRR_ERR_TIMEOUT;
     } while (0);
     if (e == cudaSuccess && loss_out) *loss_out = loss;
     return err_code(e);

@@ -731,6 +731,6 @@ extern "C" GDRR_API int gdrr_gemm_bf16(const void* A_dev, int32_t lda, const voi
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(err);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GDRR_ERR_OOM : GDRR_ERR_CUDA;
-    return bad ? GDRR_ERR_CUDA : GDRR_OK;
+    return bad ? GDRR_ERR_TIMEOUT : GDRR_OK;
 }
 

@@ -21,6 +21,14 @@
 
 using namespace gdrr;
 
+// What gdrr_project reads back at its end (pinned host memory).
+struct ProjHost {
+    double scal[8];                         // count scale, beta, mean count, below floor, scattered photons
+    unsigned long long stats[GDRR_NSTATS];
+    int overflow;
+    int status;
+};
+
 struct gdrr_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -65,8 +73,14 @@ struct gdrr_ctx {
     Job* d_jobs = nullptr;
     int jobs_cap = 0;
     double* d_denoise = nullptr;
-    size_t denoise_cap = 0;
+    size_t denoise_cap = 0;          // bytes
     int64_t* d_tune = nullptr;       // autotuner scratch tallies, 2 * nu * nv
+    int* d_status = nullptr;         // timeouts of bounded device waits since the last gdrr_sync
+    // gdrr_project scratch: tallies, coarse tally and images, device scalars,
+    // and the pinned host block the scalars come back through
+    void* d_proj = nullptr;
+    ProjHost* h_proj = nullptr;
+    cudaEvent_t ev_proj[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // step / transport / denoise
     gdrr_mc_options opt{};
 };
 
@@ -368,9 +382,12 @@ int free_ctx(gdrr_ctx* c) {
     void* bufs[] = {c->d_vox, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_kcdf_pix,
                     c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr, c->d_wr_cols,
                     c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise, c->d_tune,
-                    c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells};
+                    c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells, c->d_status, c->d_proj};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    if (c->h_proj) cudaFreeHost(c->h_proj);
+    for (cudaEvent_t e : c->ev_proj)
+        if (e) cudaEventDestroy(e);
     delete c;
     return GDRR_OK;
 }
@@ -388,6 +405,7 @@ GDRR_API const char* gdrr_error_string(int code) {
         case GDRR_ERR_TALLY_OVERFLOW: return "int64 tally overflow";
         case GDRR_ERR_STEP_LIMIT: return "histories hit the free-flight limit";
         case GDRR_ERR_UNSUPPORTED: return "unsupported input";
+        case GDRR_ERR_TIMEOUT: return "a bounded device-side wait gave up";
         default: return "unknown error";
     }
 }
@@ -407,7 +425,6 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
     if (ph.nx <= 0 || ph.ny <= 0 || ph.nz <= 0 || !(ph.dx_mm > 0 && ph.dy_mm > 0 && ph.dz_mm > 0)
         || !ph.material || !ph.density)
         return GDRR_ERR_INVALID_ARG;
-    const int64_t nvox = (int64_t)ph.nx * ph.ny * ph.nz;
     const int64_t nbrick_rec = (int64_t)16 * ((ph.nx + 3) / 4) * ((ph.ny + 1) / 2) * ((ph.nz + 1) / 2);
     if (nbrick_rec >= ((int64_t)1 << 31)) return GDRR_ERR_UNSUPPORTED;
     const gdrr_materials& mt = *materials;
@@ -554,6 +571,8 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         if ((rc = cuda_err(cudaMalloc((void**)&c->d_counter, sizeof(unsigned long long))))) break;
         if ((rc = cuda_err(cudaMalloc((void**)&c->d_stats, GDRR_NSTATS * sizeof(unsigned long long))))) break;
         if ((rc = cuda_err(cudaMalloc((void**)&c->d_flag, sizeof(int))))) break;
+        if ((rc = cuda_err(cudaMalloc((void**)&c->d_status, sizeof(int))))) break;
+        if ((rc = cuda_err(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream)))) break;
         // the host vectors above die at return: finish the copies first
         if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
     } while (0);
@@ -654,7 +673,12 @@ GDRR_API int gdrr_get_options(const gdrr_ctx* ctx, gdrr_mc_options* o) {
 
 GDRR_API int gdrr_sync(gdrr_ctx* ctx) {
     if (!ctx) return GDRR_ERR_INVALID_ARG;
-    return cuda_err(cudaStreamSynchronize(ctx->stream));
+    TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    int status = 0;
+    TRY_CUDA(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!status) return GDRR_OK;
+    TRY_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    return GDRR_ERR_TIMEOUT;
 }
 
 GDRR_API int gdrr_air_scan(gdrr_ctx* ctx, double* I0_dev) {
@@ -974,6 +998,35 @@ GDRR_API int gdrr_upsample(gdrr_ctx* ctx, const double* coarse_dev, int32_t cu, 
     return cuda_err(launch_upsample(coarse_dev, cu, cv, factor, fine_dev, ctx->stream));
 }
 
+// The context's denoiser scratch, grown to the larger of the two forms' needs.
+static int denoise_scratch(gdrr_ctx* ctx, int nu, int nv) {
+    const size_t need = std::max(denoise_scratch_doubles(nu, nv) * sizeof(double), denoise_fused_scratch_bytes(nu, nv));
+    if (need > ctx->denoise_cap) {
+        if (ctx->d_denoise) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->d_denoise); ctx->d_denoise = nullptr; }
+        ctx->denoise_cap = 0;
+        TRY_CUDA(cudaMalloc((void**)&ctx->d_denoise, need));
+        ctx->denoise_cap = need;
+    }
+    return GDRR_OK;
+}
+
+// Step 3's iteration with the scalars on the host (scal_dev NULL) or on the
+// device (scal_dev[0] count scale, [1] beta): one cooperative launch when the
+// image fits its bands, else one launch per iteration.
+static int denoise_on_ctx(gdrr_ctx* ctx, const double* S_hat_dev, double* S_dev, int nu, int nv, double count_scale,
+                          double beta, const double* scal_dev, double omega, int iters, bool* fused) {
+    int rc = denoise_scratch(ctx, nu, nv);
+    if (rc) return rc;
+    if (denoise_fused_fits(nu, nv)) {
+        if (fused) *fused = true;
+        return cuda_err(launch_denoise_fused(S_hat_dev, S_dev, nu, nv, count_scale, beta, scal_dev, omega, iters,
+                                             ctx->d_denoise, ctx->d_status, ctx->stream));
+    }
+    if (fused) *fused = false;
+    return cuda_err(launch_denoise(S_hat_dev, S_dev, nu, nv, count_scale, beta, scal_dev, omega, iters,
+                                   ctx->d_denoise, ctx->stream));
+}
+
 GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double* S_dev, int32_t nu, int32_t nv,
                                   double count_scale, double beta, double omega, int32_t iters) {
     if (!ctx || !S_hat_dev || !S_dev || nu <= 0 || nv <= 0 || iters < 0) return GDRR_ERR_INVALID_ARG;
@@ -981,14 +1034,102 @@ GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double
         || !std::isfinite(beta))
         return GDRR_ERR_INVALID_ARG;
     if ((int64_t)nu * nv > (1 << 28)) return GDRR_ERR_INVALID_ARG;
-    const size_t need = denoise_scratch_doubles(nu, nv);
-    if (need > ctx->denoise_cap) {
-        if (ctx->d_denoise) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->d_denoise); ctx->d_denoise = nullptr; }
-        TRY_CUDA(cudaMalloc((void**)&ctx->d_denoise, need * sizeof(double)));
-        ctx->denoise_cap = need;
+    return denoise_on_ctx(ctx, S_hat_dev, S_dev, nu, nv, count_scale, beta, nullptr, omega, iters, nullptr);
+}
+
+GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_projection_out* out,
+                          gdrr_projection_info* info) {
+    if (!ctx || !pr || !out) return GDRR_ERR_INVALID_ARG;
+    if (!out->P || !out->P_hat || !out->S_hat || !out->S || !out->N) return GDRR_ERR_INVALID_ARG;
+    const int nu = ctx->geo.nu, nv = ctx->geo.nv, f = pr->bin_factor;
+    if (pr->n_photons == 0 || f <= 0 || nu % f || nv % f || pr->iters < 0) return GDRR_ERR_INVALID_ARG;
+    if (!std::isfinite(pr->angle_rad) || !geometry_ok(ctx, pr->angle_rad)) return GDRR_ERR_INVALID_ARG;
+    if (!(pr->omega > 0 && pr->omega < 2) || !(pr->mAs > 0) || !(pr->zeta > 0) || !std::isfinite(pr->mAs) ||
+        !std::isfinite(pr->zeta) || !std::isfinite(pr->smoothing_px))
+        return GDRR_ERR_INVALID_ARG;
+    if (!(pr->smoothing_px > 0) && !(pr->beta > 0 && std::isfinite(pr->beta))) return GDRR_ERR_INVALID_ARG;
+    const size_t npix = (size_t)nu * nv;
+    const int cu = nu / f, cv = nv / f;
+    const int ncoarse = cu * cv;
+    // scratch: prim, scat, coarse tally (int64 [npix] each), coarse S^ and S
+    // (double [npix] each: enough for any bin factor), scalars, counters
+    const size_t scratch = 5 * npix * 8 + 8 * sizeof(double) + GDRR_NSTATS * sizeof(unsigned long long) + 64;
+    if (!ctx->d_proj) TRY_CUDA(cudaMalloc(&ctx->d_proj, scratch));
+    if (!ctx->h_proj) TRY_CUDA(cudaMallocHost((void**)&ctx->h_proj, sizeof(ProjHost)));
+    for (cudaEvent_t& e : ctx->ev_proj)
+        if (!e) TRY_CUDA(cudaEventCreate(&e));
+    cudaEvent_t* ev = ctx->ev_proj;
+    char* base = static_cast<char*>(ctx->d_proj);
+    int64_t* prim = out->prim_tally ? out->prim_tally : reinterpret_cast<int64_t*>(base);
+    int64_t* scat = out->scat_tally ? out->scat_tally : reinterpret_cast<int64_t*>(base + npix * 8);
+    int64_t* coarse = reinterpret_cast<int64_t*>(base + 2 * npix * 8);
+    double* shc = out->S_hat_coarse ? out->S_hat_coarse : reinterpret_cast<double*>(base + 3 * npix * 8);
+    double* sc = out->S_coarse ? out->S_coarse : reinterpret_cast<double*>(base + 4 * npix * 8);
+    double* scal = reinterpret_cast<double*>(base + 5 * npix * 8);
+    unsigned long long* stats = out->stats ? reinterpret_cast<unsigned long long*>(out->stats)
+                                           : reinterpret_cast<unsigned long long*>(scal + 8);
+    cudaStream_t st = ctx->stream;
+    const double omega = pr->omega;
+    const double floor_ = omega < 1.0 ? omega / (8.0 * (1.0 - omega)) : INFINITY;
+    const double t2s = ldexp(1.0, -GDRR_TALLY_BITS) / (double)pr->n_photons;
+    bool fused = false;
+    int rc = GDRR_OK;
+    TRY_CUDA(cudaEventRecord(ev[0], st));
+    // Step 1
+    if ((rc = gdrr_raytrace_primary(ctx, pr->angle_rad, out->P))) return rc;
+    // Step 2: zeroed tallies and counters, transport, signal per source photon
+    TRY_CUDA(cudaMemsetAsync(prim, 0, npix * sizeof(int64_t), st));
+    TRY_CUDA(cudaMemsetAsync(scat, 0, npix * sizeof(int64_t), st));
+    TRY_CUDA(cudaMemsetAsync(stats, 0, GDRR_NSTATS * sizeof(unsigned long long), st));
+    TRY_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+    TRY_CUDA(cudaEventRecord(ev[2], st));
+    if ((rc = gdrr_mc_project(ctx, pr->angle_rad, pr->angle_index, pr->n_photons, pr->seed, 0, prim, scat,
+                              reinterpret_cast<uint64_t*>(stats), nullptr)))
+        return rc;
+    TRY_CUDA(cudaEventRecord(ev[3], st));
+    TRY_CUDA(launch_finalize(prim, (int64_t)npix, t2s, out->P_hat, ctx->d_flag, st));
+    TRY_CUDA(launch_finalize(scat, (int64_t)npix, t2s, out->S_hat, ctx->d_flag, st));
+    // Step 3: coarse grid, scalars on the device, Eq. 5, upsampling
+    TRY_CUDA(launch_bin(scat, nu, nv, f, coarse, st));
+    TRY_CUDA(launch_finalize(coarse, ncoarse, t2s, shc, ctx->d_flag, st));
+    TRY_CUDA(launch_project_scalars(coarse, ncoarse, stats, t2s, 1.0 / (double)pr->n_photons, pr->beta,
+                                    pr->smoothing_px > 0 ? pr->smoothing_px : 0.0, floor_, scal, st));
+    TRY_CUDA(cudaEventRecord(ev[4], st));
+    if ((rc = denoise_on_ctx(ctx, shc, sc, cu, cv, 0.0, 0.0, scal, omega, pr->iters, &fused))) return rc;
+    TRY_CUDA(cudaEventRecord(ev[5], st));
+    TRY_CUDA(launch_upsample(sc, cu, cv, f, out->S, st));
+    // Step 4
+    const double alpha = sqrt((double)pr->n_photons / (pr->zeta * pr->mAs));
+    TRY_CUDA(launch_noise(out->P_hat, out->P, out->S_hat, out->S, (int64_t)npix, alpha, out->N, st));
+    TRY_CUDA(cudaEventRecord(ev[1], st));
+    // one read-back of the scalars, counters and flags, one synchronisation
+    ProjHost* h = ctx->h_proj;
+    TRY_CUDA(cudaMemcpyAsync(h->scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY_CUDA(cudaMemcpyAsync(h->stats, stats, GDRR_NSTATS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    TRY_CUDA(cudaMemcpyAsync(&h->overflow, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY_CUDA(cudaMemcpyAsync(&h->status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+        info->count_scale = h->scal[0];
+        info->beta = h->scal[1];
+        info->mean_count = h->scal[2];
+        info->below_floor = h->scal[3] != 0.0 ? 1 : 0;
+        info->tally_scatter = h->stats[GDRR_ST_TALLY_SCATTER];
+        info->step_limit = h->stats[GDRR_ST_STEP_LIMIT];
+        info->denoise_fused = fused ? 1 : 0;
+        float ms[3] = {0.0f, 0.0f, 0.0f};
+        for (int k = 0; k < 3; ++k) TRY_CUDA(cudaEventElapsedTime(&ms[k], ev[2 * k], ev[2 * k + 1]));
+        info->total_ms = ms[0];
+        info->transport_ms = ms[1];
+        info->denoise_ms = ms[2];
     }
-    return cuda_err(launch_denoise(S_hat_dev, S_dev, nu, nv, count_scale, beta, omega, iters, ctx->d_denoise,
-                                   ctx->stream));
+    if (h->status) {
+        TRY_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        return GDRR_ERR_TIMEOUT;
+    }
+    if (h->overflow) return GDRR_ERR_TALLY_OVERFLOW;
+    if (h->stats[GDRR_ST_STEP_LIMIT]) return GDRR_ERR_STEP_LIMIT;
+    return GDRR_OK;
 }
 
 GDRR_API int gdrr_noise_calibrate(gdrr_ctx* ctx, const double* P_hat_dev, const double* P_dev,

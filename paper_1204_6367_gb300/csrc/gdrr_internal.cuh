@@ -109,6 +109,40 @@ struct McParams {
     int cshift, ncx, ncy;
 };
 
+// Bounded waits on flags that another CTA publishes (release store, acquire
+// load, both at GPU scope).  Every spin ends after limit_ns nanoseconds of
+// %globaltimer, so a flag that is never set costs a bounded delay and a
+// recorded timeout, not a hung GPU.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits until flags[j] >= want for the neighbour bands j = b - 1 and b + 1
+// that exist (0 <= j < G); false once limit_ns has passed.
+__device__ __forceinline__ bool wait_band_neighbours(const unsigned* flags, int b, int G, unsigned want,
+                                                     unsigned long long limit_ns) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (int j = b - 1; j <= b + 1; j += 2) {
+        if (j < 0 || j >= G) continue;
+        while (ld_acquire_u32(flags + j) < want) {
+            if (globaltimer_ns() - t0 > limit_ns) return false;
+        }
+    }
+    return true;
+}
+
 // Material slots of the transport kernel (and of a macro-cell record) for
 // n_mat materials: 2, 4 or 8.
 __host__ __device__ __forceinline__ int material_slots(int n_mat) { return n_mat <= 2 ? 2 : (n_mat <= 4 ? 4 : 8); }
@@ -144,9 +178,23 @@ cudaError_t launch_bin(const int64_t* t, int nu, int nv, int f, int64_t* out, cu
 cudaError_t launch_upsample(const double* c, int cu, int cv, int f, double* out, cudaStream_t s);
 cudaError_t launch_noise(const double* ph, const double* p, const double* sh, const double* sc, int64_t n,
                          double alpha, double* out, cudaStream_t s);
+// Eq. 5 denoiser, one launch per iteration: scratch of denoise_scratch_doubles
+// doubles; count scale and beta from scal_dev[0], [1] when scal_dev is not
+// NULL, else the host values.
 cudaError_t launch_denoise(const double* s_hat, double* s, int nu, int nv, double count_scale, double beta,
-                           double omega, int iters, double* scratch, cudaStream_t stream);
+                           const double* scal_dev, double omega, int iters, double* scratch, cudaStream_t stream);
 size_t denoise_scratch_doubles(int nu, int nv);
+// Eq. 5 denoiser in one cooperative launch (images that fit its row bands):
+// scratch of denoise_fused_scratch_bytes; a wait that gives up sets *status.
+bool denoise_fused_fits(int nu, int nv);
+size_t denoise_fused_scratch_bytes(int nu, int nv);
+cudaError_t launch_denoise_fused(const double* s_hat, double* s_out, int nu, int nv, double count_scale,
+                                 double beta, const double* scal_dev, double omega, int iters, void* scratch,
+                                 int* status, cudaStream_t stream);
+// gdrr_project's Step 3 scalars from the coarse scatter tally and the counters.
+cudaError_t launch_project_scalars(const int64_t* coarse, int n, const unsigned long long* stats,
+                                   double tally_to_signal, double inv_n_photons, double beta, double smoothing_px,
+                                   double floor_, double* scal, cudaStream_t s);
 cudaError_t launch_scale_to_f32(const double* a, int64_t n, double scale, float* out, cudaStream_t s);
 cudaError_t launch_scale_to_f64(const float* a, int64_t n, double scale, double* out, cudaStream_t s);
 

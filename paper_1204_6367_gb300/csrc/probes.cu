@@ -8,6 +8,9 @@
 //    flops per FMA.
 // Both kernels keep their results live (a checksum store) so nothing is
 // optimised away; both run a fixed amount of work per thread.
+// A third probe checks the bounded wait that CTA-to-CTA exchanges use: a
+// wait on a flag that nothing sets must give up after its limit and report
+// GDRR_ERR_TIMEOUT.
 #include "gdrr_internal.cuh"
 
 namespace gdrr {
@@ -43,8 +46,32 @@ __global__ void __launch_bounds__(PROBE_BLOCK) fp32_fma_kernel(float seed, int i
     if (s == 12345.678f) sink[0] = s;
 }
 
+// One CTA waiting, with the bounded wait of the CTA-to-CTA exchanges, for a
+// neighbour flag that nothing sets: the wait must give up and record it.
+__global__ void wait_probe_kernel(const unsigned* flags, unsigned long long limit_ns, int* status) {
+    if (threadIdx.x == 0 && !wait_band_neighbours(flags, 0, 2, 1u, limit_ns)) atomicOr(status, 1);
+}
+
 }  // namespace
 }  // namespace gdrr
+
+extern "C" GDRR_API int gdrr_probe_bounded_wait(uint64_t limit_ns, void* cuda_stream) {
+    if (limit_ns == 0 || limit_ns > 2000000000ull) return GDRR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned* buf = nullptr;
+    int status = 0;
+    if (cudaMalloc((void**)&buf, 4 * sizeof(unsigned)) != cudaSuccess) return GDRR_ERR_OOM;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 4 * sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        gdrr::wait_probe_kernel<<<1, 32, 0, s>>>(buf, (unsigned long long)limit_ns, reinterpret_cast<int*>(buf + 2));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, buf + 2, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) return GDRR_ERR_CUDA;
+    return status ? GDRR_ERR_TIMEOUT : GDRR_OK;
+}
 
 extern "C" GDRR_API int gdrr_probe_l2_gather(int64_t working_set_bytes, double* gbs_out, void* cuda_stream) {
     if (!gbs_out || working_set_bytes < (1 << 20) || working_set_bytes > ((int64_t)1 << 32)) return GDRR_ERR_INVALID_ARG;

@@ -77,6 +77,25 @@ class McOptions(ctypes.Structure):
                 ("cell_shift", ctypes.c_int32)]
 
 
+class Projection(ctypes.Structure):
+    _fields_ = [("angle_rad", ctypes.c_double), ("angle_index", ctypes.c_uint32), ("n_photons", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("bin_factor", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("smoothing_px", ctypes.c_double), ("omega", ctypes.c_double), ("iters", ctypes.c_int32),
+                ("mAs", ctypes.c_double), ("zeta", ctypes.c_double)]
+
+
+class ProjectionOut(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("P", "P_hat", "S_hat", "S", "N", "S_hat_coarse", "S_coarse",
+                                               "prim_tally", "scat_tally", "stats")]
+
+
+class ProjectionInfo(ctypes.Structure):
+    _fields_ = [("count_scale", ctypes.c_double), ("beta", ctypes.c_double), ("mean_count", ctypes.c_double),
+                ("tally_scatter", ctypes.c_uint64), ("step_limit", ctypes.c_uint64), ("below_floor", ctypes.c_int32),
+                ("denoise_fused", ctypes.c_int32), ("transport_ms", ctypes.c_float), ("denoise_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float)]
+
+
 class FdkGeometry(ctypes.Structure):
     _fields_ = [("sad_mm", ctypes.c_double), ("sdd_mm", ctypes.c_double), ("nu", ctypes.c_int32),
                 ("nv", ctypes.c_int32), ("du_mm", ctypes.c_double), ("dv_mm", ctypes.c_double),
@@ -147,6 +166,8 @@ def lib():
             "gdrr_line_integrals": [vp, vp, i64, dbl, vp, vp],
             "gdrr_fdk_filter": [vp, i32, vp, vp, vp],
             "gdrr_fdk_backproject": [vp, i32, vp, dbl, vp, vp, i32, vp],
+            "gdrr_project": [vp, vp, vp, vp],
+            "gdrr_probe_bounded_wait": [u64, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -468,6 +489,9 @@ def gdrr_denoise_scatter_static(s_hat, count_scale: float, beta: float, omega: f
     nv, nu = s_hat.shape
     if out is None:
         out = torch.empty_like(s_hat)
+    dev = torch.cuda.current_device()
+    if s_hat.device.index != dev or out.device.index != dev:
+        raise ValueError("gdrr_denoise_scatter_static runs on the current device: s_hat and out must live there")
     h, _ = _stream_handle(stream)
     _check("gdrr_denoise_scatter_static",
            lib().gdrr_denoise_scatter_static(_dev_ptr(s_hat, torch.float64, nu * nv, "s_hat"),
@@ -520,6 +544,12 @@ def gdrr_probe_l2_gather(working_set_bytes: int = 32 << 20, stream=None) -> floa
     return out.value
 
 
+def gdrr_probe_bounded_wait(limit_ns: int, stream=None) -> int:
+    """Return code of a bounded device wait on a flag nothing sets (-7: timed out)."""
+    h, _ = _stream_handle(stream)
+    return lib().gdrr_probe_bounded_wait(int(limit_ns), h)
+
+
 def gdrr_probe_fp32(stream=None) -> float:
     """FP32 FMA throughput in TFLOP/s."""
     h, _ = _stream_handle(stream)
@@ -560,49 +590,59 @@ def denoise_stability_floor(omega: float = 0.8) -> float:
 
 def project(ctx: Context, n_photons: int, seed: int, angle_rad: float = 0.0, bin_factor: int = 4,
             beta: float = 0.02, omega: float = 0.8, iters: int = 300, mas: float = 0.4,
-            zeta: float = 5.2913e9, stats=None, angle_index: int = 0, smoothing_px: float | None = None):
-    """P (ray traced), P^ and S^ (MC), S (denoised, coarse and full), N (scaled noise).
+            zeta: float = 5.2913e9, stats=None, angle_index: int = 0, smoothing_px: float | None = None,
+            out: dict | None = None, allow_step_limit: bool = False):
+    """One projection through gdrr_project: P (ray traced), P^ and S^ (MC), S
+    (denoised, coarse and full), N (scaled noise), and the int64 tallies.
 
-    Every step is a libgdrr kernel.  The denoiser runs on the bin_factor x
-    bin_factor coarse scatter grid on the count scale: one detected scattered
-    photon deposits on average (scatter tally sum) / (scattered photons
-    tallied), the count_scale.
-
-    beta is in counts^-1, so a fixed beta smooths less as n_photons grows and
-    the iteration diverges once beta times the counts of most coarse pixels
-    falls below denoise_stability_floor(omega) (a warning says so).
-    smoothing_px, when given, replaces beta by smoothing_px^2 / (mean coarse
-    count): a smoothing length in coarse pixels, the same at any photon count.
-    stats, when given, is a device GDRR_NSTATS counter array that must be zero
-    on entry: its scatter count sets the count scale.
+    Every step and every scalar is computed by the library on the device;
+    this wrapper only allocates the outputs (or takes them from ``out``, a
+    dict of preallocated CUDA tensors with the keys of the result) and reads
+    the scalars the call returns.  The denoiser runs on the bin_factor x
+    bin_factor coarse scatter grid on the count scale (the mean signal of one
+    detected scattered photon).  beta is in counts^-1; smoothing_px, when
+    given, replaces it by smoothing_px^2 / (mean coarse count).  A warning
+    says when beta times the mean count is below the Eq. 5 convergence floor.
+    stats, when given, receives this projection's counters (overwritten).
+    GDRR_ERR_STEP_LIMIT raises unless allow_step_limit is true.
     """
     import torch
-    own_stats = stats is None
-    if own_stats:
-        stats = torch.zeros(GDRR_NSTATS, dtype=torch.int64, device="cuda")
-    P = gdrr_raytrace_primary(ctx, angle_rad)
-    prim, scat = gdrr_mc_project(ctx, n_photons, seed, angle_rad, angle_index, stats=stats)
-    P_hat = gdrr_finalize(ctx, prim, n_photons)
-    S_hat = gdrr_finalize(ctx, scat, n_photons)
-    S_hat_c = gdrr_finalize(ctx, gdrr_bin_tally(ctx, scat, bin_factor), n_photons)
-    st = stats_dict(stats) if own_stats else None
-    n_scat = (st or stats_dict(stats))["tally_scatter"]
-    n_det = max(1, n_scat)
-    count_scale = float(S_hat.sum().item()) / n_det
-    if not count_scale > 0:
-        count_scale = 1.0 / n_photons
-    mean_count = n_det / S_hat_c.numel()
-    if smoothing_px is not None:
-        beta = smoothing_px * smoothing_px / max(mean_count, 1e-6)
-    elif n_scat > 0 and beta * mean_count < denoise_stability_floor(omega):
-        warnings.warn(f"beta * mean scatter count = {beta * mean_count:.3g} is below "
+    nv, nu = ctx.nv, ctx.nu
+    if nu % bin_factor or nv % bin_factor:
+        raise ValueError("detector size must be a multiple of bin_factor")
+    cu, cv = nu // bin_factor, nv // bin_factor
+    o = dict(out or {})
+
+    def buf(key, shape, dtype):
+        if key not in o or o[key] is None:
+            o[key] = torch.empty(shape, dtype=dtype, device="cuda")
+        return o[key]
+
+    if stats is not None:
+        o["stats"] = stats
+    f64 = torch.float64
+    specs = (("P", (nv, nu), f64), ("P_hat", (nv, nu), f64), ("S_hat", (nv, nu), f64), ("S", (nv, nu), f64),
+             ("N", (nv, nu), f64), ("S_hat_coarse", (cv, cu), f64), ("S_coarse", (cv, cu), f64),
+             ("prim", (nv, nu), torch.int64), ("scat", (nv, nu), torch.int64), ("stats", (GDRR_NSTATS,), torch.int64))
+    ptr = {k: _dev_ptr(buf(k, shp, dt), dt, math.prod(shp), k) for k, shp, dt in specs}
+    po = ProjectionOut(ptr["P"], ptr["P_hat"], ptr["S_hat"], ptr["S"], ptr["N"], ptr["S_hat_coarse"],
+                       ptr["S_coarse"], ptr["prim"], ptr["scat"], ptr["stats"])
+    pr = Projection(float(angle_rad), int(angle_index), int(n_photons), int(seed), int(bin_factor), float(beta),
+                    float(smoothing_px) if smoothing_px is not None else 0.0, float(omega), int(iters), float(mas),
+                    float(zeta))
+    info = ProjectionInfo()
+    rc = lib().gdrr_project(ctx.handle, ctypes.byref(pr), ctypes.byref(po), ctypes.byref(info))
+    if rc != 0 and not (allow_step_limit and rc == -5):
+        raise GdrrError("gdrr_project", rc)
+    if info.below_floor:
+        warnings.warn(f"beta * mean scatter count = {info.beta * info.mean_count:.3g} is below "
                       f"{denoise_stability_floor(omega):.3g}: the Eq. 5 iteration diverges on most of the image "
                       "(raise beta, n_photons or bin_factor, or pass smoothing_px)", RuntimeWarning, stacklevel=2)
-    S_c = gdrr_denoise_scatter(ctx, S_hat_c, count_scale, beta, omega, iters)
-    S = gdrr_upsample(ctx, S_c, bin_factor)
-    N = gdrr_noise_calibrate(ctx, P_hat, P, S_hat, S, n_photons, mas, zeta)
-    return dict(P=P, P_hat=P_hat, S_hat=S_hat, S_hat_coarse=S_hat_c, S_coarse=S_c, S=S, N=N,
-                prim=prim, scat=scat, stats=stats, count_scale=count_scale, beta=beta)
+    res = {k: o[k] for k, _, _ in specs}
+    res.update(count_scale=info.count_scale, beta=info.beta, mean_count=info.mean_count,
+               step_limit=info.step_limit, denoise_fused=bool(info.denoise_fused),
+               transport_ms=info.transport_ms, denoise_ms=info.denoise_ms, total_ms=info.total_ms)
+    return res
 
 
 # ---- reconstruction of simulated scans (Section 3.5) ----------------------

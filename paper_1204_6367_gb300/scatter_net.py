@@ -35,24 +35,26 @@ def coarse_problem(seed: int, vox: float = 4.0):
                                 name=f"torso-seed{seed}-{vox:g}mm-coarse")
 
 
-def simulate(ctx, n: int, seed: int, angle: float, angle_index: int):
-    """MC scatter signal per source photon (device FP64 [H, W]) and counters."""
-    import torch
-    stats = torch.zeros(gdrr.GDRR_NSTATS, dtype=torch.int64, device="cuda")
-    _, s = gdrr.gdrr_mc_project(ctx, n, seed, angle, angle_index, stats=stats)
-    return gdrr.gdrr_finalize(ctx, s, n), gdrr.stats_dict(stats)
+def estimate(ctx, n: int, seed: int, angle: float, angle_index: int, length: float = 4.0, iters: int = 800):
+    """The plain method at n histories on the coarse grid, one gdrr_project
+    call: ray-traced primary and Poisson-denoised MC scatter (Eq. 5, omega =
+    0.8) per source photon, device FP64 [H, W] each.  beta is set on the
+    device so that beta times the mean count is length^2: a smoothing length
+    of about `length` pixels at any photon count."""
+    r = gdrr.project(ctx, n, seed, angle, bin_factor=1, smoothing_px=length, iters=iters, angle_index=angle_index)
+    return r["S"], r["P"]
 
 
-def denoise(ctx, s_hat, stats, n: int, length: float = 4.0, iters: int = 800):
-    """Poisson denoising (Eq. 5, omega = 0.8) on the count scale, with beta
-    set so that beta times the mean count is length^2: a smoothing length of
-    about `length` pixels at any photon count."""
-    n_det = max(1, stats["tally_scatter"])
-    total = float(s_hat.sum().item())
-    count_scale = total / n_det if total > 0 else 1.0 / n
-    mean_count = n_det / s_hat.numel()
-    beta = length * length / max(mean_count, 1e-6)
-    return gdrr.gdrr_denoise_scatter(ctx, s_hat, count_scale, beta, 0.8, iters)
+def network_flops(c: int = 32, h: int = H, w: int = W) -> float:
+    """Convolution flops of one forward pass of one image through the
+    encoder-decoder (2 x output pixels x input channels x output channels x
+    kernel taps per layer): encoder 2 -> c -> 2c -> 4c -> 8c at full, 1/2, 1/4
+    and 1/8 resolution, decoder (8c + 4c) -> 4c, (4c + 2c) -> 2c, (2c + c) -> c
+    at 1/4, 1/2 and full resolution, then the 1 x 1 output layer c -> 1."""
+    px = [h * w // (4 ** k) for k in range(4)]
+    layers = [(px[0], 2, c, 9), (px[1], c, 2 * c, 9), (px[2], 2 * c, 4 * c, 9), (px[3], 4 * c, 8 * c, 9),
+              (px[2], 12 * c, 4 * c, 9), (px[1], 6 * c, 2 * c, 9), (px[0], 3 * c, c, 9), (px[0], c, 1, 1)]
+    return float(sum(2 * p * ci * co * k for p, ci, co, k in layers))
 
 
 def plain_length(n: int) -> float:
@@ -71,9 +73,7 @@ def low_input(ctx, n_low: int, seed: int, angle: float, angle_index: int, x_slot
     """The network input for one projection: the plain method's low-photon
     estimate (MC + Poisson denoising) and the ray-traced primary, scaled into
     x_slot [2, H, W] FP32.  Returns the denoised low-photon estimate."""
-    P = gdrr.gdrr_raytrace_primary(ctx, angle)
-    s_low, st = simulate(ctx, n_low, seed, angle, angle_index)
-    d_low = denoise(ctx, s_low, st, n_low, plain_length(n_low))
+    d_low, P = estimate(ctx, n_low, seed, angle, angle_index, plain_length(n_low))
     gdrr.gdrr_scale_to_f32(d_low, SCALE, x_slot[0])
     gdrr.gdrr_scale_to_f32(P, SCALE, x_slot[1])
     return d_low
@@ -94,8 +94,8 @@ def make_dataset(seeds, angles_per_phantom: int, n_low: int, n_high: int, rng_se
             for a in range(angles_per_phantom):
                 angle = float(rng.uniform(0.0, 2.0 * math.pi))
                 low_input(ctx, n_low, 1_000_003 + 7 * k, angle, a, X[k])
-                s_high, st = simulate(ctx, n_high, 2_000_029 + 11 * k, angle, a)
-                gdrr.gdrr_scale_to_f32(denoise(ctx, s_high, st, n_high, plain_length(n_high)), SCALE, Y[k, 0])
+                s_high, _ = estimate(ctx, n_high, 2_000_029 + 11 * k, angle, a, plain_length(n_high))
+                gdrr.gdrr_scale_to_f32(s_high, SCALE, Y[k, 0])
                 k += 1
     return X, Y
 
@@ -145,14 +145,13 @@ def evaluate(net, seeds=(900, 901, 902, 903), angles_per_seed=2, n_low=10**6, n_
         with gdrr.Context(coarse_problem(int(s))) as ctx:
             for a in range(angles_per_seed):
                 ang = float(rng.uniform(0.0, 2.0 * math.pi))
-                sr, st = simulate(ctx, n_ref, 91 + 10 * s + a, ang, a)
-                ref = denoise(ctx, sr, st, n_ref, 1.5).cpu().numpy()
+                ref = estimate(ctx, n_ref, 91 + 10 * s + a, ang, a, 1.5)[0].cpu().numpy()
                 x = torch.empty((1, 2, H, W), dtype=torch.float32, device="cuda")
                 low_input(ctx, n_low, 31 + 10 * s + a, ang, a, x[0])
                 e_net.append(rel_l2(predict(net, x).cpu().numpy()[0], ref))
                 for n in plain_counts:
-                    sp, stp = simulate(ctx, n, (31 if n < 10**8 else 57) + 10 * s + a, ang, a)
-                    e_plain[n].append(rel_l2(denoise(ctx, sp, stp, n, plain_length(n)).cpu().numpy(), ref))
+                    sp, _ = estimate(ctx, n, (31 if n < 10**8 else 57) + 10 * s + a, ang, a, plain_length(n))
+                    e_plain[n].append(rel_l2(sp.cpu().numpy(), ref))
     err_net = float(np.mean(e_net))
     err_plain = {n: float(np.mean(v)) for n, v in e_plain.items()}
     lx = np.log(np.array(plain_counts, np.float64))

@@ -44,7 +44,7 @@ def test_library_exports_nothing_else(lib):
 
 
 def test_error_strings(lib):
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert lib.gdrr_error_string(code)
     assert lib.gdrr_error_string(-99) == b"unknown error"
 
@@ -99,3 +99,18 @@ def test_null_arguments(lib):
     assert lib.gdrr_raytrace_primary(None, 0.0, None) == -1
     assert lib.gdrr_denoise_scatter(None, None, None, 4, 4, 1.0, 1.0, 0.8, 1) == -1
     assert lib.gdrr_stream_words(1, 0, 0, -1, 1, None, None) == -1
+    assert lib.gdrr_project(None, None, None, None) == -1
+    assert lib.gdrr_probe_bounded_wait(0, None) == -1
+
+
+def test_projection_structs_match_the_header():
+    # the binding's ctypes layouts against the C declarations, field by field
+    import re
+    from paper_1204_6367_gb300 import gdrr
+    text = open(os.path.join(ROOT, "include", "gdrr.h")).read()
+    for cname, cls in (("gdrr_projection", gdrr.Projection), ("gdrr_projection_out", gdrr.ProjectionOut),
+                       ("gdrr_projection_info", gdrr.ProjectionInfo)):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + r";", text).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"\b(\w+)\s*;", body)
+        assert fields == [f for f, _ in cls._fields_], cname

@@ -69,14 +69,32 @@ def test_reference_leg_prints_the_contract_line():
 
 
 def test_transport_roofline_entry():
-    # with an instruction record: the issue rate against 152 x 4 x 32 lanes x 2.07 GHz
-    mem = {"hbm_roof": {"frac": 0.27}}
-    r = bench.transport_roofline(275.3, 4.593e9, 0.0988, 152, 2070.0, 51540736, mem, 6790.3)
-    assert r["bound"] == "alu" and r["unit"] == "Tinst/s"
-    assert r["peak"] == pytest.approx(40.28, rel=1e-3) and r["frac"] == pytest.approx(0.3177, rel=1e-3)
-    assert r["traffic"] == 51540736 and r["hbm_roof"] == {"frac": 0.27} and r["mc_ms"] == pytest.approx(98.8)
+    # the headline: algorithmic voxel bytes (40 B per free flight) against the HBM copy peak
+    r = bench.transport_roofline(4.593e9, 0.0988, 6790.3, 51540736, 275.3, 152, 2070.0, {"l2_gather_frac": 0.74})
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6790.3
+    assert r["frac"] == pytest.approx(40 * 4.593e9 / 0.0988 / 1e9 / 6790.3)
+    assert r["traffic"] == 51540736 and r["mc_ms"] == pytest.approx(98.8) and r["l2_gather_frac"] == 0.74
+    # the issue rate rides along: 275.3 instructions per flight against 152 x 4 x 32 lanes x 2.07 GHz
+    assert r["issue_peak_tinst_s"] == pytest.approx(40.28, rel=1e-3)
+    assert r["issue_frac"] == pytest.approx(0.3177, rel=1e-3)
     json.dumps(r)
-    # without one: algorithmic voxel bytes against the HBM copy peak
-    h = bench.transport_roofline(None, 4.593e9, 0.0988, 152, 2070.0, None, mem, 6790.3)
-    assert h["bound"] == "hbm" and h["unit"] == "GB/s" and h["traffic"] is None
-    assert h["frac"] == pytest.approx(40 * 4.593e9 / 0.0988 / 1e9 / 6790.3)
+    # without an instruction record for this source and launch configuration
+    h = bench.transport_roofline(4.593e9, 0.0988, 6790.3, None)
+    assert h["bound"] == "hbm" and h["issue_frac"] is None and h["traffic"] is None
+
+
+def test_instruction_record_is_keyed_to_the_launch_configuration(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_1204_6367_gb300" / "csrc").mkdir(parents=True)
+    kernel = open(os.path.join(ROOT, "paper_1204_6367_gb300", "csrc", "mc_transport.cu")).read()
+    (tmp_path / "paper_1204_6367_gb300" / "csrc" / "mc_transport.cu").write_text(kernel)
+    import hashlib
+    h = hashlib.sha256(kernel.encode()).hexdigest()[:16]
+    (tmp_path / "profiles" / "mc_kernel_torso2mm_issue.txt").write_text(
+        f"thread_inst_per_step 250.0\ncell_shift 2\nblock_size 64\nbatch_min 20\nhist_per_thread 8\n"
+        f"source_sha256_16 {h}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    cfg = {"block_size": 64, "batch_min": 20, "hist_per_thread": 8}
+    assert bench.kernel_inst_per_step(2, cfg) == 250.0
+    assert bench.kernel_inst_per_step(2, dict(cfg, batch_min=16)) is None
+    assert bench.kernel_inst_per_step(2, dict(cfg, block_size=128)) is None

@@ -39,8 +39,7 @@ def test_network_beats_plain_method_at_equal_photons(gd):
                 ang = float(rng.uniform(0, 2 * np.pi))
                 x = torch.empty((1, 2, sn.H, sn.W), dtype=torch.float32, device="cuda")
                 d_low = sn.low_input(ctx, 10**6, 31 + 10 * s + a, ang, a, x[0]).cpu().numpy()
-                s_ref, st = sn.simulate(ctx, 10**9, 91 + 10 * s + a, ang, a)
-                ref = sn.denoise(ctx, s_ref, st, 10**9, 1.5).cpu().numpy()
+                ref = sn.estimate(ctx, 10**9, 91 + 10 * s + a, ang, a, 1.5)[0].cpu().numpy()
                 pred = sn.predict(net, x).cpu().numpy()[0]
                 err_net.append(sn.rel_l2(pred, ref))
                 err_plain.append(sn.rel_l2(d_low, ref))

@@ -105,6 +105,12 @@ MUTATIONS = [
      "denoiser edges wrap around instead of replicating", "test_oracle_image.py"),
     ("oracle.py", "return n_hat * np.sqrt(float(n_sim) / (zeta * mas))", "return n_hat * np.sqrt(float(n_sim) * (zeta * mas))",
      "noise scaling", "test_oracle_image.py"),
+    ("oracle.py", "scale = total / max(1, int(n_scat))", "scale = total / max(1, int(n_photons))",
+     "count scale divided by the source photons", "test_oracle_project.py"),
+    ("oracle.py", "total = float(np.sum(finalize(scat_tally, n_photons)))", "total = float(np.sum(scat_tally))",
+     "count scale from the raw fixed-point tally", "test_oracle_project.py"),
+    ("oracle.py", "return smoothing_px * smoothing_px / max(", "return smoothing_px / max(",
+     "smoothing length not squared", "test_oracle_project.py"),
 ]
 
 
