@@ -673,11 +673,12 @@ GDRR_API int gdrr_get_options(const gdrr_ctx* ctx, gdrr_mc_options* o) {
 
 GDRR_API int gdrr_sync(gdrr_ctx* ctx) {
     if (!ctx) return GDRR_ERR_INVALID_ARG;
-    TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     int status = 0;
-    TRY_CUDA(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    TRY_CUDA(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     if (!status) return GDRR_OK;
-    TRY_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    TRY_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     return GDRR_ERR_TIMEOUT;
 }
 
@@ -1124,7 +1125,8 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
         info->denoise_ms = ms[2];
     }
     if (h->status) {
-        TRY_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        TRY_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+        TRY_CUDA(cudaStreamSynchronize(st));
         return GDRR_ERR_TIMEOUT;
     }
     if (h->overflow) return GDRR_ERR_TALLY_OVERFLOW;
