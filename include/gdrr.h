@@ -170,6 +170,17 @@ typedef struct {
                                   records are the same for every cell_shift; only
                                   GDRR_ST_CELL_SKIPS and the time change.  Changing it
                                   rebuilds the cell table (not while a scan exists).   */
+    int32_t photon_pool;       /* photons per thread, 1..3, in the shared-memory pool
+                                  of the pool form of the transport: blocks of 256
+                                  threads move photons between warps so that free
+                                  flights, corner gathers, interactions, tallies and
+                                  new histories each run on full warps (block_size and
+                                  batch_min do not apply to it); -1: the lane form, one
+                                  photon per lane with warp-batched services.  Runs
+                                  with records, nearest_voxel, scatter_filter or
+                                  rayleigh_form_factor always take the lane form.
+                                  Tallies, counters and records are the same for
+                                  every choice [2]                                     */
 } gdrr_mc_options;
 
 /* Transport counters, accumulated by every gdrr_mc_project* call (device
@@ -370,10 +381,12 @@ GDRR_API int gdrr_probe_fp32(double* tflops_out, void* cuda_stream);
 GDRR_API int gdrr_probe_bounded_wait(uint64_t limit_ns, void* cuda_stream);
 
 /* Autotuner: time gdrr_mc_project of n_probe histories at angle_rad for each
- * launch configuration of a fixed grid (block size 64 / 128 / 256 / 512, batch_min
- * 8 .. 32, hist_per_thread 1 / 8 / 64), into scratch tallies, and keep the
- * fastest as the context's options (also copied to *best_out when not NULL).
- * Tallies do not depend on these options, only the speed does.  Synchronises. */
+ * launch configuration of a fixed grid (the lane form: block size 64 / 128 /
+ * 256 / 512, batch_min 8 .. 32, hist_per_thread 1 / 8 / 64; the pool form:
+ * photon_pool 1 / 2 / 3, hist_per_thread 1 / 8 / 64), into scratch tallies, and
+ * keep the fastest as the context's options (also copied to *best_out when
+ * not NULL).  Tallies do not depend on these options, only the speed does.
+ * Synchronises. */
 GDRR_API int gdrr_autotune(gdrr_ctx* ctx, double angle_rad, uint64_t n_probe, uint64_t seed,
                            gdrr_mc_options* best_out);
 

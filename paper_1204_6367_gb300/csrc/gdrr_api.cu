@@ -364,6 +364,7 @@ void set_defaults(gdrr_mc_options* o) {
     if (o->block_size <= 0) o->block_size = 256;
     if (o->hist_per_thread <= 0) o->hist_per_thread = 8;
     if (o->batch_min <= 0) o->batch_min = 16;
+    if (o->photon_pool == 0) o->photon_pool = 2;
 }
 
 // Default macro cells: about 8 mm on a side, 2^s voxels of the smallest voxel
@@ -595,6 +596,7 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
         return GDRR_ERR_INVALID_ARG;
     if (n.rayleigh_form_factor < 0 || n.rayleigh_form_factor > 1 || (n.rayleigh_form_factor && !ctx->n_ff))
         return GDRR_ERR_INVALID_ARG;
+    if (n.photon_pool < -1 || n.photon_pool > 3) return GDRR_ERR_INVALID_ARG;
     if (n.cell_shift == 0) n.cell_shift = default_cell_shift(ctx);
     if (n.cell_shift < -1 || n.cell_shift > 6) return GDRR_ERR_INVALID_ARG;
     if (n.cell_shift != ctx->cell_shift) {
@@ -727,6 +729,24 @@ static int launch_grid(const gdrr_ctx* ctx, uint64_t total, bool rec) {
     return grid < 1 ? 1 : (int)grid;
 }
 
+// The transport launch: the pool form for default options without records
+// (when its pool fits the SM), else the lane form.
+static cudaError_t launch_transport(const gdrr_ctx* ctx, const McParams& p, uint64_t total, bool rec,
+                                    cudaStream_t s) {
+    const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0 || p.ray_ff != 0;
+    if (!rec && !gen && ctx->opt.photon_pool > 0) {
+        int per_sm = mc_pool_occupancy_blocks(ctx->n_mat, ctx->opt.photon_pool);
+        if (ctx->opt.blocks_per_sm > 0 && ctx->opt.blocks_per_sm < per_sm) per_sm = ctx->opt.blocks_per_sm;
+        if (per_sm > 0) {
+            int64_t grid = (int64_t)per_sm * ctx->n_sm;
+            const int64_t useful = (int64_t)((total + 31) / 32 * 32 + pool_threads() - 1) / pool_threads();
+            if (grid > useful) grid = useful;
+            return launch_mc_pool(p, ctx->opt.photon_pool, grid < 1 ? 1 : (int)grid, s);
+        }
+    }
+    return launch_mc(p, ctx->opt.block_size, launch_grid(ctx, total, rec), rec, s);
+}
+
 // The launch-independent part of the transport parameters.
 static McParams static_mc_params(const gdrr_ctx* ctx) {
     McParams p;
@@ -787,7 +807,7 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     p.scatter_filter = ctx->opt.scatter_filter;
     p.ray_ff = ctx->opt.rayleigh_form_factor;
     const bool rec = records_dev != nullptr;
-    return cuda_err(launch_mc(p, ctx->opt.block_size, launch_grid(ctx, total, rec), rec, ctx->stream));
+    return cuda_err(launch_transport(ctx, p, total, rec, ctx->stream));
 }
 
 GDRR_API int gdrr_mc_project(gdrr_ctx* ctx, double angle_rad, uint32_t angle_index, uint64_t n_photons,
@@ -892,7 +912,7 @@ GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* ang
         if (ce == cudaSuccess && !stats_dev)
             ce = cudaMemsetAsync(sc->d_stats, 0, GDRR_NSTATS * sizeof(unsigned long long), cs);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), cs);
-        if (ce == cudaSuccess) ce = launch_mc(p, ctx->opt.block_size, launch_grid(ctx, total, false), false, cs);
+        if (ce == cudaSuccess) ce = launch_transport(ctx, p, total, false, cs);
         e = cudaStreamEndCapture(cs, &sc->graph);
         if (ce != cudaSuccess) { e = ce; break; }
         if (e != cudaSuccess) break;
@@ -942,30 +962,41 @@ GDRR_API int gdrr_autotune(gdrr_ctx* ctx, double angle_rad, uint64_t n_probe, ui
     static const int blocks[] = {64, 128, 256, 512};
     static const int batch[] = {8, 12, 16, 20, 24, 28, 32};
     static const int hpt[] = {1, 8, 64};
+    static const int pools[] = {1, 2, 3};
     cudaEvent_t e0, e1;
     TRY_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return GDRR_ERR_CUDA; }
     gdrr_mc_options best = base;
     float best_ms = 3.0e38f;
     int rc = mc_launch(ctx, jobs, n_probe, seed, nullptr, nullptr);   // warm-up
+    std::vector<gdrr_mc_options> grid;
     for (int b : blocks)
         for (int m : batch)
             for (int h : hpt) {
-                if (rc) break;
                 gdrr_mc_options o = base;
-                o.block_size = b; o.batch_min = m; o.hist_per_thread = h; o.blocks_per_sm = 0;
-                ctx->opt = o;
-                float ms = 0.0f;
-                if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
-                rc = mc_launch(ctx, jobs, n_probe, seed, nullptr, nullptr);
-                if (rc) break;
-                if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess
-                    || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                    rc = GDRR_ERR_CUDA;
-                    break;
-                }
-                if (ms < best_ms) { best_ms = ms; best = o; }
+                o.block_size = b; o.batch_min = m; o.hist_per_thread = h; o.blocks_per_sm = 0; o.photon_pool = -1;
+                grid.push_back(o);
             }
+    for (int q : pools)
+        for (int h : hpt) {
+            gdrr_mc_options o = base;
+            o.hist_per_thread = h; o.blocks_per_sm = 0; o.photon_pool = q;
+            grid.push_back(o);
+        }
+    for (const gdrr_mc_options& o : grid) {
+        if (rc) break;
+        ctx->opt = o;
+        float ms = 0.0f;
+        if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
+        rc = mc_launch(ctx, jobs, n_probe, seed, nullptr, nullptr);
+        if (rc) break;
+        if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess
+            || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = GDRR_ERR_CUDA;
+            break;
+        }
+        if (ms < best_ms) { best_ms = ms; best = o; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->opt = rc ? base : best;

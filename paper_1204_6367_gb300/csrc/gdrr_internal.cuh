@@ -166,6 +166,12 @@ struct RtParams {
 
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s);
 int mc_occupancy_blocks(int n_mat, int block, bool records);
+// The photon-pool form of the transport (default options, no records):
+// blocks of pool_threads() threads, per_thread photons per thread in the
+// shared-memory pool; 0 blocks per SM when the pool does not fit.
+cudaError_t launch_mc_pool(const McParams& p, int per_thread, int grid, cudaStream_t s);
+int mc_pool_occupancy_blocks(int n_mat, int per_thread);
+int pool_threads();
 cudaError_t launch_rt(const RtParams& p, double* out, cudaStream_t s);
 cudaError_t launch_rt_siddon(const RtParams& p, double* out, cudaStream_t s);
 cudaError_t launch_air(const RtParams& p, double* out, cudaStream_t s);

@@ -756,6 +756,300 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
         if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
 }
 
+// ---------------------------------------------------------------------------
+// The photon-pool form of the same transport.
+//
+// In mc_kernel a lane keeps its photon from birth to death, so a warp flies
+// only the lanes that are not waiting for a service, and serves its waiting
+// lanes on partial warps.  Here a block of 8 warps shares a pool of photons
+// in shared memory and moves them between warps: every phase runs the
+// photons that need it on full warps.  A round of the block is
+//   START   free slots take new histories (source sampling, box entry);
+//   FLIGHT  each lane flies a photon until its flight needs the corner
+//           gathers or leaves the box, parks it, and takes the next ready
+//           photon of its class;
+//   GATHER  the eight-corner mixture of the parked flights: virtual, real;
+//   INTER   Rayleigh / Compton sampling of the real collisions;
+//   ESCAPE  box exit and imager tally;
+// with a block barrier between phases.  Lane l of every warp serves pool
+// class l only: class l holds K slots, and field f of slot s sits at word
+// (f K + s) 32 + l, so a warp's 32 lanes touch 32 different banks whatever
+// slots they hold.  Each class keeps queues of slot numbers per phase; a
+// queue's entry j goes to warp j mod 8, which packs the work into full warps.
+// The arithmetic per photon is Lane's, call for call (start, step, gather,
+// interact, escape), so every history's draws, decisions and tally are the
+// ones mc_kernel and the oracle produce; only the order in which histories
+// advance differs, and the integer tallies and counters do not depend on it.
+enum : int {
+    PF_PX, PF_PY, PF_PZ, PF_DX, PF_DY, PF_DZ, PF_E, PF_MUMAX, PF_INVMU, PF_TG,
+    PF_STATE, PF_JOB, PF_NSTEPS, PF_ANGLE, PF_HLO, PF_HHI, PF_BLK, PF_N
+};
+// queues (slot numbers, one byte each): ready by round parity, gather,
+// interaction, escape, free by round parity
+enum : int { PQ_R0, PQ_R1, PQ_G, PQ_I, PQ_E, PQ_F0, PQ_F1, PQ_N };
+// per-class counters: queue lengths (by queue), the ready queue's read head
+enum : int { PC_HEAD = PQ_N, PC_N };
+
+constexpr int POOL_WARPS = 8;
+constexpr int POOL_THREADS = 32 * POOL_WARPS;
+
+template <int NM>
+constexpr size_t pool_smem_bytes(int K) {
+    return (size_t)(PF_N + 3 * NM) * K * 32 * sizeof(float) + (size_t)PQ_N * K * 32 + (size_t)PC_N * 32 * sizeof(int);
+}
+
+template <int NM>
+struct Pool {
+    uint32_t* fld;     // [PF_N][K][32]
+    float* cf;         // [3 NM][K][32]
+    uint8_t* q;        // [PQ_N][K][32]
+    int* n;            // [PC_N][32]
+    int K;
+
+    __device__ __forceinline__ uint32_t& u(int f, int s, int l) { return fld[(f * K + s) * 32 + l]; }
+    __device__ __forceinline__ float& fl(int f, int s, int l) { return reinterpret_cast<float*>(fld)[(f * K + s) * 32 + l]; }
+    __device__ __forceinline__ uint8_t& slot(int queue, int j, int l) { return q[(queue * K + j) * 32 + l]; }
+    __device__ __forceinline__ int& cnt(int c, int l) { return n[c * 32 + l]; }
+    __device__ __forceinline__ void push(int queue, int l, int s) {
+        const int j = atomicAdd(&cnt(queue, l), 1);
+        slot(queue, j, l) = (uint8_t)s;
+    }
+    __device__ __forceinline__ void bind(Lane<NM, false, false>& L, int s, int l) {
+        L.coef = cf + s * 32 + l;
+        L.stride = K * 32;
+    }
+    __device__ __forceinline__ void load(Lane<NM, false, false>& L, int s, int l) {
+        L.px = fl(PF_PX, s, l); L.py = fl(PF_PY, s, l); L.pz = fl(PF_PZ, s, l);
+        L.dx = fl(PF_DX, s, l); L.dy = fl(PF_DY, s, l); L.dz = fl(PF_DZ, s, l);
+        L.e = fl(PF_E, s, l); L.mumax = fl(PF_MUMAX, s, l); L.inv_mumax = fl(PF_INVMU, s, l);
+        L.tg = fl(PF_TG, s, l);
+        const uint32_t st = u(PF_STATE, s, l);
+        L.state = (int)(st & 0xffu);
+        L.scattered = (int)(st >> 8);
+        L.job = (int)u(PF_JOB, s, l);
+        L.nsteps = u(PF_NSTEPS, s, l);
+        L.rs.angle = u(PF_ANGLE, s, l); L.rs.hlo = u(PF_HLO, s, l); L.rs.hhi = u(PF_HHI, s, l);
+        L.rs.blk = u(PF_BLK, s, l);
+        bind(L, s, l);
+    }
+    __device__ __forceinline__ void store(const Lane<NM, false, false>& L, int s, int l) {
+        fl(PF_PX, s, l) = L.px; fl(PF_PY, s, l) = L.py; fl(PF_PZ, s, l) = L.pz;
+        fl(PF_DX, s, l) = L.dx; fl(PF_DY, s, l) = L.dy; fl(PF_DZ, s, l) = L.dz;
+        fl(PF_E, s, l) = L.e; fl(PF_MUMAX, s, l) = L.mumax; fl(PF_INVMU, s, l) = L.inv_mumax;
+        fl(PF_TG, s, l) = L.tg;
+        u(PF_STATE, s, l) = (uint32_t)L.state | ((uint32_t)L.scattered << 8);
+        u(PF_JOB, s, l) = (uint32_t)L.job;
+        u(PF_NSTEPS, s, l) = L.nsteps;
+        u(PF_ANGLE, s, l) = L.rs.angle; u(PF_HLO, s, l) = L.rs.hlo; u(PF_HHI, s, l) = L.rs.hhi;
+        u(PF_BLK, s, l) = L.rs.blk;
+    }
+    // a flight that ended stores what the flights changed
+    __device__ __forceinline__ void store_flight(const Lane<NM, false, false>& L, int s, int l) {
+        fl(PF_PX, s, l) = L.px; fl(PF_PY, s, l) = L.py; fl(PF_PZ, s, l) = L.pz;
+        fl(PF_TG, s, l) = L.tg;
+        u(PF_STATE, s, l) = (uint32_t)L.state | ((uint32_t)L.scattered << 8);
+        u(PF_NSTEPS, s, l) = L.nsteps;
+        u(PF_BLK, s, l) = L.rs.blk;
+    }
+};
+
+// tail: once no idle lane of a warp can take another ready photon and fewer
+// than this many lanes still fly, the warp parks its photons for the next
+// round instead of flying on with a thinning warp
+constexpr int POOL_TAIL = 16;
+
+template <int NM>
+__global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams P, int K) {
+    extern __shared__ __align__(16) unsigned char pool_smem[];
+    __shared__ unsigned long long cnt[GDRR_NSTATS];
+    __shared__ int s_done[POOL_WARPS];
+    __shared__ int s_exit;
+    using L_t = Lane<NM, false, false>;
+    Pool<NM> pl;
+    pl.K = K;
+    pl.fld = reinterpret_cast<uint32_t*>(pool_smem);
+    pl.cf = reinterpret_cast<float*>(pl.fld + (size_t)PF_N * K * 32);
+    pl.q = reinterpret_cast<uint8_t*>(pl.cf + (size_t)3 * NM * K * 32);
+    pl.n = reinterpret_cast<int*>(pl.q + (size_t)PQ_N * K * 32);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x) cnt[i] = 0ull;
+    for (int i = threadIdx.x; i < PC_N * 32; i += blockDim.x) pl.n[i] = 0;
+    if (threadIdx.x < POOL_WARPS) s_done[threadIdx.x] = 0;
+    __syncthreads();
+    if (warp == 0) {
+        pl.cnt(PQ_F0, lane) = K;                          // every slot starts free
+        for (int j = 0; j < K; ++j) pl.slot(PQ_F0, j, lane) = (uint8_t)j;
+    }
+    L_t L;
+    L.state = S_DEAD;
+    uint32_t c_steps = 0, c_virt = 0, c_skip = 0;
+    unsigned long long pool_next = 0, pool_end = 0;
+    bool exhausted = false;
+    __syncthreads();
+
+    for (int round = 0;; ++round) {
+        // queues by round parity: this round's FLIGHT runs qFly (filled by
+        // the last round and by this START); photons that fly next round go
+        // to qNext; START takes the free slots of qF, freed slots go to qFn
+        const int c = round & 1;
+        const int qFly = c ? PQ_R0 : PQ_R1, qNext = c ? PQ_R1 : PQ_R0;
+        const int qF = c ? PQ_F1 : PQ_F0, qFn = c ? PQ_F0 : PQ_F1;
+
+        // ---- START: free slots of this round take new histories ----------
+        if (warp == 0) {
+            pl.cnt(PQ_E, lane) = 0;                       // consumed by the last ESCAPE
+            const int nfree = __reduce_add_sync(FULL, (unsigned)pl.cnt(qF, lane));
+            int ndone = 0;
+            for (int w = 0; w < POOL_WARPS; ++w) ndone += s_done[w];
+            if (lane == 0) s_exit = (nfree == 32 * K && ndone == POOL_WARPS) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_exit) break;
+        {
+            const int nf = pl.cnt(qF, lane);
+            int j = warp;
+            bool need = j < nf;
+            int sl = need ? pl.slot(qF, j, lane) : 0;
+            while (!exhausted) {
+                const unsigned nb = __ballot_sync(FULL, need);
+                if (nb == 0u) break;
+                if (pool_next >= pool_end) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)P.chunk);
+                    base = __shfl_sync(FULL, base, 0);
+                    if (base >= P.total) { exhausted = true; break; }
+                    pool_next = base;
+                    pool_end = base + (unsigned long long)P.chunk;
+                    if (pool_end > P.total) pool_end = P.total;
+                }
+                const unsigned avail = (unsigned)(pool_end - pool_next);
+                const unsigned want = (unsigned)__popc(nb);
+                const unsigned take = want < avail ? want : avail;
+                const unsigned rank = (unsigned)__popc(nb & ((1u << lane) - 1u));
+                if (need && rank < take) {
+                    pl.bind(L, sl, lane);
+                    L.start(P, pool_next + rank, cnt);
+                    if (L.state == S_FLY) {                 // else it missed the box and was tallied: retry
+                        pl.store(L, sl, lane);
+                        pl.push(qFly, lane, sl);
+                        j += POOL_WARPS;
+                        need = j < nf;
+                        if (need) sl = pl.slot(qF, j, lane);
+                    }
+                }
+                pool_next += take;
+            }
+            // free slots that got no history stay free for a later round
+            for (; need; ) {
+                pl.push(qFn, lane, sl);
+                j += POOL_WARPS;
+                need = j < nf;
+                if (need) sl = pl.slot(qF, j, lane);
+            }
+            if (lane == 0) s_done[warp] = (exhausted && pool_next >= pool_end) ? 1 : 0;
+        }
+        __syncthreads();
+
+        // ---- FLIGHT ---------------------------------------------------------
+        if (warp == 0) pl.cnt(qF, lane) = 0;             // consumed by START
+        {
+            const int nR = pl.cnt(qFly, lane);
+            bool have = false, drained = false;
+            int sl = 0;
+            for (;;) {
+                if (!have && !drained) {
+                    const int pos = atomicAdd(&pl.cnt(PC_HEAD, lane), 1);
+                    if (pos < nR) {
+                        sl = pl.slot(qFly, pos, lane);
+                        pl.load(L, sl, lane);
+                        have = true;
+                    } else {
+                        drained = true;
+                    }
+                }
+                const unsigned act = __ballot_sync(FULL, have);
+                const unsigned idle_open = __ballot_sync(FULL, !have && !drained);
+                if (act == 0u && idle_open == 0u) break;
+                if (idle_open == 0u && __popc(act) < POOL_TAIL) {
+                    if (have) {                           // park for the next round
+                        pl.store_flight(L, sl, lane);
+                        pl.push(qNext, lane, sl);
+                    }
+                    break;
+                }
+                if (have) {
+                    L.step(P, c_steps, c_virt, c_skip, cnt);
+                    if (L.state != S_FLY) {
+                        pl.store_flight(L, sl, lane);
+                        if (L.state == S_GATHER) pl.push(PQ_G, lane, sl);
+                        else if (L.state == S_ESC) pl.push(PQ_E, lane, sl);
+                        else pl.push(qFn, lane, sl);        // step limit: the history ended
+                        have = false;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- GATHER -----------------------------------------------------------
+        if (warp == 0) { pl.cnt(qFly, lane) = 0; pl.cnt(PC_HEAD, lane) = 0; }   // consumed by FLIGHT
+        {
+            const int nG = pl.cnt(PQ_G, lane);
+            for (int j = warp; j < nG; j += POOL_WARPS) {
+                const int sl = pl.slot(PQ_G, j, lane);
+                pl.load(L, sl, lane);
+                L.gather(P, c_virt, cnt);
+                if (L.state == S_DEAD) {
+                    pl.push(qFn, lane, sl);               // photoelectric absorption
+                } else {
+                    pl.u(PF_STATE, sl, lane) = (uint32_t)L.state | ((uint32_t)L.scattered << 8);
+                    pl.push(L.state == S_FLY ? qNext : PQ_I, lane, sl);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- INTER ------------------------------------------------------------
+        if (warp == 0) pl.cnt(PQ_G, lane) = 0;
+        {
+            const int nI = pl.cnt(PQ_I, lane);
+            for (int j = warp; j < nI; j += POOL_WARPS) {
+                const int sl = pl.slot(PQ_I, j, lane);
+                pl.load(L, sl, lane);
+                L.interact(P, cnt);
+                if (L.state == S_DEAD) {
+                    pl.push(qFn, lane, sl);               // energy cut-off
+                } else {
+                    pl.store(L, sl, lane);
+                    pl.push(qNext, lane, sl);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- ESCAPE -----------------------------------------------------------
+        if (warp == 0) pl.cnt(PQ_I, lane) = 0;
+        {
+            const int nE = pl.cnt(PQ_E, lane);
+            for (int j = warp; j < nE; j += POOL_WARPS) {
+                const int sl = pl.slot(PQ_E, j, lane);
+                pl.load(L, sl, lane);
+                L.escape(P, cnt, true);
+                pl.push(qFn, lane, sl);
+            }
+        }
+        __syncthreads();
+    }
+
+    atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)c_steps);
+    atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)c_virt);
+    atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)c_skip);
+    __syncthreads();
+    for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
+        if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
+}
+
 // Gather roofline probe: the transport's trilinear corner gather (same
 // layout, same index arithmetic) at pseudo-random cells, with nothing else,
 // so the memory system's ceiling for this access pattern can be measured.
@@ -848,7 +1142,45 @@ int occupancy_nm(int n_mat, int block) {
     return occupancy_t<8, REC, GEN>(block);
 }
 
+template <int NM>
+cudaError_t launch_pool_t(const McParams& p, int K, int grid, cudaStream_t s) {
+    const size_t bytes = pool_smem_bytes<NM>(K);
+    cudaError_t e = cudaFuncSetAttribute(mc_pool_kernel<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    mc_pool_kernel<NM><<<grid, POOL_THREADS, bytes, s>>>(p, K);
+    return cudaGetLastError();
+}
+
+template <int NM>
+int pool_occupancy_t(int K) {
+    const size_t bytes = pool_smem_bytes<NM>(K);
+    int n = 0;
+    if (cudaFuncSetAttribute(mc_pool_kernel<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess
+        || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_pool_kernel<NM>, POOL_THREADS, bytes) != cudaSuccess)
+        return 0;
+    return n;
+}
+
 }  // namespace
+
+int pool_threads() { return POOL_THREADS; }
+
+// slots per lane class for pool photons per thread
+static int pool_k(int per_thread) { return POOL_WARPS * per_thread; }
+
+cudaError_t launch_mc_pool(const McParams& p, int per_thread, int grid, cudaStream_t s) {
+    const int K = pool_k(per_thread);
+    if (p.n_mat <= 2) return launch_pool_t<2>(p, K, grid, s);
+    if (p.n_mat <= 4) return launch_pool_t<4>(p, K, grid, s);
+    return launch_pool_t<8>(p, K, grid, s);
+}
+
+int mc_pool_occupancy_blocks(int n_mat, int per_thread) {
+    const int K = pool_k(per_thread);
+    if (n_mat <= 2) return pool_occupancy_t<2>(K);
+    if (n_mat <= 4) return pool_occupancy_t<4>(K);
+    return pool_occupancy_t<8>(K);
+}
 
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s) {
     const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0 || p.ray_ff != 0;

@@ -74,7 +74,7 @@ class McOptions(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("hist_per_thread", ctypes.c_int32),
                 ("batch_min", ctypes.c_int32), ("nearest_voxel", ctypes.c_int32),
                 ("scatter_filter", ctypes.c_int32), ("rayleigh_form_factor", ctypes.c_int32),
-                ("cell_shift", ctypes.c_int32)]
+                ("cell_shift", ctypes.c_int32), ("photon_pool", ctypes.c_int32)]
 
 
 class Projection(ctypes.Structure):

@@ -88,10 +88,14 @@ def test_torso_4mm_polyenergetic_bit_exact(gd):
     np.testing.assert_array_equal(ts, ots)
 
 
-@pytest.mark.parametrize("opts", [dict(block_size=64, hist_per_thread=1, batch_min=1),
-                                  dict(block_size=128, hist_per_thread=64, batch_min=32),
-                                  dict(block_size=256, hist_per_thread=3, batch_min=3, blocks_per_sm=1),
-                                  dict(block_size=512, hist_per_thread=8, batch_min=20)])
+@pytest.mark.parametrize("opts", [dict(photon_pool=-1, block_size=64, hist_per_thread=1, batch_min=1),
+                                  dict(photon_pool=-1, block_size=128, hist_per_thread=64, batch_min=32),
+                                  dict(photon_pool=-1, block_size=256, hist_per_thread=3, batch_min=3,
+                                       blocks_per_sm=1),
+                                  dict(photon_pool=-1, block_size=512, hist_per_thread=8, batch_min=20),
+                                  dict(photon_pool=1, hist_per_thread=1),
+                                  dict(photon_pool=3, hist_per_thread=64),
+                                  dict(photon_pool=2, hist_per_thread=5, blocks_per_sm=1)])
 def test_launch_configuration_invariance(gd, small, opts):
     n = 200_003
     ref = _run_gpu(gd, small, n, seed=5)
@@ -300,6 +304,7 @@ def test_autotune_keeps_results(gd, small):
         ref = gd.gdrr_mc_project(ctx, 150_000, 8)
         best = gd.gdrr_autotune(ctx, 0.0, 200_000, 3)
         assert best["block_size"] in (64, 128, 256, 512) and 8 <= best["batch_min"] <= 32
+        assert best["photon_pool"] in (-1, 1, 2, 3)
         assert best["hist_per_thread"] in (1, 8, 64)
         assert gd.gdrr_get_options(ctx)["batch_min"] == best["batch_min"]
         got = gd.gdrr_mc_project(ctx, 150_000, 8)
@@ -457,11 +462,13 @@ def test_eight_materials_at_512_threads(gd):
     prob.density[:] = rng.uniform(0.1, 2.0, prob.density.shape).astype(np.float32)
     prob.form_factor = None
     n = 100_000
-    got = _run_gpu(gd, prob, n, seed=3, block_size=512)
     ref = oracle.mc_run(prob, n, seed=3, threads=NTH)
-    np.testing.assert_array_equal(got[0], ref[0])
-    np.testing.assert_array_equal(got[1], ref[1])
-    assert got[2] == ref[2]
+    # the lane form at 512 threads, and the pool form (8 materials: its largest pool)
+    for opts in (dict(block_size=512, photon_pool=-1), dict(photon_pool=3), dict(photon_pool=1)):
+        got = _run_gpu(gd, prob, n, seed=3, **opts)
+        np.testing.assert_array_equal(got[0], ref[0])
+        np.testing.assert_array_equal(got[1], ref[1])
+        assert got[2] == ref[2]
 
 
 def test_roofline_probes(gd):
