@@ -774,6 +774,7 @@ static McParams static_mc_params(const gdrr_ctx* ctx) {
     p.inv_hc = (float)(1.0 / 12.398419843320026);
     p.cells = ctx->d_cells;
     p.cshift = ctx->cell_shift; p.ncx = ctx->ncx; p.ncy = ctx->ncy;
+    p.status = ctx->d_status;
     p.ff_idx = ctx->ff_idx;
     return p;
 }

@@ -107,6 +107,7 @@ struct McParams {
     // slots; NULL disables the early virtual-collision test
     const float* cells;
     int cshift, ncx, ncy;
+    int* status;                   // NULL, or where a bounded loop that gave up records it
 };
 
 // Bounded waits on flags that another CTA publishes (release store, acquire

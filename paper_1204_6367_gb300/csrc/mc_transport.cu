@@ -854,9 +854,15 @@ struct Pool {
 };
 
 // tail: once no idle lane of a warp can take another ready photon and fewer
-// than this many lanes still fly, the warp parks its photons for the next
-// round instead of flying on with a thinning warp
+// than POOL_TAIL lanes still fly, the warp parks its photons for the next
+// round instead of flying on with a thinning warp, but only photons that have
+// flown at least POOL_PARK_MIN flights in this phase: every round moves every
+// photon on, so the rounds end
 constexpr int POOL_TAIL = 16;
+constexpr uint32_t POOL_PARK_MIN = 16;
+// rounds a block may run (a block's rounds number in the thousands for 1e8
+// histories); past it the block records a timeout in P.status and stops
+constexpr int POOL_MAX_ROUNDS = 1 << 22;
 
 template <int NM>
 __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams P, int K) {
@@ -889,6 +895,10 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
     __syncthreads();
 
     for (int round = 0;; ++round) {
+        if (round >= POOL_MAX_ROUNDS) {
+            if (threadIdx.x == 0 && P.status) atomicOr(P.status, 2);
+            break;
+        }
         // queues by round parity: this round's FLIGHT runs qFly (filled by
         // the last round and by this START); photons that fly next round go
         // to qNext; START takes the free slots of qF, freed slots go to qFn
@@ -957,6 +967,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
             const int nR = pl.cnt(qFly, lane);
             bool have = false, drained = false;
             int sl = 0;
+            uint32_t flown = 0;                           // flights of the held photon in this phase
             for (;;) {
                 if (!have && !drained) {
                     const int pos = atomicAdd(&pl.cnt(PC_HEAD, lane), 1);
@@ -964,14 +975,16 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                         sl = pl.slot(qFly, pos, lane);
                         pl.load(L, sl, lane);
                         have = true;
+                        flown = 0;
                     } else {
                         drained = true;
                     }
                 }
                 const unsigned act = __ballot_sync(FULL, have);
                 const unsigned idle_open = __ballot_sync(FULL, !have && !drained);
+                const unsigned fresh = __ballot_sync(FULL, have && flown < POOL_PARK_MIN);
                 if (act == 0u && idle_open == 0u) break;
-                if (idle_open == 0u && __popc(act) < POOL_TAIL) {
+                if (idle_open == 0u && fresh == 0u && __popc(act) < POOL_TAIL) {
                     if (have) {                           // park for the next round
                         pl.store_flight(L, sl, lane);
                         pl.push(qNext, lane, sl);
@@ -980,6 +993,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                 }
                 if (have) {
                     L.step(P, c_steps, c_virt, c_skip, cnt);
+                    ++flown;
                     if (L.state != S_FLY) {
                         pl.store_flight(L, sl, lane);
                         if (L.state == S_GATHER) pl.push(PQ_G, lane, sl);
