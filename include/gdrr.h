@@ -230,7 +230,8 @@ GDRR_API const char* gdrr_error_string(int code);
 GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* options);
 GDRR_API int gdrr_get_options(const gdrr_ctx* ctx, gdrr_mc_options* options);
 
-/* Synchronise the context stream; returns GDRR_ERR_CUDA on a kernel fault,
+/* Synchronise the context stream; returns GDRR_ERR_CUDA on a kernel fault
+ * or a failed self-check of the transport's photon bookkeeping,
  * GDRR_ERR_TIMEOUT when a bounded device-side wait of an earlier call on the
  * context gave up since the last gdrr_sync. */
 GDRR_API int gdrr_sync(gdrr_ctx* ctx);

@@ -100,6 +100,11 @@ struct gdrr_scan {
 
 namespace {
 
+// The device status record: bits 1 and 2, a bounded wait or loop that gave
+// up (GDRR_ERR_TIMEOUT); bit 4, a failed self-check of the transport's
+// photon bookkeeping (GDRR_ERR_CUDA).
+int status_code(int status) { return (status & 4) ? GDRR_ERR_CUDA : GDRR_ERR_TIMEOUT; }
+
 int cuda_err(cudaError_t e) {
     if (e == cudaSuccess) return GDRR_OK;
     return e == cudaErrorMemoryAllocation ? GDRR_ERR_OOM : GDRR_ERR_CUDA;
@@ -681,7 +686,7 @@ GDRR_API int gdrr_sync(gdrr_ctx* ctx) {
     if (!status) return GDRR_OK;
     TRY_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
     TRY_CUDA(cudaStreamSynchronize(ctx->stream));
-    return GDRR_ERR_TIMEOUT;
+    return status_code(status);
 }
 
 GDRR_API int gdrr_air_scan(gdrr_ctx* ctx, double* I0_dev) {
@@ -1159,7 +1164,7 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
     if (h->status) {
         TRY_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
         TRY_CUDA(cudaStreamSynchronize(st));
-        return GDRR_ERR_TIMEOUT;
+        return status_code(h->status);
     }
     if (h->overflow) return GDRR_ERR_TALLY_OVERFLOW;
     if (h->stats[GDRR_ST_STEP_LIMIT]) return GDRR_ERR_STEP_LIMIT;

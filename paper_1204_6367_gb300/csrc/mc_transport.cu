@@ -793,26 +793,29 @@ enum : int { PC_HEAD = PQ_N, PC_N };
 constexpr int POOL_WARPS = 8;
 constexpr int POOL_THREADS = 32 * POOL_WARPS;
 
+// Queue entries are whole 32-bit words: entries of different classes written
+// by different warps at the same time never share a word.
 template <int NM>
 constexpr size_t pool_smem_bytes(int K) {
-    return (size_t)(PF_N + 3 * NM) * K * 32 * sizeof(float) + (size_t)PQ_N * K * 32 + (size_t)PC_N * 32 * sizeof(int);
+    return (size_t)(PF_N + 3 * NM) * K * 32 * sizeof(float) + (size_t)PQ_N * K * 32 * sizeof(int) +
+           (size_t)PC_N * 32 * sizeof(int);
 }
 
 template <int NM>
 struct Pool {
     uint32_t* fld;     // [PF_N][K][32]
     float* cf;         // [3 NM][K][32]
-    uint8_t* q;        // [PQ_N][K][32]
+    int* q;            // [PQ_N][K][32] slot numbers
     int* n;            // [PC_N][32]
     int K;
 
     __device__ __forceinline__ uint32_t& u(int f, int s, int l) { return fld[(f * K + s) * 32 + l]; }
     __device__ __forceinline__ float& fl(int f, int s, int l) { return reinterpret_cast<float*>(fld)[(f * K + s) * 32 + l]; }
-    __device__ __forceinline__ uint8_t& slot(int queue, int j, int l) { return q[(queue * K + j) * 32 + l]; }
+    __device__ __forceinline__ int& slot(int queue, int j, int l) { return q[(queue * K + j) * 32 + l]; }
     __device__ __forceinline__ int& cnt(int c, int l) { return n[c * 32 + l]; }
     __device__ __forceinline__ void push(int queue, int l, int s) {
         const int j = atomicAdd(&cnt(queue, l), 1);
-        slot(queue, j, l) = (uint8_t)s;
+        slot(queue, j, l) = s;
     }
     __device__ __forceinline__ void bind(Lane<NM, false, false>& L, int s, int l) {
         L.coef = cf + s * 32 + l;
@@ -875,8 +878,8 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
     pl.K = K;
     pl.fld = reinterpret_cast<uint32_t*>(pool_smem);
     pl.cf = reinterpret_cast<float*>(pl.fld + (size_t)PF_N * K * 32);
-    pl.q = reinterpret_cast<uint8_t*>(pl.cf + (size_t)3 * NM * K * 32);
-    pl.n = reinterpret_cast<int*>(pl.q + (size_t)PQ_N * K * 32);
+    pl.q = reinterpret_cast<int*>(pl.cf + (size_t)3 * NM * K * 32);
+    pl.n = pl.q + (size_t)PQ_N * K * 32;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x) cnt[i] = 0ull;
@@ -885,7 +888,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
     __syncthreads();
     if (warp == 0) {
         pl.cnt(PQ_F0, lane) = K;                          // every slot starts free
-        for (int j = 0; j < K; ++j) pl.slot(PQ_F0, j, lane) = (uint8_t)j;
+        for (int j = 0; j < K; ++j) pl.slot(PQ_F0, j, lane) = j;
     }
     L_t L;
     L.state = S_DEAD;
@@ -909,10 +912,19 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
         // ---- START: free slots of this round take new histories ----------
         if (warp == 0) {
             pl.cnt(PQ_E, lane) = 0;                       // consumed by the last ESCAPE
+            // between rounds every slot of a class is free or ready to fly
+            const bool whole = pl.cnt(qF, lane) + pl.cnt(qFly, lane) == K;
+            const unsigned broken = __ballot_sync(FULL, !whole);
             const int nfree = __reduce_add_sync(FULL, (unsigned)pl.cnt(qF, lane));
             int ndone = 0;
             for (int w = 0; w < POOL_WARPS; ++w) ndone += s_done[w];
-            if (lane == 0) s_exit = (nfree == 32 * K && ndone == POOL_WARPS) ? 1 : 0;
+            if (lane == 0) {
+                s_exit = (nfree == 32 * K && ndone == POOL_WARPS) ? 1 : 0;
+                if (broken) {                             // a slot went missing: stop, and say so
+                    if (P.status) atomicOr(P.status, 4);
+                    s_exit = 1;
+                }
+            }
         }
         __syncthreads();
         if (s_exit) break;
