@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(1024) denoise_fused_kernel(
         }
     }
     if (threadIdx.x == 0) s_abort = 0;
+    __syncwarp();                                 // converged warps at every block barrier
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(1024) denoise_fused_kernel(
             }
             __threadfence();
         }
+        __syncwarp();
         __syncthreads();
         if (s_abort) return;
         const double* src = (k & 1) ? buf1 : buf0;
@@ -240,6 +242,7 @@ __global__ void __launch_bounds__(1024) denoise_fused_kernel(
                 dst[iv * nu + iu] = cur[p];
             }
         }
+        __syncwarp();
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();

@@ -790,6 +790,16 @@ enum : int { PQ_R0, PQ_R1, PQ_G, PQ_I, PQ_E, PQ_F0, PQ_F1, PQ_N };
 // per-class counters: queue lengths (by queue), the ready queue's read head
 enum : int { PC_HEAD = PQ_N, PC_N };
 
+// A block barrier reached by a converged warp.  The phases end in per-lane
+// loops of different lengths, and an aligned barrier (bar.sync) that a warp
+// reaches in several diverged groups can release before another warp has
+// arrived; reconverging the warp first keeps every phase's queue updates
+// ahead of the next phase.
+__device__ __forceinline__ void block_sync() {
+    __syncwarp();
+    __syncthreads();
+}
+
 constexpr int POOL_WARPS = 8;
 constexpr int POOL_THREADS = 32 * POOL_WARPS;
 
@@ -885,7 +895,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x) cnt[i] = 0ull;
     for (int i = threadIdx.x; i < PC_N * 32; i += blockDim.x) pl.n[i] = 0;
     if (threadIdx.x < POOL_WARPS) s_done[threadIdx.x] = 0;
-    __syncthreads();
+    block_sync();
     if (warp == 0) {
         pl.cnt(PQ_F0, lane) = K;                          // every slot starts free
         for (int j = 0; j < K; ++j) pl.slot(PQ_F0, j, lane) = j;
@@ -895,7 +905,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
     uint32_t c_steps = 0, c_virt = 0, c_skip = 0;
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
-    __syncthreads();
+    block_sync();
 
     for (int round = 0;; ++round) {
         if (round >= POOL_MAX_ROUNDS) {
@@ -926,7 +936,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                 }
             }
         }
-        __syncthreads();
+        block_sync();
         if (s_exit) break;
         {
             const int nf = pl.cnt(qF, lane);
@@ -971,7 +981,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
             }
             if (lane == 0) s_done[warp] = (exhausted && pool_next >= pool_end) ? 1 : 0;
         }
-        __syncthreads();
+        block_sync();
 
         // ---- FLIGHT ---------------------------------------------------------
         if (warp == 0) pl.cnt(qF, lane) = 0;             // consumed by START
@@ -1016,7 +1026,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                 }
             }
         }
-        __syncthreads();
+        block_sync();
 
         // ---- GATHER -----------------------------------------------------------
         if (warp == 0) { pl.cnt(qFly, lane) = 0; pl.cnt(PC_HEAD, lane) = 0; }   // consumed by FLIGHT
@@ -1034,7 +1044,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                 }
             }
         }
-        __syncthreads();
+        block_sync();
 
         // ---- INTER ------------------------------------------------------------
         if (warp == 0) pl.cnt(PQ_G, lane) = 0;
@@ -1052,7 +1062,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                 }
             }
         }
-        __syncthreads();
+        block_sync();
 
         // ---- ESCAPE -----------------------------------------------------------
         if (warp == 0) pl.cnt(PQ_I, lane) = 0;
@@ -1065,13 +1075,13 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                 pl.push(qFn, lane, sl);
             }
         }
-        __syncthreads();
+        block_sync();
     }
 
     atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)c_steps);
     atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)c_virt);
     atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)c_skip);
-    __syncthreads();
+    block_sync();
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
         if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
 }
