@@ -1029,7 +1029,14 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
         block_sync();
 
         // ---- GATHER -----------------------------------------------------------
-        if (warp == 0) { pl.cnt(qFly, lane) = 0; pl.cnt(PC_HEAD, lane) = 0; }   // consumed by FLIGHT
+        if (warp == 0) {
+            // a warp that parks can leave ready photons of a class unpopped
+            // (its lane of that class still held one): they fly next round
+            const int nR = pl.cnt(qFly, lane);
+            for (int pos = pl.cnt(PC_HEAD, lane); pos < nR; ++pos) pl.push(qNext, lane, pl.slot(qFly, pos, lane));
+            pl.cnt(qFly, lane) = 0;
+            pl.cnt(PC_HEAD, lane) = 0;
+        }
         {
             const int nG = pl.cnt(PQ_G, lane);
             for (int j = warp; j < nG; j += POOL_WARPS) {
