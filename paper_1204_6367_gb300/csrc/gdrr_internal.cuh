@@ -108,6 +108,7 @@ struct McParams {
     const float* cells;
     int cshift, ncx, ncy;
     int* status;                   // NULL, or where a bounded loop that gave up records it
+    int pool_tail, pool_park_min;  // pool form: tail width and parking minimum (0: defaults)
 };
 
 // Bounded waits on flags that another CTA publishes (release store, acquire

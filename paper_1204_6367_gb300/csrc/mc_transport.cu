@@ -867,18 +867,16 @@ struct Pool {
 };
 
 // tail: once no idle lane of a warp can take another ready photon and fewer
-// than POOL_TAIL lanes still fly, the warp parks its photons for the next
-// round instead of flying on with a thinning warp, but only photons that have
-// flown at least POOL_PARK_MIN flights in this phase: every round moves every
-// photon on, so the rounds end
-constexpr int POOL_TAIL = 16;
-constexpr uint32_t POOL_PARK_MIN = 16;
+// than `tail` lanes still fly, the warp parks its photons for the next round
+// instead of flying on with a thinning warp, but only photons that have
+// flown at least `park_min` (>= 1) flights in this phase: every round moves
+// every photon on, so the rounds end
 // rounds a block may run (a block's rounds number in the thousands for 1e8
 // histories); past it the block records a timeout in P.status and stops
 constexpr int POOL_MAX_ROUNDS = 1 << 22;
 
 template <int NM>
-__global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams P, int K) {
+__global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams P, int K, int tail, uint32_t park_min) {
     extern __shared__ __align__(16) unsigned char pool_smem[];
     __shared__ unsigned long long cnt[GDRR_NSTATS];
     __shared__ int s_done[POOL_WARPS];
@@ -1004,9 +1002,9 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                 }
                 const unsigned act = __ballot_sync(FULL, have);
                 const unsigned idle_open = __ballot_sync(FULL, !have && !drained);
-                const unsigned fresh = __ballot_sync(FULL, have && flown < POOL_PARK_MIN);
+                const unsigned fresh = __ballot_sync(FULL, have && flown < park_min);
                 if (act == 0u && idle_open == 0u) break;
-                if (idle_open == 0u && fresh == 0u && __popc(act) < POOL_TAIL) {
+                if (idle_open == 0u && fresh == 0u && __popc(act) < tail) {
                     if (have) {                           // park for the next round
                         pl.store_flight(L, sl, lane);
                         pl.push(qNext, lane, sl);
@@ -1190,7 +1188,9 @@ cudaError_t launch_pool_t(const McParams& p, int K, int grid, cudaStream_t s) {
     const size_t bytes = pool_smem_bytes<NM>(K);
     cudaError_t e = cudaFuncSetAttribute(mc_pool_kernel<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    mc_pool_kernel<NM><<<grid, POOL_THREADS, bytes, s>>>(p, K);
+    const int tail = p.pool_tail > 0 ? p.pool_tail : 16;
+    const uint32_t park_min = p.pool_park_min > 0 ? (uint32_t)p.pool_park_min : 4u;
+    mc_pool_kernel<NM><<<grid, POOL_THREADS, bytes, s>>>(p, K, tail, park_min);
     return cudaGetLastError();
 }
 
