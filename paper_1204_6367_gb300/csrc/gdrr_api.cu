@@ -369,7 +369,7 @@ void set_defaults(gdrr_mc_options* o) {
     if (o->block_size <= 0) o->block_size = 256;
     if (o->hist_per_thread <= 0) o->hist_per_thread = 8;
     if (o->batch_min <= 0) o->batch_min = 16;
-    if (o->photon_pool == 0) o->photon_pool = 2;
+    if (o->photon_pool == 0) o->photon_pool = -1;
 }
 
 // Default macro cells: about 8 mm on a side, 2^s voxels of the smallest voxel
