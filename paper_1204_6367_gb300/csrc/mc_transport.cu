@@ -655,31 +655,33 @@ struct Lane {
         }
     }
 
-    // The deferred Rayleigh or Compton interaction of a waiting lane.
+    // The deferred Rayleigh or Compton interaction of a waiting lane.  The
+    // polar angle comes from the event's own sampler; the azimuth and the
+    // rotation are common code, so a batch holding both kinds runs them once.
     __device__ __forceinline__ void interact(const McParams& P, unsigned long long* cnt) {
-        float cp, sp;
-        if (state == S_RAY) {
-            float ct;
+        const bool ray = state == S_RAY;
+        float ct, e2 = e;
+        if (ray) {
             if (GEN && P.ray_ff) {
                 ct = rayleigh_ff(rs, P, e, m_ray);
                 if (REC) r_raymat = (uint32_t)m_ray;
             } else {
                 ct = rayleigh(rs, P.rk);
             }
-            azimuth(rs, P.rk, cp, sp);
-            rotate(dx, dy, dz, ct, cp, sp);
-            scattered = 1;
+        } else {
+            compton(rs, P.rk, e, ct, e2);
+        }
+        float cp, sp;
+        azimuth(rs, P.rk, cp, sp);
+        rotate(dx, dy, dz, ct, cp, sp);
+        scattered = 1;
+        if (ray) {
             if (GEN) n_int += 0x10000u;
             count(cnt, GDRR_ST_RAYLEIGH);
             if (REC) { ++r_ray; if (!r_first) r_first = 1; }
             state = S_FLY;
             return;
         }
-        float ct, e2;
-        compton(rs, P.rk, e, ct, e2);
-        azimuth(rs, P.rk, cp, sp);
-        rotate(dx, dy, dz, ct, cp, sp);
-        scattered = 1;
         if (GEN) n_int += 1u;
         count(cnt, GDRR_ST_COMPTON);
         if (REC) { ++r_comp; if (!r_first) r_first = 2; r_dep += (double)e - (double)e2; }

@@ -280,6 +280,54 @@ def test_statistical_agreement_with_fp64_oracle(gd, small):
     assert abs(sg - so) <= 0.005 * so + 3 * sig, (sg, so, sig)
 
 
+def _bin(t, f):
+    nv, nu = t.shape
+    return t.reshape(nv // f, f, nu // f, f).sum(axis=(1, 3))
+
+
+def test_full_size_torso_statistical_agreement(gd, torso):
+    # The headline workload (2 mm poly-energetic torso, 120 kVp, bowtie,
+    # 512 x 384 detector): the FP32 GPU transport at 1e8 histories against the
+    # independent FP64 oracle at 4e7 on the host cores, on other random
+    # streams.  Per pixel: >= 99.7 % within 3 combined sigma (the binomial
+    # band of reading 16) with mean z ~ 0 and sd(z) ~ 1; total scatter within
+    # 0.5 % + 3 sigma.  The pixels are 8 x 8 bins of the detector (64 x 48):
+    # at 4e7 histories the oracle leaves ~0.5 scattered photons per full-
+    # resolution pixel, where a 3-sigma Gaussian band means nothing, and ~30
+    # per bin.
+    n_g, k_g = 100_000_000, 20
+    n_o, k_o = 40_000_000, 20
+    f = 8
+    with gd.Context(torso) as ctx:
+        gd.gdrr_autotune(ctx, 0.0, 10_000_000, 1)
+        cg_p, cg_s = [], []
+        for i in range(k_g):
+            p, s = gd.gdrr_mc_project(ctx, n_g // k_g, 1, history_offset=i * (n_g // k_g))
+            cg_p.append(_bin(p.cpu().numpy(), f)); cg_s.append(_bin(s.cpu().numpy(), f))
+    co_p, co_s = [], []
+    for i in range(k_o):
+        p, s, _, _ = oracle.mc_run(torso, n_o // k_o, seed=77, history_offset=i * (n_o // k_o), precision=64,
+                                   threads=NTH)
+        co_p.append(_bin(p, f)); co_s.append(_bin(s, f))
+    for cg, co in ((cg_p, co_p), (cg_s, co_s)):
+        tg, vg = _pooled(cg)
+        to, vo = _pooled(co)
+        g, o = tg / n_g, to / n_o
+        var = vg / n_g**2 + vo / n_o**2
+        keep = (tg > 0) | (to > 0)
+        z = (g - o)[keep] / np.sqrt(var[keep])
+        n_pix = z.size
+        assert n_pix > 2500
+        frac = float(np.mean(np.abs(z) < 3.0))
+        band = 3.0 * math.sqrt(0.0027 * 0.9973 / n_pix)
+        assert frac >= 0.997 - band, (frac, band)
+        assert abs(float(z.mean())) < 4.0 / math.sqrt(n_pix), float(z.mean())
+        assert abs(float(z.std()) - 1.0) < 0.05, float(z.std())
+    sg, so = np.sum(cg_s) / n_g, np.sum(co_s) / n_o
+    sig = math.sqrt(_pooled(cg_s)[1].sum() / n_g**2 + _pooled(co_s)[1].sum() / n_o**2)
+    assert abs(sg - so) <= 0.005 * so + 3 * sig, (sg, so, sig)
+
+
 def test_scan_graph_replays_equal_batched(gd, small):
     angles = np.linspace(0, 2 * math.pi, 5, endpoint=False)
     budgets = np.array([20_000, 7, 0, 55_555, 31_000], np.uint64)
