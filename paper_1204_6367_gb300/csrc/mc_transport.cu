@@ -304,6 +304,8 @@ struct Lane {
     uint32_t nsteps;
     uint32_t n_int;      // Compton interactions (low 16 bits) and Rayleigh (high 16 bits)
     int m_ray;           // material of the pending form-factor Rayleigh event (GEN)
+    bool defer_e;        // start / interact leave the energy tables to the caller
+    bool need_e;         // ... which must then call set_energy(P, e) before the next flight
     float tg;            // t = xi mu_max of a flight waiting for its corner gathers
     uint32_t wz;         // that flight block's third word (GEN: form-factor material pick)
     Stream rs;
@@ -508,7 +510,7 @@ struct Lane {
         px = px + tmin * dx;
         py = py + tmin * dy;
         pz = pz + tmin * dz;
-        set_energy(P, en);
+        if (defer_e) need_e = true; else set_energy(P, en);
         state = S_FLY;
     }
 
@@ -693,7 +695,12 @@ struct Lane {
             state = S_DEAD;
             return;
         }
-        set_energy(P, e2);
+        if (defer_e) {
+            e = e2;
+            need_e = true;
+        } else {
+            set_energy(P, e2);
+        }
         state = S_FLY;
     }
 };
@@ -712,6 +719,8 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
     L.coef = smem + threadIdx.x;
     L.stride = blockDim.x;
     L.state = S_DEAD;
+    L.defer_e = true;                 // new histories and Compton events share one table pass
+    L.need_e = false;
     uint32_t c_steps = 0, c_virt = 0, c_skip = 0;
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
@@ -744,6 +753,10 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
                     pool_next += take;
                     need = __ballot_sync(FULL, L.state == S_DEAD);
                 }
+            }
+            if (L.need_e) {
+                L.set_energy(P, L.e);
+                L.need_e = false;
             }
             if (exhausted && !__any_sync(FULL, L.state != S_DEAD)) break;
         }
@@ -902,6 +915,8 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
     }
     L_t L;
     L.state = S_DEAD;
+    L.defer_e = false;
+    L.need_e = false;
     uint32_t c_steps = 0, c_virt = 0, c_skip = 0;
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
