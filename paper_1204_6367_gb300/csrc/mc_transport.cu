@@ -207,30 +207,6 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float ct, f
     w = nw_ * il;
 }
 
-__device__ __forceinline__ void compton(Stream& rs, const RoundKeys& rk, float e, float& ct_out, float& e_out) {
-    const float alpha = e * (float)(1.0 / 510.99895);
-    const float ialpha = (float)510.99895 / e;
-    const float ta = 2.0f * alpha;
-    float x;
-    for (;;) {
-        const uint4 w = rs.block(rk);
-        const float r1 = uniform(w.x);
-        const float r2 = uniform(w.y);
-        const float r3 = uniform(w.z);
-        if (r1 <= (1.0f + ta) / (9.0f + ta)) {
-            x = 1.0f + ta * r2;
-            if (r3 <= 4.0f * (x - 1.0f) / (x * x)) break;
-        } else {
-            x = (1.0f + ta) / (1.0f + ta * r2);
-            const float ct = 1.0f - (x - 1.0f) * ialpha;
-            if (r3 <= 0.5f * (ct * ct + 1.0f / x)) break;
-        }
-        if (rs.blk >= MAX_BLOCKS) break;         // keep the last candidate
-    }
-    ct_out = 1.0f - (x - 1.0f) * ialpha;
-    e_out = e / x;
-}
-
 // Rayleigh polar angle with the form factor of material m at energy e: the
 // density of s = x^2 is F^2(s), linear in s between the table's nodes, so
 // its cumulative is the trapezoid sum on the nodes and quadratic within an
@@ -273,13 +249,53 @@ __device__ __forceinline__ float rayleigh_ff(Stream& rs, const McParams& P, floa
     }
 }
 
-__device__ __forceinline__ float rayleigh(Stream& rs, const RoundKeys& rk) {
+// The polar angle of a Rayleigh or Compton event, in one rejection loop for
+// both kinds: each attempt draws the history's next block and applies the
+// event's own test, so a warp serving both kinds runs one Philox per attempt
+// instead of one per kind.
+//  * Rayleigh (Thomson law): mu = 2 a - 1 accepted when 2 b <= 1 + mu^2.
+//  * Compton (Klein-Nishina, Kahn's method): with alpha = E / 511 keV, branch
+//    r1 <= (1 + 2 alpha) / (9 + 2 alpha) takes x = 1 + 2 alpha r2 and accepts
+//    when r3 <= 4 (x - 1) / x^2; else x = (1 + 2 alpha) / (1 + 2 alpha r2),
+//    accepted when r3 <= (cos^2 + 1/x) / 2; cos = 1 - (x - 1) / alpha and
+//    E' = E / x.
+// A history that has drawn MAX_BLOCKS blocks keeps its candidate.
+__device__ __forceinline__ void polar(Stream& rs, const RoundKeys& rk, bool ray, float e, float& ct_out,
+                                      float& e_out) {
+    const float alpha = e * (float)(1.0 / 510.99895);
+    const float ialpha = (float)510.99895 / e;
+    const float ta = 2.0f * alpha;
+    float x = 1.0f, mu = 1.0f;
     for (;;) {
         const uint4 w = rs.block(rk);
-        const float a = uniform(w.x);
-        const float b = uniform(w.y);
-        const float mu = 2.0f * a - 1.0f;
-        if (2.0f * b <= 1.0f + mu * mu || rs.blk >= MAX_BLOCKS) return mu;
+        bool done;
+        if (ray) {
+            const float a = uniform(w.x);
+            const float b = uniform(w.y);
+            mu = 2.0f * a - 1.0f;
+            done = 2.0f * b <= 1.0f + mu * mu || rs.blk >= MAX_BLOCKS;
+        } else {
+            const float r1 = uniform(w.x);
+            const float r2 = uniform(w.y);
+            const float r3 = uniform(w.z);
+            if (r1 <= (1.0f + ta) / (9.0f + ta)) {
+                x = 1.0f + ta * r2;
+                done = r3 <= 4.0f * (x - 1.0f) / (x * x);
+            } else {
+                x = (1.0f + ta) / (1.0f + ta * r2);
+                const float c = 1.0f - (x - 1.0f) * ialpha;
+                done = r3 <= 0.5f * (c * c + 1.0f / x);
+            }
+            done = done || rs.blk >= MAX_BLOCKS;      // keep the last candidate
+        }
+        if (done) break;
+    }
+    if (ray) {
+        ct_out = mu;
+        e_out = e;
+    } else {
+        ct_out = 1.0f - (x - 1.0f) * ialpha;
+        e_out = e / x;
     }
 }
 
@@ -304,6 +320,12 @@ struct Lane {
     uint32_t nsteps;
     uint32_t n_int;      // Compton interactions (low 16 bits) and Rayleigh (high 16 bits)
     int m_ray;           // material of the pending form-factor Rayleigh event (GEN)
+    // thread totals of free flights, virtual collisions and cell-decided
+    // virtual collisions.  Without GEN they are added once per history at its
+    // end (flights = nsteps; cell-decided = flights that neither gathered nor
+    // left the box), so the common free flight carries no counter updates.
+    uint32_t c_steps, c_virt, c_skip;
+    uint32_t ngath;      // flights of the current history that gathered corners (not GEN)
     bool defer_e;        // start / interact leave the energy tables to the caller
     bool need_e;         // ... which must then call set_energy(P, e) before the next flight
     float tg;            // t = xi mu_max of a flight waiting for its corner gathers
@@ -369,6 +391,15 @@ struct Lane {
         inv_mumax = 1.0f / mumax;
     }
 
+    // a history ended; esc: its last flight left the box
+    __device__ __forceinline__ void end_counts(uint32_t esc) {
+        if (GEN) return;
+        const uint32_t skipped = nsteps - ngath - esc;
+        c_steps += nsteps;
+        c_skip += skipped;
+        c_virt += skipped;
+    }
+
     __device__ __forceinline__ void record(const McParams& P, uint32_t outcome, int pixel, uint32_t photo) {
         if (!REC) return;
         gdrr_history_record r;
@@ -419,6 +450,7 @@ struct Lane {
         count(cnt, outcome == OUT_PRIMARY ? GDRR_ST_TALLY_PRIMARY
                                           : (outcome == OUT_SCATTER ? GDRR_ST_TALLY_SCATTER : GDRR_ST_MISS));
         record(P, outcome, pixel, 0);
+        end_counts(from_inside ? 1u : 0u);
         state = S_DEAD;
     }
 
@@ -457,6 +489,7 @@ struct Lane {
         rs.init(J.angle_index, hid);
         count(cnt, GDRR_ST_HISTORIES);
         nsteps = 0;
+        ngath = 0;
         scattered = 0;
         if (GEN) n_int = 0;
         if (REC) { r_virt = 0; r_ray = 0; r_comp = 0; r_first = 0; r_raymat = 0; r_dep = 0.0; }
@@ -515,18 +548,18 @@ struct Lane {
     }
 
     // One Woodcock free flight and the real/virtual decision at its end.
-    __device__ __forceinline__ void step(const McParams& P, uint32_t& c_steps, uint32_t& c_virt, uint32_t& c_skip,
-                                         unsigned long long* cnt) {
+    __device__ __forceinline__ void step(const McParams& P, unsigned long long* cnt) {
         if ((int)nsteps >= P.max_steps) {
             count(cnt, GDRR_ST_STEP_LIMIT);
             record(P, OUT_STEP_LIMIT, -1, 0);
+            end_counts(0u);
             state = S_DEAD;
             return;
         }
         const uint4 wf = rs.block(P.rk);            // this flight's block
         const float s = -gd_logf(uniform(wf.x)) * inv_mumax;
         ++nsteps;
-        ++c_steps;
+        if (GEN) ++c_steps;
         const float qx = px + s * dx, qy = py + s * dy, qz = pz + s * dz;
         const bool inside = (qx >= P.lo[0] && qx <= P.hi[0]) && (qy >= P.lo[1] && qy <= P.hi[1])
                          && (qz >= P.lo[2] && qz <= P.hi[2]);
@@ -567,8 +600,7 @@ struct Lane {
             // above the cell's bound the collision is virtual whatever they hold
             const int cell = (x0 >> P.cshift) + P.ncx * ((y0 >> P.cshift) + P.ncy * (z0 >> P.cshift));
             if (t > cell_bound(P, cell)) {
-                ++c_virt;
-                ++c_skip;
+                if (GEN) { ++c_virt; ++c_skip; }
                 if (REC) ++r_virt;
                 return;
             }
@@ -584,7 +616,8 @@ struct Lane {
     // decision for its t.  The warp serves its waiting lanes together, so the
     // gathers run on many lanes at once instead of on the few whose flights
     // passed the test in one iteration.
-    __device__ __forceinline__ void gather(const McParams& P, uint32_t& c_virt, unsigned long long* cnt) {
+    __device__ __forceinline__ void gather(const McParams& P, unsigned long long* cnt) {
+        if (!GEN) ++ngath;
         const float t = tg;
         const float fx = (px - P.lo[0]) * P.ivox[0] - 0.5f;
         const float fy = (py - P.lo[1]) * P.ivox[1] - 0.5f;
@@ -653,6 +686,7 @@ struct Lane {
             count(cnt, GDRR_ST_PHOTO);
             if (REC) { if (!r_first) r_first = 3; r_dep += (double)e; }
             record(P, OUT_PHOTO, -1, 1);
+            end_counts(0u);
             state = S_DEAD;
         }
     }
@@ -663,15 +697,11 @@ struct Lane {
     __device__ __forceinline__ void interact(const McParams& P, unsigned long long* cnt) {
         const bool ray = state == S_RAY;
         float ct, e2 = e;
-        if (ray) {
-            if (GEN && P.ray_ff) {
-                ct = rayleigh_ff(rs, P, e, m_ray);
-                if (REC) r_raymat = (uint32_t)m_ray;
-            } else {
-                ct = rayleigh(rs, P.rk);
-            }
+        if (GEN && ray && P.ray_ff) {
+            ct = rayleigh_ff(rs, P, e, m_ray);
+            if (REC) r_raymat = (uint32_t)m_ray;
         } else {
-            compton(rs, P.rk, e, ct, e2);
+            polar(rs, P.rk, ray, e, ct, e2);
         }
         float cp, sp;
         azimuth(rs, P.rk, cp, sp);
@@ -692,6 +722,7 @@ struct Lane {
             if (REC) r_dep += (double)e;
             count(cnt, GDRR_ST_CUTOFF);
             record(P, OUT_CUTOFF, -1, 0);
+            end_counts(0u);
             state = S_DEAD;
             return;
         }
@@ -721,7 +752,7 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
     L.state = S_DEAD;
     L.defer_e = true;                 // new histories and Compton events share one table pass
     L.need_e = false;
-    uint32_t c_steps = 0, c_virt = 0, c_skip = 0;
+    L.c_steps = 0; L.c_virt = 0; L.c_skip = 0;
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
 
@@ -730,7 +761,7 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
         if (32 - __popc(fly) >= P.batch_min || fly == 0u) {
             // serve waiting lanes together: corner gathers, interactions,
             // tallies, new histories
-            if (L.state == S_GATHER) L.gather(P, c_virt, cnt);
+            if (L.state == S_GATHER) L.gather(P, cnt);
             if (L.state == S_RAY || L.state == S_COMP) L.interact(P, cnt);
             if (L.state == S_ESC) L.escape(P, cnt, true);
             if (!exhausted) {
@@ -760,12 +791,12 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
             }
             if (exhausted && !__any_sync(FULL, L.state != S_DEAD)) break;
         }
-        if (L.state == S_FLY) L.step(P, c_steps, c_virt, c_skip, cnt);
+        if (L.state == S_FLY) L.step(P, cnt);
     }
 
-    atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)c_steps);
-    atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)c_virt);
-    atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)c_skip);
+    atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)L.c_steps);
+    atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)L.c_virt);
+    atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)L.c_skip);
     __syncthreads();
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
         if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
@@ -797,7 +828,7 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
 // advance differs, and the integer tallies and counters do not depend on it.
 enum : int {
     PF_PX, PF_PY, PF_PZ, PF_DX, PF_DY, PF_DZ, PF_E, PF_MUMAX, PF_INVMU, PF_TG,
-    PF_STATE, PF_JOB, PF_NSTEPS, PF_ANGLE, PF_HLO, PF_HHI, PF_BLK, PF_N
+    PF_STATE, PF_JOB, PF_NSTEPS, PF_NGATH, PF_ANGLE, PF_HLO, PF_HHI, PF_BLK, PF_N
 };
 // queues (slot numbers, one byte each): ready by round parity, gather,
 // interaction, escape, free by round parity
@@ -856,6 +887,7 @@ struct Pool {
         L.scattered = (int)(st >> 8);
         L.job = (int)u(PF_JOB, s, l);
         L.nsteps = u(PF_NSTEPS, s, l);
+        L.ngath = u(PF_NGATH, s, l);
         L.rs.angle = u(PF_ANGLE, s, l); L.rs.hlo = u(PF_HLO, s, l); L.rs.hhi = u(PF_HHI, s, l);
         L.rs.blk = u(PF_BLK, s, l);
         bind(L, s, l);
@@ -868,6 +900,7 @@ struct Pool {
         u(PF_STATE, s, l) = (uint32_t)L.state | ((uint32_t)L.scattered << 8);
         u(PF_JOB, s, l) = (uint32_t)L.job;
         u(PF_NSTEPS, s, l) = L.nsteps;
+        u(PF_NGATH, s, l) = L.ngath;
         u(PF_ANGLE, s, l) = L.rs.angle; u(PF_HLO, s, l) = L.rs.hlo; u(PF_HHI, s, l) = L.rs.hhi;
         u(PF_BLK, s, l) = L.rs.blk;
     }
@@ -917,7 +950,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
     L.state = S_DEAD;
     L.defer_e = false;
     L.need_e = false;
-    uint32_t c_steps = 0, c_virt = 0, c_skip = 0;
+    L.c_steps = 0; L.c_virt = 0; L.c_skip = 0;
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
     block_sync();
@@ -1029,7 +1062,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                     break;
                 }
                 if (have) {
-                    L.step(P, c_steps, c_virt, c_skip, cnt);
+                    L.step(P, cnt);
                     ++flown;
                     if (L.state != S_FLY) {
                         pl.store_flight(L, sl, lane);
@@ -1057,11 +1090,12 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
             for (int j = warp; j < nG; j += POOL_WARPS) {
                 const int sl = pl.slot(PQ_G, j, lane);
                 pl.load(L, sl, lane);
-                L.gather(P, c_virt, cnt);
+                L.gather(P, cnt);
                 if (L.state == S_DEAD) {
                     pl.push(qFn, lane, sl);               // photoelectric absorption
                 } else {
                     pl.u(PF_STATE, sl, lane) = (uint32_t)L.state | ((uint32_t)L.scattered << 8);
+                    pl.u(PF_NGATH, sl, lane) = L.ngath;
                     pl.push(L.state == S_FLY ? qNext : PQ_I, lane, sl);
                 }
             }
@@ -1100,9 +1134,9 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
         block_sync();
     }
 
-    atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)c_steps);
-    atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)c_virt);
-    atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)c_skip);
+    atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)L.c_steps);
+    atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)L.c_virt);
+    atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)L.c_skip);
     block_sync();
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
         if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
