@@ -16,10 +16,12 @@
 // Loss: mean squared error against the target.
 //
 // A 3x3 convolution is a GEMM over im2col columns:
-//   forward   Y[P x Co]   = cols[P x K9] . W[Co x K9]^T
-//   data grad dcols[P x K9] = dZ[P x Co] . Wt[K9 x Co]^T, then col2im
-//   weight    dW[Co x K9] = dZ^T[Co x P] . colsT[K9 x P]^T   (split over P)
-// with P = batch * H * W pixels and K9 = Cin * 9 rounded up to 64.
+//   forward   Y[P x Co]   = cols(x)[P x K9] . W[Co x K9]^T
+//   data grad dX[P x Ci]  = cols(dZ)[P x K9d] . Wf[Ci x K9d]^T  (Wf: taps flipped)
+//   weight    dW[Co x K9] = dZ^T[Co x P] . colsT(x)[K9 x P]^T   (split over P)
+// with P = batch * H * W pixels, K9 = Ci * 9 and K9d = Co * 9 rounded up to
+// 64.  The decoder's inputs [up(prev), skip] are read in place by the column
+// builders (Src), not copied.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -48,54 +50,136 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, int64_t n, bf16* __r
     if (i < n) y[i] = __float2bfloat16_rn(x[i]);
 }
 
-// cols[p][k], p = (b, y, x), k = ci * ks * ks + ky * ks + kx (zero beyond C * ks * ks);
-// transposed = colsT[k][p] with row length ldp.
-__global__ void im2col_kernel(const bf16* __restrict__ x, int B, int C, int H, int W, int ks, int K9p, int ldp,
-                              int transposed, bf16* __restrict__ out) {
-    const int64_t P = (int64_t)B * H * W;
-    const int64_t cols = transposed ? (int64_t)ldp : P;       // pixel columns written, padding included
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cols * K9p) return;
-    int64_t p;
-    int k;
-    if (transposed) { k = (int)(i / ldp); p = i % ldp; }
-    else { p = i / K9p; k = (int)(i % K9p); }
-    bf16 v = __float2bfloat16_rn(0.0f);
-    const int kk = ks * ks;
-    if (k < C * kk && p < P) {
-        const int ci = k / kk, r = k % kk, ky = r / ks, kx = r % ks;
-        const int b = (int)(p / ((int64_t)H * W));
-        const int yx = (int)(p % ((int64_t)H * W));
-        const int yy = yx / W + ky - ks / 2, xx = yx % W + kx - ks / 2;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = x[(((int64_t)b * C + ci) * H + yy) * W + xx];
+// The input of a convolution as the channel concatenation of two BF16
+// tensors [a, s]: channel c < Ca reads a at resolution (H / up) x (W / up)
+// (up = 2: nearest upsampling), channel c >= Ca reads s at H x W.  Element
+// (b, c, y, x) of a tensor sits at base + b * batch_stride + c * chan_stride +
+// y * width + x (NCHW: batch_stride = C H W, chan_stride = H W; the
+// channel-major gradient rows [c][b H W] of the backward: batch_stride = H W,
+// chan_stride = padded pixel count).  The decoder's concatenations and
+// upsamplings are read in place instead of being copied.
+struct Src {
+    const bf16* a;
+    int Ca, up;
+    int64_t a_bs, a_cs;
+    const bf16* s;
+    int64_t s_bs, s_cs;
+    int C, H, W;                        // total channels and the output resolution
+};
+
+__device__ __forceinline__ bf16 src_at(const Src& S, int b, int c, int y, int x) {
+    if (y < 0 || y >= S.H || x < 0 || x >= S.W) return __float2bfloat16_rn(0.0f);
+    if (c < S.Ca) {
+        const int wa = S.W / S.up;
+        return S.a[(int64_t)b * S.a_bs + (int64_t)c * S.a_cs + (int64_t)(y / S.up) * wa + x / S.up];
     }
-    if (transposed) out[(int64_t)k * ldp + p] = v;
-    else out[p * K9p + k] = v;
+    return S.s[(int64_t)b * S.s_bs + (int64_t)(c - S.Ca) * S.s_cs + (int64_t)y * S.W + x];
 }
 
-// Y[b][co][y][x] (BF16, channel offset in a wider tensor) = act(G[p][co] + bias[co]);
-// also the FP32 value when yf != NULL.
-__global__ void bias_act_kernel(const float* __restrict__ G, int ldg, const float* __restrict__ bias, int B, int Co,
-                                int H, int W, int relu, bf16* __restrict__ y, int y_channels, float* __restrict__ yf) {
-    const int64_t n = (int64_t)B * Co * H * W;
+// cols[p][k] (row length K9p), p = (b, y, x), k = ci * ks * ks + ky * ks + kx,
+// zero beyond C * ks * ks.  One block builds a tile of 32 pixels x 64 k:
+// the reads go along pixels (coalesced on the input rows), the tile is
+// transposed in shared memory, and each row segment of 64 k (128 bytes) is
+// written with 16-byte stores.
+constexpr int I2C_PIX = 32, I2C_K = 64;
+
+__global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, int ks, int K9p,
+                                                        bf16* __restrict__ out) {
+    __shared__ bf16 tile[I2C_K][I2C_PIX + 2];
+    const int64_t P = (int64_t)B * S.H * S.W;
+    const int64_t p0 = (int64_t)blockIdx.x * I2C_PIX;
+    const int k0 = blockIdx.y * I2C_K;
+    const int kk = ks * ks, half = ks / 2, HW = S.H * S.W;
+    {
+        const int pl = threadIdx.x & (I2C_PIX - 1);
+        const int64_t p = p0 + pl;
+        const int b = (int)(p / HW), yx = (int)(p % HW), y = yx / S.W, x = yx % S.W;
+        for (int kr = threadIdx.x >> 5; kr < I2C_K; kr += 8) {
+            const int k = k0 + kr;
+            bf16 v = __float2bfloat16_rn(0.0f);
+            if (p < P && k < S.C * kk) {
+                const int ci = k / kk, r = k - ci * kk, ky = r / ks, kx = r - ky * ks;
+                v = src_at(S, b, ci, y + ky - half, x + kx - half);
+            }
+            tile[kr][pl] = v;
+        }
+    }
+    __syncthreads();
+    const int pix = threadIdx.x >> 3, chunk = threadIdx.x & 7;
+    const int64_t p = p0 + pix;
+    if (p < P) {
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = tile[chunk * 8 + j][pix];
+        *reinterpret_cast<uint4*>(out + p * K9p + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(v);
+    }
+}
+
+// colsT[k][p] (row length ldp >= P, padding pixels zero): each thread writes
+// 8 consecutive pixels of one k (16 bytes); W is a multiple of 8, so the 8
+// pixels share an image row and their reads are consecutive input elements.
+__global__ void __launch_bounds__(256) im2col_cols_kernel(const Src S, int B, int ks, int K9p, int ldp,
+                                                        bf16* __restrict__ out) {
+    const int64_t P = (int64_t)B * S.H * S.W;
+    const int64_t groups = ldp / 8;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int x = (int)(i % W);
-    const int yy = (int)((i / W) % H);
-    const int co = (int)((i / ((int64_t)W * H)) % Co);
-    const int b = (int)(i / ((int64_t)W * H * Co));
-    const int64_t p = ((int64_t)b * H + yy) * W + x;
-    float v = G[p * ldg + co] + bias[co];
-    if (relu) v = fmaxf(v, 0.0f);
-    if (y) y[(((int64_t)b * y_channels + co) * H + yy) * W + x] = __float2bfloat16_rn(v);
-    if (yf) yf[i] = v;
+    if (i >= groups * K9p) return;
+    const int k = (int)(i / groups);
+    const int64_t p0 = (i - (int64_t)k * groups) * 8;
+    const int kk = ks * ks, half = ks / 2, HW = S.H * S.W;
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn(0.0f);
+    if (p0 < P && k < S.C * kk) {
+        const int ci = k / kk, r = k - ci * kk, ky = r / ks, kx = r - ky * ks;
+        const int b = (int)(p0 / HW), yx = (int)(p0 % HW), y = yx / S.W, x = yx % S.W;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = src_at(S, b, ci, y + ky - half, x + j + kx - half);
+    }
+    *reinterpret_cast<uint4*>(out + (int64_t)k * ldp + p0) = *reinterpret_cast<const uint4*>(v);
 }
 
-// dZ = dY * (Y > 0) (or dY when relu == 0), written as BF16 in two layouts:
-// dz_pc[p][co] (row length ldc_pad) and dz_cp[co][p] (row length ldp).
+// Y[b][co][y][x] (BF16, channel offset in a wider tensor) = act(G[p][co] +
+// bias[co]); also the FP32 value when yf != NULL (bias NULL: no bias, no
+// activation).  A 32-pixel x 32-channel tile goes through shared memory, so
+// both the reads of G's rows and the writes of the NCHW rows are coalesced.
+__global__ void __launch_bounds__(256) bias_act_kernel(const float* __restrict__ G, int ldg,
+                                                     const float* __restrict__ bias, int B, int Co, int HW, int relu,
+                                                     bf16* __restrict__ y, int y_channels, float* __restrict__ yf) {
+    __shared__ float t[32][33];
+    const int64_t P = (int64_t)B * HW;
+    const int64_t p0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32, lane = threadIdx.x & 31;
+    for (int r = threadIdx.x >> 5; r < 32; r += 8) {
+        const int64_t p = p0 + r;
+        const int c = c0 + lane;
+        float v = 0.0f;
+        if (p < P && c < Co) {
+            v = G[p * ldg + c];
+            if (bias) v = v + bias[c];
+            if (relu) v = fmaxf(v, 0.0f);
+        }
+        t[r][lane] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x >> 5; r < 32; r += 8) {
+        const int c = c0 + r;
+        const int64_t p = p0 + lane;
+        if (p < P && c < Co) {
+            const int64_t b = p / HW, yx = p % HW;
+            const float v = t[lane][r];
+            if (y) y[(b * y_channels + c) * HW + yx] = __float2bfloat16_rn(v);
+            if (yf) yf[(b * Co + c) * HW + yx] = v;
+        }
+    }
+}
+
+// dZ = dY * (Y > 0) (or dY when relu == 0), as BF16 channel-major rows
+// dz_cp[co][p] (row length ldp; the weight gradient's operand and the data
+// gradient's convolution input) and as FP32 NCHW (the bias gradient).
 __global__ void act_back_kernel(const float* __restrict__ dy, const bf16* __restrict__ y, int y_channels, int B,
-                                int Co, int H, int W, int relu, bf16* __restrict__ dz_pc, int ldc_pad,
-                                bf16* __restrict__ dz_cp, int ldp, float* __restrict__ dz_f) {
+                                int Co, int H, int W, int relu, bf16* __restrict__ dz_cp, int ldp,
+                                float* __restrict__ dz_f) {
     const int64_t n = (int64_t)B * Co * H * W;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -109,19 +193,24 @@ __global__ void act_back_kernel(const float* __restrict__ dy, const bf16* __rest
         if (!(yv > 0.0f)) g = 0.0f;
     }
     const int64_t p = ((int64_t)b * H + yy) * W + x;
-    const bf16 gb = __float2bfloat16_rn(g);
-    dz_pc[p * ldc_pad + co] = gb;
-    dz_cp[(int64_t)co * ldp + p] = gb;
+    dz_cp[(int64_t)co * ldp + p] = __float2bfloat16_rn(g);
     dz_f[i] = g;
 }
 
-// db[co] = sum over pixels of dZ (FP32), one block per channel.
-__global__ void bias_grad_kernel(const float* __restrict__ dz, int B, int Co, int HW, float* __restrict__ db) {
-    const int co = blockIdx.x;
+// db[co] = sum over pixels of dZ (FP32) in two ordered stages: block (co,
+// s) reduces the s-th of n_part equal pixel ranges of channel co into
+// part[co][s]; then one thread per channel adds its parts in order.  The
+// partition and both orders are fixed, so the sum is bit-reproducible.
+__global__ void bias_grad_part_kernel(const float* __restrict__ dz, int B, int Co, int HW, int n_part,
+                                      float* __restrict__ part) {
+    const int co = blockIdx.x, sp = blockIdx.y;
+    const int64_t n = (int64_t)B * HW;
+    const int64_t per = (n + n_part - 1) / n_part;
+    const int64_t i0 = (int64_t)sp * per, i1 = min(n, i0 + per);
     float s = 0.0f;
-    for (int64_t i = threadIdx.x; i < (int64_t)B * HW; i += blockDim.x) {
-        const int b = (int)(i / HW), r = (int)(i % HW);
-        s += dz[((int64_t)b * Co + co) * HW + r];
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t b = i / HW, r = i % HW;
+        s += dz[(b * Co + co) * HW + r];
     }
     __shared__ float red[TB];
     red[threadIdx.x] = s;
@@ -130,29 +219,15 @@ __global__ void bias_grad_kernel(const float* __restrict__ dz, int B, int Co, in
         if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) db[co] = red[0];
+    if (threadIdx.x == 0) part[(int64_t)co * n_part + sp] = red[0];
 }
 
-// dX[b][ci][y][x] = sum over (ky, kx) of dcols[p(b, y - ky + h, x - kx + h)][ci * kk + ky * ks + kx].
-__global__ void col2im_kernel(const float* __restrict__ dcols, int K9p, int B, int C, int H, int W, int ks,
-                              float* __restrict__ dx) {
-    const int64_t n = (int64_t)B * C * H * W;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int x = (int)(i % W);
-    const int y = (int)((i / W) % H);
-    const int ci = (int)((i / ((int64_t)W * H)) % C);
-    const int b = (int)(i / ((int64_t)W * H * C));
-    const int kk = ks * ks, h = ks / 2;
+__global__ void bias_grad_sum_kernel(const float* __restrict__ part, int Co, int n_part, float* __restrict__ db) {
+    const int co = blockIdx.x * blockDim.x + threadIdx.x;
+    if (co >= Co) return;
     float s = 0.0f;
-    for (int ky = 0; ky < ks; ++ky)
-        for (int kx = 0; kx < ks; ++kx) {
-            const int yo = y - ky + h, xo = x - kx + h;
-            if (yo < 0 || yo >= H || xo < 0 || xo >= W) continue;
-            const int64_t p = ((int64_t)b * H + yo) * W + xo;
-            s += dcols[p * K9p + ci * kk + ky * ks + kx];
-        }
-    dx[i] = s;
+    for (int k = 0; k < n_part; ++k) s += part[(int64_t)co * n_part + k];
+    db[co] = s;
 }
 
 __global__ void pool_kernel(const bf16* __restrict__ x, int B, int C, int H, int W, bf16* __restrict__ y) {
@@ -178,20 +253,8 @@ __global__ void pool_back_kernel(const float* __restrict__ dy, int B, int C, int
     dx[i] += 0.25f * dy[bc * (H / 2) * (W / 2) + (int64_t)(y / 2) * (W / 2) + x / 2];
 }
 
-// dst[b][off + c][y][x] = src[b][c][y / s][x / s], s = 2 (upsample) or 1 (copy)
-__global__ void place_kernel(const bf16* __restrict__ src, int B, int C, int H, int W, int s, bf16* __restrict__ dst,
-                             int dst_channels, int off) {
-    const int64_t n = (int64_t)B * C * H * W;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int x = (int)(i % W), y = (int)((i / W) % H);
-    const int c = (int)((i / ((int64_t)W * H)) % C);
-    const int b = (int)(i / ((int64_t)W * H * C));
-    dst[(((int64_t)b * dst_channels + off + c) * H + y) * W + x] =
-        src[(((int64_t)b * C + c) * (H / s) + y / s) * (W / s) + x / s];
-}
-
-// adjoint of place: dsrc[b][c][y][x] (+)= sum over the s x s block of dcat[b][off + c]
+// gradient of a channel range of a concatenated input: dsrc[b][c][y][x] (+)=
+// the sum over the s x s block of dcat[b][off + c] (s = 2: nearest upsampling)
 __global__ void place_back_kernel(const float* __restrict__ dcat, int cat_channels, int off, int B, int C, int h,
                                   int w, int s, int accumulate, float* __restrict__ dsrc) {
     const int64_t n = (int64_t)B * C * h * w;
@@ -240,16 +303,29 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// BF16 copies of a conv's weights: w16[co][k] (row K9p) and wt16[k][co] (row Co_p)
-__global__ void weight_copies_kernel(const float* __restrict__ w, int Co, int K9, int K9p, int Cop,
-                                     bf16* __restrict__ w16, bf16* __restrict__ wt16) {
-    const int64_t n = (int64_t)Co * K9p;
+// BF16 copies of a conv's weights w[co][ci][tap] (tap = ky ks + kx):
+// w16[co][k] (row K9p) for the forward, and wf16[ci][co kk + t] = w[co][ci][kk -
+// 1 - t] (row K9dp), the weights with the taps flipped for the data gradient
+// (a convolution of dZ: dX(y, x) = sum over co, ky, kx of dZ(y + ky - h,
+// x + kx - h) w[co][ci][ks - 1 - ky][ks - 1 - kx]).
+__global__ void weight_copies_kernel(const float* __restrict__ w, int Co, int Ci, int kk, int K9p, int K9dp,
+                                     bf16* __restrict__ w16, bf16* __restrict__ wf16) {
+    const int K9 = Ci * kk;
+    const int64_t n1 = (int64_t)Co * K9p, n2 = (int64_t)Ci * K9dp;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int co = (int)(i / K9p), k = (int)(i % K9p);
-    const bf16 v = __float2bfloat16_rn(k < K9 ? w[(int64_t)co * K9 + k] : 0.0f);
-    w16[i] = v;
-    wt16[(int64_t)k * Cop + co] = v;
+    if (i < n1) {
+        const int co = (int)(i / K9p), k = (int)(i % K9p);
+        w16[i] = __float2bfloat16_rn(k < K9 ? w[(int64_t)co * K9 + k] : 0.0f);
+    }
+    if (i < n2) {
+        const int ci = (int)(i / K9dp), k = (int)(i % K9dp);
+        float v = 0.0f;
+        if (k < Co * kk) {
+            const int co = k / kk, t = k % kk;
+            v = w[(int64_t)co * K9 + (int64_t)ci * kk + (kk - 1 - t)];
+        }
+        wf16[i] = __float2bfloat16_rn(v);
+    }
 }
 
 // dW[co][k] for k < K9 from the padded GEMM output (row K9p)
@@ -261,11 +337,11 @@ __global__ void unpad_kernel(const float* __restrict__ src, int rows, int cols, 
 
 struct Conv {
     int ci, co, ks, H, W, relu;
-    int K9, K9p, Cop;
+    int K9, K9p, K9dp;     // ci ks^2, padded to 64; co ks^2 padded to 64 (data gradient)
     // parameters (FP32 master), gradients, Adam moments; offsets into the flat arrays
     int64_t w_off, b_off;
     bf16* w16 = nullptr;   // [co][K9p]
-    bf16* wt16 = nullptr;  // [K9p][Cop]
+    bf16* wf16 = nullptr;  // [ci][K9dp], taps flipped
 };
 
 // K splits of a weight-gradient product over P pixels (a function of P alone,
@@ -301,7 +377,7 @@ struct gdrr_cnn {
     int adam_t = 0;
     // activations (BF16) for the last forward
     bf16 *x16 = nullptr, *e1 = nullptr, *e2 = nullptr, *e3 = nullptr, *e4 = nullptr;
-    bf16 *p1 = nullptr, *p2 = nullptr, *p3 = nullptr, *c3 = nullptr, *c2 = nullptr, *c1 = nullptr;
+    bf16 *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
     bf16 *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;
     float* out = nullptr;
     // gradients of activations (FP32)
@@ -311,8 +387,7 @@ struct gdrr_cnn {
     // workspaces
     bf16* cols = nullptr;      // im2col, either layout
     float* gemm = nullptr;     // GEMM output
-    float* partials = nullptr; // per-split partial products of the weight gradients
-    bf16* dz_pc = nullptr;
+    float* partials = nullptr; // per-split partial products of the weight gradients; bias-gradient parts
     bf16* dz_cp = nullptr;
     float* dz_f = nullptr;
     int* err = nullptr;
@@ -356,42 +431,88 @@ int err_code(cudaError_t e) {
 
 cudaError_t refresh_weights(gdrr_cnn* n) {
     for (Conv& L : n->conv) {
-        const int64_t cnt = (int64_t)L.co * L.K9p;
-        weight_copies_kernel<<<nblk(cnt), TB, 0, n->stream>>>(n->params + L.w_off, L.co, L.K9, L.K9p, L.Cop, L.w16,
-                                                              L.wt16);
+        const int64_t cnt = std::max((int64_t)L.co * L.K9p, (int64_t)L.ci * L.K9dp);
+        weight_copies_kernel<<<nblk(cnt), TB, 0, n->stream>>>(n->params + L.w_off, L.co, L.ci, L.ks * L.ks, L.K9p,
+                                                              L.K9dp, L.w16, L.wf16);
         CK(cudaGetLastError());
     }
     return cudaSuccess;
 }
 
-// Forward of one convolution from x (BF16 [B][ci][H][W]) into y (BF16, channel
-// count y_channels, written at channels 0 .. co-1) and/or yf (FP32).
-cudaError_t conv_forward(gdrr_cnn* n, const Conv& L, int B, const bf16* x, bf16* y, int y_channels, float* yf) {
-    const int64_t P = (int64_t)B * L.H * L.W;
-    im2col_kernel<<<nblk(P * L.K9p), TB, 0, n->stream>>>(x, B, L.ci, L.H, L.W, L.ks, L.K9p, 0, 0, n->cols);
-    CK(cudaGetLastError());
-    CK(launch_gemm_bf16(n->cols, L.K9p, L.w16, L.K9p, n->gemm, L.co, (int)P, L.co, L.K9p, 1, n->err, n->stream));
-    bias_act_kernel<<<nblk(P * L.co), TB, 0, n->stream>>>(n->gemm, L.co, n->params + L.b_off, B, L.co, L.H, L.W,
-                                                          L.relu, y, y_channels, yf);
+// A tensor [B][C][H][W] (NCHW) as a convolution input.
+Src nchw(const bf16* t, int C, int H, int W) {
+    Src S;
+    memset(&S, 0, sizeof S);
+    S.up = 1;
+    S.s = t;
+    S.s_bs = (int64_t)C * H * W;
+    S.s_cs = (int64_t)H * W;
+    S.C = C; S.H = H; S.W = W;
+    return S;
+}
+
+// [up(a), s]: a with Ca channels at H/2 x W/2, upsampled, then s (Cs channels).
+Src concat_up(const bf16* a, int Ca, const bf16* s, int Cs, int H, int W) {
+    Src S = nchw(s, Cs, H, W);
+    S.a = a;
+    S.Ca = Ca;
+    S.up = 2;
+    S.a_bs = (int64_t)Ca * (H / 2) * (W / 2);
+    S.a_cs = (int64_t)(H / 2) * (W / 2);
+    S.C = Ca + Cs;
+    return S;
+}
+
+// Channel-major rows t[c][p] (row length ldp, p = b H W + y W + x) as a
+// convolution input.
+Src chan_major(const bf16* t, int C, int H, int W, int64_t ldp) {
+    Src S = nchw(t, C, H, W);
+    S.s_bs = (int64_t)H * W;
+    S.s_cs = ldp;
+    return S;
+}
+
+cudaError_t im2col_rows(gdrr_cnn* n, const Src& X, int B, int ks, int K9p) {
+    const int64_t P = (int64_t)B * X.H * X.W;
+    const dim3 grid((unsigned)((P + I2C_PIX - 1) / I2C_PIX), (unsigned)(K9p / I2C_K));
+    im2col_rows_kernel<<<grid, 256, 0, n->stream>>>(X, B, ks, K9p, n->cols);
     return cudaGetLastError();
 }
 
+// Y = act(conv(X) + bias): BF16 y (channel count y_channels, written at
+// channels 0 .. co-1) and/or FP32 yf.
+cudaError_t conv_forward(gdrr_cnn* n, const Conv& L, int B, const Src& X, bf16* y, int y_channels, float* yf) {
+    const int64_t P = (int64_t)B * L.H * L.W;
+    CK(im2col_rows(n, X, B, L.ks, L.K9p));
+    CK(launch_gemm_bf16(n->cols, L.K9p, L.w16, L.K9p, n->gemm, L.co, (int)P, L.co, L.K9p, 1, n->err, n->stream));
+    const dim3 grid((unsigned)((P + 31) / 32), (unsigned)((L.co + 31) / 32));
+    bias_act_kernel<<<grid, 256, 0, n->stream>>>(n->gemm, L.co, n->params + L.b_off, B, L.co, L.H * L.W, L.relu, y,
+                                                 y_channels, yf);
+    return cudaGetLastError();
+}
+
+int bias_parts(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 8191) / 8192)); }
+
 // Backward of one convolution: dy (FP32 [B][co][H][W], gradient of the
-// layer output), y (its BF16 output, for the ReLU mask), x (its BF16 input).
-// Writes the parameter gradients and, when dx != NULL, dx (FP32 input grad).
+// layer output), y (its BF16 output, for the ReLU mask), X (its input).
+// Writes the parameter gradients and, when dx != NULL, dx (FP32 NCHW input
+// gradient).
 cudaError_t conv_backward(gdrr_cnn* n, const Conv& L, int B, const float* dy, const bf16* y, int y_channels,
-                          const bf16* x, float* dx) {
+                          const Src& X, float* dx) {
     const int64_t P = (int64_t)B * L.H * L.W;
     const int Pp = pad64(P);
-    CK(cudaMemsetAsync(n->dz_pc, 0, (size_t)P * L.Cop * sizeof(bf16), n->stream));
+    const int HW = L.H * L.W;
     CK(cudaMemsetAsync(n->dz_cp, 0, (size_t)L.co * Pp * sizeof(bf16), n->stream));
-    act_back_kernel<<<nblk(P * L.co), TB, 0, n->stream>>>(dy, y, y_channels, B, L.co, L.H, L.W, L.relu, n->dz_pc,
-                                                          L.Cop, n->dz_cp, Pp, n->dz_f);
+    act_back_kernel<<<nblk(P * L.co), TB, 0, n->stream>>>(dy, y, y_channels, B, L.co, L.H, L.W, L.relu, n->dz_cp, Pp,
+                                                          n->dz_f);
     CK(cudaGetLastError());
-    bias_grad_kernel<<<L.co, TB, 0, n->stream>>>(n->dz_f, B, L.co, L.H * L.W, n->grads + L.b_off);
+    const int parts = bias_parts(P);
+    bias_grad_part_kernel<<<dim3((unsigned)L.co, (unsigned)parts), TB, 0, n->stream>>>(n->dz_f, B, L.co, HW, parts,
+                                                                                       n->partials);
+    bias_grad_sum_kernel<<<(L.co + 127) / 128, 128, 0, n->stream>>>(n->partials, L.co, parts, n->grads + L.b_off);
     CK(cudaGetLastError());
     // weight gradient: dW[co][k] = sum_p dZ[p][co] cols[p][k]
-    im2col_kernel<<<nblk((int64_t)Pp * L.K9p), TB, 0, n->stream>>>(x, B, L.ci, L.H, L.W, L.ks, L.K9p, Pp, 1, n->cols);
+    im2col_cols_kernel<<<nblk((int64_t)(Pp / 8) * L.K9p), TB, 0, n->stream>>>(X, B, L.ks, L.K9p, Pp, n->cols);
     CK(cudaGetLastError());
     // the pixel sum is split across CTAs; each split writes its own partial
     // product and one ordered pass adds them, so training is bit-reproducible
@@ -409,10 +530,13 @@ cudaError_t conv_backward(gdrr_cnn* n, const Conv& L, int B, const float* dy, co
     unpad_kernel<<<nblk((int64_t)L.co * L.K9), TB, 0, n->stream>>>(n->gemm, L.co, L.K9, L.K9p, n->grads + L.w_off);
     CK(cudaGetLastError());
     if (dx) {
-        // data gradient: dcols[p][k] = sum_co dZ[p][co] W[co][k]; then col2im
-        CK(launch_gemm_bf16(n->dz_pc, L.Cop, L.wt16, L.Cop, n->gemm, L.K9p, (int)P, L.K9p, L.Cop, 1, n->err,
+        // data gradient: the convolution of dZ with the flipped weights,
+        // dX[p][ci] = sum_k cols(dZ)[p][k] Wf[ci][k], then to NCHW
+        CK(im2col_rows(n, chan_major(n->dz_cp, L.co, L.H, L.W, Pp), B, L.ks, L.K9dp));
+        CK(launch_gemm_bf16(n->cols, L.K9dp, L.wf16, L.K9dp, n->gemm, L.ci, (int)P, L.ci, L.K9dp, 1, n->err,
                             n->stream));
-        col2im_kernel<<<nblk(P * L.ci), TB, 0, n->stream>>>(n->gemm, L.K9p, B, L.ci, L.H, L.W, L.ks, dx);
+        const dim3 grid((unsigned)((P + 31) / 32), (unsigned)((L.ci + 31) / 32));
+        bias_act_kernel<<<grid, 256, 0, n->stream>>>(n->gemm, L.ci, nullptr, B, L.ci, HW, 0, nullptr, 0, dx);
         CK(cudaGetLastError());
     }
     return cudaSuccess;
@@ -446,7 +570,7 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
         L.ci = s.ci; L.co = s.co; L.ks = s.ks; L.H = s.h; L.W = s.w; L.relu = s.relu;
         L.K9 = s.ci * s.ks * s.ks;
         L.K9p = pad64(L.K9);
-        L.Cop = pad64(s.co);
+        L.K9dp = pad64((int64_t)s.co * s.ks * s.ks);
         L.w_off = off;
         off += (int64_t)L.co * L.K9;
         L.b_off = off;
@@ -458,10 +582,10 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
     int64_t max_cols = 0, max_gemm = 0, max_dz = 0, max_part = 0;
     for (const Conv& L : n->conv) {
         const int64_t P = B * L.H * L.W, Pp = pad64(P);
-        max_cols = std::max(max_cols, Pp * L.K9p);
-        max_gemm = std::max({max_gemm, P * L.K9p, (int64_t)L.co * L.K9p, P * L.co});
-        max_dz = std::max({max_dz, P * L.Cop, (int64_t)L.co * Pp});
-        max_part = std::max(max_part, (int64_t)wgrad_splits(P) * L.co * L.K9p);
+        max_cols = std::max({max_cols, Pp * L.K9p, P * L.K9dp});
+        max_gemm = std::max({max_gemm, P * L.ci, (int64_t)L.co * L.K9p, P * L.co});
+        max_dz = std::max({max_dz, P * L.co, (int64_t)L.co * Pp});
+        max_part = std::max({max_part, (int64_t)wgrad_splits(P) * L.co * L.K9p, (int64_t)L.co * bias_parts(P)});
     }
     cudaError_t e = cudaSuccess;
     do {
@@ -470,19 +594,15 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
             break;
         bool bad = false;
         for (Conv& L : n->conv) {
-            if (dalloc(n, &L.w16, (size_t)L.co * L.K9p) || dalloc(n, &L.wt16, (size_t)L.K9p * L.Cop)) bad = true;
-            // padded output-channel columns of wt16 stay zero (weight copies write co < Co only)
-            else if (cudaMemset(L.wt16, 0, (size_t)L.K9p * L.Cop * sizeof(bf16)) != cudaSuccess) bad = true;
+            if (dalloc(n, &L.w16, (size_t)L.co * L.K9p) || dalloc(n, &L.wf16, (size_t)L.ci * L.K9dp)) bad = true;
         }
         if (bad) { e = cudaErrorMemoryAllocation; break; }
         const int64_t s1 = B * HW, s2 = s1 / 4, s3 = s1 / 16, s4 = s1 / 64;
         if ((e = dalloc(n, &n->x16, 2 * s1)) || (e = dalloc(n, &n->e1, c * s1)) || (e = dalloc(n, &n->p1, c * s2)) ||
             (e = dalloc(n, &n->e2, 2 * c * s2)) || (e = dalloc(n, &n->p2, 2 * c * s3)) ||
             (e = dalloc(n, &n->e3, 4 * c * s3)) || (e = dalloc(n, &n->p3, 4 * c * s4)) ||
-            (e = dalloc(n, &n->e4, 8 * c * s4)) || (e = dalloc(n, &n->c3, 12 * c * s3)) ||
-            (e = dalloc(n, &n->d3, 4 * c * s3)) || (e = dalloc(n, &n->c2, 6 * c * s2)) ||
-            (e = dalloc(n, &n->d2, 2 * c * s2)) || (e = dalloc(n, &n->c1, 3 * c * s1)) ||
-            (e = dalloc(n, &n->d1, c * s1)) || (e = dalloc(n, &n->out, s1)))
+            (e = dalloc(n, &n->e4, 8 * c * s4)) || (e = dalloc(n, &n->d3, 4 * c * s3)) ||
+            (e = dalloc(n, &n->d2, 2 * c * s2)) || (e = dalloc(n, &n->d1, c * s1)) || (e = dalloc(n, &n->out, s1)))
             break;
         if ((e = dalloc(n, &n->g_out, s1)) || (e = dalloc(n, &n->g_d1, c * s1)) || (e = dalloc(n, &n->g_c1, 3 * c * s1)) ||
             (e = dalloc(n, &n->g_d2, 2 * c * s2)) || (e = dalloc(n, &n->g_c2, 6 * c * s2)) ||
@@ -493,7 +613,7 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
             (e = dalloc(n, &n->g_e1, c * s1)) || (e = dalloc(n, &n->g_x, 2 * s1)))
             break;
         if ((e = dalloc(n, &n->cols, max_cols)) || (e = dalloc(n, &n->gemm, max_gemm)) ||
-            (e = dalloc(n, &n->dz_pc, max_dz)) || (e = dalloc(n, &n->dz_cp, max_dz)) ||
+            (e = dalloc(n, &n->dz_cp, max_dz)) ||
             (e = dalloc(n, &n->dz_f, max_dz)) || (e = dalloc(n, &n->partials, max_part)) ||
             (e = dalloc(n, &n->err, 1)))
             break;
@@ -568,24 +688,22 @@ GDRR_API int gdrr_cnn_forward(gdrr_cnn* n, int32_t batch, const float* in_dev, f
         to_bf16_kernel<<<nblk(2 * s1), TB, 0, st>>>(in_dev, 2 * s1, n->x16);
         if ((e = cudaGetLastError())) break;
         const std::vector<Conv>& L = n->conv;
-        if ((e = conv_forward(n, L[0], B, n->x16, n->e1, c, nullptr))) break;
+        if ((e = conv_forward(n, L[0], B, nchw(n->x16, 2, H, W), n->e1, c, nullptr))) break;
         pool_kernel<<<nblk(c * s1 / 4), TB, 0, st>>>(n->e1, B, c, H, W, n->p1);
-        if ((e = conv_forward(n, L[1], B, n->p1, n->e2, 2 * c, nullptr))) break;
+        if ((e = conv_forward(n, L[1], B, nchw(n->p1, c, H / 2, W / 2), n->e2, 2 * c, nullptr))) break;
         pool_kernel<<<nblk(2 * c * s1 / 16), TB, 0, st>>>(n->e2, B, 2 * c, H / 2, W / 2, n->p2);
-        if ((e = conv_forward(n, L[2], B, n->p2, n->e3, 4 * c, nullptr))) break;
+        if ((e = conv_forward(n, L[2], B, nchw(n->p2, 2 * c, H / 4, W / 4), n->e3, 4 * c, nullptr))) break;
         pool_kernel<<<nblk(4 * c * s1 / 64), TB, 0, st>>>(n->e3, B, 4 * c, H / 4, W / 4, n->p3);
-        if ((e = conv_forward(n, L[3], B, n->p3, n->e4, 8 * c, nullptr))) break;
-        // decoder: [up(prev), skip]
-        place_kernel<<<nblk(8 * c * s1 / 16), TB, 0, st>>>(n->e4, B, 8 * c, H / 4, W / 4, 2, n->c3, 12 * c, 0);
-        place_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->e3, B, 4 * c, H / 4, W / 4, 1, n->c3, 12 * c, 8 * c);
-        if ((e = conv_forward(n, L[4], B, n->c3, n->d3, 4 * c, nullptr))) break;
-        place_kernel<<<nblk(4 * c * s1 / 4), TB, 0, st>>>(n->d3, B, 4 * c, H / 2, W / 2, 2, n->c2, 6 * c, 0);
-        place_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->e2, B, 2 * c, H / 2, W / 2, 1, n->c2, 6 * c, 4 * c);
-        if ((e = conv_forward(n, L[5], B, n->c2, n->d2, 2 * c, nullptr))) break;
-        place_kernel<<<nblk(2 * c * s1), TB, 0, st>>>(n->d2, B, 2 * c, H, W, 2, n->c1, 3 * c, 0);
-        place_kernel<<<nblk(c * s1), TB, 0, st>>>(n->e1, B, c, H, W, 1, n->c1, 3 * c, 2 * c);
-        if ((e = conv_forward(n, L[6], B, n->c1, n->d1, c, nullptr))) break;
-        if ((e = conv_forward(n, L[7], B, n->d1, nullptr, 1, n->out))) break;
+        if ((e = conv_forward(n, L[3], B, nchw(n->p3, 4 * c, H / 8, W / 8), n->e4, 8 * c, nullptr))) break;
+        // decoder: [up(prev), skip], read in place
+        if ((e = conv_forward(n, L[4], B, concat_up(n->e4, 8 * c, n->e3, 4 * c, H / 4, W / 4), n->d3, 4 * c,
+                              nullptr)))
+            break;
+        if ((e = conv_forward(n, L[5], B, concat_up(n->d3, 4 * c, n->e2, 2 * c, H / 2, W / 2), n->d2, 2 * c,
+                              nullptr)))
+            break;
+        if ((e = conv_forward(n, L[6], B, concat_up(n->d2, 2 * c, n->e1, c, H, W), n->d1, c, nullptr))) break;
+        if ((e = conv_forward(n, L[7], B, nchw(n->d1, c, H, W), nullptr, 1, n->out))) break;
         residual_kernel<<<nblk(s1), TB, 0, st>>>(in_dev, B, H * W, n->out);
         if ((e = cudaGetLastError())) break;
         if (out_dev) e = cudaMemcpyAsync(out_dev, n->out, s1 * sizeof(float), cudaMemcpyDeviceToDevice, st);
@@ -607,28 +725,33 @@ GDRR_API int gdrr_cnn_backward(gdrr_cnn* n, const float* target_dev, double* los
         mse_kernel<<<nblk(s1), TB, 0, st>>>(n->out, target_dev, s1, n->g_out, dloss);
         if ((e = cudaMemcpyAsync(&loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, st))) break;
         if ((e = cudaStreamSynchronize(st))) break;
-        if ((e = conv_backward(n, L[7], B, n->g_out, nullptr, 1, n->d1, n->g_d1))) break;
-        if ((e = conv_backward(n, L[6], B, n->g_d1, n->d1, c, n->c1, n->g_c1))) break;
+        if ((e = conv_backward(n, L[7], B, n->g_out, nullptr, 1, nchw(n->d1, c, H, W), n->g_d1))) break;
+        if ((e = conv_backward(n, L[6], B, n->g_d1, n->d1, c, concat_up(n->d2, 2 * c, n->e1, c, H, W), n->g_c1)))
+            break;
         // c1 = [up(d2), e1]
         place_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_c1, 3 * c, 0, B, 2 * c, H / 2, W / 2, 2, 0, n->g_d2);
         place_back_kernel<<<nblk(c * s1), TB, 0, st>>>(n->g_c1, 3 * c, 2 * c, B, c, H, W, 1, 0, n->g_e1);
-        if ((e = conv_backward(n, L[5], B, n->g_d2, n->d2, 2 * c, n->c2, n->g_c2))) break;
+        if ((e = conv_backward(n, L[5], B, n->g_d2, n->d2, 2 * c, concat_up(n->d3, 4 * c, n->e2, 2 * c, H / 2, W / 2),
+                               n->g_c2)))
+            break;
         place_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_c2, 6 * c, 0, B, 4 * c, H / 4, W / 4, 2, 0, n->g_d3);
         place_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_c2, 6 * c, 4 * c, B, 2 * c, H / 2, W / 2, 1, 0,
                                                               n->g_e2);
-        if ((e = conv_backward(n, L[4], B, n->g_d3, n->d3, 4 * c, n->c3, n->g_c3))) break;
+        if ((e = conv_backward(n, L[4], B, n->g_d3, n->d3, 4 * c, concat_up(n->e4, 8 * c, n->e3, 4 * c, H / 4, W / 4),
+                               n->g_c3)))
+            break;
         place_back_kernel<<<nblk(8 * c * s1 / 64), TB, 0, st>>>(n->g_c3, 12 * c, 0, B, 8 * c, H / 8, W / 8, 2, 0,
                                                                n->g_e4);
         place_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_c3, 12 * c, 8 * c, B, 4 * c, H / 4, W / 4, 1, 0,
                                                                n->g_e3);
         // encoder
-        if ((e = conv_backward(n, L[3], B, n->g_e4, n->e4, 8 * c, n->p3, n->g_p3))) break;
+        if ((e = conv_backward(n, L[3], B, n->g_e4, n->e4, 8 * c, nchw(n->p3, 4 * c, H / 8, W / 8), n->g_p3))) break;
         pool_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_p3, B, 4 * c, H / 4, W / 4, n->g_e3);
-        if ((e = conv_backward(n, L[2], B, n->g_e3, n->e3, 4 * c, n->p2, n->g_p2))) break;
+        if ((e = conv_backward(n, L[2], B, n->g_e3, n->e3, 4 * c, nchw(n->p2, 2 * c, H / 4, W / 4), n->g_p2))) break;
         pool_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_p2, B, 2 * c, H / 2, W / 2, n->g_e2);
-        if ((e = conv_backward(n, L[1], B, n->g_e2, n->e2, 2 * c, n->p1, n->g_p1))) break;
+        if ((e = conv_backward(n, L[1], B, n->g_e2, n->e2, 2 * c, nchw(n->p1, c, H / 2, W / 2), n->g_p1))) break;
         pool_back_kernel<<<nblk(c * s1), TB, 0, st>>>(n->g_p1, B, c, H, W, n->g_e1);
-        if ((e = conv_backward(n, L[0], B, n->g_e1, n->e1, c, n->x16, nullptr))) break;
+        if ((e = conv_backward(n, L[0], B, n->g_e1, n->e1, c, nchw(n->x16, 2, H, W), nullptr))) break;
         int bad = 0;
         if ((e = cudaMemcpyAsync(&bad, n->err, sizeof(int), cudaMemcpyDeviceToHost, st))) break;
         if ((e = cudaStreamSynchronize(st))) break;

@@ -1,8 +1,9 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) of sm_103a, for the
-// convolutions of the learned scatter estimator.  Three forms: the one below
-// for narrow outputs (N <= 64), whose threads stage the tiles; a TMA-fed,
-// multi-stage, warp-specialised form with one tile per CTA for 64 < N < 256;
-// and its persistent form with two TMEM accumulators for N >= 256.  Both read
+// convolutions of the learned scatter estimator.  Three forms: the one below,
+// whose threads stage the tiles (outputs narrower than 32 columns, or no
+// tensor-map encoder); a TMA-fed, multi-stage, warp-specialised form with one
+// tile per CTA for 64 < N < 256; and its persistent form with two TMEM
+// accumulators for N >= 256 and for 32 <= N <= 64.  Both read
 // operand rows in 16-byte pieces: A and B start on 16-byte boundaries.
 //
 //   C[M x N] (FP32)  =  A[M x K] . B[N x K]^T      (A, B BF16, rows K-contiguous)
@@ -697,16 +698,24 @@ cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, flo
         const int per = (k_slices + sp - 1) / sp;
         *splits_used = (k_slices + per - 1) / per;
     }
-    if (N <= 32) return launch_gemm_t<32>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
-    if (N <= 64) return launch_gemm_t<64>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
+    if (N < 32) return launch_gemm_t<32>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
     // measured at 8192^3 (fraction of the BF16 peak): persistent 256-wide tiles
     // with two TMEM accumulators 0.78; per-tile CTAs, two per SM, 256 x 2
-    // stages 0.74 and 128 x 3 stages 0.67 (persistent 128-wide: 0.52)
+    // stages 0.74 and 128 x 3 stages 0.67 (persistent 128-wide: 0.52).
+    // Narrow outputs (the 32- and 64-channel convolutions: tall A streams
+    // from memory, little work per tile) take the persistent form with a deep
+    // operand ring.
     if (encode_fn()) {
+        if (N <= 32)
+            return launch_persistent_t<32, 8>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
+        if (N <= 64)
+            return launch_persistent_t<64, 6>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
         if (N >= 256)
             return launch_persistent_t<256, 4>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
         return launch_tma_t<128, 3>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
     }
+    if (N <= 32) return launch_gemm_t<32>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
+    if (N <= 64) return launch_gemm_t<64>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
     return launch_gemm_t<128>(a, lda, b, ldb, C, ldc, M, N, K, splits, partial_stride, err, s);
 }
 

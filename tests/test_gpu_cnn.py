@@ -51,7 +51,10 @@ def test_gemm_bf16(gd, M, N, K, splits):
                                              (512, 384, 2048, 1),    # ring wraps many times
                                              (8192, 2048, 64, 1),    # persistent: 3-4 tiles per CTA
                                              (4000, 1024, 384, 3),   # persistent with K splits (atomics)
-                                             (3000, 768, 128, 1)])   # persistent, fewer tiles than SMs
+                                             (3000, 768, 128, 1),    # persistent, fewer tiles than SMs
+                                             (5000, 32, 896, 1),     # persistent 32-wide, deep ring wraps
+                                             (3000, 64, 1728, 1),    # persistent 64-wide
+                                             (1000, 48, 512, 3)])    # persistent 64-wide, ragged N, K splits
 def test_gemm_bf16_tma_path(gd, M, N, K, splits):
     rng = np.random.default_rng(M + 3 * N + K)
     a = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
