@@ -116,8 +116,10 @@ __global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, in
 }
 
 // colsT[k][p] (row length ldp >= P, padding pixels zero): each thread writes
-// 8 consecutive pixels of one k (16 bytes); W is a multiple of 8, so the 8
-// pixels share an image row and their reads are consecutive input elements.
+// 8 consecutive pixels of one k (16 bytes).  Where the width is a multiple of
+// 8 the 8 pixels share an image row and read consecutive input elements; the
+// coarse levels of small images may wrap rows, so each pixel finds its own
+// coordinates.
 __global__ void __launch_bounds__(256) im2col_cols_kernel(const Src S, int B, int ks, int K9p, int ldp,
                                                         bf16* __restrict__ out) {
     const int64_t P = (int64_t)B * S.H * S.W;
@@ -130,11 +132,16 @@ __global__ void __launch_bounds__(256) im2col_cols_kernel(const Src S, int B, in
     __align__(16) bf16 v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn(0.0f);
-    if (p0 < P && k < S.C * kk) {
+    if (k < S.C * kk) {
         const int ci = k / kk, r = k - ci * kk, ky = r / ks, kx = r - ky * ks;
-        const int b = (int)(p0 / HW), yx = (int)(p0 % HW), y = yx / S.W, x = yx % S.W;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = src_at(S, b, ci, y + ky - half, x + j + kx - half);
+        for (int j = 0; j < 8; ++j) {
+            const int64_t p = p0 + j;
+            if (p < P) {
+                const int b = (int)(p / HW), yx = (int)(p % HW), y = yx / S.W, x = yx % S.W;
+                v[j] = src_at(S, b, ci, y + ky - half, x + kx - half);
+            }
+        }
     }
     *reinterpret_cast<uint4*>(out + (int64_t)k * ldp + p0) = *reinterpret_cast<const uint4*>(v);
 }
