@@ -67,11 +67,14 @@ struct Src {
     int C, H, W;                        // total channels and the output resolution
 };
 
+// UP is the kernel's compile-time copy of S.up (1 or 2), so the upsampling
+// index arithmetic is shifts.
+template <int UP>
 __device__ __forceinline__ bf16 src_at(const Src& S, int b, int c, int y, int x) {
     if (y < 0 || y >= S.H || x < 0 || x >= S.W) return __float2bfloat16_rn(0.0f);
     if (c < S.Ca) {
-        const int wa = S.W / S.up;
-        return S.a[(int64_t)b * S.a_bs + (int64_t)c * S.a_cs + (int64_t)(y / S.up) * wa + x / S.up];
+        const int wa = S.W / UP;
+        return S.a[(int64_t)b * S.a_bs + (int64_t)c * S.a_cs + (int64_t)(y / UP) * wa + x / UP];
     }
     return S.s[(int64_t)b * S.s_bs + (int64_t)(c - S.Ca) * S.s_cs + (int64_t)y * S.W + x];
 }
@@ -83,13 +86,14 @@ __device__ __forceinline__ bf16 src_at(const Src& S, int b, int c, int y, int x)
 // written with 16-byte stores.
 constexpr int I2C_PIX = 32, I2C_K = 64;
 
-__global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, int ks, int K9p,
-                                                        bf16* __restrict__ out) {
+template <int KS, int UP>
+__global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, int K9p, bf16* __restrict__ out) {
     __shared__ bf16 tile[I2C_K][I2C_PIX + 2];
     const int64_t P = (int64_t)B * S.H * S.W;
     const int64_t p0 = (int64_t)blockIdx.x * I2C_PIX;
     const int k0 = blockIdx.y * I2C_K;
-    const int kk = ks * ks, half = ks / 2, HW = S.H * S.W;
+    constexpr int kk = KS * KS, half = KS / 2;
+    const int HW = S.H * S.W;
     {
         const int pl = threadIdx.x & (I2C_PIX - 1);
         const int64_t p = p0 + pl;
@@ -98,8 +102,8 @@ __global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, in
             const int k = k0 + kr;
             bf16 v = __float2bfloat16_rn(0.0f);
             if (p < P && k < S.C * kk) {
-                const int ci = k / kk, r = k - ci * kk, ky = r / ks, kx = r - ky * ks;
-                v = src_at(S, b, ci, y + ky - half, x + kx - half);
+                const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
+                v = src_at<UP>(S, b, ci, y + ky - half, x + kx - half);
             }
             tile[kr][pl] = v;
         }
@@ -120,7 +124,8 @@ __global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, in
 // 8 the 8 pixels share an image row and read consecutive input elements; the
 // coarse levels of small images may wrap rows, so each pixel finds its own
 // coordinates.
-__global__ void __launch_bounds__(256) im2col_cols_kernel(const Src S, int B, int ks, int K9p, int ldp,
+template <int KS, int UP>
+__global__ void __launch_bounds__(256) im2col_cols_kernel(const Src S, int B, int K9p, int ldp,
                                                         bf16* __restrict__ out) {
     const int64_t P = (int64_t)B * S.H * S.W;
     const int64_t groups = ldp / 8;
@@ -128,18 +133,20 @@ __global__ void __launch_bounds__(256) im2col_cols_kernel(const Src S, int B, in
     if (i >= groups * K9p) return;
     const int k = (int)(i / groups);
     const int64_t p0 = (i - (int64_t)k * groups) * 8;
-    const int kk = ks * ks, half = ks / 2, HW = S.H * S.W;
+    constexpr int kk = KS * KS, half = KS / 2;
+    const int HW = S.H * S.W;
     __align__(16) bf16 v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn(0.0f);
-    if (k < S.C * kk) {
-        const int ci = k / kk, r = k - ci * kk, ky = r / ks, kx = r - ky * ks;
+    if (k < S.C * kk && p0 < P) {
+        const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
+        int b = (int)(p0 / HW), yx = (int)(p0 % HW), y = yx / S.W, x = yx % S.W;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int64_t p = p0 + j;
-            if (p < P) {
-                const int b = (int)(p / HW), yx = (int)(p % HW), y = yx / S.W, x = yx % S.W;
-                v[j] = src_at(S, b, ci, y + ky - half, x + kx - half);
+            if (p0 + j < P) v[j] = src_at<UP>(S, b, ci, y + ky - half, x + kx - half);
+            if (++x == S.W) {                           // next pixel: wrap to the next row / image
+                x = 0;
+                if (++y == S.H) { y = 0; ++b; }
             }
         }
     }
@@ -482,7 +489,17 @@ Src chan_major(const bf16* t, int C, int H, int W, int64_t ldp) {
 cudaError_t im2col_rows(gdrr_cnn* n, const Src& X, int B, int ks, int K9p) {
     const int64_t P = (int64_t)B * X.H * X.W;
     const dim3 grid((unsigned)((P + I2C_PIX - 1) / I2C_PIX), (unsigned)(K9p / I2C_K));
-    im2col_rows_kernel<<<grid, 256, 0, n->stream>>>(X, B, ks, K9p, n->cols);
+    if (ks == 1) im2col_rows_kernel<1, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
+    else if (X.up == 2) im2col_rows_kernel<3, 2><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
+    else im2col_rows_kernel<3, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
+    return cudaGetLastError();
+}
+
+cudaError_t im2col_cols(gdrr_cnn* n, const Src& X, int B, int ks, int K9p, int ldp) {
+    const int blocks = nblk((int64_t)(ldp / 8) * K9p);
+    if (ks == 1) im2col_cols_kernel<1, 1><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
+    else if (X.up == 2) im2col_cols_kernel<3, 2><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
+    else im2col_cols_kernel<3, 1><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
     return cudaGetLastError();
 }
 
@@ -519,8 +536,7 @@ cudaError_t conv_backward(gdrr_cnn* n, const Conv& L, int B, const float* dy, co
     bias_grad_sum_kernel<<<(L.co + 127) / 128, 128, 0, n->stream>>>(n->partials, L.co, parts, n->grads + L.b_off);
     CK(cudaGetLastError());
     // weight gradient: dW[co][k] = sum_p dZ[p][co] cols[p][k]
-    im2col_cols_kernel<<<nblk((int64_t)(Pp / 8) * L.K9p), TB, 0, n->stream>>>(X, B, L.ks, L.K9p, Pp, n->cols);
-    CK(cudaGetLastError());
+    CK(im2col_cols(n, X, B, L.ks, L.K9p, Pp));
     // the pixel sum is split across CTAs; each split writes its own partial
     // product and one ordered pass adds them, so training is bit-reproducible
     const int splits = wgrad_splits(P);
