@@ -119,6 +119,40 @@ __global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, in
     }
 }
 
+// The same tile where the width is a multiple of 32: the tile's 32 pixels
+// are one image-row segment, so the image, the row, each k's channel, tap and
+// source row are the same on every lane and only the column differs.
+template <int KS, int UP>
+__global__ void __launch_bounds__(256) im2col_rows_w32_kernel(const Src S, int K9p, bf16* __restrict__ out) {
+    __shared__ bf16 tile[I2C_K][I2C_PIX + 2];
+    const int64_t p0 = (int64_t)blockIdx.x * I2C_PIX;
+    const int k0 = blockIdx.y * I2C_K;
+    constexpr int kk = KS * KS, half = KS / 2;
+    const int HW = S.H * S.W;
+    const int b = (int)(p0 / HW), yx0 = (int)(p0 % HW), y = yx0 / S.W;
+    const int lane = threadIdx.x & 31, x = yx0 % S.W + lane;
+    const int wa = S.W / UP;
+    for (int kr = threadIdx.x >> 5; kr < I2C_K; kr += 8) {
+        const int k = k0 + kr;
+        bf16 v = __float2bfloat16_rn(0.0f);
+        if (k < S.C * kk) {
+            const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
+            const int yy = y + ky - half, xx = x + kx - half;
+            if (yy >= 0 && yy < S.H && xx >= 0 && xx < S.W) {
+                if (ci < S.Ca) v = S.a[(int64_t)b * S.a_bs + (int64_t)ci * S.a_cs + (yy / UP) * wa + xx / UP];
+                else v = S.s[(int64_t)b * S.s_bs + (int64_t)(ci - S.Ca) * S.s_cs + yy * S.W + xx];
+            }
+        }
+        tile[kr][lane] = v;
+    }
+    __syncthreads();
+    const int pix = threadIdx.x >> 3, chunk = threadIdx.x & 7;
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = tile[chunk * 8 + j][pix];
+    *reinterpret_cast<uint4*>(out + (p0 + pix) * K9p + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(v);
+}
+
 // colsT[k][p] (row length ldp >= P, padding pixels zero): each thread writes
 // 8 consecutive pixels of one k (16 bytes).  Where the width is a multiple of
 // 8 the 8 pixels share an image row and read consecutive input elements; the
@@ -349,6 +383,41 @@ __global__ void unpad_kernel(const float* __restrict__ src, int rows, int cols, 
     if (i < n) dst[i] = src[(i / cols) * ld + i % cols];
 }
 
+// colsT for widths that are multiples of 8: a thread's 8 pixels are one row
+// segment, read through one source row pointer.
+template <int KS, int UP>
+__global__ void __launch_bounds__(256) im2col_cols_w8_kernel(const Src S, int B, int K9p, int ldp,
+                                                           bf16* __restrict__ out) {
+    const int64_t P = (int64_t)B * S.H * S.W;
+    const int64_t groups = ldp / 8;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= groups * K9p) return;
+    const int k = (int)(i / groups);
+    const int64_t p0 = (i - (int64_t)k * groups) * 8;
+    constexpr int kk = KS * KS, half = KS / 2;
+    const int HW = S.H * S.W;
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn(0.0f);
+    if (k < S.C * kk && p0 < P) {
+        const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
+        const int b = (int)(p0 / HW), yx = (int)(p0 % HW), y = yx / S.W, x = yx % S.W;
+        const int yy = y + ky - half;
+        if (yy >= 0 && yy < S.H) {
+            const bf16* row;
+            if (ci < S.Ca) row = S.a + (int64_t)b * S.a_bs + (int64_t)ci * S.a_cs + (int64_t)(yy / UP) * (S.W / UP);
+            else row = S.s + (int64_t)b * S.s_bs + (int64_t)(ci - S.Ca) * S.s_cs + (int64_t)yy * S.W;
+            const int up = ci < S.Ca ? UP : 1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int xx = x + j + kx - half;
+                if (xx >= 0 && xx < S.W) v[j] = row[up == 2 ? (xx >> 1) : xx];
+            }
+        }
+    }
+    *reinterpret_cast<uint4*>(out + (int64_t)k * ldp + p0) = *reinterpret_cast<const uint4*>(v);
+}
+
 struct Conv {
     int ci, co, ks, H, W, relu;
     int K9, K9p, K9dp;     // ci ks^2, padded to 64; co ks^2 padded to 64 (data gradient)
@@ -489,14 +558,26 @@ Src chan_major(const bf16* t, int C, int H, int W, int64_t ldp) {
 cudaError_t im2col_rows(gdrr_cnn* n, const Src& X, int B, int ks, int K9p) {
     const int64_t P = (int64_t)B * X.H * X.W;
     const dim3 grid((unsigned)((P + I2C_PIX - 1) / I2C_PIX), (unsigned)(K9p / I2C_K));
-    if (ks == 1) im2col_rows_kernel<1, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
-    else if (X.up == 2) im2col_rows_kernel<3, 2><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
-    else im2col_rows_kernel<3, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
+    if (X.W % I2C_PIX == 0 && ks == 3) {
+        if (X.up == 2) im2col_rows_w32_kernel<3, 2><<<grid, 256, 0, n->stream>>>(X, K9p, n->cols);
+        else im2col_rows_w32_kernel<3, 1><<<grid, 256, 0, n->stream>>>(X, K9p, n->cols);
+    } else if (ks == 1) {
+        im2col_rows_kernel<1, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
+    } else if (X.up == 2) {
+        im2col_rows_kernel<3, 2><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
+    } else {
+        im2col_rows_kernel<3, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t im2col_cols(gdrr_cnn* n, const Src& X, int B, int ks, int K9p, int ldp) {
     const int blocks = nblk((int64_t)(ldp / 8) * K9p);
+    if (X.W % 8 == 0 && ks == 3) {
+        if (X.up == 2) im2col_cols_w8_kernel<3, 2><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
+        else im2col_cols_w8_kernel<3, 1><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
+        return cudaGetLastError();
+    }
     if (ks == 1) im2col_cols_kernel<1, 1><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
     else if (X.up == 2) im2col_cols_kernel<3, 2><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
     else im2col_cols_kernel<3, 1><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
