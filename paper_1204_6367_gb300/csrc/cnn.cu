@@ -95,18 +95,22 @@ __global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, in
     constexpr int kk = KS * KS, half = KS / 2;
     const int HW = S.H * S.W;
     {
-        const int pl = threadIdx.x & (I2C_PIX - 1);
+        // the thread's 8 loads go out together, then land in the tile
+        const int pl = threadIdx.x & (I2C_PIX - 1), w = threadIdx.x >> 5;
         const int64_t p = p0 + pl;
         const int b = (int)(p / HW), yx = (int)(p % HW), y = yx / S.W, x = yx % S.W;
-        for (int kr = threadIdx.x >> 5; kr < I2C_K; kr += 8) {
-            const int k = k0 + kr;
-            bf16 v = __float2bfloat16_rn(0.0f);
+        bf16 vals[I2C_K / 8];
+#pragma unroll
+        for (int j = 0; j < I2C_K / 8; ++j) {
+            const int k = k0 + w + 8 * j;
+            vals[j] = __float2bfloat16_rn(0.0f);
             if (p < P && k < S.C * kk) {
                 const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
-                v = src_at<UP>(S, b, ci, y + ky - half, x + kx - half);
+                vals[j] = src_at<UP>(S, b, ci, y + ky - half, x + kx - half);
             }
-            tile[kr][pl] = v;
         }
+#pragma unroll
+        for (int j = 0; j < I2C_K / 8; ++j) tile[w + 8 * j][pl] = vals[j];
     }
     __syncthreads();
     const int pix = threadIdx.x >> 3, chunk = threadIdx.x & 7;
@@ -130,21 +134,24 @@ __global__ void __launch_bounds__(256) im2col_rows_w32_kernel(const Src S, int K
     constexpr int kk = KS * KS, half = KS / 2;
     const int HW = S.H * S.W;
     const int b = (int)(p0 / HW), yx0 = (int)(p0 % HW), y = yx0 / S.W;
-    const int lane = threadIdx.x & 31, x = yx0 % S.W + lane;
+    const int lane = threadIdx.x & 31, x = yx0 % S.W + lane, w = threadIdx.x >> 5;
     const int wa = S.W / UP;
-    for (int kr = threadIdx.x >> 5; kr < I2C_K; kr += 8) {
-        const int k = k0 + kr;
-        bf16 v = __float2bfloat16_rn(0.0f);
+    bf16 vals[I2C_K / 8];
+#pragma unroll
+    for (int j = 0; j < I2C_K / 8; ++j) {           // the thread's 8 loads go out together
+        const int k = k0 + w + 8 * j;
+        vals[j] = __float2bfloat16_rn(0.0f);
         if (k < S.C * kk) {
             const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
             const int yy = y + ky - half, xx = x + kx - half;
             if (yy >= 0 && yy < S.H && xx >= 0 && xx < S.W) {
-                if (ci < S.Ca) v = S.a[(int64_t)b * S.a_bs + (int64_t)ci * S.a_cs + (yy / UP) * wa + xx / UP];
-                else v = S.s[(int64_t)b * S.s_bs + (int64_t)(ci - S.Ca) * S.s_cs + yy * S.W + xx];
+                if (ci < S.Ca) vals[j] = S.a[(int64_t)b * S.a_bs + (int64_t)ci * S.a_cs + (yy / UP) * wa + xx / UP];
+                else vals[j] = S.s[(int64_t)b * S.s_bs + (int64_t)(ci - S.Ca) * S.s_cs + yy * S.W + xx];
             }
         }
-        tile[kr][lane] = v;
     }
+#pragma unroll
+    for (int j = 0; j < I2C_K / 8; ++j) tile[w + 8 * j][lane] = vals[j];
     __syncthreads();
     const int pix = threadIdx.x >> 3, chunk = threadIdx.x & 7;
     __align__(16) bf16 v[8];
