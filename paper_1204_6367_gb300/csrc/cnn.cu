@@ -123,41 +123,65 @@ __global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, in
     }
 }
 
-// The same tile where the width is a multiple of 32: the tile's 32 pixels
-// are one image-row segment, so the image, the row, each k's channel, tap and
-// source row are the same on every lane and only the column differs.
-template <int KS, int UP>
-__global__ void __launch_bounds__(256) im2col_rows_w32_kernel(const Src S, int K9p, bf16* __restrict__ out) {
-    __shared__ bf16 tile[I2C_K][I2C_PIX + 2];
-    const int64_t p0 = (int64_t)blockIdx.x * I2C_PIX;
-    const int k0 = blockIdx.y * I2C_K;
-    constexpr int kk = KS * KS, half = KS / 2;
+// 3x3 columns of a 32-pixel row segment, all k at once: warp w builds the 9
+// taps of channels w, w + 8, ...; for each of the 3 source rows a lane loads
+// its own pixel's value and the segment's two halo values come from lanes 0
+// and 31, so the left and right taps are warp shuffles instead of loads.  The
+// whole row segment [32][K9p] is assembled in shared memory (row pitch
+// K9p + 8 elements) and written out with 16-byte stores.
+template <int UP>
+__global__ void __launch_bounds__(256) im2col_rows_shfl_kernel(const Src S, int K9p, bf16* __restrict__ out) {
+    extern __shared__ __align__(16) bf16 seg[];
+    const int pitch = K9p + 8;
+    const int64_t p0 = (int64_t)blockIdx.x * 32;
     const int HW = S.H * S.W;
-    const int b = (int)(p0 / HW), yx0 = (int)(p0 % HW), y = yx0 / S.W;
-    const int lane = threadIdx.x & 31, x = yx0 % S.W + lane, w = threadIdx.x >> 5;
-    const int wa = S.W / UP;
-    bf16 vals[I2C_K / 8];
+    const int b = (int)(p0 / HW), yx0 = (int)(p0 % HW), y = yx0 / S.W, x0 = yx0 % S.W;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = x0 + lane;
+    const bf16 zero = __float2bfloat16_rn(0.0f);
+    for (int ci = w; ci < S.C; ci += 8) {
+        bf16 taps[9];
 #pragma unroll
-    for (int j = 0; j < I2C_K / 8; ++j) {           // the thread's 8 loads go out together
-        const int k = k0 + w + 8 * j;
-        vals[j] = __float2bfloat16_rn(0.0f);
-        if (k < S.C * kk) {
-            const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
-            const int yy = y + ky - half, xx = x + kx - half;
-            if (yy >= 0 && yy < S.H && xx >= 0 && xx < S.W) {
-                if (ci < S.Ca) vals[j] = S.a[(int64_t)b * S.a_bs + (int64_t)ci * S.a_cs + (yy / UP) * wa + xx / UP];
-                else vals[j] = S.s[(int64_t)b * S.s_bs + (int64_t)(ci - S.Ca) * S.s_cs + yy * S.W + xx];
+        for (int ky = 0; ky < 3; ++ky) {
+            const int yy = y + ky - 1;
+            bf16 c = zero, edge = zero;
+            if (yy >= 0 && yy < S.H) {
+                const bf16* row;
+                int up = 1;
+                if (ci < S.Ca) {
+                    row = S.a + (int64_t)b * S.a_bs + (int64_t)ci * S.a_cs + (int64_t)(yy / UP) * (S.W / UP);
+                    up = UP;
+                } else {
+                    row = S.s + (int64_t)b * S.s_bs + (int64_t)(ci - S.Ca) * S.s_cs + (int64_t)yy * S.W;
+                }
+                c = row[up == 2 ? (x >> 1) : x];
+                const int xe = lane == 0 ? x0 - 1 : x0 + 32;          // halo: lane 0 left, lane 31 right
+                if ((lane == 0 || lane == 31) && xe >= 0 && xe < S.W) edge = row[up == 2 ? (xe >> 1) : xe];
             }
+            bf16 left = __shfl_up_sync(0xffffffffu, c, 1);
+            bf16 right = __shfl_down_sync(0xffffffffu, c, 1);
+            if (lane == 0) left = edge;
+            if (lane == 31) right = edge;
+            taps[ky * 3 + 0] = left;
+            taps[ky * 3 + 1] = c;
+            taps[ky * 3 + 2] = right;
         }
+        bf16* dst = seg + lane * pitch + ci * 9;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) dst[t] = taps[t];
     }
-#pragma unroll
-    for (int j = 0; j < I2C_K / 8; ++j) tile[w + 8 * j][lane] = vals[j];
+    // zero the padded k columns of each row
+    for (int i = threadIdx.x; i < 32 * (K9p - S.C * 9); i += blockDim.x) {
+        const int r = i / (K9p - S.C * 9), k = S.C * 9 + i % (K9p - S.C * 9);
+        seg[r * pitch + k] = zero;
+    }
     __syncthreads();
-    const int pix = threadIdx.x >> 3, chunk = threadIdx.x & 7;
-    __align__(16) bf16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = tile[chunk * 8 + j][pix];
-    *reinterpret_cast<uint4*>(out + (p0 + pix) * K9p + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(v);
+    const int chunks = K9p / 8;
+    for (int i = threadIdx.x; i < 32 * chunks; i += blockDim.x) {
+        const int r = i / chunks, ck = i % chunks;
+        *reinterpret_cast<uint4*>(out + (p0 + r) * K9p + ck * 8) =
+            *reinterpret_cast<const uint4*>(seg + r * pitch + ck * 8);
+    }
 }
 
 // colsT[k][p] (row length ldp >= P, padding pixels zero): each thread writes
@@ -565,9 +589,18 @@ Src chan_major(const bf16* t, int C, int H, int W, int64_t ldp) {
 cudaError_t im2col_rows(gdrr_cnn* n, const Src& X, int B, int ks, int K9p) {
     const int64_t P = (int64_t)B * X.H * X.W;
     const dim3 grid((unsigned)((P + I2C_PIX - 1) / I2C_PIX), (unsigned)(K9p / I2C_K));
-    if (X.W % I2C_PIX == 0 && ks == 3) {
-        if (X.up == 2) im2col_rows_w32_kernel<3, 2><<<grid, 256, 0, n->stream>>>(X, K9p, n->cols);
-        else im2col_rows_w32_kernel<3, 1><<<grid, 256, 0, n->stream>>>(X, K9p, n->cols);
+    const size_t seg_bytes = (size_t)32 * (K9p + 8) * sizeof(bf16);
+    if (X.W % 32 == 0 && ks == 3 && seg_bytes <= 200 * 1024) {
+        const unsigned blocks = (unsigned)(P / 32);
+        if (X.up == 2) {
+            CK(cudaFuncSetAttribute(im2col_rows_shfl_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)seg_bytes));
+            im2col_rows_shfl_kernel<2><<<blocks, 256, seg_bytes, n->stream>>>(X, K9p, n->cols);
+        } else {
+            CK(cudaFuncSetAttribute(im2col_rows_shfl_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)seg_bytes));
+            im2col_rows_shfl_kernel<1><<<blocks, 256, seg_bytes, n->stream>>>(X, K9p, n->cols);
+        }
     } else if (ks == 1) {
         im2col_rows_kernel<1, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
     } else if (X.up == 2) {
