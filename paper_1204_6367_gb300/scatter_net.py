@@ -161,6 +161,43 @@ def evaluate(net, seeds=(900, 901, 902, 903), angles_per_seed=2, n_low=10**6, n_
     return {"learned": err_net, "plain": err_plain, "plain_histories_at_learned_error": matched}
 
 
+def bench_network(batch: int = 64, train_batch: int = 16, reps: int = 5, channels: int = 32) -> dict:
+    """Device time of the network on random inputs: a forward pass of `batch`
+    images and a training step (forward, backward, Adam) of `train_batch`,
+    best of `reps` after a warm-up, with the convolution flops of Section
+    network_flops and the resulting TFLOP/s."""
+    import torch
+    net = gdrr.Cnn(max(batch, train_batch), H, W, channels, seed=1)
+    x = torch.rand((batch, 2, H, W), dtype=torch.float32, device="cuda")
+    t = torch.rand((train_batch, 1, H, W), dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            ev[0].record()
+            fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            best = min(best, ev[0].elapsed_time(ev[1]))
+        return best
+
+    def step():
+        net.forward(x[:train_batch])
+        net.backward(t)
+        net.adam_step(1e-4)
+
+    f_ms = timed(lambda: net.forward(x))
+    s_ms = timed(step)
+    net.close()
+    flops = network_flops(channels)
+    return {"forward_batch": batch, "forward_ms": f_ms, "forward_tflops": batch * flops / f_ms / 1e9,
+            "train_batch": train_batch, "train_step_ms": s_ms,
+            "train_tflops": 3 * train_batch * flops / s_ms / 1e9, "gflop_per_image": flops / 1e9}
+
+
 def main(argv=None):
     """Train and evaluate the estimator at a chosen scale; prints one JSON line."""
     import argparse
@@ -169,6 +206,8 @@ def main(argv=None):
 
     import torch
     ap = argparse.ArgumentParser(description="train the learned scatter estimator on method-generated pairs")
+    ap.add_argument("--bench-network", action="store_true",
+                    help="only time the network's forward pass and training step on random inputs")
     ap.add_argument("--phantoms", type=int, default=256, help="training torsos (one random angle each)")
     ap.add_argument("--steps", type=int, default=4000, help="Adam steps")
     ap.add_argument("--batch", type=int, default=16)
@@ -178,6 +217,9 @@ def main(argv=None):
     ap.add_argument("--channels", type=int, default=32, help="base channels of the network (<= 64)")
     args = ap.parse_args(argv)
     gdrr.lib()
+    if args.bench_network:
+        print(json.dumps(bench_network(channels=args.channels)))
+        return
     t0 = time.perf_counter()
     # training torsos from seed 10000 on; the held-out torsos are 900 ... 903
     X, Y = make_dataset(range(10000, 10000 + args.phantoms), 1, int(args.low), int(args.high), rng_seed=1)
