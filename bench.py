@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip training / evaluating the learned estimator")
     ap.add_argument("--no-variants", action="store_true", help="skip the nearest-voxel / Siddon / filter timings")
     ap.add_argument("--no-fdk", action="store_true", help="skip the 360-view FDK reconstruction timing")
+    ap.add_argument("--mc-config", default=None, metavar="BLOCK,BATCH_MIN,HIST_PER_THREAD",
+                    help="fix the transport's launch configuration (lane form) instead of autotuning it")
     return ap.parse_args()
 
 
@@ -119,17 +121,27 @@ def measured_peak(key, fallback):
         return fallback
 
 
-def profile_record(name, cell_shift=None, config=None):
-    """Key/value counters of the transport kernel from a committed ncu summary
-    (profiles/<name>), or None when the kernel source changed since those
-    counters were taken, or they were taken with other macro cells
-    (cell_shift given) or another launch configuration (config given: the
-    record's block_size, batch_min and hist_per_thread must match)."""
+def profile_record(name, cell_shift=None):
+    """Counters of the transport kernel from a committed ncu summary
+    (profiles/<name>): its "key value" lines as a dict, with its "config ..."
+    lines (one per launch configuration measured) as a list under "configs";
+    None when the kernel source changed since those counters were taken, or
+    they were taken with other macro cells (cell_shift given)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", name)
+    vals, configs = {}, []
     try:
-        vals = dict(l.split() for l in open(path) if l.strip() and not l.startswith("#"))
-    except (OSError, ValueError):
+        for l in open(path):
+            f = l.split()
+            if not f or l.startswith("#"):
+                continue
+            if f[0] == "config":
+                configs.append(f[1:])
+            elif len(f) == 2:
+                vals[f[0]] = f[1]
+            else:
+                return None
+    except OSError:
         return None
     h = hashlib.sha256()
     h.update(open(os.path.join(ROOT, "paper_1204_6367_gb300", "csrc", "mc_transport.cu"), "rb").read())
@@ -137,10 +149,7 @@ def profile_record(name, cell_shift=None, config=None):
         return None
     if cell_shift is not None and str(cell_shift) != vals.get("cell_shift"):
         return None
-    if config is not None:
-        for k in ("block_size", "batch_min", "hist_per_thread"):
-            if str(config.get(k)) != vals.get(k):
-                return None
+    vals["configs"] = configs
     return vals
 
 
@@ -151,13 +160,22 @@ def kernel_traffic(cell_shift=None):
     return int(v["bytes_per_launch"]) if v else None
 
 
+ISSUE_CONFIG_KEYS = ("block_size", "batch_min", "hist_per_thread")
+
+
 def kernel_inst_per_step(cell_shift=None, config=None):
     """Thread instructions the transport executes per Woodcock free flight
-    (ncu smsp__thread_inst_executed.sum / free flights of the same launch), or
-    None for another kernel source, other macro cells or another launch
-    configuration."""
-    v = profile_record("mc_kernel_torso2mm_issue.txt", cell_shift, config)
-    return float(v["thread_inst_per_step"]) if v else None
+    (ncu smsp__thread_inst_executed.sum / free flights of the same launch)
+    from the record's line for the launch configuration given (block_size,
+    batch_min, hist_per_thread; config None: the first line), or None for
+    another kernel source, other macro cells or an unmeasured configuration."""
+    v = profile_record("mc_kernel_torso2mm_issue.txt", cell_shift)
+    if not v:
+        return None
+    for c in v["configs"]:
+        if config is None or [str(config.get(k)) for k in ISSUE_CONFIG_KEYS] == c[:3]:
+            return float(c[3])
+    return None
 
 
 def transport_roofline(steps, mc_s, hbm_peak, traffic, inst_per_step=None, n_sm=152, sm_max_mhz=2070.0,
@@ -281,9 +299,14 @@ def run_ours(args):
     def step():
         return gdrr.project(ctx, n_hist, seed, angle, bin_factor=4, beta=0.02, iters=iters, stats=stats, out=out)
 
-    # launch configuration from the project's autotuner (tallies do not
-    # depend on it)
-    tuned = gdrr.gdrr_autotune(ctx, angle, 20_000_000, seed)
+    # launch configuration from the project's autotuner, or the one given
+    # (tallies do not depend on it)
+    if args.mc_config:
+        b, m, h = (int(x) for x in args.mc_config.split(","))
+        gdrr.gdrr_set_options(ctx, block_size=b, batch_min=m, hist_per_thread=h, blocks_per_sm=0, photon_pool=-1)
+        tuned = gdrr.gdrr_get_options(ctx)
+    else:
+        tuned = gdrr.gdrr_autotune(ctx, angle, 20_000_000, seed)
 
     for _ in range(max(args.warmup, 3)):
         res = step()

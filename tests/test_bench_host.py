@@ -91,10 +91,11 @@ def test_instruction_record_is_keyed_to_the_launch_configuration(tmp_path, monke
     import hashlib
     h = hashlib.sha256(kernel.encode()).hexdigest()[:16]
     (tmp_path / "profiles" / "mc_kernel_torso2mm_issue.txt").write_text(
-        f"thread_inst_per_step 250.0\ncell_shift 2\nblock_size 64\nbatch_min 20\nhist_per_thread 8\n"
-        f"source_sha256_16 {h}\n")
+        f"cell_shift 2\nsource_sha256_16 {h}\nconfig 64 20 8 250.0 20.0 1000\nconfig 512 16 1 260.0 18.0 1000\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     cfg = {"block_size": 64, "batch_min": 20, "hist_per_thread": 8}
     assert bench.kernel_inst_per_step(2, cfg) == 250.0
     assert bench.kernel_inst_per_step(2, dict(cfg, batch_min=16)) is None
     assert bench.kernel_inst_per_step(2, dict(cfg, block_size=128)) is None
+    assert bench.kernel_inst_per_step(2, dict(cfg, block_size=512, batch_min=16, hist_per_thread=1)) == 260.0
+    assert bench.kernel_inst_per_step(3, cfg) is None
