@@ -592,9 +592,13 @@ GDRR_API int gdrr_gemm_bf16(const void* A_dev, int32_t lda, const void* B_dev, i
  * on pairs the method itself generates.  BF16 weights and activations, FP32
  * accumulation on the tensor cores; FP32 master weights, gradients and Adam
  * state.  Inputs are device FP32 [batch][2][height][width], outputs and
- * targets [batch][1][height][width]; height and width multiples of 8.
+ * targets [batch][1][height][width]; height and width multiples of 8;
+ * base_channels a multiple of 8, at most 64 (else GDRR_ERR_INVALID_ARG).
  * Parameters flatten layer by layer as (weights [co][ci][ky][kx], biases
- * [co]), encoder first, then decoder, then the 1x1 layer. */
+ * [co]), encoder first, then decoder, then the 1x1 layer.  Convolutions whose
+ * grid tiles into 128-pixel groups of whole rows (or of part of one row) run
+ * as implicit GEMMs on the tensor cores; the others, and the weight
+ * gradients, through column matrices. */
 typedef struct gdrr_cnn gdrr_cnn;
 GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, int32_t base_channels, uint64_t seed,
                              void* cuda_stream, gdrr_cnn** out);

@@ -33,7 +33,7 @@ SOURCES = {
     "fdk.cu": [],
     "probes.cu": [],
 }
-HEADERS = [os.path.join(INCLUDE, "gdrr.h"), os.path.join(CSRC, "gdrr_internal.cuh")]
+HEADERS = [os.path.join(INCLUDE, "gdrr.h"), os.path.join(CSRC, "gdrr_internal.cuh"), os.path.join(CSRC, "cnn_epi.cuh")]
 
 
 def nvcc() -> str:

@@ -15,13 +15,22 @@
 // pool = 2 x 2 average, up = nearest 2x, [a, b] = channel concatenation.
 // Loss: mean squared error against the target.
 //
-// A 3x3 convolution is a GEMM over im2col columns:
-//   forward   Y[P x Co]   = cols(x)[P x K9] . W[Co x K9]^T
-//   data grad dX[P x Ci]  = cols(dZ)[P x K9d] . Wf[Ci x K9d]^T  (Wf: taps flipped)
-//   weight    dW[Co x K9] = dZ^T[Co x P] . colsT(x)[K9 x P]^T   (split over P)
-// with P = batch * H * W pixels, K9 = Ci * 9 and K9d = Co * 9 rounded up to
-// 64.  The decoder's inputs [up(prev), skip] are read in place by the column
-// builders (Src), not copied.
+// Layout.  Activations are NHWC BF16.  Each decoder input [up(prev), skip]
+// is one buffer cat_k (H_k x W_k pixels, pitch C_prev + C_skip): the
+// encoder convolution that makes the skip writes it in place (channels
+// C_prev ..), and the convolution one level down writes its output there
+// upsampled (channels 0 .. C_prev - 1, each pixel to its 2 x 2 block).  The
+// encoder output e4 and the decoder outputs d3, d2 exist only in that form.
+//
+// Convolutions.  A 3 x 3 convolution is a GEMM with K = (tap, channel):
+//   forward   Y[P x Co]   = cols(x)[P x 9Ci] . W[Co x 9Ci]^T
+//   data grad dX[P x Ci]  = cols(dZ)[P x 9Co] . Wf[Ci x 9Co]^T   (Wf: taps flipped)
+//   weight    dW[Co x 9Ci] = dZ^T[Co x P] . cols(x)[P x 9Ci]
+// The forward and data-gradient products run as implicit GEMMs
+// (launch_conv_implicit: the tensor-core kernel loads each tap's shifted input
+// tile by TMA, no column matrix) where the layer's grid tiles into 128-pixel
+// rows; otherwise, and for the weight gradient (whose K runs over pixels),
+// a column matrix is built and multiplied by launch_gemm_bf16.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -30,6 +39,7 @@
 #include <new>
 #include <vector>
 
+#include "cnn_epi.cuh"
 #include "gdrr_internal.cuh"
 
 namespace gdrr {
@@ -45,316 +55,318 @@ constexpr int TB = 256;
 inline int nblk(int64_t n) { return (int)((n + TB - 1) / TB); }
 inline int pad64(int64_t n) { return (int)((n + 63) / 64 * 64); }
 
-__global__ void to_bf16_kernel(const float* __restrict__ x, int64_t n, bf16* __restrict__ y) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
-}
-
-// The input of a convolution as the channel concatenation of two BF16
-// tensors [a, s]: channel c < Ca reads a at resolution (H / up) x (W / up)
-// (up = 2: nearest upsampling), channel c >= Ca reads s at H x W.  Element
-// (b, c, y, x) of a tensor sits at base + b * batch_stride + c * chan_stride +
-// y * width + x (NCHW: batch_stride = C H W, chan_stride = H W; the
-// channel-major gradient rows [c][b H W] of the backward: batch_stride = H W,
-// chan_stride = padded pixel count).  The decoder's concatenations and
-// upsamplings are read in place instead of being copied.
-struct Src {
-    const bf16* a;
-    int Ca, up;
-    int64_t a_bs, a_cs;
-    const bf16* s;
-    int64_t s_bs, s_cs;
-    int C, H, W;                        // total channels and the output resolution
+// A BF16 NHWC tensor on a grid H x W: pixel (b, y, x) channel c at
+// p[q ld + off + c] with q = (b H s + y s) (W s) + x s; s = up = 2 when the
+// tensor is stored upsampled on a 2H x 2W grid (it reads pixel (2y, 2x)).
+struct View {
+    const bf16* p;
+    int ld, off, up;
 };
 
-// UP is the kernel's compile-time copy of S.up (1 or 2), so the upsampling
-// index arithmetic is shifts.
-template <int UP>
-__device__ __forceinline__ bf16 src_at(const Src& S, int b, int c, int y, int x) {
-    if (y < 0 || y >= S.H || x < 0 || x >= S.W) return __float2bfloat16_rn(0.0f);
-    if (c < S.Ca) {
-        const int wa = S.W / UP;
-        return S.a[(int64_t)b * S.a_bs + (int64_t)c * S.a_cs + (int64_t)(y / UP) * wa + x / UP];
-    }
-    return S.s[(int64_t)b * S.s_bs + (int64_t)(c - S.Ca) * S.s_cs + (int64_t)y * S.W + x];
+View plain(const bf16* p, int ld, int off = 0) { return View{p, ld, off, 1}; }
+
+__device__ __forceinline__ int64_t view_pixel(const View& v, int64_t p, int H, int W) {
+    const int64_t hw = (int64_t)H * W;
+    const int64_t b = p / hw;
+    const int r = (int)(p - b * hw);
+    const int y = r / W, x = r - y * W;
+    const int s = v.up;
+    return (b * H * s + (int64_t)y * s) * ((int64_t)W * s) + (int64_t)x * s;
 }
 
-// cols[p][k] (row length K9p), p = (b, y, x), k = ci * ks * ks + ky * ks + kx,
-// zero beyond C * ks * ks.  One block builds a tile of 32 pixels x 64 k:
-// the reads go along pixels (coalesced on the input rows), the tile is
-// transposed in shared memory, and each row segment of 64 k (128 bytes) is
-// written with 16-byte stores.
-constexpr int I2C_PIX = 32, I2C_K = 64;
-
-template <int KS, int UP>
-__global__ void __launch_bounds__(256) im2col_rows_kernel(const Src S, int B, int K9p, bf16* __restrict__ out) {
-    __shared__ bf16 tile[I2C_K][I2C_PIX + 2];
-    const int64_t P = (int64_t)B * S.H * S.W;
-    const int64_t p0 = (int64_t)blockIdx.x * I2C_PIX;
-    const int k0 = blockIdx.y * I2C_K;
-    constexpr int kk = KS * KS, half = KS / 2;
-    const int HW = S.H * S.W;
-    {
-        // the thread's 8 loads go out together, then land in the tile
-        const int pl = threadIdx.x & (I2C_PIX - 1), w = threadIdx.x >> 5;
-        const int64_t p = p0 + pl;
-        const int b = (int)(p / HW), yx = (int)(p % HW), y = yx / S.W, x = yx % S.W;
-        bf16 vals[I2C_K / 8];
-#pragma unroll
-        for (int j = 0; j < I2C_K / 8; ++j) {
-            const int k = k0 + w + 8 * j;
-            vals[j] = __float2bfloat16_rn(0.0f);
-            if (p < P && k < S.C * kk) {
-                const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
-                vals[j] = src_at<UP>(S, b, ci, y + ky - half, x + kx - half);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < I2C_K / 8; ++j) tile[w + 8 * j][pl] = vals[j];
-    }
-    __syncthreads();
-    const int pix = threadIdx.x >> 3, chunk = threadIdx.x & 7;
-    const int64_t p = p0 + pix;
-    if (p < P) {
-        __align__(16) bf16 v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = tile[chunk * 8 + j][pix];
-        *reinterpret_cast<uint4*>(out + p * K9p + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(v);
-    }
+// x[b][2][H][W] (FP32 NCHW) -> BF16 NHWC [b][H][W][2]
+__global__ void to_nhwc2_kernel(const float* __restrict__ x, int64_t P, int HW, bf16* __restrict__ y) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int64_t b = p / HW, r = p % HW;
+    __nv_bfloat162 v;
+    v.x = __float2bfloat16_rn(x[(b * 2) * HW + r]);
+    v.y = __float2bfloat16_rn(x[(b * 2 + 1) * HW + r]);
+    reinterpret_cast<__nv_bfloat162*>(y)[p] = v;
 }
 
-// 3x3 columns of a 32-pixel row segment, all k at once: warp w builds the 9
-// taps of channels w, w + 8, ...; for each of the 3 source rows a lane loads
-// its own pixel's value and the segment's two halo values come from lanes 0
-// and 31, so the left and right taps are warp shuffles instead of loads.  The
-// whole row segment [32][K9p] is assembled in shared memory (row pitch
-// K9p + 8 elements) and written out with 16-byte stores.
-template <int UP>
-__global__ void __launch_bounds__(256) im2col_rows_shfl_kernel(const Src S, int K9p, bf16* __restrict__ out) {
-    extern __shared__ __align__(16) bf16 seg[];
-    const int pitch = K9p + 8;
-    const int64_t p0 = (int64_t)blockIdx.x * 32;
-    const int HW = S.H * S.W;
-    const int b = (int)(p0 / HW), yx0 = (int)(p0 % HW), y = yx0 / S.W, x0 = yx0 % S.W;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = x0 + lane;
-    const bf16 zero = __float2bfloat16_rn(0.0f);
-    for (int ci = w; ci < S.C; ci += 8) {
-        bf16 taps[9];
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-            const int yy = y + ky - 1;
-            bf16 c = zero, edge = zero;
-            if (yy >= 0 && yy < S.H) {
-                const bf16* row;
-                int up = 1;
-                if (ci < S.Ca) {
-                    row = S.a + (int64_t)b * S.a_bs + (int64_t)ci * S.a_cs + (int64_t)(yy / UP) * (S.W / UP);
-                    up = UP;
-                } else {
-                    row = S.s + (int64_t)b * S.s_bs + (int64_t)(ci - S.Ca) * S.s_cs + (int64_t)yy * S.W;
-                }
-                c = row[up == 2 ? (x >> 1) : x];
-                const int xe = lane == 0 ? x0 - 1 : x0 + 32;          // halo: lane 0 left, lane 31 right
-                if ((lane == 0 || lane == 31) && xe >= 0 && xe < S.W) edge = row[up == 2 ? (xe >> 1) : xe];
-            }
-            bf16 left = __shfl_up_sync(0xffffffffu, c, 1);
-            bf16 right = __shfl_down_sync(0xffffffffu, c, 1);
-            if (lane == 0) left = edge;
-            if (lane == 31) right = edge;
-            taps[ky * 3 + 0] = left;
-            taps[ky * 3 + 1] = c;
-            taps[ky * 3 + 2] = right;
-        }
-        bf16* dst = seg + lane * pitch + ci * 9;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) dst[t] = taps[t];
-    }
-    // zero the padded k columns of each row
-    for (int i = threadIdx.x; i < 32 * (K9p - S.C * 9); i += blockDim.x) {
-        const int r = i / (K9p - S.C * 9), k = S.C * 9 + i % (K9p - S.C * 9);
-        seg[r * pitch + k] = zero;
-    }
-    __syncthreads();
-    const int chunks = K9p / 8;
-    for (int i = threadIdx.x; i < 32 * chunks; i += blockDim.x) {
-        const int r = i / chunks, ck = i % chunks;
-        *reinterpret_cast<uint4*>(out + (p0 + r) * K9p + ck * 8) =
-            *reinterpret_cast<const uint4*>(seg + r * pitch + ck * 8);
-    }
-}
-
-// colsT[k][p] (row length ldp >= P, padding pixels zero): each thread writes
-// 8 consecutive pixels of one k (16 bytes).  Where the width is a multiple of
-// 8 the 8 pixels share an image row and read consecutive input elements; the
-// coarse levels of small images may wrap rows, so each pixel finds its own
-// coordinates.
-template <int KS, int UP>
-__global__ void __launch_bounds__(256) im2col_cols_kernel(const Src S, int B, int K9p, int ldp,
-                                                        bf16* __restrict__ out) {
-    const int64_t P = (int64_t)B * S.H * S.W;
-    const int64_t groups = ldp / 8;
+// Column matrix rows: cols[p][k] (row K9p), k = tap C + c (tap = ky ks +
+// kx), zero for k >= ks^2 C and outside the image.  One thread per 8
+// consecutive k of a row: one 16-byte load and store when C is a multiple of
+// 8 (the 8 channels lie in one tap), else element by element.
+__global__ void im2col_nhwc_kernel(const View X, int C, int B, int H, int W, int ks, int K9p,
+                                   bf16* __restrict__ out) {
+    const int kc_per_row = K9p / 8;
+    const int64_t P = (int64_t)B * H * W;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= groups * K9p) return;
-    const int k = (int)(i / groups);
-    const int64_t p0 = (i - (int64_t)k * groups) * 8;
-    constexpr int kk = KS * KS, half = KS / 2;
-    const int HW = S.H * S.W;
+    if (i >= P * kc_per_row) return;
+    const int64_t p = i / kc_per_row;
+    const int k0 = (int)(i - p * kc_per_row) * 8;
+    const int HW = H * W;
+    const int b = (int)(p / HW), r = (int)(p % HW), y = r / W, x = r % W;
+    const int K9 = ks * ks * C, half = ks / 2;
     __align__(16) bf16 v[8];
+    if (C % 8 == 0 && X.up == 1) {
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (k0 < K9) {
+            const int tap = k0 / C, c = k0 - tap * C;
+            const int ky = tap / ks, kx = tap - ky * ks;
+            const int yy = y + ky - half, xx = x + kx - half;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                val = *reinterpret_cast<const uint4*>(X.p + (((int64_t)b * H + yy) * W + xx) * X.ld + X.off + c);
+        }
+        *reinterpret_cast<uint4*>(out + p * K9p + k0) = val;
+        return;
+    }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn(0.0f);
-    if (k < S.C * kk && p0 < P) {
-        const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
-        int b = (int)(p0 / HW), yx = (int)(p0 % HW), y = yx / S.W, x = yx % S.W;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (p0 + j < P) v[j] = src_at<UP>(S, b, ci, y + ky - half, x + kx - half);
-            if (++x == S.W) {                           // next pixel: wrap to the next row / image
-                x = 0;
-                if (++y == S.H) { y = 0; ++b; }
+    for (int j = 0; j < 8; ++j) {
+        const int k = k0 + j;
+        v[j] = __float2bfloat16_rn(0.0f);
+        if (k < K9) {
+            const int tap = k / C, c = k - tap * C;
+            const int ky = tap / ks, kx = tap - ky * ks;
+            const int yy = y + ky - half, xx = x + kx - half;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const int s = X.up;
+                const int64_t q = ((int64_t)b * H * s + (int64_t)yy * s) * ((int64_t)W * s) + (int64_t)xx * s;
+                v[j] = X.p[q * X.ld + X.off + c];
             }
         }
     }
-    *reinterpret_cast<uint4*>(out + (int64_t)k * ldp + p0) = *reinterpret_cast<const uint4*>(v);
+    *reinterpret_cast<uint4*>(out + p * K9p + k0) = *reinterpret_cast<const uint4*>(v);
 }
 
-// Y[b][co][y][x] (BF16, channel offset in a wider tensor) = act(G[p][co] +
-// bias[co]); also the FP32 value when yf != NULL (bias NULL: no bias, no
-// activation).  A 32-pixel x 32-channel tile goes through shared memory, so
-// both the reads of G's rows and the writes of the NCHW rows are coalesced.
-__global__ void __launch_bounds__(256) bias_act_kernel(const float* __restrict__ G, int ldg,
-                                                     const float* __restrict__ bias, int B, int Co, int HW, int relu,
-                                                     bf16* __restrict__ y, int y_channels, float* __restrict__ yf) {
-    __shared__ float t[32][33];
-    const int64_t P = (int64_t)B * HW;
-    const int64_t p0 = (int64_t)blockIdx.x * 32;
-    const int c0 = blockIdx.y * 32, lane = threadIdx.x & 31;
-    for (int r = threadIdx.x >> 5; r < 32; r += 8) {
-        const int64_t p = p0 + r;
-        const int c = c0 + lane;
-        float v = 0.0f;
-        if (p < P && c < Co) {
-            v = G[p * ldg + c];
-            if (bias) v = v + bias[c];
-            if (relu) v = fmaxf(v, 0.0f);
+// Transposed column matrix for the weight gradient: colsT[k][p] (row ldp),
+// k = tap C + c, zero for p >= P.  A block takes 64 pixels and 32 channels:
+// it loads the 9 taps' shifted 32-channel pixel rows (64-byte pieces along
+// the NHWC rows) into shared memory as [tap][c][pixel] and writes the 288
+// rows of 64 pixels with 16-byte stores.  C a multiple of 32, ks = 3.
+constexpr int CT_PIX = 64, CT_PITCH = 72;
+
+__global__ void __launch_bounds__(256) im2col_t_kernel(const View X, int C, int B, int H, int W, int ldp,
+                                                       bf16* __restrict__ out) {
+    __shared__ __align__(16) bf16 tile[9 * 32 * CT_PITCH];
+    const int64_t P = (int64_t)B * H * W;
+    const int64_t p0 = (int64_t)blockIdx.x * CT_PIX;
+    const int c0 = blockIdx.y * 32;
+    const int HW = H * W;
+    // loads: 9 taps x 64 pixels x 4 chunks of 8 channels
+    for (int idx = threadIdx.x; idx < 9 * CT_PIX * 4; idx += blockDim.x) {
+        const int tap = idx / (CT_PIX * 4), rem = idx - tap * CT_PIX * 4;
+        const int px = rem >> 2, ch = rem & 3;
+        const int64_t p = p0 + px;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (p < P) {
+            const int b = (int)(p / HW), r = (int)(p % HW), y = r / W, x = r % W;
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                val = *reinterpret_cast<const uint4*>(X.p + (((int64_t)b * H + yy) * W + xx) * X.ld + X.off + c0 +
+                                                      ch * 8);
         }
-        t[r][lane] = v;
+        const bf16* e = reinterpret_cast<const bf16*>(&val);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tile[(tap * 32 + ch * 8 + j) * CT_PITCH + px] = e[j];
     }
     __syncthreads();
-    for (int r = threadIdx.x >> 5; r < 32; r += 8) {
-        const int c = c0 + r;
-        const int64_t p = p0 + lane;
-        if (p < P && c < Co) {
-            const int64_t b = p / HW, yx = p % HW;
-            const float v = t[lane][r];
-            if (y) y[(b * y_channels + c) * HW + yx] = __float2bfloat16_rn(v);
-            if (yf) yf[(b * Co + c) * HW + yx] = v;
-        }
+    for (int idx = threadIdx.x; idx < 9 * 32 * (CT_PIX / 8); idx += blockDim.x) {
+        const int row = idx >> 3, seg = idx & 7;          // row = tap * 32 + c
+        const int tap = row >> 5, c = row & 31;
+        const int64_t k = (int64_t)tap * C + c0 + c;
+        *reinterpret_cast<uint4*>(out + k * ldp + p0 + seg * 8) =
+            *reinterpret_cast<const uint4*>(tile + row * CT_PITCH + seg * 8);
     }
 }
 
-// dZ = dY * (Y > 0) (or dY when relu == 0), as BF16 channel-major rows
-// dz_cp[co][p] (row length ldp; the weight gradient's operand and the data
-// gradient's convolution input) and as FP32 NCHW (the bias gradient).
-__global__ void act_back_kernel(const float* __restrict__ dy, const bf16* __restrict__ y, int y_channels, int B,
-                                int Co, int H, int W, int relu, bf16* __restrict__ dz_cp, int ldp,
-                                float* __restrict__ dz_f) {
-    const int64_t n = (int64_t)B * Co * H * W;
+// The same, element by element, for any C and kernel size.
+__global__ void im2col_t_any_kernel(const View X, int C, int B, int H, int W, int ks, int K9p, int ldp,
+                                    bf16* __restrict__ out) {
+    const int64_t P = (int64_t)B * H * W;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)K9p * ldp) return;
+    const int k = (int)(i / ldp);
+    const int64_t p = i % ldp;
+    bf16 v = __float2bfloat16_rn(0.0f);
+    if (p < P && k < ks * ks * C) {
+        const int HW = H * W;
+        const int b = (int)(p / HW), r = (int)(p % HW), y = r / W, x = r % W;
+        const int tap = k / C, c = k - tap * C, half = ks / 2;
+        const int yy = y + tap / ks - half, xx = x + tap % ks - half;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            const int s = X.up;
+            const int64_t q = ((int64_t)b * H * s + (int64_t)yy * s) * ((int64_t)W * s) + (int64_t)xx * s;
+            v = X.p[q * X.ld + X.off + c];
+        }
+    }
+    out[i] = v;
+}
+
+// Epilogue of the column-matrix path: G[p][c] (row ldg) through epi, one
+// thread per 16 columns of a pixel.
+__global__ void bias_act_kernel(const float* __restrict__ G, int ldg, int64_t P, int N, const ConvEpi epi) {
+    const int chunks = (N + 15) / 16;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * chunks) return;
+    const int64_t p = i / chunks;
+    const int c0 = (int)(i - p * chunks) * 16;
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = c0 + j < N ? G[p * ldg + c0 + j] : 0.0f;
+    epi_store(epi, p, c0, min(16, N - c0), v);
+}
+
+// 2 x 2 average of an NHWC view on the grid H x W into a plain [B][H/2][W/2][C]
+// tensor, one thread per 8 channels of an output pixel: (a + b) + (c + d) in
+// FP32 (exact for BF16 inputs), times 1/4, rounded to BF16.
+__global__ void pool_kernel(const View X, int C, int B, int H, int W, bf16* __restrict__ y) {
+    const int h = H / 2, w = W / 2, cc = C / 8;
+    const int64_t n = (int64_t)B * h * w * cc;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int x = (int)(i % W);
-    const int yy = (int)((i / W) % H);
-    const int co = (int)((i / ((int64_t)W * H)) % Co);
-    const int b = (int)(i / ((int64_t)W * H * Co));
-    float g = dy[i];
-    if (relu) {
-        const float yv = __bfloat162float(y[(((int64_t)b * y_channels + co) * H + yy) * W + x]);
-        if (!(yv > 0.0f)) g = 0.0f;
-    }
-    const int64_t p = ((int64_t)b * H + yy) * W + x;
-    dz_cp[(int64_t)co * ldp + p] = __float2bfloat16_rn(g);
-    dz_f[i] = g;
+    const int64_t q = i / cc;
+    const int c = (int)(i - q * cc) * 8;
+    const int64_t b = q / ((int64_t)h * w);
+    const int r = (int)(q - b * h * w), yy = r / w, xx = r % w;
+    const bf16* s = X.p + ((b * H + 2 * yy) * W + 2 * xx) * X.ld + X.off + c;
+    const int64_t row = (int64_t)W * X.ld;
+    const uint4 a4 = *reinterpret_cast<const uint4*>(s), b4 = *reinterpret_cast<const uint4*>(s + X.ld);
+    const uint4 c4 = *reinterpret_cast<const uint4*>(s + row), d4 = *reinterpret_cast<const uint4*>(s + row + X.ld);
+    const bf16 *pa = reinterpret_cast<const bf16*>(&a4), *pb = reinterpret_cast<const bf16*>(&b4);
+    const bf16 *pc = reinterpret_cast<const bf16*>(&c4), *pd = reinterpret_cast<const bf16*>(&d4);
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        o[j] = __float2bfloat16_rn(0.25f * ((__bfloat162float(pa[j]) + __bfloat162float(pb[j])) +
+                                            (__bfloat162float(pc[j]) + __bfloat162float(pd[j]))));
+    *reinterpret_cast<uint4*>(y + q * C + c) = *reinterpret_cast<const uint4*>(o);
 }
 
-// db[co] = sum over pixels of dZ (FP32) in two ordered stages: block (co,
-// s) reduces the s-th of n_part equal pixel ranges of channel co into
-// part[co][s]; then one thread per channel adds its parts in order.  The
-// partition and both orders are fixed, so the sum is bit-reproducible.
-__global__ void bias_grad_part_kernel(const float* __restrict__ dz, int B, int Co, int HW, int n_part,
-                                      float* __restrict__ part) {
-    const int co = blockIdx.x, sp = blockIdx.y;
-    const int64_t n = (int64_t)B * HW;
-    const int64_t per = (n + n_part - 1) / n_part;
-    const int64_t i0 = (int64_t)sp * per, i1 = min(n, i0 + per);
-    float s = 0.0f;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const int64_t b = i / HW, r = i % HW;
-        s += dz[(b * Co + co) * HW + r];
+// dZ = dY * (Y > 0) (or dY when relu == 0) for a block of 64 pixels and all
+// Co channels: BF16 NHWC dz16[p][c] (the data gradient's convolution input),
+// BF16 channel-major dz_cp[c][p] (row ldp; the weight gradient's operand,
+// zero for P <= p < ldp) through a shared-memory transpose, and the block's
+// FP32 bias-gradient part part[block][c] (its 64 pixels added in order).
+__global__ void __launch_bounds__(256) act_back_kernel(const float* __restrict__ dy, const View Y, int H, int W,
+                                                       int64_t P, int Co, int relu, bf16* __restrict__ dz16,
+                                                       bf16* __restrict__ dz_cp, int ldp, float* __restrict__ part) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    float* sf = reinterpret_cast<float*>(sm);                          // [64][Co + 1]
+    bf16* sb = reinterpret_cast<bf16*>(sm + (size_t)64 * (Co + 1) * 4); // [Co][72]
+    const int64_t p0 = (int64_t)blockIdx.x * 64;
+    for (int i = threadIdx.x; i < 64 * Co; i += blockDim.x) {
+        const int px = i / Co, c = i - px * Co;
+        const int64_t p = p0 + px;
+        float g = 0.0f;
+        if (p < P) {
+            g = dy[p * Co + c];
+            if (relu) {
+                const float yv = __bfloat162float(Y.p[view_pixel(Y, p, H, W) * Y.ld + Y.off + c]);
+                if (!(yv > 0.0f)) g = 0.0f;
+            }
+            dz16[p * Co + c] = __float2bfloat16_rn(g);
+        }
+        sf[px * (Co + 1) + c] = g;
+        sb[c * CT_PITCH + px] = __float2bfloat16_rn(g);
     }
-    __shared__ float red[TB];
-    red[threadIdx.x] = s;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    for (int c = threadIdx.x; c < Co; c += blockDim.x) {
+        float s = 0.0f;
+        for (int px = 0; px < 64; ++px) s += sf[px * (Co + 1) + c];
+        part[(int64_t)blockIdx.x * Co + c] = s;
+    }
+    for (int i = threadIdx.x; i < Co * 8; i += blockDim.x) {
+        const int c = i >> 3, seg = i & 7;
+        if (p0 + seg * 8 < ldp)
+            *reinterpret_cast<uint4*>(dz_cp + (int64_t)c * ldp + p0 + seg * 8) =
+                *reinterpret_cast<const uint4*>(sb + c * CT_PITCH + seg * 8);
+    }
+}
+
+// out[c] = sum over k of part[k][c], k = 0, 1, ... in order
+__global__ void parts_sum_kernel(const float* __restrict__ part, int n_part, int Co, float* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Co) return;
+    float s = 0.0f;
+    for (int k = 0; k < n_part; ++k) s += part[(int64_t)k * Co + c];
+    out[c] = s;
+}
+
+// Gradient of the upsampled part of a decoder input: g[b][y][x][c] = the sum
+// over the 2 x 2 block of dcat[b][2y + i][2x + j][c] (row pitch ldc; order
+// (0,0), (0,1), (1,0), (1,1)), c < C, on the low grid h x w.
+__global__ void place_back_kernel(const float* __restrict__ dcat, int ldc, int B, int C, int h, int w,
+                                  float* __restrict__ g) {
+    const int64_t n = (int64_t)B * h * w * C;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t q = i / C;
+    const int c = (int)(i - q * C);
+    const int64_t b = q / ((int64_t)h * w);
+    const int r = (int)(q - b * h * w), y = r / w, x = r % w;
+    const int W = 2 * w;
+    const float* d = dcat + ((b * 2 * h + 2 * y) * W + 2 * x) * ldc + c;
+    float acc = 0.0f;
+    acc += d[0];
+    acc += d[ldc];
+    acc += d[(int64_t)W * ldc];
+    acc += d[(int64_t)W * ldc + ldc];
+    g[i] = acc;
+}
+
+// Gradient of an encoder output that feeds both a skip and a pool:
+// g[b][y][x][c] = dcat[b][y][x][off + c] (row pitch ldc) + dp[b][y/2][x/2][c] / 4.
+__global__ void pool_back_kernel(const float* __restrict__ dcat, int ldc, int off, const float* __restrict__ dp, int B,
+                                 int C, int H, int W, float* __restrict__ g) {
+    const int64_t n = (int64_t)B * H * W * C;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t q = i / C;
+    const int c = (int)(i - q * C);
+    const int64_t b = q / ((int64_t)H * W);
+    const int r = (int)(q - b * H * W), y = r / W, x = r % W;
+    const float skip = dcat[q * ldc + off + c];
+    g[i] = skip + 0.25f * dp[((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+}
+
+// The 1 x 1 output layer with the residual: out[p] = (sum over c of w[c]
+// d1[p][c] + bias) + x[b][0][y][x].
+__global__ void head_kernel(const bf16* __restrict__ d1, int C, const bf16* __restrict__ w, const float* __restrict__ bias,
+                            const float* __restrict__ x, int64_t P, int HW, float* __restrict__ out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float acc = 0.0f;
+    for (int c = 0; c < C; ++c) acc += __bfloat162float(w[c]) * __bfloat162float(d1[p * C + c]);
+    out[p] = (acc + bias[0]) + x[(p / HW) * 2 * HW + p % HW];
+}
+
+// Backward of the 1 x 1 layer for a block of 256 pixels: with g = dL/dout
+// and gr = BF16(g), the input gradient gd1[p][c] = gr[p] w[c], and the
+// block's parts of the weight gradient (sum of gr[p] d1[p][c]) and of the
+// bias gradient (sum of g[p]), each added over the block's pixels in order.
+__global__ void __launch_bounds__(256) head_back_kernel(const float* __restrict__ g, const bf16* __restrict__ d1, int C,
+                                                        const bf16* __restrict__ w, int64_t P, float* __restrict__ gd1,
+                                                        float* __restrict__ part_w, float* __restrict__ part_b) {
+    __shared__ float sw[256][33];
+    __shared__ float sg[256];
+    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    float gv = 0.0f;
+    if (p < P) gv = g[p];
+    sg[threadIdx.x] = gv;
+    const float gr = __bfloat162float(__float2bfloat16_rn(gv));
+    for (int c0 = 0; c0 < C; c0 += 32) {
+        const int nc = min(32, C - c0);
+        for (int j = 0; j < nc; ++j) {
+            const float xv = p < P ? __bfloat162float(d1[p * C + c0 + j]) : 0.0f;
+            sw[threadIdx.x][j] = gr * xv;
+            if (p < P) gd1[p * C + c0 + j] = gr * __bfloat162float(w[c0 + j]);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < nc) {
+            float s = 0.0f;
+            for (int k = 0; k < 256; ++k) s += sw[k][threadIdx.x];
+            part_w[(int64_t)blockIdx.x * C + c0 + threadIdx.x] = s;
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[(int64_t)co * n_part + sp] = red[0];
-}
-
-__global__ void bias_grad_sum_kernel(const float* __restrict__ part, int Co, int n_part, float* __restrict__ db) {
-    const int co = blockIdx.x * blockDim.x + threadIdx.x;
-    if (co >= Co) return;
-    float s = 0.0f;
-    for (int k = 0; k < n_part; ++k) s += part[(int64_t)co * n_part + k];
-    db[co] = s;
-}
-
-__global__ void pool_kernel(const bf16* __restrict__ x, int B, int C, int H, int W, bf16* __restrict__ y) {
-    const int h = H / 2, w = W / 2;
-    const int64_t n = (int64_t)B * C * h * w;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int xx = (int)(i % w), yy = (int)((i / w) % h);
-    const int64_t bc = i / ((int64_t)w * h);
-    const bf16* s = x + bc * H * W + (int64_t)(2 * yy) * W + 2 * xx;
-    const float v = 0.25f * ((__bfloat162float(s[0]) + __bfloat162float(s[1])) +
-                             (__bfloat162float(s[W]) + __bfloat162float(s[W + 1])));
-    y[i] = __float2bfloat16_rn(v);
-}
-
-// dX += up(dY) / 4 (adjoint of the 2 x 2 average)
-__global__ void pool_back_kernel(const float* __restrict__ dy, int B, int C, int H, int W, float* __restrict__ dx) {
-    const int64_t n = (int64_t)B * C * H * W;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int x = (int)(i % W), y = (int)((i / W) % H);
-    const int64_t bc = i / ((int64_t)W * H);
-    dx[i] += 0.25f * dy[bc * (H / 2) * (W / 2) + (int64_t)(y / 2) * (W / 2) + x / 2];
-}
-
-// gradient of a channel range of a concatenated input: dsrc[b][c][y][x] (+)=
-// the sum over the s x s block of dcat[b][off + c] (s = 2: nearest upsampling)
-__global__ void place_back_kernel(const float* __restrict__ dcat, int cat_channels, int off, int B, int C, int h,
-                                  int w, int s, int accumulate, float* __restrict__ dsrc) {
-    const int64_t n = (int64_t)B * C * h * w;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int x = (int)(i % w), y = (int)((i / w) % h);
-    const int c = (int)((i / ((int64_t)w * h)) % C);
-    const int b = (int)(i / ((int64_t)w * h * C));
-    const int H = h * s, W = w * s;
-    const float* d = dcat + (((int64_t)b * cat_channels + off + c) * H + y * s) * W + x * s;
-    float acc = 0.0f;
-    for (int dy = 0; dy < s; ++dy)
-        for (int dx = 0; dx < s; ++dx) acc += d[(int64_t)dy * W + dx];
-    if (accumulate) dsrc[i] += acc; else dsrc[i] = acc;
-}
-
-// out[b][0][y][x] += in[b][0][y][x] (in has two channels)
-__global__ void residual_kernel(const float* __restrict__ in, int B, int HW, float* __restrict__ out) {
-    const int64_t n = (int64_t)B * HW;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] += in[(i / HW) * 2 * HW + i % HW];
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int k = 0; k < 256; ++k) s += sg[k];
+        part_b[blockIdx.x] = s;
+    }
 }
 
 __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, int64_t n, float* __restrict__ dy,
@@ -382,11 +394,12 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// BF16 copies of a conv's weights w[co][ci][tap] (tap = ky ks + kx):
-// w16[co][k] (row K9p) for the forward, and wf16[ci][co kk + t] = w[co][ci][kk -
-// 1 - t] (row K9dp), the weights with the taps flipped for the data gradient
-// (a convolution of dZ: dX(y, x) = sum over co, ky, kx of dZ(y + ky - h,
-// x + kx - h) w[co][ci][ks - 1 - ky][ks - 1 - kx]).
+// BF16 copies of a conv's weights w[co][ci][tap] (tap = ky ks + kx) in the
+// products' K order (tap-major): w16[co][tap Ci + ci] (row K9p) for the
+// forward, and wf16[ci][tap Co + co] = w[co][ci][kk - 1 - tap] (row K9dp),
+// the weights with the taps flipped for the data gradient (a convolution of
+// dZ: dX(y, x) = sum over co, ky, kx of dZ(y + ky - h, x + kx - h)
+// w[co][ci][ks - 1 - ky][ks - 1 - kx]); zero beyond the K extent.
 __global__ void weight_copies_kernel(const float* __restrict__ w, int Co, int Ci, int kk, int K9p, int K9dp,
                                      bf16* __restrict__ w16, bf16* __restrict__ wf16) {
     const int K9 = Ci * kk;
@@ -394,75 +407,32 @@ __global__ void weight_copies_kernel(const float* __restrict__ w, int Co, int Ci
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n1) {
         const int co = (int)(i / K9p), k = (int)(i % K9p);
-        w16[i] = __float2bfloat16_rn(k < K9 ? w[(int64_t)co * K9 + k] : 0.0f);
+        float v = 0.0f;
+        if (k < K9) {
+            const int tap = k / Ci, ci = k - tap * Ci;
+            v = w[(int64_t)co * K9 + (int64_t)ci * kk + tap];
+        }
+        w16[i] = __float2bfloat16_rn(v);
     }
     if (i < n2) {
         const int ci = (int)(i / K9dp), k = (int)(i % K9dp);
         float v = 0.0f;
         if (k < Co * kk) {
-            const int co = k / kk, t = k % kk;
-            v = w[(int64_t)co * K9 + (int64_t)ci * kk + (kk - 1 - t)];
+            const int tap = k / Co, co = k - tap * Co;
+            v = w[(int64_t)co * K9 + (int64_t)ci * kk + (kk - 1 - tap)];
         }
         wf16[i] = __float2bfloat16_rn(v);
     }
 }
 
-// dW[co][k] for k < K9 from the padded GEMM output (row K9p)
-__global__ void unpad_kernel(const float* __restrict__ src, int rows, int cols, int ld, float* __restrict__ dst) {
-    const int64_t n = (int64_t)rows * cols;
+// dW[co][ci][tap] from the weight-gradient product G[co][tap Ci + ci] (row ld)
+__global__ void unpad_kernel(const float* __restrict__ G, int Co, int Ci, int kk, int ld, float* __restrict__ dw) {
+    const int64_t n = (int64_t)Co * Ci * kk;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[(i / cols) * ld + i % cols];
-}
-
-// colsT for widths that are multiples of 8: a thread's 8 pixels are one row
-// segment, read through one source row pointer.
-template <int KS, int UP>
-__global__ void __launch_bounds__(256) im2col_cols_w8_kernel(const Src S, int B, int K9p, int ldp,
-                                                           bf16* __restrict__ out) {
-    const int64_t P = (int64_t)B * S.H * S.W;
-    const int64_t groups = ldp / 8;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= groups * K9p) return;
-    const int k = (int)(i / groups);
-    const int64_t p0 = (i - (int64_t)k * groups) * 8;
-    constexpr int kk = KS * KS, half = KS / 2;
-    const int HW = S.H * S.W;
-    __align__(16) bf16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn(0.0f);
-    if (k < S.C * kk && p0 < P) {
-        const int ci = k / kk, r = k - ci * kk, ky = r / KS, kx = r - ky * KS;
-        const int b = (int)(p0 / HW), yx = (int)(p0 % HW), y = yx / S.W, x = yx % S.W;
-        const int yy = y + ky - half;
-        if (yy >= 0 && yy < S.H) {
-            const bf16* row;
-            if (ci < S.Ca) row = S.a + (int64_t)b * S.a_bs + (int64_t)ci * S.a_cs + (int64_t)(yy / UP) * (S.W / UP);
-            else row = S.s + (int64_t)b * S.s_bs + (int64_t)(ci - S.Ca) * S.s_cs + (int64_t)yy * S.W;
-            const int up = ci < S.Ca ? UP : 1;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int xx = x + j + kx - half;
-                if (xx >= 0 && xx < S.W) v[j] = row[up == 2 ? (xx >> 1) : xx];
-            }
-        }
-    }
-    *reinterpret_cast<uint4*>(out + (int64_t)k * ldp + p0) = *reinterpret_cast<const uint4*>(v);
-}
-
-struct Conv {
-    int ci, co, ks, H, W, relu;
-    int K9, K9p, K9dp;     // ci ks^2, padded to 64; co ks^2 padded to 64 (data gradient)
-    // parameters (FP32 master), gradients, Adam moments; offsets into the flat arrays
-    int64_t w_off, b_off;
-    bf16* w16 = nullptr;   // [co][K9p]
-    bf16* wf16 = nullptr;  // [ci][K9dp], taps flipped
-};
-
-// K splits of a weight-gradient product over P pixels (a function of P alone,
-// so the workspace for the largest batch bounds every call).
-int wgrad_splits(int64_t P) {
-    const int Pp = pad64(P);
-    return std::max(1, std::min(Pp / 64, (int)(P / 4096) + 1));
+    if (i >= n) return;
+    const int co = (int)(i / ((int64_t)Ci * kk));
+    const int r = (int)(i - (int64_t)co * Ci * kk), ci = r / kk, tap = r - ci * kk;
+    dw[i] = G[(int64_t)co * ld + tap * Ci + ci];
 }
 
 // out[i] = sum over z of p[z * stride + i], in the order z = 0, 1, ...
@@ -472,6 +442,22 @@ __global__ void splits_sum_kernel(const float* __restrict__ p, int n_splits, int
     float s = 0.0f;
     for (int z = 0; z < n_splits; ++z) s += p[(int64_t)z * stride + i];
     out[i] = s;
+}
+
+struct Conv {
+    int ci, co, ks, H, W, relu;
+    int K9, K9p, K9dp;     // ci ks^2, padded to 64; co ks^2 padded to 64 (data gradient)
+    // parameters (FP32 master), gradients, Adam moments; offsets into the flat arrays
+    int64_t w_off, b_off;
+    bf16* w16 = nullptr;   // [co][K9p], K = (tap, ci)
+    bf16* wf16 = nullptr;  // [ci][K9dp], K = (tap, co), taps flipped
+};
+
+// K splits of a weight-gradient product over P pixels (a function of P alone,
+// so the workspace for the largest batch bounds every call).
+int wgrad_splits(int64_t P) {
+    const int Pp = pad64(P);
+    return std::max(1, std::min(Pp / 64, (int)(P / 4096) + 1));
 }
 
 }  // namespace
@@ -489,21 +475,21 @@ struct gdrr_cnn {
     float* adam_m = nullptr;
     float* adam_v = nullptr;
     int adam_t = 0;
-    // activations (BF16) for the last forward
-    bf16 *x16 = nullptr, *e1 = nullptr, *e2 = nullptr, *e3 = nullptr, *e4 = nullptr;
-    bf16 *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
-    bf16 *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;
+    // activations (BF16 NHWC) of the last forward
+    bf16 *x16 = nullptr, *cat1 = nullptr, *cat2 = nullptr, *cat3 = nullptr;
+    bf16 *p1 = nullptr, *p2 = nullptr, *p3 = nullptr, *d1 = nullptr;
     float* out = nullptr;
-    // gradients of activations (FP32)
-    float *g_out = nullptr, *g_d1 = nullptr, *g_c1 = nullptr, *g_d2 = nullptr, *g_c2 = nullptr, *g_d3 = nullptr;
-    float *g_c3 = nullptr, *g_e4 = nullptr, *g_p3 = nullptr, *g_e3 = nullptr, *g_p2 = nullptr, *g_e2 = nullptr;
-    float *g_p1 = nullptr, *g_e1 = nullptr, *g_x = nullptr;
+    // gradients (FP32 NHWC)
+    float *g_out = nullptr, *g_d1 = nullptr, *g_cat1 = nullptr, *g_d2 = nullptr, *g_cat2 = nullptr;
+    float *g_d3 = nullptr, *g_cat3 = nullptr, *g_e4 = nullptr, *g_p3 = nullptr, *g_e3 = nullptr, *g_p2 = nullptr;
+    float *g_e2 = nullptr, *g_p1 = nullptr, *g_e1 = nullptr;
     // workspaces
-    bf16* cols = nullptr;      // im2col, either layout
-    float* gemm = nullptr;     // GEMM output
+    bf16* cols = nullptr;      // column matrix, either layout
+    float* gemm = nullptr;     // column-path GEMM output
     float* partials = nullptr; // per-split partial products of the weight gradients; bias-gradient parts
-    bf16* dz_cp = nullptr;
-    float* dz_f = nullptr;
+    bf16* dz16 = nullptr;      // dZ, NHWC
+    bf16* dz_cp = nullptr;     // dZ, channel-major
+    double* dloss = nullptr;
     int* err = nullptr;
     int last_batch = 0;
     std::vector<void*> allocs;
@@ -553,135 +539,91 @@ cudaError_t refresh_weights(gdrr_cnn* n) {
     return cudaSuccess;
 }
 
-// A tensor [B][C][H][W] (NCHW) as a convolution input.
-Src nchw(const bf16* t, int C, int H, int W) {
-    Src S;
-    memset(&S, 0, sizeof S);
-    S.up = 1;
-    S.s = t;
-    S.s_bs = (int64_t)C * H * W;
-    S.s_cs = (int64_t)H * W;
-    S.C = C; S.H = H; S.W = W;
-    return S;
+ConvEpi epi_bf16(const float* bias, int relu, bf16* y, int ldy, int off, int up, int H, int W) {
+    ConvEpi e;
+    memset(&e, 0, sizeof e);
+    e.bias = bias; e.relu = relu; e.y16 = y; e.ldy = ldy; e.off = off; e.up = up; e.H = H; e.W = W;
+    return e;
 }
 
-// [up(a), s]: a with Ca channels at H/2 x W/2, upsampled, then s (Cs channels).
-Src concat_up(const bf16* a, int Ca, const bf16* s, int Cs, int H, int W) {
-    Src S = nchw(s, Cs, H, W);
-    S.a = a;
-    S.Ca = Ca;
-    S.up = 2;
-    S.a_bs = (int64_t)Ca * (H / 2) * (W / 2);
-    S.a_cs = (int64_t)(H / 2) * (W / 2);
-    S.C = Ca + Cs;
-    return S;
+ConvEpi epi_f32(float* y, int ld, int H, int W) {
+    ConvEpi e;
+    memset(&e, 0, sizeof e);
+    e.yf = y; e.ldf = ld; e.up = 1; e.H = H; e.W = W;
+    return e;
 }
 
-// Channel-major rows t[c][p] (row length ldp, p = b H W + y W + x) as a
-// convolution input.
-Src chan_major(const bf16* t, int C, int H, int W, int64_t ldp) {
-    Src S = nchw(t, C, H, W);
-    S.s_bs = (int64_t)H * W;
-    S.s_cs = ldp;
-    return S;
-}
-
-cudaError_t im2col_rows(gdrr_cnn* n, const Src& X, int B, int ks, int K9p) {
-    const int64_t P = (int64_t)B * X.H * X.W;
-    const dim3 grid((unsigned)((P + I2C_PIX - 1) / I2C_PIX), (unsigned)(K9p / I2C_K));
-    const size_t seg_bytes = (size_t)32 * (K9p + 8) * sizeof(bf16);
-    if (X.W % 32 == 0 && ks == 3 && seg_bytes <= 200 * 1024) {
-        const unsigned blocks = (unsigned)(P / 32);
-        if (X.up == 2) {
-            CK(cudaFuncSetAttribute(im2col_rows_shfl_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)seg_bytes));
-            im2col_rows_shfl_kernel<2><<<blocks, 256, seg_bytes, n->stream>>>(X, K9p, n->cols);
-        } else {
-            CK(cudaFuncSetAttribute(im2col_rows_shfl_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)seg_bytes));
-            im2col_rows_shfl_kernel<1><<<blocks, 256, seg_bytes, n->stream>>>(X, K9p, n->cols);
-        }
-    } else if (ks == 1) {
-        im2col_rows_kernel<1, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
-    } else if (X.up == 2) {
-        im2col_rows_kernel<3, 2><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
-    } else {
-        im2col_rows_kernel<3, 1><<<grid, 256, 0, n->stream>>>(X, B, K9p, n->cols);
+// One convolution on the grid H x W of the plain NHWC input X (C channels)
+// with weights w (row ldw, K = (tap, c)) into N output columns through epi:
+// the implicit GEMM where the grid tiles, else a column matrix (row K9p), the
+// column-path GEMM into n->gemm and the elementwise epilogue.
+cudaError_t conv_product(gdrr_cnn* n, const View& X, int C, int B, int H, int W, int ks, const bf16* w, int ldw, int N,
+                         const ConvEpi& epi) {
+    const int64_t P = (int64_t)B * H * W;
+    if (X.up == 1 && conv_implicit_ok(C, H, W, ks) && X.ld % 8 == 0 && X.off % 8 == 0) {
+        ConvArgs a;
+        a.x = X.p + X.off; a.C = C; a.ldx = X.ld;
+        a.B = B; a.H = H; a.W = W; a.ks = ks;
+        a.w = w; a.ldw = ldw; a.N = N;
+        a.epi = epi;
+        return launch_conv_implicit(a, n->err, n->stream);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t im2col_cols(gdrr_cnn* n, const Src& X, int B, int ks, int K9p, int ldp) {
-    const int blocks = nblk((int64_t)(ldp / 8) * K9p);
-    if (X.W % 8 == 0 && ks == 3) {
-        if (X.up == 2) im2col_cols_w8_kernel<3, 2><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
-        else im2col_cols_w8_kernel<3, 1><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
-        return cudaGetLastError();
+    const int K9p = pad64((int64_t)ks * ks * C);
+    im2col_nhwc_kernel<<<nblk(P * (K9p / 8)), TB, 0, n->stream>>>(X, C, B, H, W, ks, K9p, n->cols);
+    CK(cudaGetLastError());
+    if (epi.yf && !epi.bias && epi.ldf >= N && !epi.y16) {
+        // FP32 output without bias: the GEMM writes it in place
+        return launch_gemm_bf16(n->cols, K9p, w, ldw, epi.yf, epi.ldf, (int)P, N, K9p, 1, n->err, n->stream);
     }
-    if (ks == 1) im2col_cols_kernel<1, 1><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
-    else if (X.up == 2) im2col_cols_kernel<3, 2><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
-    else im2col_cols_kernel<3, 1><<<blocks, TB, 0, n->stream>>>(X, B, K9p, ldp, n->cols);
+    CK(launch_gemm_bf16(n->cols, K9p, w, ldw, n->gemm, N, (int)P, N, K9p, 1, n->err, n->stream));
+    bias_act_kernel<<<nblk(P * ((N + 15) / 16)), TB, 0, n->stream>>>(n->gemm, N, P, N, epi);
     return cudaGetLastError();
 }
 
-// Y = act(conv(X) + bias): BF16 y (channel count y_channels, written at
-// channels 0 .. co-1) and/or FP32 yf.
-cudaError_t conv_forward(gdrr_cnn* n, const Conv& L, int B, const Src& X, bf16* y, int y_channels, float* yf) {
-    const int64_t P = (int64_t)B * L.H * L.W;
-    CK(im2col_rows(n, X, B, L.ks, L.K9p));
-    CK(launch_gemm_bf16(n->cols, L.K9p, L.w16, L.K9p, n->gemm, L.co, (int)P, L.co, L.K9p, 1, n->err, n->stream));
-    const dim3 grid((unsigned)((P + 31) / 32), (unsigned)((L.co + 31) / 32));
-    bias_act_kernel<<<grid, 256, 0, n->stream>>>(n->gemm, L.co, n->params + L.b_off, B, L.co, L.H * L.W, L.relu, y,
-                                                 y_channels, yf);
-    return cudaGetLastError();
-}
-
-int bias_parts(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 8191) / 8192)); }
-
-// Backward of one convolution: dy (FP32 [B][co][H][W], gradient of the
-// layer output), y (its BF16 output, for the ReLU mask), X (its input).
-// Writes the parameter gradients and, when dx != NULL, dx (FP32 NCHW input
-// gradient).
-cudaError_t conv_backward(gdrr_cnn* n, const Conv& L, int B, const float* dy, const bf16* y, int y_channels,
-                          const Src& X, float* dx) {
+// Backward of one 3 x 3 convolution L on the grid H x W: dy (FP32 [P][co],
+// gradient of the layer output), Y (view of its BF16 output, for the ReLU
+// mask), X (its plain NHWC input, ci channels).  Writes the parameter
+// gradients and, when dx != NULL, dx (FP32 [P][ci]).
+cudaError_t conv_backward(gdrr_cnn* n, const Conv& L, int B, const float* dy, const View& Y, const View& X,
+                          float* dx) {
     const int64_t P = (int64_t)B * L.H * L.W;
     const int Pp = pad64(P);
-    const int HW = L.H * L.W;
-    CK(cudaMemsetAsync(n->dz_cp, 0, (size_t)L.co * Pp * sizeof(bf16), n->stream));
-    act_back_kernel<<<nblk(P * L.co), TB, 0, n->stream>>>(dy, y, y_channels, B, L.co, L.H, L.W, L.relu, n->dz_cp, Pp,
-                                                          n->dz_f);
+    cudaStream_t st = n->stream;
+    const int n_blk = (int)((P + 63) / 64);
+    const size_t smem = (size_t)64 * (L.co + 1) * 4 + (size_t)L.co * CT_PITCH * 2;
+    CK(cudaFuncSetAttribute(act_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    act_back_kernel<<<n_blk, TB, smem, st>>>(dy, Y, L.H, L.W, P, L.co, L.relu, n->dz16, n->dz_cp, Pp, n->partials);
     CK(cudaGetLastError());
-    const int parts = bias_parts(P);
-    bias_grad_part_kernel<<<dim3((unsigned)L.co, (unsigned)parts), TB, 0, n->stream>>>(n->dz_f, B, L.co, HW, parts,
-                                                                                       n->partials);
-    bias_grad_sum_kernel<<<(L.co + 127) / 128, 128, 0, n->stream>>>(n->partials, L.co, parts, n->grads + L.b_off);
+    parts_sum_kernel<<<(L.co + 127) / 128, 128, 0, st>>>(n->partials, n_blk, L.co, n->grads + L.b_off);
     CK(cudaGetLastError());
     // weight gradient: dW[co][k] = sum_p dZ[p][co] cols[p][k]
-    CK(im2col_cols(n, X, B, L.ks, L.K9p, Pp));
+    if (L.ci % 32 == 0 && L.ks == 3 && X.up == 1 && X.ld % 8 == 0 && X.off % 8 == 0) {
+        im2col_t_kernel<<<dim3((unsigned)(Pp / CT_PIX), (unsigned)(L.ci / 32)), TB, 0, st>>>(X, L.ci, B, L.H, L.W, Pp,
+                                                                                            n->cols);
+    } else {
+        im2col_t_any_kernel<<<nblk((int64_t)L.K9p * Pp), TB, 0, st>>>(X, L.ci, B, L.H, L.W, L.ks, L.K9p, Pp, n->cols);
+    }
+    CK(cudaGetLastError());
     // the pixel sum is split across CTAs; each split writes its own partial
     // product and one ordered pass adds them, so training is bit-reproducible
     const int splits = wgrad_splits(P);
     if (splits > 1) {
         const int64_t slice = (int64_t)L.co * L.K9p;
         int used = 1;
-        CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->partials, L.K9p, L.co, L.K9p, Pp, splits, n->err, n->stream,
-                            slice, &used));
-        splits_sum_kernel<<<nblk(slice), TB, 0, n->stream>>>(n->partials, used, slice, n->gemm);
+        CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->partials, L.K9p, L.co, L.K9p, Pp, splits, n->err, st, slice,
+                            &used));
+        splits_sum_kernel<<<nblk(slice), TB, 0, st>>>(n->partials, used, slice, n->gemm);
         CK(cudaGetLastError());
     } else {
-        CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->gemm, L.K9p, L.co, L.K9p, Pp, 1, n->err, n->stream));
+        CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->gemm, L.K9p, L.co, L.K9p, Pp, 1, n->err, st));
     }
-    unpad_kernel<<<nblk((int64_t)L.co * L.K9), TB, 0, n->stream>>>(n->gemm, L.co, L.K9, L.K9p, n->grads + L.w_off);
+    unpad_kernel<<<nblk((int64_t)L.co * L.K9), TB, 0, st>>>(n->gemm, L.co, L.ci, L.ks * L.ks, L.K9p,
+                                                            n->grads + L.w_off);
     CK(cudaGetLastError());
     if (dx) {
-        // data gradient: the convolution of dZ with the flipped weights,
-        // dX[p][ci] = sum_k cols(dZ)[p][k] Wf[ci][k], then to NCHW
-        CK(im2col_rows(n, chan_major(n->dz_cp, L.co, L.H, L.W, Pp), B, L.ks, L.K9dp));
-        CK(launch_gemm_bf16(n->cols, L.K9dp, L.wf16, L.K9dp, n->gemm, L.ci, (int)P, L.ci, L.K9dp, 1, n->err,
-                            n->stream));
-        const dim3 grid((unsigned)((P + 31) / 32), (unsigned)((L.ci + 31) / 32));
-        bias_act_kernel<<<grid, 256, 0, n->stream>>>(n->gemm, L.ci, nullptr, B, L.ci, HW, 0, nullptr, 0, dx);
-        CK(cudaGetLastError());
+        // data gradient: the convolution of dZ with the flipped weights
+        CK(conv_product(n, plain(n->dz16, L.co), L.co, B, L.H, L.W, L.ks, L.wf16, L.K9dp, L.ci,
+                        epi_f32(dx, L.ci, L.H, L.W)));
     }
     return cudaSuccess;
 }
@@ -693,7 +635,7 @@ extern "C" {
 GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, int32_t base_channels, uint64_t seed,
                              void* cuda_stream, gdrr_cnn** out) {
     if (!out || max_batch <= 0 || height <= 0 || width <= 0 || height % 8 || width % 8 || base_channels <= 0 ||
-        base_channels > 64)
+        base_channels > 64 || base_channels % 8)
         return GDRR_ERR_INVALID_ARG;
     gdrr_cnn* n = new (std::nothrow) gdrr_cnn();
     if (!n) return GDRR_ERR_OOM;
@@ -729,7 +671,8 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
         max_cols = std::max({max_cols, Pp * L.K9p, P * L.K9dp});
         max_gemm = std::max({max_gemm, P * L.ci, (int64_t)L.co * L.K9p, P * L.co});
         max_dz = std::max({max_dz, P * L.co, (int64_t)L.co * Pp});
-        max_part = std::max({max_part, (int64_t)wgrad_splits(P) * L.co * L.K9p, (int64_t)L.co * bias_parts(P)});
+        max_part = std::max({max_part, (int64_t)wgrad_splits(P) * L.co * L.K9p, (Pp / 64) * L.co,
+                             (Pp / 256 + 1) * (L.ci + 1)});
     }
     cudaError_t e = cudaSuccess;
     do {
@@ -742,24 +685,22 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
         }
         if (bad) { e = cudaErrorMemoryAllocation; break; }
         const int64_t s1 = B * HW, s2 = s1 / 4, s3 = s1 / 16, s4 = s1 / 64;
-        if ((e = dalloc(n, &n->x16, 2 * s1)) || (e = dalloc(n, &n->e1, c * s1)) || (e = dalloc(n, &n->p1, c * s2)) ||
-            (e = dalloc(n, &n->e2, 2 * c * s2)) || (e = dalloc(n, &n->p2, 2 * c * s3)) ||
-            (e = dalloc(n, &n->e3, 4 * c * s3)) || (e = dalloc(n, &n->p3, 4 * c * s4)) ||
-            (e = dalloc(n, &n->e4, 8 * c * s4)) || (e = dalloc(n, &n->d3, 4 * c * s3)) ||
-            (e = dalloc(n, &n->d2, 2 * c * s2)) || (e = dalloc(n, &n->d1, c * s1)) || (e = dalloc(n, &n->out, s1)))
+        if ((e = dalloc(n, &n->x16, 2 * s1)) || (e = dalloc(n, &n->cat1, 3 * c * s1)) ||
+            (e = dalloc(n, &n->p1, c * s2)) || (e = dalloc(n, &n->cat2, 6 * c * s2)) ||
+            (e = dalloc(n, &n->p2, 2 * c * s3)) || (e = dalloc(n, &n->cat3, 12 * c * s3)) ||
+            (e = dalloc(n, &n->p3, 4 * c * s4)) || (e = dalloc(n, &n->d1, c * s1)) || (e = dalloc(n, &n->out, s1)))
             break;
-        if ((e = dalloc(n, &n->g_out, s1)) || (e = dalloc(n, &n->g_d1, c * s1)) || (e = dalloc(n, &n->g_c1, 3 * c * s1)) ||
-            (e = dalloc(n, &n->g_d2, 2 * c * s2)) || (e = dalloc(n, &n->g_c2, 6 * c * s2)) ||
-            (e = dalloc(n, &n->g_d3, 4 * c * s3)) || (e = dalloc(n, &n->g_c3, 12 * c * s3)) ||
-            (e = dalloc(n, &n->g_e4, 8 * c * s4)) || (e = dalloc(n, &n->g_p3, 4 * c * s4)) ||
-            (e = dalloc(n, &n->g_e3, 4 * c * s3)) || (e = dalloc(n, &n->g_p2, 2 * c * s3)) ||
-            (e = dalloc(n, &n->g_e2, 2 * c * s2)) || (e = dalloc(n, &n->g_p1, c * s2)) ||
-            (e = dalloc(n, &n->g_e1, c * s1)) || (e = dalloc(n, &n->g_x, 2 * s1)))
+        if ((e = dalloc(n, &n->g_out, s1)) || (e = dalloc(n, &n->g_d1, c * s1)) ||
+            (e = dalloc(n, &n->g_cat1, 3 * c * s1)) || (e = dalloc(n, &n->g_d2, 2 * c * s2)) ||
+            (e = dalloc(n, &n->g_cat2, 6 * c * s2)) || (e = dalloc(n, &n->g_d3, 4 * c * s3)) ||
+            (e = dalloc(n, &n->g_cat3, 12 * c * s3)) || (e = dalloc(n, &n->g_e4, 8 * c * s4)) ||
+            (e = dalloc(n, &n->g_p3, 4 * c * s4)) || (e = dalloc(n, &n->g_e3, 4 * c * s3)) ||
+            (e = dalloc(n, &n->g_p2, 2 * c * s3)) || (e = dalloc(n, &n->g_e2, 2 * c * s2)) ||
+            (e = dalloc(n, &n->g_p1, c * s2)) || (e = dalloc(n, &n->g_e1, c * s1)))
             break;
         if ((e = dalloc(n, &n->cols, max_cols)) || (e = dalloc(n, &n->gemm, max_gemm)) ||
-            (e = dalloc(n, &n->dz_cp, max_dz)) ||
-            (e = dalloc(n, &n->dz_f, max_dz)) || (e = dalloc(n, &n->partials, max_part)) ||
-            (e = dalloc(n, &n->err, 1)))
+            (e = dalloc(n, &n->dz16, max_dz)) || (e = dalloc(n, &n->dz_cp, max_dz)) ||
+            (e = dalloc(n, &n->partials, max_part)) || (e = dalloc(n, &n->dloss, 1)) || (e = dalloc(n, &n->err, 1)))
             break;
         // He-normal initial weights, zero biases
         std::vector<float> h(off, 0.0f);
@@ -826,29 +767,38 @@ GDRR_API int gdrr_cnn_forward(gdrr_cnn* n, int32_t batch, const float* in_dev, f
     const int B = batch, c = n->c, H = n->H, W = n->W;
     const int64_t s1 = (int64_t)B * H * W;
     cudaStream_t st = n->stream;
+    const std::vector<Conv>& L = n->conv;
     cudaError_t e = cudaSuccess;
     n->last_batch = B;
+    auto conv = [&](int i, const View& X, const ConvEpi& epi) {
+        const Conv& l = L[i];
+        return conv_product(n, X, l.ci, B, l.H, l.W, l.ks, l.w16, l.K9p, l.co, epi);
+    };
+    auto pool = [&](const View& X, int C, int h, int w, bf16* y) {
+        pool_kernel<<<nblk((int64_t)B * (h / 2) * (w / 2) * (C / 8)), TB, 0, st>>>(X, C, B, h, w, y);
+        return cudaGetLastError();
+    };
+    const float* P = n->params;
     do {
-        to_bf16_kernel<<<nblk(2 * s1), TB, 0, st>>>(in_dev, 2 * s1, n->x16);
+        to_nhwc2_kernel<<<nblk(s1), TB, 0, st>>>(in_dev, s1, H * W, n->x16);
         if ((e = cudaGetLastError())) break;
-        const std::vector<Conv>& L = n->conv;
-        if ((e = conv_forward(n, L[0], B, nchw(n->x16, 2, H, W), n->e1, c, nullptr))) break;
-        pool_kernel<<<nblk(c * s1 / 4), TB, 0, st>>>(n->e1, B, c, H, W, n->p1);
-        if ((e = conv_forward(n, L[1], B, nchw(n->p1, c, H / 2, W / 2), n->e2, 2 * c, nullptr))) break;
-        pool_kernel<<<nblk(2 * c * s1 / 16), TB, 0, st>>>(n->e2, B, 2 * c, H / 2, W / 2, n->p2);
-        if ((e = conv_forward(n, L[2], B, nchw(n->p2, 2 * c, H / 4, W / 4), n->e3, 4 * c, nullptr))) break;
-        pool_kernel<<<nblk(4 * c * s1 / 64), TB, 0, st>>>(n->e3, B, 4 * c, H / 4, W / 4, n->p3);
-        if ((e = conv_forward(n, L[3], B, nchw(n->p3, 4 * c, H / 8, W / 8), n->e4, 8 * c, nullptr))) break;
-        // decoder: [up(prev), skip], read in place
-        if ((e = conv_forward(n, L[4], B, concat_up(n->e4, 8 * c, n->e3, 4 * c, H / 4, W / 4), n->d3, 4 * c,
-                              nullptr)))
+        // encoder: e1 -> cat1[2c..3c), e2 -> cat2[4c..6c), e3 -> cat3[8c..12c), e4 -> cat3[0..8c) upsampled
+        if ((e = conv(0, plain(n->x16, 2), epi_bf16(P + L[0].b_off, 1, n->cat1, 3 * c, 2 * c, 1, H, W)))) break;
+        if ((e = pool(plain(n->cat1, 3 * c, 2 * c), c, H, W, n->p1))) break;
+        if ((e = conv(1, plain(n->p1, c), epi_bf16(P + L[1].b_off, 1, n->cat2, 6 * c, 4 * c, 1, H / 2, W / 2)))) break;
+        if ((e = pool(plain(n->cat2, 6 * c, 4 * c), 2 * c, H / 2, W / 2, n->p2))) break;
+        if ((e = conv(2, plain(n->p2, 2 * c), epi_bf16(P + L[2].b_off, 1, n->cat3, 12 * c, 8 * c, 1, H / 4, W / 4))))
             break;
-        if ((e = conv_forward(n, L[5], B, concat_up(n->d3, 4 * c, n->e2, 2 * c, H / 2, W / 2), n->d2, 2 * c,
-                              nullptr)))
+        if ((e = pool(plain(n->cat3, 12 * c, 8 * c), 4 * c, H / 4, W / 4, n->p3))) break;
+        if ((e = conv(3, plain(n->p3, 4 * c), epi_bf16(P + L[3].b_off, 1, n->cat3, 12 * c, 0, 2, H / 8, W / 8))))
             break;
-        if ((e = conv_forward(n, L[6], B, concat_up(n->d2, 2 * c, n->e1, c, H, W), n->d1, c, nullptr))) break;
-        if ((e = conv_forward(n, L[7], B, nchw(n->d1, c, H, W), nullptr, 1, n->out))) break;
-        residual_kernel<<<nblk(s1), TB, 0, st>>>(in_dev, B, H * W, n->out);
+        // decoder: d3 -> cat2[0..4c) upsampled, d2 -> cat1[0..2c) upsampled, d1
+        if ((e = conv(4, plain(n->cat3, 12 * c), epi_bf16(P + L[4].b_off, 1, n->cat2, 6 * c, 0, 2, H / 4, W / 4))))
+            break;
+        if ((e = conv(5, plain(n->cat2, 6 * c), epi_bf16(P + L[5].b_off, 1, n->cat1, 3 * c, 0, 2, H / 2, W / 2))))
+            break;
+        if ((e = conv(6, plain(n->cat1, 3 * c), epi_bf16(P + L[6].b_off, 1, n->d1, c, 0, 1, H, W)))) break;
+        head_kernel<<<nblk(s1), TB, 0, st>>>(n->d1, c, L[7].w16, P + L[7].b_off, in_dev, s1, H * W, n->out);
         if ((e = cudaGetLastError())) break;
         if (out_dev) e = cudaMemcpyAsync(out_dev, n->out, s1 * sizeof(float), cudaMemcpyDeviceToDevice, st);
     } while (0);
@@ -861,41 +811,43 @@ GDRR_API int gdrr_cnn_backward(gdrr_cnn* n, const float* target_dev, double* los
     const int64_t s1 = (int64_t)B * H * W;
     cudaStream_t st = n->stream;
     const std::vector<Conv>& L = n->conv;
-    double* dloss = reinterpret_cast<double*>(n->dz_f);   // scratch for the loss sum before dz_f is used
     cudaError_t e = cudaSuccess;
     double loss = 0.0;
     do {
-        if ((e = cudaMemsetAsync(dloss, 0, sizeof(double), st))) break;
-        mse_kernel<<<nblk(s1), TB, 0, st>>>(n->out, target_dev, s1, n->g_out, dloss);
-        if ((e = cudaMemcpyAsync(&loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, st))) break;
-        if ((e = cudaStreamSynchronize(st))) break;
-        if ((e = conv_backward(n, L[7], B, n->g_out, nullptr, 1, nchw(n->d1, c, H, W), n->g_d1))) break;
-        if ((e = conv_backward(n, L[6], B, n->g_d1, n->d1, c, concat_up(n->d2, 2 * c, n->e1, c, H, W), n->g_c1)))
+        if ((e = cudaMemsetAsync(n->dloss, 0, sizeof(double), st))) break;
+        mse_kernel<<<nblk(s1), TB, 0, st>>>(n->out, target_dev, s1, n->g_out, n->dloss);
+        if ((e = cudaMemcpyAsync(&loss, n->dloss, sizeof(double), cudaMemcpyDeviceToHost, st))) break;
+        // the 1 x 1 output layer
+        {
+            const int nb = (int)((s1 + 255) / 256);
+            float* pw = n->partials;
+            float* pb = n->partials + (int64_t)nb * c;
+            head_back_kernel<<<nb, 256, 0, st>>>(n->g_out, n->d1, c, L[7].w16, s1, n->g_d1, pw, pb);
+            parts_sum_kernel<<<(c + 127) / 128, 128, 0, st>>>(pw, nb, c, n->grads + L[7].w_off);
+            parts_sum_kernel<<<1, 32, 0, st>>>(pb, nb, 1, n->grads + L[7].b_off);
+            if ((e = cudaGetLastError())) break;
+        }
+        // decoder: each input gradient g_cat splits into the upsampled part
+        // (summed over 2 x 2 blocks) and the skip's part
+        if ((e = conv_backward(n, L[6], B, n->g_d1, plain(n->d1, c), plain(n->cat1, 3 * c), n->g_cat1))) break;
+        place_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_cat1, 3 * c, B, 2 * c, H / 2, W / 2, n->g_d2);
+        if ((e = conv_backward(n, L[5], B, n->g_d2, View{n->cat1, 3 * c, 0, 2}, plain(n->cat2, 6 * c), n->g_cat2)))
             break;
-        // c1 = [up(d2), e1]
-        place_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_c1, 3 * c, 0, B, 2 * c, H / 2, W / 2, 2, 0, n->g_d2);
-        place_back_kernel<<<nblk(c * s1), TB, 0, st>>>(n->g_c1, 3 * c, 2 * c, B, c, H, W, 1, 0, n->g_e1);
-        if ((e = conv_backward(n, L[5], B, n->g_d2, n->d2, 2 * c, concat_up(n->d3, 4 * c, n->e2, 2 * c, H / 2, W / 2),
-                               n->g_c2)))
+        place_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_cat2, 6 * c, B, 4 * c, H / 4, W / 4, n->g_d3);
+        if ((e = conv_backward(n, L[4], B, n->g_d3, View{n->cat2, 6 * c, 0, 2}, plain(n->cat3, 12 * c), n->g_cat3)))
             break;
-        place_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_c2, 6 * c, 0, B, 4 * c, H / 4, W / 4, 2, 0, n->g_d3);
-        place_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_c2, 6 * c, 4 * c, B, 2 * c, H / 2, W / 2, 1, 0,
-                                                              n->g_e2);
-        if ((e = conv_backward(n, L[4], B, n->g_d3, n->d3, 4 * c, concat_up(n->e4, 8 * c, n->e3, 4 * c, H / 4, W / 4),
-                               n->g_c3)))
+        place_back_kernel<<<nblk(8 * c * s1 / 64), TB, 0, st>>>(n->g_cat3, 12 * c, B, 8 * c, H / 8, W / 8, n->g_e4);
+        // encoder: an output's gradient is its skip's part plus its pool's
+        if ((e = conv_backward(n, L[3], B, n->g_e4, View{n->cat3, 12 * c, 0, 2}, plain(n->p3, 4 * c), n->g_p3))) break;
+        pool_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_cat3, 12 * c, 8 * c, n->g_p3, B, 4 * c, H / 4,
+                                                              W / 4, n->g_e3);
+        if ((e = conv_backward(n, L[2], B, n->g_e3, plain(n->cat3, 12 * c, 8 * c), plain(n->p2, 2 * c), n->g_p2)))
             break;
-        place_back_kernel<<<nblk(8 * c * s1 / 64), TB, 0, st>>>(n->g_c3, 12 * c, 0, B, 8 * c, H / 8, W / 8, 2, 0,
-                                                               n->g_e4);
-        place_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_c3, 12 * c, 8 * c, B, 4 * c, H / 4, W / 4, 1, 0,
-                                                               n->g_e3);
-        // encoder
-        if ((e = conv_backward(n, L[3], B, n->g_e4, n->e4, 8 * c, nchw(n->p3, 4 * c, H / 8, W / 8), n->g_p3))) break;
-        pool_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_p3, B, 4 * c, H / 4, W / 4, n->g_e3);
-        if ((e = conv_backward(n, L[2], B, n->g_e3, n->e3, 4 * c, nchw(n->p2, 2 * c, H / 4, W / 4), n->g_p2))) break;
-        pool_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_p2, B, 2 * c, H / 2, W / 2, n->g_e2);
-        if ((e = conv_backward(n, L[1], B, n->g_e2, n->e2, 2 * c, nchw(n->p1, c, H / 2, W / 2), n->g_p1))) break;
-        pool_back_kernel<<<nblk(c * s1), TB, 0, st>>>(n->g_p1, B, c, H, W, n->g_e1);
-        if ((e = conv_backward(n, L[0], B, n->g_e1, n->e1, c, nchw(n->x16, 2, H, W), nullptr))) break;
+        pool_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_cat2, 6 * c, 4 * c, n->g_p2, B, 2 * c, H / 2, W / 2,
+                                                             n->g_e2);
+        if ((e = conv_backward(n, L[1], B, n->g_e2, plain(n->cat2, 6 * c, 4 * c), plain(n->p1, c), n->g_p1))) break;
+        pool_back_kernel<<<nblk(c * s1), TB, 0, st>>>(n->g_cat1, 3 * c, 2 * c, n->g_p1, B, c, H, W, n->g_e1);
+        if ((e = conv_backward(n, L[0], B, n->g_e1, plain(n->cat1, 3 * c, 2 * c), plain(n->x16, 2), nullptr))) break;
         int bad = 0;
         if ((e = cudaMemcpyAsync(&bad, n->err, sizeof(int), cudaMemcpyDeviceToHost, st))) break;
         if ((e = cudaStreamSynchronize(st))) break;

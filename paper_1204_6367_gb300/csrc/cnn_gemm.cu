@@ -1,10 +1,12 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) of sm_103a, for the
-// convolutions of the learned scatter estimator.  Three forms: the one below,
-// whose threads stage the tiles (outputs narrower than 32 columns, or no
-// tensor-map encoder); a TMA-fed, multi-stage, warp-specialised form with one
-// tile per CTA for 64 < N < 256; and its persistent form with two TMEM
-// accumulators for N >= 256 and for 32 <= N <= 64.  Both read
-// operand rows in 16-byte pieces: A and B start on 16-byte boundaries.
+// convolutions of the learned scatter estimator.  Three GEMM forms: the one
+// below, whose threads stage the tiles (outputs narrower than 32 columns, or
+// no tensor-map encoder); a TMA-fed, multi-stage, warp-specialised form with
+// one tile per CTA for 64 < N < 256; and its persistent form with two TMEM
+// accumulators for N >= 256 and for 32 <= N <= 64.  All read operand rows in
+// 16-byte pieces: A and B start on 16-byte boundaries.  A fourth kernel, the
+// implicit-GEMM convolution, takes its A tiles straight from an NHWC
+// activation tensor by 4-D TMA copies (further below).
 //
 //   C[M x N] (FP32)  =  A[M x K] . B[N x K]^T      (A, B BF16, rows K-contiguous)
 //
@@ -29,6 +31,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "cnn_epi.cuh"
 #include "gdrr_internal.cuh"
 
 namespace gdrr {
@@ -593,6 +596,210 @@ __global__ void __launch_bounds__(PERSIST_THREADS) gemm_persistent_kernel(
                      :: "r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Implicit-GEMM convolution over an NHWC BF16 tensor (persistent, with the
+// roles and the two TMEM accumulators of the form above).  The GEMM's K runs
+// over (tap, channel) in slices of 32 channels of one tap.  The A tile of a
+// slice, 128 output pixels x 32 channels, is one 4-D TMA copy (channels, x,
+// y, image) of the input at the tap's offset: a tile is whole rows of one
+// image (or part of one row), so the shifted box is exactly the tile's
+// neighbours, and the rows and columns that fall outside the image are
+// filled with zeros by the copy, which is the convolution's zero padding.
+// No column matrix is written.  The tile lands in the 64-byte-swizzled
+// K-major layout (rows of 64 bytes, 16-byte chunk j of row r at j ^ ((r >> 1)
+// & 3), 8-row groups 512 bytes apart); B is the matching 32-wide K slice of
+// the weights, a 2-D copy in the same layout.  A stage feeds two K16 MMAs.
+// The epilogue applies bias and activation and stores BF16 (optionally
+// upsampled into the next level's concatenated input) or FP32.
+constexpr int CONV_BK = 32;
+
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                       // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;             // stride byte offset: 8-row groups 512 bytes apart
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= (uint64_t)4 << 61;                       // layout: 64-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c, int x, int y, int b,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(b), "r"(bar)
+        : "memory");
+}
+
+struct ConvGeo {
+    int H, W;          // grid of the input and the output
+    int c32;           // input channels / 32
+    int ks;            // kernel size (1 or 3)
+    int n_kb;          // K slices: ks * ks * c32
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(PERSIST_THREADS) conv_implicit_kernel(
+        const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapW, const ConvGeo g, int M,
+        int N, const ConvEpi epi, int* err) {
+    constexpr uint32_t A_BYTES = GEMM_BM * CONV_BK * 2, B_BYTES = BN * CONV_BK * 2;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const uint32_t ring = (smem_addr(smem_raw) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_n = (N + BN - 1) / BN;
+    const int n_tiles = (M / GEMM_BM) * tiles_n;
+    const int pad = g.ks / 2;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_base)), "r"((uint32_t)(2 * BN)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_addr(&full_bar[s]), 1);
+            mbar_init(smem_addr(&empty_bar[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_addr(&tfull[a]), 1);
+            mbar_init(smem_addr(&tempty[a]), 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&mapX)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&mapW)) : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    // tile t: pixel rows m0 .. m0 + 127, output columns n0 .. n0 + BN - 1
+    // (the column tiles of one pixel tile are consecutive, so they share the
+    // pixel tile's input in L2)
+    if (warp == 0 && lane == 0) {
+        // producer: the ring's stage counter runs across tiles
+        const int hw = g.H * g.W;
+        int it = 0;
+        for (int t = blockIdx.x; t < n_tiles && !*(volatile int*)&s_fail; t += gridDim.x) {
+            const int m0 = (t / tiles_n) * GEMM_BM, n0 = (t % tiles_n) * BN;
+            const int b = m0 / hw, r = m0 - b * hw;
+            const int y0 = r / g.W, x0 = r - y0 * g.W;
+            for (int kb = 0; kb < g.n_kb; ++kb, ++it) {
+                const int s = it % STAGES;
+                if (it >= STAGES && !mbar_wait(smem_addr(&empty_bar[s]), (uint32_t)((it / STAGES - 1) & 1))) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                const int tap = kb / g.c32, ch = kb - tap * g.c32;
+                const int ky = tap / g.ks, kx = tap - ky * g.ks;
+                const uint32_t sa = ring + (uint32_t)s * (A_BYTES + B_BYTES);
+                const uint32_t fb = smem_addr(&full_bar[s]);
+                mbar_expect_tx(fb, A_BYTES + B_BYTES);
+                tma_load_4d(sa, &mapX, ch * CONV_BK, x0 + kx - pad, y0 + ky - pad, b, fb);
+                tma_load_2d(sa + A_BYTES, &mapW, kb * CONV_BK, n0, fb);
+            }
+        }
+        // the ring's last loads land before the CTA can leave (bounded)
+        for (int j = max(0, it - STAGES); j < it; ++j)
+            mbar_wait(smem_addr(&full_bar[j % STAGES]), (uint32_t)((j / STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = instr_desc(GEMM_BM, BN);
+        int it = 0, local = 0;
+        for (int t = blockIdx.x; t < n_tiles && !*(volatile int*)&s_fail; t += gridDim.x, ++local) {
+            const int a = local & 1;
+            if (!mbar_wait(smem_addr(&tempty[a]), (uint32_t)(((local >> 1) & 1) ^ 1))) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc_tmem = tmem + (uint32_t)(a * BN);
+            for (int kb = 0; kb < g.n_kb; ++kb, ++it) {
+                const int s = it % STAGES;
+                if (!mbar_wait(smem_addr(&full_bar[s]), (uint32_t)((it / STAGES) & 1))) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = ring + (uint32_t)s * (A_BYTES + B_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < CONV_BK / 16; ++kk) {
+                    // K16 step inside the 64-byte swizzle atom: advance the start by 32 bytes
+                    const uint64_t ad = smem_desc_sw64(sa + kk * 32);
+                    const uint64_t bd = smem_desc_sw64(sa + A_BYTES + kk * 32);
+                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                        :: "r"(acc_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_addr(&empty_bar[s])) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_addr(&tfull[a])) : "memory");
+        }
+    } else if (warp >= 2) {
+        // epilogue
+        const int q = warp & 3;                               // TMEM lane quarter of this warp
+        int local = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++local) {
+            const int m0 = (t / tiles_n) * GEMM_BM, n0 = (t % tiles_n) * BN;
+            const int a = local & 1;
+            const bool got = mbar_wait(smem_addr(&tfull[a]), (uint32_t)((local >> 1) & 1));
+            const bool good = __all_sync(0xffffffffu, got) && !*(volatile int*)&s_fail;
+            if (!good) {
+                if (lane == 0) atomicExch(&s_fail, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int64_t row = (int64_t)m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                    "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int col = n0 + c0;
+                if (row < M && col < N) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+                    epi_store(epi, row, col, min(16, N - col), v);
+                }
+            }
+            // this warp's TMEM reads are done: release the accumulator
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&tempty[a])) : "memory");
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int*)&s_fail) atomicExch(err, 1);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -619,6 +826,22 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int K, int ld, int b
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, elem,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_conv_t(const CUtensorMap& mX, const CUtensorMap& mW, const ConvGeo& g, int M, int N,
+                          const ConvEpi& epi, int* err, cudaStream_t s) {
+    const size_t smem = (size_t)STAGES * (GEMM_BM + BN) * CONV_BK * 2 + 1024;
+    cudaError_t e = cudaFuncSetAttribute(conv_implicit_kernel<BN, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n_sm = 1;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t n_tiles = (int64_t)(M / GEMM_BM) * ((N + BN - 1) / BN);
+    const int grid = (int)std::min<int64_t>(n_tiles, n_sm);
+    conv_implicit_kernel<BN, STAGES><<<grid, PERSIST_THREADS, smem, s>>>(mX, mW, g, M, N, epi, err);
+    return cudaGetLastError();
 }
 
 template <int BN, int STAGES>
@@ -678,6 +901,57 @@ cudaError_t launch_gemm_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* 
 }
 
 }  // namespace
+
+// The implicit-GEMM convolution: tensor maps of the NHWC input (box 32
+// channels x a tile of 128 pixels, 64-byte swizzle, zero fill outside) and of
+// the weights (box 32 x BN), then the persistent kernel with the narrowest
+// output tile that covers N (N > 256: column tiles of 128 or 256).
+cudaError_t launch_conv_implicit(const ConvArgs& a, int* err, cudaStream_t s) {
+    if (!conv_implicit_ok(a.C, a.H, a.W, a.ks) || a.B <= 0 || a.N <= 0 || a.ldx % 8 || a.ldw % 8 ||
+        a.ldw < a.ks * a.ks * a.C || a.ldx < a.C)
+        return cudaErrorInvalidValue;
+    if (((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.w)) & 15u) != 0) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const int wb = a.W >= GEMM_BM ? GEMM_BM : a.W, hb = GEMM_BM / wb;
+    CUtensorMap mX, mW;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)a.C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
+        const cuuint64_t px = (cuuint64_t)a.ldx * 2;
+        const cuuint64_t strides[3] = {px, px * a.W, px * a.W * a.H};
+        const cuuint32_t box[4] = {(cuuint32_t)CONV_BK, (cuuint32_t)wb, (cuuint32_t)hb, 1};
+        const cuuint32_t elem[4] = {1, 1, 1, 1};
+        if (fn(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(a.x), dims, strides, box, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const int BN = a.N <= 32 ? 32 : a.N <= 64 ? 64 : a.N <= 128 ? 128 : a.N <= 256 ? 256 : (a.N % 128 == 0 ? 128 : 256);
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)(a.ks * a.ks * a.C), (cuuint64_t)a.N};
+        const cuuint64_t strides[1] = {(cuuint64_t)a.ldw * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)CONV_BK, (cuuint32_t)BN};
+        const cuuint32_t elem[2] = {1, 1};
+        if (fn(&mW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.w), dims, strides, box, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    ConvGeo g;
+    g.H = a.H;
+    g.W = a.W;
+    g.c32 = a.C / CONV_BK;
+    g.ks = a.ks;
+    g.n_kb = a.ks * a.ks * g.c32;
+    const int64_t M = (int64_t)a.B * a.H * a.W;
+    if (M % GEMM_BM || M > INT32_MAX) return cudaErrorInvalidValue;
+    switch (BN) {
+        case 32: return launch_conv_t<32, 16>(mX, mW, g, (int)M, a.N, a.epi, err, s);
+        case 64: return launch_conv_t<64, 14>(mX, mW, g, (int)M, a.N, a.epi, err, s);
+        case 128: return launch_conv_t<128, 12>(mX, mW, g, (int)M, a.N, a.epi, err, s);
+        default: return launch_conv_t<256, 8>(mX, mW, g, (int)M, a.N, a.epi, err, s);
+    }
+}
 
 // C = A . B^T; K a multiple of 64; lda, ldb multiples of 8 (16-byte rows).
 // With splits > 1 and partial_stride == 0 the caller zeroes C first and the

@@ -91,8 +91,14 @@ def test_gemm_bf16_strided_and_unaligned_operands(gd):
     assert ei.value.code == -1
 
 
-def test_cnn_forward_backward_against_oracle(gd):
-    c, H, W, B = 32, 32, 32, 2
+# Grids that take each product form: at 32 x 32 the 16 x 16 and 32 x 32
+# levels tile into 128-pixel row groups (implicit GEMM) and the 8 x 8 and
+# 4 x 4 levels take the column matrix; at the estimator's 96 x 128 every
+# level but 12 x 16 tiles (one, two and four rows per tile); at 16 x 256 a
+# tile is half an image row.
+@pytest.mark.parametrize("H,W,B", [(32, 32, 2), (96, 128, 2), (16, 256, 1)])
+def test_cnn_forward_backward_against_oracle(gd, H, W, B):
+    c = 32
     rng = np.random.default_rng(9)
     x = rng.normal(size=(B, 2, H, W)).astype(np.float32)
     t = rng.normal(size=(B, 1, H, W)).astype(np.float32)
