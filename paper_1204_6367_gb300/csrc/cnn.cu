@@ -172,18 +172,20 @@ __global__ void __launch_bounds__(256) im2col_t_kernel(const View X, int C, int 
     }
 }
 
-// The same, element by element, for any C and kernel size.
-__global__ void im2col_t_any_kernel(const View X, int C, int B, int H, int W, int ks, int K9p, int ldp,
+// The same, element by element, for any C and kernel size; rows k >=
+// ks^2 C are not written (they reach only product columns that are dropped).
+__global__ void im2col_t_any_kernel(const View X, int C, int B, int H, int W, int ks, int ldp,
                                     bf16* __restrict__ out) {
     const int64_t P = (int64_t)B * H * W;
+    const int K9 = ks * ks * C;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)K9p * ldp) return;
+    if (i >= (int64_t)K9 * ldp) return;
     const int k = (int)(i / ldp);
-    const int64_t p = i % ldp;
+    const int64_t p = i - (int64_t)k * ldp;
     bf16 v = __float2bfloat16_rn(0.0f);
-    if (p < P && k < ks * ks * C) {
+    if (p < P) {
         const int HW = H * W;
-        const int b = (int)(p / HW), r = (int)(p % HW), y = r / W, x = r % W;
+        const int b = (int)(p / HW), r = (int)(p - (int64_t)b * HW), y = r / W, x = r - y * W;
         const int tap = k / C, c = k - tap * C, half = ks / 2;
         const int yy = y + tap / ks - half, xx = x + tap % ks - half;
         if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
@@ -193,6 +195,46 @@ __global__ void im2col_t_any_kernel(const View X, int C, int B, int H, int W, in
         }
     }
     out[i] = v;
+}
+
+// A 3 x 3 convolution of an input with few channels (CI <= 4), computed
+// directly: one thread per output pixel loads its 9 CI input values once and
+// accumulates 16 output channels at a time in FP32 over k = tap CI + c in
+// order, with the weights w[co][k] (row ldw) from shared memory.
+template <int CI>
+__global__ void __launch_bounds__(128) conv_small_kernel(const View X, int B, int H, int W,
+                                                         const bf16* __restrict__ w, int ldw, int N,
+                                                         const ConvEpi epi) {
+    constexpr int K = 9 * CI;
+    __shared__ float sw[64 * K];
+    for (int i = threadIdx.x; i < N * K; i += blockDim.x) sw[i] = __bfloat162float(w[(i / K) * ldw + i % K]);
+    __syncthreads();
+    const int64_t P = (int64_t)B * H * W;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int HW = H * W;
+    const int b = (int)(p / HW), r = (int)(p - (int64_t)b * HW), y = r / W, x = r - y * W;
+    float xin[K];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+        const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        const bf16* src = X.p + (((int64_t)b * H + yy) * W + xx) * X.ld + X.off;
+#pragma unroll
+        for (int c = 0; c < CI; ++c) xin[tap * CI + c] = in ? __bfloat162float(src[c]) : 0.0f;
+    }
+    for (int c0 = 0; c0 < N; c0 += 16) {
+        float acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c0 + j < N) acc[j] += xin[k] * sw[(c0 + j) * K + k];
+        }
+        epi_store(epi, p, c0, min(16, N - c0), acc);
+    }
 }
 
 // Epilogue of the column-matrix path: G[p][c] (row ldg) through epi, one
@@ -246,21 +288,40 @@ __global__ void __launch_bounds__(256) act_back_kernel(const float* __restrict__
     extern __shared__ __align__(16) uint8_t sm[];
     float* sf = reinterpret_cast<float*>(sm);                          // [64][Co + 1]
     bf16* sb = reinterpret_cast<bf16*>(sm + (size_t)64 * (Co + 1) * 4); // [Co][72]
+    __shared__ int64_t ybase[64];
     const int64_t p0 = (int64_t)blockIdx.x * 64;
-    for (int i = threadIdx.x; i < 64 * Co; i += blockDim.x) {
-        const int px = i / Co, c = i - px * Co;
-        const int64_t p = p0 + px;
-        float g = 0.0f;
-        if (p < P) {
-            g = dy[p * Co + c];
-            if (relu) {
-                const float yv = __bfloat162float(Y.p[view_pixel(Y, p, H, W) * Y.ld + Y.off + c]);
-                if (!(yv > 0.0f)) g = 0.0f;
+    if (threadIdx.x < 64) {
+        const int64_t p = p0 + threadIdx.x;
+        ybase[threadIdx.x] = p < P ? view_pixel(Y, p, H, W) * Y.ld + Y.off : 0;
+    }
+    __syncthreads();
+    const int n = 64 * Co;
+    for (int base = 0; base < n; base += 4 * 256) {
+        float g[4], yv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + u * 256 + threadIdx.x;
+            g[u] = 0.0f;
+            yv[u] = 1.0f;
+            if (i < n) {
+                const int px = i / Co, c = i - px * Co;
+                if (p0 + px < P) {
+                    g[u] = dy[p0 * Co + i];
+                    if (relu) yv[u] = __bfloat162float(Y.p[ybase[px] + c]);
+                }
             }
-            dz16[p * Co + c] = __float2bfloat16_rn(g);
         }
-        sf[px * (Co + 1) + c] = g;
-        sb[c * CT_PITCH + px] = __float2bfloat16_rn(g);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + u * 256 + threadIdx.x;
+            if (i < n) {
+                const int px = i / Co, c = i - px * Co;
+                const float gg = (relu && !(yv[u] > 0.0f)) ? 0.0f : g[u];
+                if (p0 + px < P) dz16[p0 * Co + i] = __float2bfloat16_rn(gg);
+                sf[px * (Co + 1) + c] = gg;
+                sb[c * CT_PITCH + px] = __float2bfloat16_rn(gg);
+            }
+        }
     }
     __syncthreads();
     for (int c = threadIdx.x; c < Co; c += blockDim.x) {
@@ -276,50 +337,69 @@ __global__ void __launch_bounds__(256) act_back_kernel(const float* __restrict__
     }
 }
 
-// out[c] = sum over k of part[k][c], k = 0, 1, ... in order
-__global__ void parts_sum_kernel(const float* __restrict__ part, int n_part, int Co, float* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= Co) return;
+// out[c] = the sum over k of part[k][c] in a fixed order: one block per
+// channel, thread t adds parts t, t + 256, ... in turn, then a fixed tree
+// over the threads.
+__global__ void __launch_bounds__(256) parts_sum_kernel(const float* __restrict__ part, int n_part, int Co,
+                                                        float* __restrict__ out) {
+    __shared__ float red[256];
+    const int c = blockIdx.x;
     float s = 0.0f;
-    for (int k = 0; k < n_part; ++k) s += part[(int64_t)k * Co + c];
-    out[c] = s;
+    for (int k = threadIdx.x; k < n_part; k += 256) s += part[(int64_t)k * Co + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
 }
 
 // Gradient of the upsampled part of a decoder input: g[b][y][x][c] = the sum
 // over the 2 x 2 block of dcat[b][2y + i][2x + j][c] (row pitch ldc; order
-// (0,0), (0,1), (1,0), (1,1)), c < C, on the low grid h x w.
+// (0,0), (0,1), (1,0), (1,1)), c < C, on the low grid h x w.  Four channels
+// per thread (C and ldc multiples of 4).
 __global__ void place_back_kernel(const float* __restrict__ dcat, int ldc, int B, int C, int h, int w,
                                   float* __restrict__ g) {
-    const int64_t n = (int64_t)B * h * w * C;
+    const int c4 = C / 4;
+    const int64_t n = (int64_t)B * h * w * c4;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int64_t q = i / C;
-    const int c = (int)(i - q * C);
+    const int64_t q = i / c4;
+    const int c = (int)(i - q * c4) * 4;
     const int64_t b = q / ((int64_t)h * w);
-    const int r = (int)(q - b * h * w), y = r / w, x = r % w;
+    const int r = (int)(q - b * h * w), y = r / w, x = r - y * w;
     const int W = 2 * w;
     const float* d = dcat + ((b * 2 * h + 2 * y) * W + 2 * x) * ldc + c;
-    float acc = 0.0f;
-    acc += d[0];
-    acc += d[ldc];
-    acc += d[(int64_t)W * ldc];
-    acc += d[(int64_t)W * ldc + ldc];
-    g[i] = acc;
+    const float4 a0 = *reinterpret_cast<const float4*>(d);
+    const float4 a1 = *reinterpret_cast<const float4*>(d + ldc);
+    const float4 a2 = *reinterpret_cast<const float4*>(d + (int64_t)W * ldc);
+    const float4 a3 = *reinterpret_cast<const float4*>(d + (int64_t)W * ldc + ldc);
+    float4 o;
+    o.x = ((0.0f + a0.x) + a1.x + a2.x) + a3.x;
+    o.y = ((0.0f + a0.y) + a1.y + a2.y) + a3.y;
+    o.z = ((0.0f + a0.z) + a1.z + a2.z) + a3.z;
+    o.w = ((0.0f + a0.w) + a1.w + a2.w) + a3.w;
+    *reinterpret_cast<float4*>(g + q * C + c) = o;
 }
 
 // Gradient of an encoder output that feeds both a skip and a pool:
 // g[b][y][x][c] = dcat[b][y][x][off + c] (row pitch ldc) + dp[b][y/2][x/2][c] / 4.
+// Four channels per thread (C, ldc and off multiples of 4).
 __global__ void pool_back_kernel(const float* __restrict__ dcat, int ldc, int off, const float* __restrict__ dp, int B,
                                  int C, int H, int W, float* __restrict__ g) {
-    const int64_t n = (int64_t)B * H * W * C;
+    const int c4 = C / 4;
+    const int64_t n = (int64_t)B * H * W * c4;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int64_t q = i / C;
-    const int c = (int)(i - q * C);
+    const int64_t q = i / c4;
+    const int c = (int)(i - q * c4) * 4;
     const int64_t b = q / ((int64_t)H * W);
-    const int r = (int)(q - b * H * W), y = r / W, x = r % W;
-    const float skip = dcat[q * ldc + off + c];
-    g[i] = skip + 0.25f * dp[((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+    const int r = (int)(q - b * H * W), y = r / W, x = r - y * W;
+    const float4 s = *reinterpret_cast<const float4*>(dcat + q * ldc + off + c);
+    const float4 d = *reinterpret_cast<const float4*>(dp + ((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c);
+    *reinterpret_cast<float4*>(g + q * C + c) =
+        make_float4(s.x + 0.25f * d.x, s.y + 0.25f * d.y, s.z + 0.25f * d.z, s.w + 0.25f * d.w);
 }
 
 // The 1 x 1 output layer with the residual: out[p] = (sum over c of w[c]
@@ -340,31 +420,25 @@ __global__ void head_kernel(const bf16* __restrict__ d1, int C, const bf16* __re
 __global__ void __launch_bounds__(256) head_back_kernel(const float* __restrict__ g, const bf16* __restrict__ d1, int C,
                                                         const bf16* __restrict__ w, int64_t P, float* __restrict__ gd1,
                                                         float* __restrict__ part_w, float* __restrict__ part_b) {
-    __shared__ float sw[256][33];
-    __shared__ float sg[256];
-    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    float gv = 0.0f;
-    if (p < P) gv = g[p];
+    __shared__ float sg[256], sgr[256];
+    const int64_t p0 = (int64_t)blockIdx.x * 256;
+    const int np = (int)min((int64_t)256, P - p0);
+    const float gv = (int)threadIdx.x < np ? g[p0 + threadIdx.x] : 0.0f;
     sg[threadIdx.x] = gv;
-    const float gr = __bfloat162float(__float2bfloat16_rn(gv));
-    for (int c0 = 0; c0 < C; c0 += 32) {
-        const int nc = min(32, C - c0);
-        for (int j = 0; j < nc; ++j) {
-            const float xv = p < P ? __bfloat162float(d1[p * C + c0 + j]) : 0.0f;
-            sw[threadIdx.x][j] = gr * xv;
-            if (p < P) gd1[p * C + c0 + j] = gr * __bfloat162float(w[c0 + j]);
-        }
-        __syncthreads();
-        if ((int)threadIdx.x < nc) {
-            float s = 0.0f;
-            for (int k = 0; k < 256; ++k) s += sw[k][threadIdx.x];
-            part_w[(int64_t)blockIdx.x * C + c0 + threadIdx.x] = s;
-        }
-        __syncthreads();
+    sgr[threadIdx.x] = __bfloat162float(__float2bfloat16_rn(gv));
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * C; i += 256) {
+        const int px = i / C, c = i - px * C;
+        gd1[p0 * C + i] = sgr[px] * __bfloat162float(w[c]);
+    }
+    if ((int)threadIdx.x < C) {
+        float s = 0.0f;
+        for (int px = 0; px < np; ++px) s += sgr[px] * __bfloat162float(d1[(p0 + px) * C + threadIdx.x]);
+        part_w[(int64_t)blockIdx.x * C + threadIdx.x] = s;
     }
     if (threadIdx.x == 0) {
         float s = 0.0f;
-        for (int k = 0; k < 256; ++k) s += sg[k];
+        for (int px = 0; px < np; ++px) s += sg[px];
         part_b[blockIdx.x] = s;
     }
 }
@@ -395,13 +469,16 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
 }
 
 // BF16 copies of a conv's weights w[co][ci][tap] (tap = ky ks + kx) in the
-// products' K order (tap-major): w16[co][tap Ci + ci] (row K9p) for the
+// products' K order: w16[co][tap Ci + ci] (row K9p) for the column path's
 // forward, and wf16[ci][tap Co + co] = w[co][ci][kk - 1 - tap] (row K9dp),
 // the weights with the taps flipped for the data gradient (a convolution of
 // dZ: dX(y, x) = sum over co, ky, kx of dZ(y + ky - h, x + kx - h)
-// w[co][ci][ks - 1 - ky][ks - 1 - kx]); zero beyond the K extent.
+// w[co][ci][ks - 1 - ky][ks - 1 - kx]); zero beyond the K extent.  For 3 x 3
+// layers also the implicit GEMM's ky-major copies w3[ky][co][kx Ci + ci] and
+// wf3[ky][ci][kx Co + co] (flipped).
 __global__ void weight_copies_kernel(const float* __restrict__ w, int Co, int Ci, int kk, int K9p, int K9dp,
-                                     bf16* __restrict__ w16, bf16* __restrict__ wf16) {
+                                     bf16* __restrict__ w16, bf16* __restrict__ wf16, bf16* __restrict__ w3,
+                                     bf16* __restrict__ wf3) {
     const int K9 = Ci * kk;
     const int64_t n1 = (int64_t)Co * K9p, n2 = (int64_t)Ci * K9dp;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -423,16 +500,26 @@ __global__ void weight_copies_kernel(const float* __restrict__ w, int Co, int Ci
         }
         wf16[i] = __float2bfloat16_rn(v);
     }
+    if (w3 && i < (int64_t)Co * K9) {
+        // w3[ky][co][kx Ci + ci] and wf3[ky][ci][kx Co + co], ky, kx < 3
+        const int ky = (int)(i / ((int64_t)Co * 3 * Ci));
+        const int r = (int)(i - (int64_t)ky * Co * 3 * Ci);
+        const int co = r / (3 * Ci), q = r - co * 3 * Ci, kx = q / Ci, ci = q - kx * Ci;
+        w3[i] = __float2bfloat16_rn(w[(int64_t)co * K9 + (int64_t)ci * kk + ky * 3 + kx]);
+        const int ci2 = r / (3 * Co), q2 = r - ci2 * 3 * Co, kx2 = q2 / Co, co2 = q2 - kx2 * Co;
+        wf3[i] = __float2bfloat16_rn(w[(int64_t)co2 * K9 + (int64_t)ci2 * kk + (8 - (ky * 3 + kx2))]);
+    }
 }
 
-// dW[co][ci][tap] from the weight-gradient product G[co][tap Ci + ci] (row ld)
-__global__ void unpad_kernel(const float* __restrict__ G, int Co, int Ci, int kk, int ld, float* __restrict__ dw) {
+// dW[co][ci][tap] from the transposed weight-gradient product
+// GT[tap Ci + ci][co] (row Co)
+__global__ void unpad_kernel(const float* __restrict__ GT, int Co, int Ci, int kk, float* __restrict__ dw) {
     const int64_t n = (int64_t)Co * Ci * kk;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int co = (int)(i / ((int64_t)Ci * kk));
     const int r = (int)(i - (int64_t)co * Ci * kk), ci = r / kk, tap = r - ci * kk;
-    dw[i] = G[(int64_t)co * ld + tap * Ci + ci];
+    dw[i] = GT[((int64_t)tap * Ci + ci) * Co + co];
 }
 
 // out[i] = sum over z of p[z * stride + i], in the order z = 0, 1, ...
@@ -451,6 +538,8 @@ struct Conv {
     int64_t w_off, b_off;
     bf16* w16 = nullptr;   // [co][K9p], K = (tap, ci)
     bf16* wf16 = nullptr;  // [ci][K9dp], K = (tap, co), taps flipped
+    bf16* w3 = nullptr;    // 3 x 3 layers: [ky][co][kx ci + c], the implicit GEMM's weights
+    bf16* wf3 = nullptr;   // 3 x 3 layers: [ky][ci][kx co + c], flipped
 };
 
 // K splits of a weight-gradient product over P pixels (a function of P alone,
@@ -531,9 +620,9 @@ int err_code(cudaError_t e) {
 
 cudaError_t refresh_weights(gdrr_cnn* n) {
     for (Conv& L : n->conv) {
-        const int64_t cnt = std::max((int64_t)L.co * L.K9p, (int64_t)L.ci * L.K9dp);
+        const int64_t cnt = std::max({(int64_t)L.co * L.K9p, (int64_t)L.ci * L.K9dp, (int64_t)L.co * L.K9});
         weight_copies_kernel<<<nblk(cnt), TB, 0, n->stream>>>(n->params + L.w_off, L.co, L.ci, L.ks * L.ks, L.K9p,
-                                                              L.K9dp, L.w16, L.wf16);
+                                                              L.K9dp, L.w16, L.wf16, L.w3, L.wf3);
         CK(cudaGetLastError());
     }
     return cudaSuccess;
@@ -554,19 +643,30 @@ ConvEpi epi_f32(float* y, int ld, int H, int W) {
 }
 
 // One convolution on the grid H x W of the plain NHWC input X (C channels)
-// with weights w (row ldw, K = (tap, c)) into N output columns through epi:
-// the implicit GEMM where the grid tiles, else a column matrix (row K9p), the
-// column-path GEMM into n->gemm and the elementwise epilogue.
-cudaError_t conv_product(gdrr_cnn* n, const View& X, int C, int B, int H, int W, int ks, const bf16* w, int ldw, int N,
-                         const ConvEpi& epi) {
+// into N output columns through epi: the implicit GEMM (ky-major weights w3)
+// where the grid tiles, a direct kernel for inputs of at most 4 channels,
+// else a column matrix (row K9p), the column-path GEMM with w (row ldw, K =
+// (tap, c)) into n->gemm and the elementwise epilogue.
+cudaError_t conv_product(gdrr_cnn* n, const View& X, int C, int B, int H, int W, int ks, const bf16* w, int ldw,
+                         const bf16* w3, int N, const ConvEpi& epi) {
     const int64_t P = (int64_t)B * H * W;
-    if (X.up == 1 && conv_implicit_ok(C, H, W, ks) && X.ld % 8 == 0 && X.off % 8 == 0) {
+    if (ks == 3 && w3 && X.up == 1 && conv_implicit_ok(C, H, W) && X.ld % 8 == 0 && X.off % 8 == 0) {
         ConvArgs a;
         a.x = X.p + X.off; a.C = C; a.ldx = X.ld;
-        a.B = B; a.H = H; a.W = W; a.ks = ks;
-        a.w = w; a.ldw = ldw; a.N = N;
+        a.B = B; a.H = H; a.W = W;
+        a.w3 = w3; a.N = N;
         a.epi = epi;
         return launch_conv_implicit(a, n->err, n->stream);
+    }
+    if (ks == 3 && C <= 4 && N <= 64) {
+        const unsigned g = (unsigned)((P + 127) / 128);
+        switch (C) {
+            case 1: conv_small_kernel<1><<<g, 128, 0, n->stream>>>(X, B, H, W, w, ldw, N, epi); break;
+            case 2: conv_small_kernel<2><<<g, 128, 0, n->stream>>>(X, B, H, W, w, ldw, N, epi); break;
+            case 3: conv_small_kernel<3><<<g, 128, 0, n->stream>>>(X, B, H, W, w, ldw, N, epi); break;
+            default: conv_small_kernel<4><<<g, 128, 0, n->stream>>>(X, B, H, W, w, ldw, N, epi); break;
+        }
+        return cudaGetLastError();
     }
     const int K9p = pad64((int64_t)ks * ks * C);
     im2col_nhwc_kernel<<<nblk(P * (K9p / 8)), TB, 0, n->stream>>>(X, C, B, H, W, ks, K9p, n->cols);
@@ -594,35 +694,36 @@ cudaError_t conv_backward(gdrr_cnn* n, const Conv& L, int B, const float* dy, co
     CK(cudaFuncSetAttribute(act_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     act_back_kernel<<<n_blk, TB, smem, st>>>(dy, Y, L.H, L.W, P, L.co, L.relu, n->dz16, n->dz_cp, Pp, n->partials);
     CK(cudaGetLastError());
-    parts_sum_kernel<<<(L.co + 127) / 128, 128, 0, st>>>(n->partials, n_blk, L.co, n->grads + L.b_off);
+    parts_sum_kernel<<<L.co, 256, 0, st>>>(n->partials, n_blk, L.co, n->grads + L.b_off);
     CK(cudaGetLastError());
     // weight gradient: dW[co][k] = sum_p dZ[p][co] cols[p][k]
     if (L.ci % 32 == 0 && L.ks == 3 && X.up == 1 && X.ld % 8 == 0 && X.off % 8 == 0) {
         im2col_t_kernel<<<dim3((unsigned)(Pp / CT_PIX), (unsigned)(L.ci / 32)), TB, 0, st>>>(X, L.ci, B, L.H, L.W, Pp,
                                                                                             n->cols);
     } else {
-        im2col_t_any_kernel<<<nblk((int64_t)L.K9p * Pp), TB, 0, st>>>(X, L.ci, B, L.H, L.W, L.ks, L.K9p, Pp, n->cols);
+        im2col_t_any_kernel<<<nblk((int64_t)L.K9 * Pp), TB, 0, st>>>(X, L.ci, B, L.H, L.W, L.ks, Pp, n->cols);
     }
     CK(cudaGetLastError());
-    // the pixel sum is split across CTAs; each split writes its own partial
-    // product and one ordered pass adds them, so training is bit-reproducible
+    // dW^T[k][co] = sum_p cols[p][k] dZ[p][co]: M runs over k (no tile
+    // wasted on narrow layers), N over the output channels.  The pixel sum is
+    // split across CTAs; each split writes its own partial product and one
+    // ordered pass adds them, so training is bit-reproducible.
     const int splits = wgrad_splits(P);
     if (splits > 1) {
         const int64_t slice = (int64_t)L.co * L.K9p;
         int used = 1;
-        CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->partials, L.K9p, L.co, L.K9p, Pp, splits, n->err, st, slice,
+        CK(launch_gemm_bf16(n->cols, Pp, n->dz_cp, Pp, n->partials, L.co, L.K9p, L.co, Pp, splits, n->err, st, slice,
                             &used));
         splits_sum_kernel<<<nblk(slice), TB, 0, st>>>(n->partials, used, slice, n->gemm);
         CK(cudaGetLastError());
     } else {
-        CK(launch_gemm_bf16(n->dz_cp, Pp, n->cols, Pp, n->gemm, L.K9p, L.co, L.K9p, Pp, 1, n->err, st));
+        CK(launch_gemm_bf16(n->cols, Pp, n->dz_cp, Pp, n->gemm, L.co, L.K9p, L.co, Pp, 1, n->err, st));
     }
-    unpad_kernel<<<nblk((int64_t)L.co * L.K9), TB, 0, st>>>(n->gemm, L.co, L.ci, L.ks * L.ks, L.K9p,
-                                                            n->grads + L.w_off);
+    unpad_kernel<<<nblk((int64_t)L.co * L.K9), TB, 0, st>>>(n->gemm, L.co, L.ci, L.ks * L.ks, n->grads + L.w_off);
     CK(cudaGetLastError());
     if (dx) {
         // data gradient: the convolution of dZ with the flipped weights
-        CK(conv_product(n, plain(n->dz16, L.co), L.co, B, L.H, L.W, L.ks, L.wf16, L.K9dp, L.ci,
+        CK(conv_product(n, plain(n->dz16, L.co), L.co, B, L.H, L.W, L.ks, L.wf16, L.K9dp, L.wf3, L.ci,
                         epi_f32(dx, L.ci, L.H, L.W)));
     }
     return cudaSuccess;
@@ -682,6 +783,7 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
         bool bad = false;
         for (Conv& L : n->conv) {
             if (dalloc(n, &L.w16, (size_t)L.co * L.K9p) || dalloc(n, &L.wf16, (size_t)L.ci * L.K9dp)) bad = true;
+            if (L.ks == 3 && (dalloc(n, &L.w3, (size_t)L.co * L.K9) || dalloc(n, &L.wf3, (size_t)L.co * L.K9))) bad = true;
         }
         if (bad) { e = cudaErrorMemoryAllocation; break; }
         const int64_t s1 = B * HW, s2 = s1 / 4, s3 = s1 / 16, s4 = s1 / 64;
@@ -772,7 +874,7 @@ GDRR_API int gdrr_cnn_forward(gdrr_cnn* n, int32_t batch, const float* in_dev, f
     n->last_batch = B;
     auto conv = [&](int i, const View& X, const ConvEpi& epi) {
         const Conv& l = L[i];
-        return conv_product(n, X, l.ci, B, l.H, l.W, l.ks, l.w16, l.K9p, l.co, epi);
+        return conv_product(n, X, l.ci, B, l.H, l.W, l.ks, l.w16, l.K9p, l.w3, l.co, epi);
     };
     auto pool = [&](const View& X, int C, int h, int w, bf16* y) {
         pool_kernel<<<nblk((int64_t)B * (h / 2) * (w / 2) * (C / 8)), TB, 0, st>>>(X, C, B, h, w, y);
@@ -797,9 +899,21 @@ GDRR_API int gdrr_cnn_forward(gdrr_cnn* n, int32_t batch, const float* in_dev, f
             break;
         if ((e = conv(5, plain(n->cat2, 6 * c), epi_bf16(P + L[5].b_off, 1, n->cat1, 3 * c, 0, 2, H / 2, W / 2))))
             break;
-        if ((e = conv(6, plain(n->cat1, 3 * c), epi_bf16(P + L[6].b_off, 1, n->d1, c, 0, 1, H, W)))) break;
-        head_kernel<<<nblk(s1), TB, 0, st>>>(n->d1, c, L[7].w16, P + L[7].b_off, in_dev, s1, H * W, n->out);
-        if ((e = cudaGetLastError())) break;
+        // d1 and the 1 x 1 output layer: fused into the implicit GEMM's
+        // epilogue when d1's grid tiles, else a separate pass
+        ConvEpi e6 = epi_bf16(P + L[6].b_off, 1, n->d1, c, 0, 1, H, W);
+        const bool fuse_head = conv_implicit_ok(3 * c, H, W) && c <= 256;
+        if (fuse_head) {
+            e6.head_w = L[7].w16;
+            e6.head_b = P + L[7].b_off;
+            e6.head_x = in_dev;
+            e6.head_out = n->out;
+        }
+        if ((e = conv(6, plain(n->cat1, 3 * c), e6))) break;
+        if (!fuse_head) {
+            head_kernel<<<nblk(s1), TB, 0, st>>>(n->d1, c, L[7].w16, P + L[7].b_off, in_dev, s1, H * W, n->out);
+            if ((e = cudaGetLastError())) break;
+        }
         if (out_dev) e = cudaMemcpyAsync(out_dev, n->out, s1 * sizeof(float), cudaMemcpyDeviceToDevice, st);
     } while (0);
     return err_code(e);
@@ -823,30 +937,30 @@ GDRR_API int gdrr_cnn_backward(gdrr_cnn* n, const float* target_dev, double* los
             float* pw = n->partials;
             float* pb = n->partials + (int64_t)nb * c;
             head_back_kernel<<<nb, 256, 0, st>>>(n->g_out, n->d1, c, L[7].w16, s1, n->g_d1, pw, pb);
-            parts_sum_kernel<<<(c + 127) / 128, 128, 0, st>>>(pw, nb, c, n->grads + L[7].w_off);
-            parts_sum_kernel<<<1, 32, 0, st>>>(pb, nb, 1, n->grads + L[7].b_off);
+            parts_sum_kernel<<<c, 256, 0, st>>>(pw, nb, c, n->grads + L[7].w_off);
+            parts_sum_kernel<<<1, 256, 0, st>>>(pb, nb, 1, n->grads + L[7].b_off);
             if ((e = cudaGetLastError())) break;
         }
         // decoder: each input gradient g_cat splits into the upsampled part
         // (summed over 2 x 2 blocks) and the skip's part
         if ((e = conv_backward(n, L[6], B, n->g_d1, plain(n->d1, c), plain(n->cat1, 3 * c), n->g_cat1))) break;
-        place_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_cat1, 3 * c, B, 2 * c, H / 2, W / 2, n->g_d2);
+        place_back_kernel<<<nblk(2 * c * s1 / 16), TB, 0, st>>>(n->g_cat1, 3 * c, B, 2 * c, H / 2, W / 2, n->g_d2);
         if ((e = conv_backward(n, L[5], B, n->g_d2, View{n->cat1, 3 * c, 0, 2}, plain(n->cat2, 6 * c), n->g_cat2)))
             break;
-        place_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_cat2, 6 * c, B, 4 * c, H / 4, W / 4, n->g_d3);
+        place_back_kernel<<<nblk(4 * c * s1 / 64), TB, 0, st>>>(n->g_cat2, 6 * c, B, 4 * c, H / 4, W / 4, n->g_d3);
         if ((e = conv_backward(n, L[4], B, n->g_d3, View{n->cat2, 6 * c, 0, 2}, plain(n->cat3, 12 * c), n->g_cat3)))
             break;
-        place_back_kernel<<<nblk(8 * c * s1 / 64), TB, 0, st>>>(n->g_cat3, 12 * c, B, 8 * c, H / 8, W / 8, n->g_e4);
+        place_back_kernel<<<nblk(8 * c * s1 / 256), TB, 0, st>>>(n->g_cat3, 12 * c, B, 8 * c, H / 8, W / 8, n->g_e4);
         // encoder: an output's gradient is its skip's part plus its pool's
         if ((e = conv_backward(n, L[3], B, n->g_e4, View{n->cat3, 12 * c, 0, 2}, plain(n->p3, 4 * c), n->g_p3))) break;
-        pool_back_kernel<<<nblk(4 * c * s1 / 16), TB, 0, st>>>(n->g_cat3, 12 * c, 8 * c, n->g_p3, B, 4 * c, H / 4,
+        pool_back_kernel<<<nblk(4 * c * s1 / 64), TB, 0, st>>>(n->g_cat3, 12 * c, 8 * c, n->g_p3, B, 4 * c, H / 4,
                                                               W / 4, n->g_e3);
         if ((e = conv_backward(n, L[2], B, n->g_e3, plain(n->cat3, 12 * c, 8 * c), plain(n->p2, 2 * c), n->g_p2)))
             break;
-        pool_back_kernel<<<nblk(2 * c * s1 / 4), TB, 0, st>>>(n->g_cat2, 6 * c, 4 * c, n->g_p2, B, 2 * c, H / 2, W / 2,
+        pool_back_kernel<<<nblk(2 * c * s1 / 16), TB, 0, st>>>(n->g_cat2, 6 * c, 4 * c, n->g_p2, B, 2 * c, H / 2, W / 2,
                                                              n->g_e2);
         if ((e = conv_backward(n, L[1], B, n->g_e2, plain(n->cat2, 6 * c, 4 * c), plain(n->p1, c), n->g_p1))) break;
-        pool_back_kernel<<<nblk(c * s1), TB, 0, st>>>(n->g_cat1, 3 * c, 2 * c, n->g_p1, B, c, H, W, n->g_e1);
+        pool_back_kernel<<<nblk(c * s1 / 4), TB, 0, st>>>(n->g_cat1, 3 * c, 2 * c, n->g_p1, B, c, H, W, n->g_e1);
         if ((e = conv_backward(n, L[0], B, n->g_e1, plain(n->cat1, 3 * c, 2 * c), plain(n->x16, 2), nullptr))) break;
         int bad = 0;
         if ((e = cudaMemcpyAsync(&bad, n->err, sizeof(int), cudaMemcpyDeviceToHost, st))) break;

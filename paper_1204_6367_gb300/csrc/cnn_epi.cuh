@@ -20,6 +20,10 @@ namespace gdrr {
 //                up == 2 writes the value to the four pixels (2y + i, 2x + j)
 //                of a 2H x 2W grid (nearest upsampling);
 //   yf  != NULL: FP32 acc (+ bias when given) at yf[p ldf + c].
+// head_out != NULL (BF16 output, one column tile holding every column): a
+// 1 x 1 convolution to one channel follows, fused: head_out[p] = (sum over c
+// in order of head_w[c] y16[p][c] + head_b[0]) + head_x[b][0][y][x] (head_x
+// FP32 [b][2][H][W]).
 struct ConvEpi {
     const float* bias;          // NULL: no bias
     int relu;
@@ -28,11 +32,18 @@ struct ConvEpi {
     float* yf;
     int ldf;
     int H, W;                   // output grid of the convolution
+    const __nv_bfloat16* head_w;
+    const float* head_b;
+    const float* head_x;
+    float* head_out;
 };
 
 // Stores columns [c0, c0 + n) (n <= 16) of pixel p from v[0 .. n).  The
 // 16-column BF16 store is two 16-byte stores when the address allows it.
-__device__ __forceinline__ void epi_store(const ConvEpi& e, int64_t p, int c0, int n, const float* v) {
+// With head != NULL, adds head_w[c] times the stored BF16 value of each
+// column c to *head, in column order.
+__device__ __forceinline__ void epi_store(const ConvEpi& e, int64_t p, int c0, int n, const float* v,
+                                          float* head = nullptr) {
     if (e.y16) {
         __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
@@ -43,6 +54,11 @@ __device__ __forceinline__ void epi_store(const ConvEpi& e, int64_t p, int c0, i
                 if (e.relu) a = fmaxf(a, 0.0f);
             }
             o[j] = __float2bfloat16_rn(a);
+        }
+        if (head) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < n) *head += __bfloat162float(e.head_w[c0 + j]) * __bfloat162float(o[j]);
         }
         const int64_t hw = (int64_t)e.H * e.W;
         const int64_t b = p / hw;
@@ -76,15 +92,23 @@ __device__ __forceinline__ void epi_store(const ConvEpi& e, int64_t p, int c0, i
     }
 }
 
-// A 3 x 3 (or 1 x 1) convolution with zero padding over an NHWC BF16 tensor
-// x (C channels read, pixel pitch ldx; batch B, grid H x W, output on the same
-// grid) with weights w[N][ldw], k = tap C + c (tap = ky ks + kx), into epi.
+// The fused 1 x 1 head of pixel p once every column has been added to acc.
+__device__ __forceinline__ void epi_head(const ConvEpi& e, int64_t p, float acc) {
+    const int64_t hw = (int64_t)e.H * e.W;
+    const int64_t b = p / hw;
+    e.head_out[p] = (acc + e.head_b[0]) + e.head_x[b * 2 * hw + (p - b * hw)];
+}
+
+// A 3 x 3 convolution with zero padding over an NHWC BF16 tensor x (C
+// channels read, pixel pitch ldx; batch B, grid H x W, output on the same
+// grid) into N output columns through epi, with the weights stored ky-major:
+// w3[ky][n][kx C + c] for tap (ky, kx).
 struct ConvArgs {
     const __nv_bfloat16* x;
     int C, ldx;
-    int B, H, W, ks;
-    const __nv_bfloat16* w;
-    int ldw, N;
+    int B, H, W;
+    const __nv_bfloat16* w3;
+    int N;
     ConvEpi epi;
 };
 
@@ -92,8 +116,8 @@ struct ConvArgs {
 // 128 output pixels is whole rows of one image (W divides 128 and the rows
 // of an image split into whole tiles) or part of one row (W a multiple of
 // 128).
-inline bool conv_implicit_ok(int C, int H, int W, int ks) {
-    if (C % 32 || C <= 0 || ks < 1 || ks > 3 || !(ks & 1)) return false;
+inline bool conv_implicit_ok(int C, int H, int W) {
+    if (C % 32 || C <= 0) return false;
     if (W % 128 == 0) return true;
     return W > 0 && 128 % W == 0 && H % (128 / W) == 0;
 }

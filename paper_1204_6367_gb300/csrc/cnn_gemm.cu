@@ -597,21 +597,25 @@ __global__ void __launch_bounds__(PERSIST_THREADS) gemm_persistent_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Implicit-GEMM convolution over an NHWC BF16 tensor (persistent, with the
-// roles and the two TMEM accumulators of the form above).  The GEMM's K runs
-// over (tap, channel) in slices of 32 channels of one tap.  The A tile of a
-// slice, 128 output pixels x 32 channels, is one 4-D TMA copy (channels, x,
-// y, image) of the input at the tap's offset: a tile is whole rows of one
-// image (or part of one row), so the shifted box is exactly the tile's
-// neighbours, and the rows and columns that fall outside the image are
-// filled with zeros by the copy, which is the convolution's zero padding.
-// No column matrix is written.  The tile lands in the 64-byte-swizzled
-// K-major layout (rows of 64 bytes, 16-byte chunk j of row r at j ^ ((r >> 1)
-// & 3), 8-row groups 512 bytes apart); B is the matching 32-wide K slice of
-// the weights, a 2-D copy in the same layout.  A stage feeds two K16 MMAs.
-// The epilogue applies bias and activation and stores BF16 (optionally
-// upsampled into the next level's concatenated input) or FP32.
+// Implicit-GEMM 3 x 3 convolution over an NHWC BF16 tensor (persistent, with
+// the roles and the two TMEM accumulators of the form above).  A tile is 128
+// output pixels: whole rows of one image (Hb rows of W = Wb pixels) or part
+// of one row (Wb = 128).  The GEMM's K runs over (kx, 32-channel slice, ky):
+// one pipeline stage holds, for one kx and one slice of 32 input channels,
+// the tile's Hb + 2 input rows shifted by kx, a single 4-D TMA copy
+// (channels, x, y, image) with rows and columns outside the image filled
+// with zeros by the copy (the zero padding), plus the three matching weight
+// slices (ky = 0, 1, 2), a single 3-D copy.  The A operand of tap (ky, kx)
+// is the stage's rows ky Wb .. ky Wb + 127, so the three vertical taps share
+// one copy and no column matrix is written.  Operands use the 64-byte-
+// swizzled K-major layout (rows of 64 bytes, 16-byte chunk j of row r at
+// j ^ ((r >> 1) & 3), 8-row groups 512 bytes apart; every operand starts on
+// a 1024-byte boundary).  A stage feeds 3 x 2 K16 MMAs.  The epilogue
+// applies bias and activation and stores BF16 (optionally upsampled into the
+// next level's concatenated input, optionally with the fused 1 x 1 head) or
+// FP32.
 constexpr int CONV_BK = 32;
+constexpr int CONV_MAX_STAGES = 8;
 
 __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     uint64_t d = 0;
@@ -621,6 +625,14 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     d |= (uint64_t)1 << 46;                       // descriptor version
     d |= (uint64_t)4 << 61;                       // layout: 64-byte swizzle
     return d;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c, int x, int y, int b,
@@ -634,25 +646,30 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 
 struct ConvGeo {
     int H, W;          // grid of the input and the output
-    int c32;           // input channels / 32
-    int ks;            // kernel size (1 or 3)
-    int n_kb;          // K slices: ks * ks * c32
+    int Wb;            // tile width: min(W, 128); the tile has 128 / Wb rows
+    int C;             // input channels
+    int c32;           // C / 32
+    int n_kb;          // stages per tile: 3 * c32
+    int stages;        // ring depth (<= CONV_MAX_STAGES)
+    uint32_t a_bytes;  // A part of a stage: (128 + 2 Wb) rows of 64 bytes
 };
 
-template <int BN, int STAGES>
+template <int BN>
 __global__ void __launch_bounds__(PERSIST_THREADS) conv_implicit_kernel(
         const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapW, const ConvGeo g, int M,
         int N, const ConvEpi epi, int* err) {
-    constexpr uint32_t A_BYTES = GEMM_BM * CONV_BK * 2, B_BYTES = BN * CONV_BK * 2;
+    constexpr uint32_t B_TAP = BN * CONV_BK * 2, B_BYTES = 3 * B_TAP;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full_bar[CONV_MAX_STAGES], empty_bar[CONV_MAX_STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const uint32_t ring = (smem_addr(smem_raw) + 1023u) & ~1023u;
+    const uint32_t stage_bytes = g.a_bytes + B_BYTES;
+    const int stages = g.stages;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = (N + BN - 1) / BN;
     const int n_tiles = (M / GEMM_BM) * tiles_n;
-    const int pad = g.ks / 2;
+    const uint32_t row_bytes = (uint32_t)g.Wb * (CONV_BK * 2);     // one input row of the tile in shared memory
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -660,7 +677,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS) conv_implicit_kernel(
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 32) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < stages; ++s) {
             mbar_init(smem_addr(&full_bar[s]), 1);
             mbar_init(smem_addr(&empty_bar[s]), 1);
         }
@@ -686,33 +703,37 @@ __global__ void __launch_bounds__(PERSIST_THREADS) conv_implicit_kernel(
     if (warp == 0 && lane == 0) {
         // producer: the ring's stage counter runs across tiles
         const int hw = g.H * g.W;
-        int it = 0;
+        int it = 0, s = 0;
+        uint32_t ph = 0;                                   // parity of the pass over the ring
         for (int t = blockIdx.x; t < n_tiles && !*(volatile int*)&s_fail; t += gridDim.x) {
             const int m0 = (t / tiles_n) * GEMM_BM, n0 = (t % tiles_n) * BN;
             const int b = m0 / hw, r = m0 - b * hw;
             const int y0 = r / g.W, x0 = r - y0 * g.W;
             for (int kb = 0; kb < g.n_kb; ++kb, ++it) {
-                const int s = it % STAGES;
-                if (it >= STAGES && !mbar_wait(smem_addr(&empty_bar[s]), (uint32_t)((it / STAGES - 1) & 1))) {
+                if (it >= stages && !mbar_wait(smem_addr(&empty_bar[s]), ph ^ 1u)) {
                     atomicExch(&s_fail, 1);
                     break;
                 }
-                const int tap = kb / g.c32, ch = kb - tap * g.c32;
-                const int ky = tap / g.ks, kx = tap - ky * g.ks;
-                const uint32_t sa = ring + (uint32_t)s * (A_BYTES + B_BYTES);
+                const int kx = kb / g.c32, ch = kb - kx * g.c32;
+                const uint32_t sa = ring + (uint32_t)s * stage_bytes;
                 const uint32_t fb = smem_addr(&full_bar[s]);
-                mbar_expect_tx(fb, A_BYTES + B_BYTES);
-                tma_load_4d(sa, &mapX, ch * CONV_BK, x0 + kx - pad, y0 + ky - pad, b, fb);
-                tma_load_2d(sa + A_BYTES, &mapW, kb * CONV_BK, n0, fb);
+                mbar_expect_tx(fb, stage_bytes);
+                tma_load_4d(sa, &mapX, ch * CONV_BK, x0 + kx - 1, y0 - 1, b, fb);
+                tma_load_3d(sa + g.a_bytes, &mapW, kx * g.C + ch * CONV_BK, n0, 0, fb);   // ky = 0, 1, 2
+                if (++s == stages) { s = 0; ph ^= 1u; }
             }
         }
         // the ring's last loads land before the CTA can leave (bounded)
-        for (int j = max(0, it - STAGES); j < it; ++j)
-            mbar_wait(smem_addr(&full_bar[j % STAGES]), (uint32_t)((j / STAGES) & 1));
+        const int last = min(it, stages);
+        for (int j = 0; j < last; ++j) {
+            const int jt = it - 1 - j;                     // one of the last `last` stages issued
+            mbar_wait(smem_addr(&full_bar[jt % stages]), (uint32_t)((jt / stages) & 1));
+        }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         constexpr uint32_t idesc = instr_desc(GEMM_BM, BN);
-        int it = 0, local = 0;
+        int local = 0, s = 0;
+        uint32_t ph = 0;
         for (int t = blockIdx.x; t < n_tiles && !*(volatile int*)&s_fail; t += gridDim.x, ++local) {
             const int a = local & 1;
             if (!mbar_wait(smem_addr(&tempty[a]), (uint32_t)(((local >> 1) & 1) ^ 1))) {
@@ -721,29 +742,32 @@ __global__ void __launch_bounds__(PERSIST_THREADS) conv_implicit_kernel(
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc_tmem = tmem + (uint32_t)(a * BN);
-            for (int kb = 0; kb < g.n_kb; ++kb, ++it) {
-                const int s = it % STAGES;
-                if (!mbar_wait(smem_addr(&full_bar[s]), (uint32_t)((it / STAGES) & 1))) {
+            for (int kb = 0; kb < g.n_kb; ++kb) {
+                if (!mbar_wait(smem_addr(&full_bar[s]), ph)) {
                     atomicExch(&s_fail, 1);
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = ring + (uint32_t)s * (A_BYTES + B_BYTES);
+                const uint32_t sa = ring + (uint32_t)s * stage_bytes;
 #pragma unroll
-                for (int kk = 0; kk < CONV_BK / 16; ++kk) {
-                    // K16 step inside the 64-byte swizzle atom: advance the start by 32 bytes
-                    const uint64_t ad = smem_desc_sw64(sa + kk * 32);
-                    const uint64_t bd = smem_desc_sw64(sa + A_BYTES + kk * 32);
-                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\t"
-                        "setp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                        :: "r"(acc_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                        : "memory");
+                for (int ky = 0; ky < 3; ++ky) {
+#pragma unroll
+                    for (int kk = 0; kk < CONV_BK / 16; ++kk) {
+                        // K16 step inside the 64-byte swizzle atom: advance the start by 32 bytes
+                        const uint64_t ad = smem_desc_sw64(sa + ky * row_bytes + kk * 32);
+                        const uint64_t bd = smem_desc_sw64(sa + g.a_bytes + ky * B_TAP + kk * 32);
+                        const uint32_t acc = (kb > 0 || ky > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\t"
+                            "setp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                            :: "r"(acc_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              :: "r"(smem_addr(&empty_bar[s])) : "memory");
+                if (++s == stages) { s = 0; ph ^= 1u; }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_addr(&tfull[a])) : "memory");
@@ -763,6 +787,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS) conv_implicit_kernel(
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int64_t row = (int64_t)m0 + q * 32 + lane;
+            float head = 0.0f;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 uint32_t r[16];
@@ -781,9 +806,10 @@ __global__ void __launch_bounds__(PERSIST_THREADS) conv_implicit_kernel(
                     float v[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-                    epi_store(epi, row, col, min(16, N - col), v);
+                    epi_store(epi, row, col, min(16, N - col), v, epi.head_out ? &head : nullptr);
                 }
             }
+            if (epi.head_out && row < M) epi_head(epi, row, head);
             // this warp's TMEM reads are done: release the accumulator
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -828,19 +854,23 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int K, int ld, int b
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES>
-cudaError_t launch_conv_t(const CUtensorMap& mX, const CUtensorMap& mW, const ConvGeo& g, int M, int N,
-                          const ConvEpi& epi, int* err, cudaStream_t s) {
-    const size_t smem = (size_t)STAGES * (GEMM_BM + BN) * CONV_BK * 2 + 1024;
-    cudaError_t e = cudaFuncSetAttribute(conv_implicit_kernel<BN, STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int BN>
+cudaError_t launch_conv_t(const CUtensorMap& mX, const CUtensorMap& mW, ConvGeo g, int M, int N, const ConvEpi& epi,
+                          int* err, cudaStream_t s) {
+    // the deepest ring that fits 216 KB of shared memory
+    const uint32_t stage = g.a_bytes + 3u * BN * CONV_BK * 2;
+    g.stages = (int)std::min<uint32_t>(CONV_MAX_STAGES, (216u * 1024u) / stage);
+    if (g.stages < 2) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)g.stages * stage + 1024;
+    cudaError_t e = cudaFuncSetAttribute(conv_implicit_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, n_sm = 1;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int64_t n_tiles = (int64_t)(M / GEMM_BM) * ((N + BN - 1) / BN);
     const int grid = (int)std::min<int64_t>(n_tiles, n_sm);
-    conv_implicit_kernel<BN, STAGES><<<grid, PERSIST_THREADS, smem, s>>>(mX, mW, g, M, N, epi, err);
+    conv_implicit_kernel<BN><<<grid, PERSIST_THREADS, smem, s>>>(mX, mW, g, M, N, epi, err);
     return cudaGetLastError();
 }
 
@@ -903,14 +933,14 @@ cudaError_t launch_gemm_t(const __nv_bfloat16* A, int lda, const __nv_bfloat16* 
 }  // namespace
 
 // The implicit-GEMM convolution: tensor maps of the NHWC input (box 32
-// channels x a tile of 128 pixels, 64-byte swizzle, zero fill outside) and of
-// the weights (box 32 x BN), then the persistent kernel with the narrowest
-// output tile that covers N (N > 256: column tiles of 128 or 256).
+// channels x Wb pixels x (128 / Wb + 2) rows, 64-byte swizzle, zero fill
+// outside) and of the ky-major weights [ky][N][kx C + c] (box 32 x BN x 3),
+// then the persistent kernel with the narrowest output tile that covers N
+// (N > 256: column tiles of 128 or 256).
 cudaError_t launch_conv_implicit(const ConvArgs& a, int* err, cudaStream_t s) {
-    if (!conv_implicit_ok(a.C, a.H, a.W, a.ks) || a.B <= 0 || a.N <= 0 || a.ldx % 8 || a.ldw % 8 ||
-        a.ldw < a.ks * a.ks * a.C || a.ldx < a.C)
+    if (!conv_implicit_ok(a.C, a.H, a.W) || a.B <= 0 || a.N <= 0 || a.ldx % 8 || a.ldx < a.C)
         return cudaErrorInvalidValue;
-    if (((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.w)) & 15u) != 0) return cudaErrorInvalidValue;
+    if (((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.w3)) & 15u) != 0) return cudaErrorInvalidValue;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     const int wb = a.W >= GEMM_BM ? GEMM_BM : a.W, hb = GEMM_BM / wb;
@@ -919,7 +949,7 @@ cudaError_t launch_conv_implicit(const ConvArgs& a, int* err, cudaStream_t s) {
         const cuuint64_t dims[4] = {(cuuint64_t)a.C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
         const cuuint64_t px = (cuuint64_t)a.ldx * 2;
         const cuuint64_t strides[3] = {px, px * a.W, px * a.W * a.H};
-        const cuuint32_t box[4] = {(cuuint32_t)CONV_BK, (cuuint32_t)wb, (cuuint32_t)hb, 1};
+        const cuuint32_t box[4] = {(cuuint32_t)CONV_BK, (cuuint32_t)wb, (cuuint32_t)(hb + 2), 1};
         const cuuint32_t elem[4] = {1, 1, 1, 1};
         if (fn(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(a.x), dims, strides, box, elem,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -927,12 +957,14 @@ cudaError_t launch_conv_implicit(const ConvArgs& a, int* err, cudaStream_t s) {
             return cudaErrorInvalidValue;
     }
     const int BN = a.N <= 32 ? 32 : a.N <= 64 ? 64 : a.N <= 128 ? 128 : a.N <= 256 ? 256 : (a.N % 128 == 0 ? 128 : 256);
+    if (a.epi.head_out && (a.N > BN || !a.epi.y16)) return cudaErrorInvalidValue;
     {
-        const cuuint64_t dims[2] = {(cuuint64_t)(a.ks * a.ks * a.C), (cuuint64_t)a.N};
-        const cuuint64_t strides[1] = {(cuuint64_t)a.ldw * 2};
-        const cuuint32_t box[2] = {(cuuint32_t)CONV_BK, (cuuint32_t)BN};
-        const cuuint32_t elem[2] = {1, 1};
-        if (fn(&mW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.w), dims, strides, box, elem,
+        // w3[ky][n][kx C + c]
+        const cuuint64_t dims[3] = {(cuuint64_t)(3 * a.C), (cuuint64_t)a.N, 3};
+        const cuuint64_t strides[2] = {(cuuint64_t)(3 * a.C) * 2, (cuuint64_t)a.N * (3 * a.C) * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)CONV_BK, (cuuint32_t)BN, 3};
+        const cuuint32_t elem[3] = {1, 1, 1};
+        if (fn(&mW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(a.w3), dims, strides, box, elem,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
@@ -940,16 +972,19 @@ cudaError_t launch_conv_implicit(const ConvArgs& a, int* err, cudaStream_t s) {
     ConvGeo g;
     g.H = a.H;
     g.W = a.W;
+    g.Wb = wb;
+    g.C = a.C;
     g.c32 = a.C / CONV_BK;
-    g.ks = a.ks;
-    g.n_kb = a.ks * a.ks * g.c32;
+    g.n_kb = 3 * g.c32;
+    g.stages = 0;
+    g.a_bytes = (uint32_t)(wb * (hb + 2)) * (CONV_BK * 2);
     const int64_t M = (int64_t)a.B * a.H * a.W;
     if (M % GEMM_BM || M > INT32_MAX) return cudaErrorInvalidValue;
     switch (BN) {
-        case 32: return launch_conv_t<32, 16>(mX, mW, g, (int)M, a.N, a.epi, err, s);
-        case 64: return launch_conv_t<64, 14>(mX, mW, g, (int)M, a.N, a.epi, err, s);
-        case 128: return launch_conv_t<128, 12>(mX, mW, g, (int)M, a.N, a.epi, err, s);
-        default: return launch_conv_t<256, 8>(mX, mW, g, (int)M, a.N, a.epi, err, s);
+        case 32: return launch_conv_t<32>(mX, mW, g, (int)M, a.N, a.epi, err, s);
+        case 64: return launch_conv_t<64>(mX, mW, g, (int)M, a.N, a.epi, err, s);
+        case 128: return launch_conv_t<128>(mX, mW, g, (int)M, a.N, a.epi, err, s);
+        default: return launch_conv_t<256>(mX, mW, g, (int)M, a.N, a.epi, err, s);
     }
 }
 
