@@ -145,10 +145,10 @@ __global__ void __launch_bounds__(256) im2col_t_kernel(const View X, int C, int 
     const int64_t p0 = (int64_t)blockIdx.x * CT_PIX;
     const int c0 = blockIdx.y * 32;
     const int HW = H * W;
-    // loads: 9 taps x 64 pixels x 4 chunks of 8 channels
+    // loads: 9 taps x 4 chunks of 8 channels x 64 pixels (a warp takes 32
+    // consecutive pixels, so its shared-memory stores are conflict-free)
     for (int idx = threadIdx.x; idx < 9 * CT_PIX * 4; idx += blockDim.x) {
-        const int tap = idx / (CT_PIX * 4), rem = idx - tap * CT_PIX * 4;
-        const int px = rem >> 2, ch = rem & 3;
+        const int px = idx & (CT_PIX - 1), ch = (idx >> 6) & 3, tap = idx >> 8;
         const int64_t p = p0 + px;
         uint4 val = make_uint4(0u, 0u, 0u, 0u);
         if (p < P) {
@@ -200,14 +200,19 @@ __global__ void im2col_t_any_kernel(const View X, int C, int B, int H, int W, in
 // A 3 x 3 convolution of an input with few channels (CI <= 4), computed
 // directly: one thread per output pixel loads its 9 CI input values once and
 // accumulates 16 output channels at a time in FP32 over k = tap CI + c in
-// order, with the weights w[co][k] (row ldw) from shared memory.
+// order, with the weights w[co][k] (row ldw) from shared memory transposed
+// to [k][co] (16-byte loads of four channels).
 template <int CI>
 __global__ void __launch_bounds__(128) conv_small_kernel(const View X, int B, int H, int W,
                                                          const bf16* __restrict__ w, int ldw, int N,
                                                          const ConvEpi epi) {
     constexpr int K = 9 * CI;
-    __shared__ float sw[64 * K];
-    for (int i = threadIdx.x; i < N * K; i += blockDim.x) sw[i] = __bfloat162float(w[(i / K) * ldw + i % K]);
+    __shared__ __align__(16) float sw[K * 64];
+    const int Np = (N + 15) / 16 * 16;
+    for (int i = threadIdx.x; i < K * Np; i += blockDim.x) {
+        const int k = i / Np, co = i - k * Np;
+        sw[i] = co < N ? __bfloat162float(w[co * ldw + k]) : 0.0f;
+    }
     __syncthreads();
     const int64_t P = (int64_t)B * H * W;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -229,9 +234,15 @@ __global__ void __launch_bounds__(128) conv_small_kernel(const View X, int B, in
         for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
+            const float4* wk = reinterpret_cast<const float4*>(sw + k * Np + c0);
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (c0 + j < N) acc[j] += xin[k] * sw[(c0 + j) * K + k];
+            for (int q = 0; q < 4; ++q) {
+                const float4 w4 = wk[q];
+                acc[4 * q] += xin[k] * w4.x;
+                acc[4 * q + 1] += xin[k] * w4.y;
+                acc[4 * q + 2] += xin[k] * w4.z;
+                acc[4 * q + 3] += xin[k] * w4.w;
+            }
         }
         epi_store(epi, p, c0, min(16, N - c0), acc);
     }
@@ -277,25 +288,31 @@ __global__ void pool_kernel(const View X, int C, int B, int H, int W, bf16* __re
     *reinterpret_cast<uint4*>(y + q * C + c) = *reinterpret_cast<const uint4*>(o);
 }
 
-// dZ = dY * (Y > 0) (or dY when relu == 0) for a block of 64 pixels and all
-// Co channels: BF16 NHWC dz16[p][c] (the data gradient's convolution input),
-// BF16 channel-major dz_cp[c][p] (row ldp; the weight gradient's operand,
-// zero for P <= p < ldp) through a shared-memory transpose, and the block's
-// FP32 bias-gradient part part[block][c] (its 64 pixels added in order).
+// Pixels per block of the activation backward: the block holds pt x Co
+// values, at most 4096 for wide layers.
+inline int act_tile(int co) { return co >= 256 ? 16 : (co >= 128 ? 32 : 64); }
+
+// dZ = dY * (Y > 0) (or dY when relu == 0) for a block of pt pixels (a
+// multiple of 16, at most 64) and all Co channels: BF16 NHWC dz16[p][c] (the
+// data gradient's convolution input), BF16 channel-major dz_cp[c][p] (row
+// ldp; the weight gradient's operand, zero for P <= p < ldp) through a
+// shared-memory transpose, and the block's FP32 bias-gradient part
+// part[block][c] (its pt pixels added in order).
 __global__ void __launch_bounds__(256) act_back_kernel(const float* __restrict__ dy, const View Y, int H, int W,
-                                                       int64_t P, int Co, int relu, bf16* __restrict__ dz16,
+                                                       int64_t P, int Co, int relu, int pt, bf16* __restrict__ dz16,
                                                        bf16* __restrict__ dz_cp, int ldp, float* __restrict__ part) {
     extern __shared__ __align__(16) uint8_t sm[];
-    float* sf = reinterpret_cast<float*>(sm);                          // [64][Co + 1]
-    bf16* sb = reinterpret_cast<bf16*>(sm + (size_t)64 * (Co + 1) * 4); // [Co][72]
+    float* sf = reinterpret_cast<float*>(sm);                          // [pt][Co + 1]
+    bf16* sb = reinterpret_cast<bf16*>(sm + (size_t)pt * (Co + 1) * 4); // [Co][pt + 8]
+    const int sp = pt + 8;
     __shared__ int64_t ybase[64];
-    const int64_t p0 = (int64_t)blockIdx.x * 64;
-    if (threadIdx.x < 64) {
+    const int64_t p0 = (int64_t)blockIdx.x * pt;
+    if ((int)threadIdx.x < pt) {
         const int64_t p = p0 + threadIdx.x;
         ybase[threadIdx.x] = p < P ? view_pixel(Y, p, H, W) * Y.ld + Y.off : 0;
     }
     __syncthreads();
-    const int n = 64 * Co;
+    const int n = pt * Co;
     for (int base = 0; base < n; base += 4 * 256) {
         float g[4], yv[4];
 #pragma unroll
@@ -319,21 +336,22 @@ __global__ void __launch_bounds__(256) act_back_kernel(const float* __restrict__
                 const float gg = (relu && !(yv[u] > 0.0f)) ? 0.0f : g[u];
                 if (p0 + px < P) dz16[p0 * Co + i] = __float2bfloat16_rn(gg);
                 sf[px * (Co + 1) + c] = gg;
-                sb[c * CT_PITCH + px] = __float2bfloat16_rn(gg);
+                sb[c * sp + px] = __float2bfloat16_rn(gg);
             }
         }
     }
     __syncthreads();
     for (int c = threadIdx.x; c < Co; c += blockDim.x) {
         float s = 0.0f;
-        for (int px = 0; px < 64; ++px) s += sf[px * (Co + 1) + c];
+        for (int px = 0; px < pt; ++px) s += sf[px * (Co + 1) + c];
         part[(int64_t)blockIdx.x * Co + c] = s;
     }
-    for (int i = threadIdx.x; i < Co * 8; i += blockDim.x) {
-        const int c = i >> 3, seg = i & 7;
+    const int segs = pt / 8;
+    for (int i = threadIdx.x; i < Co * segs; i += blockDim.x) {
+        const int c = i / segs, seg = i - c * segs;
         if (p0 + seg * 8 < ldp)
             *reinterpret_cast<uint4*>(dz_cp + (int64_t)c * ldp + p0 + seg * 8) =
-                *reinterpret_cast<const uint4*>(sb + c * CT_PITCH + seg * 8);
+                *reinterpret_cast<const uint4*>(sb + c * sp + seg * 8);
     }
 }
 
@@ -689,10 +707,12 @@ cudaError_t conv_backward(gdrr_cnn* n, const Conv& L, int B, const float* dy, co
     const int64_t P = (int64_t)B * L.H * L.W;
     const int Pp = pad64(P);
     cudaStream_t st = n->stream;
-    const int n_blk = (int)((P + 63) / 64);
-    const size_t smem = (size_t)64 * (L.co + 1) * 4 + (size_t)L.co * CT_PITCH * 2;
+    const int pt = act_tile(L.co);
+    const int n_blk = (int)((P + pt - 1) / pt);
+    const size_t smem = (size_t)pt * (L.co + 1) * 4 + (size_t)L.co * (pt + 8) * 2;
     CK(cudaFuncSetAttribute(act_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    act_back_kernel<<<n_blk, TB, smem, st>>>(dy, Y, L.H, L.W, P, L.co, L.relu, n->dz16, n->dz_cp, Pp, n->partials);
+    act_back_kernel<<<n_blk, TB, smem, st>>>(dy, Y, L.H, L.W, P, L.co, L.relu, pt, n->dz16, n->dz_cp, Pp,
+                                             n->partials);
     CK(cudaGetLastError());
     parts_sum_kernel<<<L.co, 256, 0, st>>>(n->partials, n_blk, L.co, n->grads + L.b_off);
     CK(cudaGetLastError());
@@ -772,7 +792,7 @@ GDRR_API int gdrr_cnn_create(int32_t max_batch, int32_t height, int32_t width, i
         max_cols = std::max({max_cols, Pp * L.K9p, P * L.K9dp});
         max_gemm = std::max({max_gemm, P * L.ci, (int64_t)L.co * L.K9p, P * L.co});
         max_dz = std::max({max_dz, P * L.co, (int64_t)L.co * Pp});
-        max_part = std::max({max_part, (int64_t)wgrad_splits(P) * L.co * L.K9p, (Pp / 64) * L.co,
+        max_part = std::max({max_part, (int64_t)wgrad_splits(P) * L.co * L.K9p, (Pp / act_tile(L.co) + 1) * L.co,
                              (Pp / 256 + 1) * (L.ci + 1)});
     }
     cudaError_t e = cudaSuccess;
