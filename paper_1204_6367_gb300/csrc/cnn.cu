@@ -145,10 +145,10 @@ __global__ void __launch_bounds__(256) im2col_t_kernel(const View X, int C, int 
     const int64_t p0 = (int64_t)blockIdx.x * CT_PIX;
     const int c0 = blockIdx.y * 32;
     const int HW = H * W;
-    // loads: 9 taps x 4 chunks of 8 channels x 64 pixels (a warp takes 32
-    // consecutive pixels, so its shared-memory stores are conflict-free)
+    // loads: 9 taps x 64 pixels x 4 chunks of 8 channels
     for (int idx = threadIdx.x; idx < 9 * CT_PIX * 4; idx += blockDim.x) {
-        const int px = idx & (CT_PIX - 1), ch = (idx >> 6) & 3, tap = idx >> 8;
+        const int tap = idx / (CT_PIX * 4), rem = idx - tap * CT_PIX * 4;
+        const int px = rem >> 2, ch = rem & 3;
         const int64_t p = p0 + px;
         uint4 val = make_uint4(0u, 0u, 0u, 0u);
         if (p < P) {
