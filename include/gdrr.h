@@ -263,7 +263,13 @@ GDRR_API int gdrr_raytrace_primary_siddon(gdrr_ctx* ctx, double angle_rad, doubl
  * prim_dev / scat_dev: caller-owned device int64[nv*nu], ACCUMULATED (not
  * cleared) in units of 2^-24 keV.  stats_dev: NULL or device
  * uint64[GDRR_NSTATS], accumulated.  records_dev: NULL or device
- * gdrr_history_record[n_photons], written (debug / parity use; slower). */
+ * gdrr_history_record[n_photons], written (debug / parity use; slower).
+ * With default options and no records, the source points, directions and
+ * energies are first sampled by a separate full-warp pass into a workspace
+ * the context owns (32 bytes per history, at most 2^27 histories per pass,
+ * allocated on first use; a scan keeps its own); the arithmetic is the same,
+ * and when the workspace cannot be allocated the transport samples them
+ * itself, with the same results. */
 GDRR_API int gdrr_mc_project(gdrr_ctx* ctx, double angle_rad, uint32_t angle_index,
                              uint64_t n_photons, uint64_t seed, uint64_t history_offset,
                              int64_t* prim_dev, int64_t* scat_dev, uint64_t* stats_dev,

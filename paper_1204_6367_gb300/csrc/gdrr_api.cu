@@ -76,6 +76,8 @@ struct gdrr_ctx {
     size_t denoise_cap = 0;          // bytes
     int64_t* d_tune = nullptr;       // autotuner scratch tallies, 2 * nu * nv
     int* d_status = nullptr;         // timeouts of bounded device waits since the last gdrr_sync
+    float4* d_src = nullptr;         // source records of the lane form's source pass
+    uint64_t src_cap = 0;            // ... in histories
     // gdrr_project scratch: tallies, coarse tally and images, device scalars,
     // and the pinned host block the scalars come back through
     void* d_proj = nullptr;
@@ -95,6 +97,8 @@ struct gdrr_scan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t total = 0;
+    float4* d_src = nullptr;  // the scan's own source records (the graph captured the pointer)
+    uint64_t src_cap = 0;
     bool counted = false;     // included in ctx->n_scans
 };
 
@@ -388,7 +392,7 @@ int free_ctx(gdrr_ctx* c) {
     void* bufs[] = {c->d_vox, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_kcdf_pix,
                     c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr, c->d_wr_cols,
                     c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise, c->d_tune,
-                    c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells, c->d_status, c->d_proj};
+                    c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells, c->d_status, c->d_proj, c->d_src};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_proj) cudaFreeHost(c->h_proj);
@@ -734,10 +738,43 @@ static int launch_grid(const gdrr_ctx* ctx, uint64_t total, bool rec) {
     return grid < 1 ? 1 : (int)grid;
 }
 
+// Histories per segment of the lane form's source pass: MC_SRC_BYTES each,
+// at most 2^27 (4 GiB) per buffer.
+constexpr uint64_t SRC_MAX = 1ull << 27;
+
+// The source pass serves the lane form with default options and no records.
+static bool source_pass_applies(const gdrr_ctx* ctx, bool rec) {
+    return !rec && ctx->opt.nearest_voxel == 0 && ctx->opt.scatter_filter == 0 && ctx->opt.rayleigh_form_factor == 0 &&
+           ctx->opt.photon_pool <= 0;
+}
+
+// Grows a source-record buffer to min(total, SRC_MAX) histories.  When the
+// memory is not there the buffer stays empty and the transport samples the
+// sources inline (the same arithmetic, so the same results).
+static void ensure_src(cudaStream_t s, float4** buf, uint64_t* cap, uint64_t total) {
+    const uint64_t want = std::min(total, SRC_MAX);
+    if (*cap >= want) return;
+    if (*buf) {
+        cudaStreamSynchronize(s);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    if (cudaMalloc((void**)buf, want * MC_SRC_BYTES) == cudaSuccess) {
+        *cap = want;
+    } else {
+        *buf = nullptr;
+        cudaGetLastError();   // an allocation failure here is not an error of the call
+    }
+}
+
 // The transport launch: the pool form for default options without records
-// (when its pool fits the SM), else the lane form.
+// (when its pool fits the SM), else the lane form; the lane form with
+// default options and a source buffer runs in segments of at most src_cap
+// histories, each a source pass and a transport launch (the caller zeroes
+// the work counter for the first).
 static cudaError_t launch_transport(const gdrr_ctx* ctx, const McParams& p, uint64_t total, bool rec,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, const float4* src = nullptr, uint64_t src_cap = 0) {
     const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0 || p.ray_ff != 0;
     if (!rec && !gen && ctx->opt.photon_pool > 0) {
         int per_sm = mc_pool_occupancy_blocks(ctx->n_mat, ctx->opt.photon_pool);
@@ -748,6 +785,19 @@ static cudaError_t launch_transport(const gdrr_ctx* ctx, const McParams& p, uint
             if (grid > useful) grid = useful;
             return launch_mc_pool(p, ctx->opt.photon_pool, grid < 1 ? 1 : (int)grid, s);
         }
+    }
+    if (!rec && !gen && src && src_cap > 0) {
+        for (uint64_t seg0 = 0; seg0 < total; seg0 += src_cap) {
+            McParams q = p;
+            q.seg0 = seg0;
+            q.total = std::min(src_cap, total - seg0);
+            q.src = src;
+            cudaError_t e = launch_mc_source(q, s);
+            if (e == cudaSuccess && seg0 > 0) e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) e = launch_mc(q, ctx->opt.block_size, launch_grid(ctx, q.total, false), false, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     return launch_mc(p, ctx->opt.block_size, launch_grid(ctx, total, rec), rec, s);
 }
@@ -813,6 +863,10 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     p.scatter_filter = ctx->opt.scatter_filter;
     p.ray_ff = ctx->opt.rayleigh_form_factor;
     const bool rec = records_dev != nullptr;
+    if (source_pass_applies(ctx, rec)) {
+        ensure_src(ctx->stream, &ctx->d_src, &ctx->src_cap, total);
+        return cuda_err(launch_transport(ctx, p, total, rec, ctx->stream, ctx->d_src, ctx->src_cap));
+    }
     return cuda_err(launch_transport(ctx, p, total, rec, ctx->stream));
 }
 
@@ -907,6 +961,7 @@ GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* ang
         p.nearest_voxel = ctx->opt.nearest_voxel;
         p.scatter_filter = ctx->opt.scatter_filter;
         p.ray_ff = ctx->opt.rayleigh_form_factor;
+        if (source_pass_applies(ctx, false)) ensure_src(ctx->stream, &sc->d_src, &sc->src_cap, total);
         if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
         const size_t tally_bytes = (size_t)n_angles * ctx->geo.nu * ctx->geo.nv * sizeof(int64_t);
@@ -918,7 +973,7 @@ GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* ang
         if (ce == cudaSuccess && !stats_dev)
             ce = cudaMemsetAsync(sc->d_stats, 0, GDRR_NSTATS * sizeof(unsigned long long), cs);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), cs);
-        if (ce == cudaSuccess) ce = launch_transport(ctx, p, total, false, cs);
+        if (ce == cudaSuccess) ce = launch_transport(ctx, p, total, false, cs, sc->d_src, sc->src_cap);
         e = cudaStreamEndCapture(cs, &sc->graph);
         if (ce != cudaSuccess) { e = ce; break; }
         if (e != cudaSuccess) break;
@@ -948,6 +1003,7 @@ GDRR_API void gdrr_scan_destroy(gdrr_scan* scan) {
     if (scan->d_jobs) cudaFree(scan->d_jobs);
     if (scan->d_counter) cudaFree(scan->d_counter);
     if (scan->d_stats) cudaFree(scan->d_stats);
+    if (scan->d_src) cudaFree(scan->d_src);
     if (scan->counted && scan->ctx) --scan->ctx->n_scans;
     delete scan;
 }

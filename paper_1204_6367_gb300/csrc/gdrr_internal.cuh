@@ -109,6 +109,12 @@ struct McParams {
     int cshift, ncx, ncy;
     int* status;                   // NULL, or where a bounded loop that gave up records it
     int pool_tail, pool_park_min;  // pool form: tail width and parking minimum (0: defaults)
+    // the launch covers flattened histories seg0 .. seg0 + total - 1; with src
+    // != NULL their source points were sampled by the source pass: src[2 i],
+    // src[2 i + 1] = {px, py, pz, dx}, {dy, dz, E, job + 1 as bits, or 0 when
+    // the history ended there} for history seg0 + i
+    uint64_t seg0;
+    const float4* src;
 };
 
 // Bounded waits on flags that another CTA publishes (release store, acquire
@@ -167,6 +173,11 @@ struct RtParams {
 };
 
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s);
+// The source pass of the lane form (default options, no records): samples
+// the source point, direction and energy of histories p.seg0 .. p.seg0 +
+// p.total - 1 into p.src, and tallies and counts those that miss the box.
+cudaError_t launch_mc_source(const McParams& p, cudaStream_t s);
+constexpr size_t MC_SRC_BYTES = 32;    // bytes of one history's source record
 int mc_occupancy_blocks(int n_mat, int block, bool records);
 // The photon-pool form of the transport (default options, no records):
 // blocks of pool_threads() threads, per_thread photons per thread in the

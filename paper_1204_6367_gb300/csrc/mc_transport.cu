@@ -547,6 +547,30 @@ struct Lane {
         state = S_FLY;
     }
 
+    // Start history P.seg0 + i from the source pass's record: the state
+    // start() leaves (source block drawn, position at the box entry, energy
+    // tables pending), or nothing when the history already ended there.
+    __device__ __forceinline__ void start_src(const McParams& P, uint64_t i) {
+        const float4 b = __ldcs(P.src + 2 * i + 1);
+        const uint32_t j1 = __float_as_uint(b.w);
+        if (j1 == 0u) return;
+        const float4 a = __ldcs(P.src + 2 * i);
+        const uint64_t g = P.seg0 + i;
+        gidx = g;
+        job = (int)j1 - 1;
+        const Job& J = P.jobs[job];
+        rs.init(J.angle_index, J.hid_offset + (g - J.first));
+        rs.blk = 1;
+        nsteps = 0;
+        ngath = 0;
+        scattered = 0;
+        px = a.x; py = a.y; pz = a.z;
+        dx = a.w; dy = b.x; dz = b.y;
+        e = b.z;
+        if (defer_e) need_e = true; else set_energy(P, e);
+        state = S_FLY;
+    }
+
     // One Woodcock free flight and the real/virtual decision at its end.
     __device__ __forceinline__ void step(const McParams& P, unsigned long long* cnt) {
         if ((int)nsteps >= P.max_steps) {
@@ -780,7 +804,10 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
                     const unsigned want = (unsigned)__popc(need);
                     const unsigned take = want < avail ? want : avail;
                     const unsigned rank = (unsigned)__popc(need & ((1u << lane) - 1u));
-                    if (((need >> lane) & 1u) && rank < take) L.start(P, pool_next + rank, cnt);
+                    if (((need >> lane) & 1u) && rank < take) {
+                        if (!REC && !GEN && P.src) L.start_src(P, pool_next + rank);
+                        else L.start(P, P.seg0 + pool_next + rank, cnt);
+                    }
                     pool_next += take;
                     need = __ballot_sync(FULL, L.state == S_DEAD);
                 }
@@ -797,6 +824,41 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
     atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)L.c_steps);
     atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)L.c_virt);
     atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)L.c_skip);
+    __syncthreads();
+    for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
+        if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
+}
+
+// ---------------------------------------------------------------------------
+// The source pass: Lane::start for every history of the launch, on full
+// warps (one history per thread), apart from the transport's service
+// batches.  A history that misses the box is tallied and counted here; the
+// others leave their state (position at the box entry, direction, energy)
+// for Lane::start_src.  The arithmetic is start()'s, call for call, so the
+// transport's draws, decisions and tallies do not change.
+template <int NM>
+__global__ void __launch_bounds__(256) mc_source_kernel(const McParams P, float4* __restrict__ out) {
+    __shared__ unsigned long long cnt[GDRR_NSTATS];
+    for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x) cnt[i] = 0ull;
+    __syncthreads();
+    Lane<NM, false, false> L;
+    L.coef = nullptr;
+    L.stride = 0;
+    L.defer_e = true;
+    L.need_e = false;
+    L.c_steps = 0; L.c_virt = 0; L.c_skip = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        L.state = S_DEAD;
+        L.start(P, P.seg0 + i, cnt);
+        float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), b = a;
+        if (L.state == S_FLY) {
+            a = make_float4(L.px, L.py, L.pz, L.dx);
+            b = make_float4(L.dy, L.dz, L.e, __uint_as_float((uint32_t)L.job + 1u));
+        }
+        __stcs(out + 2 * i, a);
+        __stcs(out + 2 * i + 1, b);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
         if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
@@ -1009,7 +1071,7 @@ __global__ void __launch_bounds__(POOL_THREADS, 3) mc_pool_kernel(const McParams
                 const unsigned rank = (unsigned)__popc(nb & ((1u << lane) - 1u));
                 if (need && rank < take) {
                     pl.bind(L, sl, lane);
-                    L.start(P, pool_next + rank, cnt);
+                    L.start(P, P.seg0 + pool_next + rank, cnt);
                     if (L.state == S_FLY) {                 // else it missed the box and was tallied: retry
                         pl.store(L, sl, lane);
                         pl.push(qFly, lane, sl);
@@ -1276,6 +1338,22 @@ int mc_pool_occupancy_blocks(int n_mat, int per_thread) {
     if (n_mat <= 2) return pool_occupancy_t<2>(K);
     if (n_mat <= 4) return pool_occupancy_t<4>(K);
     return pool_occupancy_t<8>(K);
+}
+
+cudaError_t launch_mc_source(const McParams& p, cudaStream_t s) {
+    if (!p.src || p.total == 0) return cudaErrorInvalidValue;
+    int dev = 0, n_sm = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = (p.total + 255) / 256;
+    const uint64_t cap = (uint64_t)n_sm * 8;
+    const int grid = (int)(blocks < cap ? blocks : cap);
+    float4* out = const_cast<float4*>(p.src);
+    if (p.n_mat <= 2) mc_source_kernel<2><<<grid, 256, 0, s>>>(p, out);
+    else if (p.n_mat <= 4) mc_source_kernel<4><<<grid, 256, 0, s>>>(p, out);
+    else mc_source_kernel<8><<<grid, 256, 0, s>>>(p, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s) {
