@@ -115,6 +115,33 @@ def test_split_and_accumulate(gd, small):
         assert torch.equal(full[0], a_p) and torch.equal(full[1], a_s)
 
 
+def test_source_pass_segments_and_inline_start_agree(gd, small):
+    """With default options the transport starts histories from the source
+    pass's records, in passes of at most 2^27 histories.  A call of 1.5e8
+    histories takes two passes; the same histories split at another point
+    (two calls) and a call whose histories start inline (records requested)
+    give the same tallies and counters."""
+    n, k = 150_000_000, 90_000_000
+    with gd.Context(small) as ctx:
+        s_full = torch.zeros(gd.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+        full = gd.gdrr_mc_project(ctx, n, 5, stats=s_full)
+        s_split = torch.zeros(gd.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+        a_p, a_s = gd.gdrr_mc_project(ctx, k, 5, stats=s_split)
+        gd.gdrr_mc_project(ctx, n - k, 5, history_offset=k, prim=a_p, scat=a_s, stats=s_split)
+        gd.gdrr_sync(ctx)
+        assert torch.equal(full[0], a_p) and torch.equal(full[1], a_s)
+        assert torch.equal(s_full, s_split)
+        # inline starts (the records path) on a window of the same histories
+        m = 200_000
+        s_w = torch.zeros(gd.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+        w_p, w_s = gd.gdrr_mc_project(ctx, m, 5, history_offset=k - m // 2, stats=s_w)
+        s_r = torch.zeros(gd.GDRR_NSTATS, dtype=torch.int64, device="cuda")
+        rec = torch.zeros(m * gd.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        r_p, r_s = gd.gdrr_mc_project(ctx, m, 5, history_offset=k - m // 2, stats=s_r, records=rec)
+        gd.gdrr_sync(ctx)
+        assert torch.equal(w_p, r_p) and torch.equal(w_s, r_s) and torch.equal(s_w, s_r)
+
+
 def test_zero_photons_is_a_noop(gd, small):
     with gd.Context(small) as ctx:
         p, s = gd.new_tallies(ctx)
