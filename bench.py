@@ -160,20 +160,25 @@ def kernel_traffic(cell_shift=None):
     return int(v["bytes_per_launch"]) if v else None
 
 
-ISSUE_CONFIG_KEYS = ("block_size", "batch_min", "hist_per_thread")
+# The instruction count per flight depends on batch_min (how often the warp
+# serves its waiting lanes) and is keyed to the block size as well; the
+# histories a lane claims at a time (hist_per_thread) leave it unchanged
+# (measured: 266.14 and 266.12 per flight at 1 and 8), so a line's third
+# field is informational.
+ISSUE_CONFIG_KEYS = ("block_size", "batch_min")
 
 
 def kernel_inst_per_step(cell_shift=None, config=None):
     """Thread instructions the transport executes per Woodcock free flight
     (ncu smsp__thread_inst_executed.sum / free flights of the same launch)
-    from the record's line for the launch configuration given (block_size,
-    batch_min, hist_per_thread; config None: the first line), or None for
-    another kernel source, other macro cells or an unmeasured configuration."""
+    from the record's line for the launch configuration given (block_size
+    and batch_min; config None: the first line), or None for another kernel
+    source, other macro cells or an unmeasured configuration."""
     v = profile_record("mc_kernel_torso2mm_issue.txt", cell_shift)
     if not v:
         return None
     for c in v["configs"]:
-        if config is None or [str(config.get(k)) for k in ISSUE_CONFIG_KEYS] == c[:3]:
+        if config is None or [str(config.get(k)) for k in ISSUE_CONFIG_KEYS] == c[:2]:
             return float(c[3])
     return None
 
@@ -326,10 +331,12 @@ def run_ours(args):
     # machine ceilings measured on this GPU: random 8-byte L2 gathers, FP32 FMA
     l2_probe_gbs = gdrr.gdrr_probe_l2_gather(32 << 20)
     fp32_probe_tflops = gdrr.gdrr_probe_fp32()
-    # kernels per step: ray trace, transport, 3 finalisations, binning, the
-    # scalars, the denoiser (one cooperative launch, else one per iteration +
-    # 2), upsampling, noise
-    launches_per_step = 9 + (1 if res["denoise_fused"] else iters + 2)
+    # kernels per step: ray trace, 3 finalisations, binning, the scalars,
+    # upsampling, noise (8); the transport (the pool form: one launch; the
+    # lane form: a source pass and a transport launch per 2^27 histories);
+    # the denoiser (one cooperative launch, else one per iteration + 2)
+    transport_launches = 1 if tuned["photon_pool"] > 0 else 2 * -(-n_hist // (1 << 27))
+    launches_per_step = 8 + transport_launches + (1 if res["denoise_fused"] else iters + 2)
 
     clocks = ClockSampler(dev)
     if world > 1:
