@@ -216,6 +216,27 @@ def dist_env():
     return world, rank, local
 
 
+def rank_angle(rank, world):
+    """Gantry angle of a rank's projection: the ranks split one scan's orbit,
+    one angle each (independent histories, no data-path exchange)."""
+    return 2.0 * math.pi * rank / max(world, 1)
+
+
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values: the job's time is its slowest rank's."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(n_hist, world, steps, tot_ms):
+    """Whole-job histories/s: every rank's histories over the slowest rank's time."""
+    return n_hist * world * steps / (tot_ms / 1e3)
+
+
 def cpu_oracle_rate(prob, target_s, threads, seed=1, first=400000):
     """Histories/s of the CPU oracle (FP32 transport, the parity reference) on
     a bounded sample of the same workload: first history ids of the stream."""
@@ -287,7 +308,7 @@ def run_ours(args):
     gdrr.lib()
     prob = inputs.torso_problem()
     n_hist = int(args.histories)
-    angle = 2.0 * math.pi * rank / max(world, 1)     # one projection angle per rank
+    angle = rank_angle(rank, world)                  # one projection angle per rank
     seed = 1
     stream = torch.cuda.current_stream()
     ctx = gdrr.Context(prob, stream)
@@ -356,12 +377,7 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(step_ms), world)
 
     # end to end through the public API: inputs from pinned host memory
     # (gdrr_create stages phantom and tables), one projection, results read
@@ -664,7 +680,7 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    value = n_hist * world * args.steps / (tot_ms / 1e3)
+    value = job_rate(n_hist, world, args.steps, tot_ms)
     traffic = kernel_traffic(tuned["cell_shift"])
 
     # The transport on its algorithmic unit (40 B of voxel data per free

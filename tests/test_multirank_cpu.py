@@ -58,3 +58,37 @@ def test_history_shards_sum_to_single_run(tmp_path):
     for r in range(world):
         ap, _, _, _ = oracle.mc_run(prob, 3000, seed=13, phi=0.5 * r, angle_index=r)
         np.testing.assert_array_equal(np.load(tmp_path / f"angle{r}.npy"), ap)
+
+
+def _bench_rank_main(rank, world, port, out_dir):
+    # bench.py's rank plumbing with gloo on CPU: each rank's angle, the job
+    # time as the slowest rank's, the whole-job rate from it
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    os.environ["WORLD_SIZE"] = str(world)
+    os.environ["RANK"] = str(rank)
+    os.environ["LOCAL_RANK"] = str(rank)
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    w, r, local = bench.dist_env()
+    dist.init_process_group("gloo", rank=r, world_size=w)
+    step_ms = 10.0 + 5.0 * r                          # rank 1 is the slower one
+    tot = bench.max_over_ranks(step_ms, w, device="cpu")
+    rate = bench.job_rate(1000, w, 3, tot)
+    np.save(os.path.join(out_dir, f"bench{r}.npy"), np.array([bench.rank_angle(r, w), tot, rate, local]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_rank_plumbing(tmp_path):
+    world = 2
+    mp.start_processes(_bench_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       start_method="spawn", join=True)
+    got = [np.load(tmp_path / f"bench{r}.npy") for r in range(world)]
+    angles = [g[0] for g in got]
+    assert angles == [0.0, np.pi]                     # one projection angle per rank, an orbit split
+    for r, g in enumerate(got):
+        assert g[1] == 15.0                           # every rank reports the slowest rank's time
+        assert g[2] == pytest.approx(1000 * 2 * 3 / 0.015)   # all ranks' histories over that time
+        assert g[3] == r
