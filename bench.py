@@ -501,11 +501,12 @@ def run_ours(args):
         for name, kw in (("mc_nearest_voxel_ms", dict(nearest_voxel=1)),
                          ("mc_first_order_compton_ms", dict(scatter_filter=1)),
                          ("mc_rayleigh_form_factor_ms", dict(rayleigh_form_factor=1)),
-                         # the macro-cell test of virtual collisions: off, and cells of 4 and 16 voxels
-                         # (the default is 8); tallies are identical in every case
+                         # the macro-cell test of virtual collisions: off, and cells of 8 and 16 mm
+                         # (4 and 8 voxels; the default is 4 mm, 2 voxels); tallies are identical
+                         # in every case
                          ("mc_no_cell_bound_ms", dict(cell_shift=-1)),
-                         ("mc_cells_4_ms", dict(cell_shift=2)),
-                         ("mc_cells_16_ms", dict(cell_shift=4))):
+                         ("mc_cells_8mm_ms", dict(cell_shift=2)),
+                         ("mc_cells_16mm_ms", dict(cell_shift=3))):
             gdrr.gdrr_set_options(ctx, **kw)
             vp, vs = gdrr.gdrr_mc_project(ctx, n_hist, seed, angle)
             torch.cuda.synchronize()

@@ -157,8 +157,8 @@ typedef struct {
                                   coefficient); 0: Thomson (1 + cos^2), the paper's
                                   default reading [0]                                 */
     int32_t cell_shift;        /* macro cells of 2^cell_shift voxels per edge, 1..6;
-                                  -1: none; [0: cells of about 8 mm, cell_shift =
-                                  round(log2(8 mm / smallest voxel edge)) in 1..6].
+                                  -1: none; [0: cells of about 4 mm, cell_shift =
+                                  round(log2(4 mm / smallest voxel edge)) in 1..6].
                                   Before gathering the eight corner voxels of
                                   a tentative collision, the transport compares it with
                                   a bound on mu over the macro cell that holds the

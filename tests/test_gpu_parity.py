@@ -656,8 +656,9 @@ def test_cell_bound_skips_most_virtual_collisions_in_the_torso(gd):
 
 
 def test_cell_shift_option_checks(gd, small):
-    # the default cells are about 8 mm: 2 voxels of 4 mm, 4 of 2 mm, 8 of 1 mm
-    for vox, shift in ((4.0, 1), (2.0, 2), (1.0, 3), (0.5, 4)):
+    # the default cells are about 4 mm: 2 voxels of 2 mm, 4 of 1 mm, 8 of 0.5 mm
+    # (at least 2 voxels: 8 mm at 4 mm voxels)
+    for vox, shift in ((4.0, 1), (2.0, 1), (1.0, 2), (0.5, 3)):
         prob = inputs.uniform_slab_problem(nx=8, ny=8, nz=8, vox=vox)
         with gd.Context(prob) as ctx:
             assert gd.gdrr_get_options(ctx)["cell_shift"] == shift
