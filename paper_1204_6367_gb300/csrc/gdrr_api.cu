@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -76,6 +77,7 @@ struct gdrr_ctx {
     size_t denoise_cap = 0;          // bytes
     int64_t* d_tune = nullptr;       // autotuner scratch tallies, 2 * nu * nv
     int* d_status = nullptr;         // timeouts of bounded device waits since the last gdrr_sync
+    void* d_arena = nullptr;         // one allocation holding the tables and counters above
     float4* d_src = nullptr;         // source records of the lane form's source pass
     uint64_t src_cap = 0;            // ... in histories
     // gdrr_project scratch: tallies, coarse tally and images, device scalars,
@@ -126,6 +128,27 @@ int upload(T** dst, const T* src, size_t n, cudaStream_t s) {
     if (n) TRY_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
     return GDRR_OK;
 }
+
+// The context's small tables and counters in one device allocation, staged
+// in one host buffer and copied once: each piece starts on a 256-byte
+// boundary; pieces without source data are zero.
+struct Arena {
+    std::vector<char> host;
+    std::vector<std::function<void(char*)>> bind;
+    template <typename T>
+    void add(T** dst, const T* src, size_t n) {
+        const size_t off = (host.size() + 255) / 256 * 256;
+        host.resize(off + std::max<size_t>(n, 1) * sizeof(T), 0);
+        if (src && n) memcpy(host.data() + off, src, n * sizeof(T));
+        bind.push_back([dst, off](char* base) { *dst = reinterpret_cast<T*>(base + off); });
+    }
+    int commit(void** base, cudaStream_t s) {
+        TRY_CUDA(cudaMalloc(base, std::max<size_t>(host.size(), 1)));
+        TRY_CUDA(cudaMemcpyAsync(*base, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+        for (auto& b : bind) b(static_cast<char*>(*base));
+        return GDRR_OK;
+    }
+};
 
 // Device staging of the voxel phantom: one thread per voxel (x fastest)
 // checks its material index and density, raises its block's maximum density
@@ -232,17 +255,27 @@ int build_cells(gdrr_ctx* c, int shift) {
 int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, std::vector<double>& rho_max) {
     const int64_t nvox = (int64_t)ph.nx * ph.ny * ph.nz;
     cudaStream_t s = c->stream;
-    uint8_t* d_mat = nullptr;
+    // the inputs staged in one temporary allocation: densities, counters,
+    // material indices (each on a 256-byte boundary)
+    const size_t den_bytes = (size_t)nvox * sizeof(float);
+    const size_t aux_off = (den_bytes + 255) / 256 * 256;
+    const size_t mat_off = aux_off + 256 * (size_t)((sizeof(unsigned int) * (1 + c->n_mat) + 255) / 256);
+    char* d_tmp = nullptr;
     float* d_den = nullptr;
     unsigned int* d_aux = nullptr;
+    uint8_t* d_mat = nullptr;
     int rc = GDRR_OK;
     std::vector<unsigned int> aux(1 + c->n_mat, 0u);
     do {
         if ((rc = cuda_err(cudaMalloc((void**)&c->d_vox, n_rec * sizeof(uint2))))) break;
         if ((rc = cuda_err(cudaMemsetAsync(c->d_vox, 0, n_rec * sizeof(uint2), s)))) break;
-        if ((rc = upload(&d_mat, ph.material, (size_t)nvox, s))) break;
-        if ((rc = upload(&d_den, ph.density, (size_t)nvox, s))) break;
-        if ((rc = upload(&d_aux, aux.data(), aux.size(), s))) break;
+        if ((rc = cuda_err(cudaMalloc((void**)&d_tmp, mat_off + (size_t)nvox)))) break;
+        d_den = reinterpret_cast<float*>(d_tmp);
+        d_aux = reinterpret_cast<unsigned int*>(d_tmp + aux_off);
+        d_mat = reinterpret_cast<uint8_t*>(d_tmp + mat_off);
+        if ((rc = cuda_err(cudaMemcpyAsync(d_den, ph.density, den_bytes, cudaMemcpyHostToDevice, s)))) break;
+        if ((rc = cuda_err(cudaMemcpyAsync(d_mat, ph.material, (size_t)nvox, cudaMemcpyHostToDevice, s)))) break;
+        if ((rc = cuda_err(cudaMemsetAsync(d_aux, 0, aux.size() * sizeof(unsigned int), s)))) break;
         const int block = 256;
         stage_voxels_kernel<<<(unsigned)((nvox + block - 1) / block), block, 0, s>>>(
             d_mat, d_den, ph.nx, ph.ny, ph.nz, c->n_mat, c->bsy, c->bsz, c->d_vox, d_aux);
@@ -251,9 +284,7 @@ int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, std::vector
                                            cudaMemcpyDeviceToHost, s)))) break;
         if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
     } while (0);
-    cudaFree(d_mat);
-    cudaFree(d_den);
-    cudaFree(d_aux);
+    if (d_tmp) cudaFree(d_tmp);
     if (rc) return rc;
     if (aux[0]) return GDRR_ERR_INVALID_ARG;
     rho_max.assign(c->n_mat, 0.0);
@@ -390,10 +421,8 @@ int default_cell_shift(const gdrr_ctx* c) {
 int free_ctx(gdrr_ctx* c) {
     if (!c) return GDRR_OK;
     cudaStreamSynchronize(c->stream);
-    void* bufs[] = {c->d_vox, c->d_tab, c->d_major, c->d_resp, c->d_bin_e, c->d_kcdf_pix,
-                    c->d_guide_pix, c->d_kcdf_e, c->d_guide_e, c->d_wnorm, c->d_mu_rt, c->d_wr, c->d_wr_cols,
-                    c->d_counter, c->d_stats, c->d_flag, c->d_jobs, c->d_denoise, c->d_tune,
-                    c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells, c->d_status, c->d_proj, c->d_src};
+    void* bufs[] = {c->d_vox, c->d_arena, c->d_jobs, c->d_denoise, c->d_tune,
+                    c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells, c->d_proj, c->d_src};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_proj) cudaFreeHost(c->h_proj);
@@ -566,24 +595,25 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         std::vector<double> wnorm(npix);
         for (int i = 0; i < npix; ++i) wnorm[i] = bowtie->fluence[i] / fsum;
 
-        if ((rc = upload(&c->d_tab, tab.data(), tab.size(), s))) break;
-        if ((rc = upload(&c->d_major, major.data(), major.size(), s))) break;
-        if ((rc = upload(&c->d_resp, dt.response, (size_t)dt.n_energies, s))) break;
-        if ((rc = upload(&c->d_bin_e, bin_e.data(), bin_e.size(), s))) break;
+        Arena ar;
+        ar.add(&c->d_tab, tab.data(), tab.size());
+        ar.add(&c->d_major, major.data(), major.size());
+        ar.add(&c->d_resp, dt.response, (size_t)dt.n_energies);
+        ar.add(&c->d_bin_e, bin_e.data(), bin_e.size());
         const std::vector<uint32_t> kcdf_pix = kcdf_of(cdf_pix);
-        if ((rc = upload(&c->d_kcdf_pix, kcdf_pix.data(), kcdf_pix.size(), s))) break;
-        if ((rc = upload(&c->d_guide_pix, guide_pix.data(), guide_pix.size(), s))) break;
-        if ((rc = upload(&c->d_kcdf_e, kcdf_e.data(), kcdf_e.size(), s))) break;
-        if ((rc = upload(&c->d_guide_e, guide_e.data(), guide_e.size(), s))) break;
-        if ((rc = upload(&c->d_wnorm, wnorm.data(), wnorm.size(), s))) break;
-        if ((rc = upload(&c->d_mu_rt, mu_rt.data(), mu_rt.size(), s))) break;
-        if ((rc = upload(&c->d_wr, wr.data(), wr.size(), s))) break;
-        if (e_col && (rc = upload(&c->d_wr_cols, wr_cols.data(), wr_cols.size(), s))) break;
-        if ((rc = cuda_err(cudaMalloc((void**)&c->d_counter, sizeof(unsigned long long))))) break;
-        if ((rc = cuda_err(cudaMalloc((void**)&c->d_stats, GDRR_NSTATS * sizeof(unsigned long long))))) break;
-        if ((rc = cuda_err(cudaMalloc((void**)&c->d_flag, sizeof(int))))) break;
-        if ((rc = cuda_err(cudaMalloc((void**)&c->d_status, sizeof(int))))) break;
-        if ((rc = cuda_err(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream)))) break;
+        ar.add(&c->d_kcdf_pix, kcdf_pix.data(), kcdf_pix.size());
+        ar.add(&c->d_guide_pix, guide_pix.data(), guide_pix.size());
+        ar.add(&c->d_kcdf_e, kcdf_e.data(), kcdf_e.size());
+        ar.add(&c->d_guide_e, guide_e.data(), guide_e.size());
+        ar.add(&c->d_wnorm, wnorm.data(), wnorm.size());
+        ar.add(&c->d_mu_rt, mu_rt.data(), mu_rt.size());
+        ar.add(&c->d_wr, wr.data(), wr.size());
+        if (e_col) ar.add(&c->d_wr_cols, wr_cols.data(), wr_cols.size());
+        ar.add(&c->d_counter, (const unsigned long long*)nullptr, 1);
+        ar.add(&c->d_stats, (const unsigned long long*)nullptr, GDRR_NSTATS);
+        ar.add(&c->d_flag, (const int*)nullptr, 1);
+        ar.add(&c->d_status, (const int*)nullptr, 1);
+        if ((rc = ar.commit(&c->d_arena, s))) break;
         // the host vectors above die at return: finish the copies first
         if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
     } while (0);
