@@ -259,6 +259,28 @@ def test_full_size_torso_sampled_windows(gd):
             np.testing.assert_array_equal(ws.cpu().numpy(), ots)
 
 
+def test_full_size_1mm_torso_sampled_windows(gd):
+    # The 1 mm torso (512 x 512 x 256 voxels: 537 MB of records, beyond L2)
+    # at 1e8 histories in the default launch configuration and macro cells:
+    # history windows of the full run's streams (start, middle, end) equal
+    # the oracle bit for bit, and the full run equals its split parts.
+    prob = inputs.torso_problem(vox=1.0)
+    n = 100_000_000
+    with gd.Context(prob) as ctx:
+        assert gd.gdrr_get_options(ctx)["cell_shift"] == 2          # 4 mm cells of 1 mm voxels
+        full_p, full_s = gd.gdrr_mc_project(ctx, n, 3)
+        parts_p, parts_s = gd.new_tallies(ctx)
+        for lo, hi in ((0, 61_000_000), (61_000_000, n)):
+            gd.gdrr_mc_project(ctx, hi - lo, 3, history_offset=lo, prim=parts_p, scat=parts_s)
+        gd.gdrr_sync(ctx)
+        assert torch.equal(full_p, parts_p) and torch.equal(full_s, parts_s)
+        for off in (0, 42_424_242, n - 30_000):
+            wp, ws = gd.gdrr_mc_project(ctx, 30_000, 3, history_offset=off)
+            otp, ots, _, _ = oracle.mc_run(prob, 30_000, seed=3, history_offset=off, threads=NTH)
+            np.testing.assert_array_equal(wp.cpu().numpy(), otp)
+            np.testing.assert_array_equal(ws.cpu().numpy(), ots)
+
+
 def _pooled(chunks):
     """Per-pixel estimate and variance of a tally summed over k independent
     chunks.  A tally is a compound-Poisson sum of deposits, Var = R * mean,
