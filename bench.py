@@ -407,8 +407,8 @@ def run_ours(args):
                 for h, key in zip(host_out, ("P", "P_hat", "S_hat", "S", "N")):
                     h.copy_(o[key], non_blocking=True)
                 torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        e2e = {"value": n_hist * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)   # the slowest rank's
+        e2e = {"value": job_rate(n_hist, world, 1, 1e3 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "s_per_projection": e2e_s}
 
     # multi-angle scan: 64 angles over 360 degrees with per-angle budgets
