@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-fdk", action="store_true", help="skip the 360-view FDK reconstruction timing")
     ap.add_argument("--mc-config", default=None, metavar="BLOCK,BATCH_MIN,HIST_PER_THREAD",
                     help="fix the transport's launch configuration (lane form) instead of autotuning it")
+    ap.add_argument("--local-majorant", type=int, default=None, metavar="CELL_SHIFT",
+                    help="run the transport with the local-majorant option (cells of 2^CELL_SHIFT voxels) "
+                         "instead of the paper's global Woodcock majorant, to profile the option")
     return ap.parse_args()
 
 
@@ -325,6 +328,8 @@ def run_ours(args):
     def step():
         return gdrr.project(ctx, n_hist, seed, angle, bin_factor=4, beta=0.02, iters=iters, stats=stats, out=out)
 
+    if args.local_majorant is not None:
+        gdrr.gdrr_set_options(ctx, local_majorant=1, cell_shift=args.local_majorant)
     # launch configuration from the project's autotuner, or the one given
     # (tallies do not depend on it)
     if args.mc_config:
@@ -506,7 +511,14 @@ def run_ours(args):
                          # in every case
                          ("mc_no_cell_bound_ms", dict(cell_shift=-1)),
                          ("mc_cells_8mm_ms", dict(cell_shift=2)),
-                         ("mc_cells_16mm_ms", dict(cell_shift=3))):
+                         ("mc_cells_16mm_ms", dict(cell_shift=3)),
+                         # delta tracking with local majorants (an option beside the paper's
+                         # global one): the cell bounds of 32 mm (default) or 16 mm cells as
+                         # the flights' majorant, lane form, batch_min 24; same expected images
+                         ("mc_local_majorant_32mm_ms", dict(local_majorant=1, cell_shift=4, batch_min=24,
+                                                            photon_pool=-1)),
+                         ("mc_local_majorant_16mm_ms", dict(local_majorant=1, cell_shift=3, batch_min=24,
+                                                            photon_pool=-1))):
             gdrr.gdrr_set_options(ctx, **kw)
             vp, vs = gdrr.gdrr_mc_project(ctx, n_hist, seed, angle)
             torch.cuda.synchronize()
@@ -723,6 +735,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "histories_per_projection": n_hist, "angle_rad": angle,
                    "woodcock_steps_per_projection": steps_per_proj, "l2": "256 MB buffer written between timed steps",
+                   "tracking": "global majorant (Woodcock, Section 2.4)" if not tuned.get("local_majorant")
+                               else f"local majorants, cells of 2^{tuned['cell_shift']} voxels (option)",
                    "parallelism": f"one projection angle per GPU x{world}"},
         "roofline": roofline,
         "cpu_baseline": cpu,

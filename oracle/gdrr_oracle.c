@@ -132,7 +132,7 @@ static int orc_cdf_search(const double* cdf, int n, double xi) {
 /* ------------------------------------------------------------------------ */
 /* Derived per-projection quantities in both precisions. */
 #define GEO_FIELDS(T)                                                         \
-    T S[3], n[3], P[3], eu[3], ev[3], lo[3], hi[3], ivox[3];                  \
+    T S[3], n[3], P[3], eu[3], ev[3], lo[3], hi[3], ivox[3], vox[3];          \
     T hu, hv, du, dv, idu, idv, e0, inv_de, r0, inv_dr, e_cut;                \
     T* tab;   /* [m][k][e] mm^-1 per g/cm^3 */                                \
     T* major; /* [e] majorant node values, mm^-1 */                           \
@@ -154,6 +154,10 @@ typedef struct {
     double* cdf_e_cols;   /* [nu][n_bins] when the spectrum depends on the column */
     orc_geo_f gf;
     orc_geo_d gd;
+    /* local majorants: cells per axis and the per-cell, per-material largest
+     * density (orc_lm_build), NULL without the option */
+    int nc[3];
+    float* lm_rho;
 } orc_ctx;
 
 static double* orc_build_cdf(const double* w, int n) {
@@ -191,6 +195,43 @@ static void orc_build_major(const orc_problem* p, const float* tab, float* major
         }
         major[e] = (float)(mx * (1.0 + 1e-5));
     }
+}
+
+/* The macro cells of the local-majorant option.  Cell k of an axis (2^s
+ * voxels per edge, s = cell_shift) holds the points whose lower trilinear
+ * corner, max(floor((x - lo) / vox - 1/2), 0), has index k 2^s ... (k + 1) 2^s
+ * - 1; the eight corners of such a point lie among the voxels k 2^s ...
+ * (k + 1) 2^s, which is the cover whose largest density per material the
+ * table keeps.  Every corner term rho_c mu(m_c, E) of the mixture is then at
+ * most max_m rho_max(cell, m) mu(m, E), and so is the mixture (its weights sum
+ * to one).  Written as that definition: for each cell, a scan of its cover. */
+static int orc_lm_build(orc_ctx* c) {
+    const orc_problem* p = c->p;
+    const int s = p->cell_shift;
+    if (s < 0 || s > 10) return -1;
+    for (int a = 0; a < 3; ++a) c->nc[a] = ((c->dims[a] - 1) >> s) + 1;
+    size_t ncell = (size_t)c->nc[0] * c->nc[1] * c->nc[2];
+    c->lm_rho = (float*)calloc(ncell * (size_t)p->n_mat, sizeof(float));
+    if (!c->lm_rho) return -1;
+    for (int kz = 0; kz < c->nc[2]; ++kz)
+        for (int ky = 0; ky < c->nc[1]; ++ky)
+            for (int kx = 0; kx < c->nc[0]; ++kx) {
+                float* r = c->lm_rho + (((size_t)kz * c->nc[1] + ky) * c->nc[0] + kx) * p->n_mat;
+                int k[3] = {kx, ky, kz}, v0[3], v1[3];
+                for (int a = 0; a < 3; ++a) {
+                    v0[a] = k[a] << s;
+                    v1[a] = (k[a] + 1) << s;
+                    if (v1[a] > c->dims[a] - 1) v1[a] = c->dims[a] - 1;
+                }
+                for (int z = v0[2]; z <= v1[2]; ++z)
+                    for (int y = v0[1]; y <= v1[1]; ++y)
+                        for (int x = v0[0]; x <= v1[0]; ++x) {
+                            size_t v = (size_t)x + (size_t)p->nx * ((size_t)y + (size_t)p->ny * z);
+                            float rho = p->density[v];
+                            if (rho > r[p->material[v]]) r[p->material[v]] = rho;
+                        }
+            }
+    return 0;
 }
 
 static int orc_ctx_init(orc_ctx* c, const orc_problem* p, double phi) {
@@ -234,6 +275,8 @@ static int orc_ctx_init(orc_ctx* c, const orc_problem* p, double phi) {
         c->gf.eu[k] = (float)eu[k]; c->gf.ev[k] = (float)ev[k];
         c->gf.lo[k] = (float)(-half); c->gf.hi[k] = (float)half;
         c->gf.ivox[k] = (float)(1.0 / vox[k]);
+        c->gd.vox[k] = vox[k];
+        c->gf.vox[k] = (float)vox[k];
     }
     /* The source must lie outside the box and the whole box on the source
      * side of the imager plane, so that a photon leaving the box towards the
@@ -327,6 +370,7 @@ static int orc_ctx_init(orc_ctx* c, const orc_problem* p, double phi) {
         c->gd.ff_idx = 1.0 / p->ff_dx;
         c->gf.ff_idx = (float)(1.0 / p->ff_dx);
     }
+    if (p->local_majorant && orc_lm_build(c)) return -1;
     return 0;
 }
 
@@ -336,6 +380,7 @@ static void orc_ctx_free(orc_ctx* c) {
     free(c->gf.resp); free(c->gd.resp); free(c->gf.bin_e); free(c->gd.bin_e);
     free(c->gf.ff_s); free(c->gd.ff_s); free(c->gf.ff_a); free(c->gd.ff_a);
     free(c->gf.ff_g); free(c->gd.ff_g);
+    free(c->lm_rho);
 }
 
 int orc_majorant(const orc_problem* p, float* node_out) {
@@ -350,6 +395,7 @@ int orc_majorant(const orc_problem* p, float* node_out) {
 /* The history, once per precision. */
 #define REAL float
 #define ORC_MAX_BLOCKS (1u << 24)   /* Philox blocks per history after which samplers stop rejecting */
+#define ORC_LM_MARGIN 1.0009765625  /* local-majorant bounds are raised by 2^-10 */
 
 #define FN(name) name##_f32
 #define GEO(x) (c->gf.x)
@@ -381,6 +427,28 @@ int orc_majorant(const orc_problem* p, float* node_out) {
 #undef SQRTR
 #undef FLOORR
 #undef LLRINTR
+
+int orc_lm_cells(const orc_problem* p, float* out) {
+    orc_problem q = *p;
+    q.local_majorant = 1;
+    orc_ctx c;
+    if (orc_ctx_init(&c, &q, 0.0)) { orc_ctx_free(&c); return -1; }
+    memcpy(out, c.lm_rho, sizeof(float) * (size_t)c.nc[0] * c.nc[1] * c.nc[2] * (size_t)p->n_mat);
+    orc_ctx_free(&c);
+    return 0;
+}
+
+int orc_lm_walk(const orc_problem* p, int precision, const double pos[3], const double dir[3], double e,
+                double tau, double out[5]) {
+    if (precision != 32 && precision != 64) return -1;
+    orc_problem q = *p;
+    q.local_majorant = 1;
+    orc_ctx c;
+    if (orc_ctx_init(&c, &q, 0.0)) { orc_ctx_free(&c); return -1; }
+    int hit = precision == 64 ? lm_walk_once_f64(&c, pos, dir, e, tau, out) : lm_walk_once_f32(&c, pos, dir, e, tau, out);
+    orc_ctx_free(&c);
+    return hit;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Samplers on their own (for the angular-distribution pins). */

@@ -61,6 +61,13 @@ typedef struct {
     int n_ff;
     double ff_dx;
     const float* ff;
+    /* Free-flight majorant: 0 the global one of Woodcock tracking (Section 2.4);
+     * 1 local majorants, one per macro cell of 2^cell_shift voxels per edge
+     * (cell_shift 0..10): delta tracking with a piecewise-constant majorant,
+     * the optical depth of each flight spent cell by cell along the ray.  An
+     * option beside the paper's method; the expected images are the same. */
+    int local_majorant;
+    int cell_shift;
 } orc_problem;
 
 /* One record per history, for tiny-run event-by-event parity. */
@@ -80,7 +87,7 @@ enum { ORC_INT_NONE = 0, ORC_INT_RAYLEIGH = 1, ORC_INT_COMPTON = 2, ORC_INT_PHOT
 /* stats[] order */
 enum { ORC_ST_HISTORIES = 0, ORC_ST_STEPS, ORC_ST_VIRTUAL, ORC_ST_RAYLEIGH, ORC_ST_COMPTON,
        ORC_ST_PHOTO, ORC_ST_TALLY_P, ORC_ST_TALLY_S, ORC_ST_MISS, ORC_ST_CUTOFF,
-       ORC_ST_STEP_LIMIT, ORC_NSTATS };
+       ORC_ST_STEP_LIMIT, ORC_ST_CROSSINGS, ORC_NSTATS };
 
 /* Philox4x32-10 (Salmon et al., SC'11).  Pinned against cuRAND's host generator. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -119,6 +126,17 @@ int orc_rt_primary_siddon(const orc_problem* p, double phi, const int32_t* pixel
 
 /* Derived tables, exposed for the pins. */
 int orc_majorant(const orc_problem* p, float* node_out /* n_e */);
+
+/* Local majorants: the macro-cell table, per cell (x fastest) and material,
+ * the largest density over the voxels [c 2^s, (c + 1) 2^s] of each axis
+ * (clamped to the phantom), [ncz][ncy][ncx][n_mat]; and one free flight of
+ * the tracking with that table (precision 32 or 64) from pos along unit dir
+ * at energy e with optical depth tau: returns 1 at a tentative collision
+ * (out = position, bound there, cell crossings), 0 when the ray leaves the
+ * box first (out = last position inside, 0, crossings), negative on error. */
+int orc_lm_cells(const orc_problem* p, float* out);
+int orc_lm_walk(const orc_problem* p, int precision, const double pos[3], const double dir[3], double e,
+                double tau, double out[5]);
 
 #ifdef __cplusplus
 }

@@ -29,9 +29,9 @@ _lock = threading.Lock()
 _lib = None
 
 FIXED_POINT_BITS = 24           # tally unit: 2^-24 keV
-N_STATS = 11
+N_STATS = 12
 STAT_NAMES = ("histories", "steps", "virtual", "rayleigh", "compton", "photo",
-              "tally_primary", "tally_scatter", "miss", "cutoff", "step_limit")
+              "tally_primary", "tally_scatter", "miss", "cutoff", "step_limit", "crossings")
 OUTCOMES = ("primary", "scatter", "photo", "cutoff", "miss", "step_limit")
 
 RECORD_DTYPE = np.dtype([
@@ -74,6 +74,7 @@ class _Problem(ctypes.Structure):
         ("nearest_voxel", ctypes.c_int), ("scatter_filter", ctypes.c_int),
         ("rayleigh_ff", ctypes.c_int), ("n_ff", ctypes.c_int), ("ff_dx", ctypes.c_double),
         ("ff", ctypes.c_void_p),
+        ("local_majorant", ctypes.c_int), ("cell_shift", ctypes.c_int),
     ]
 
 
@@ -91,6 +92,10 @@ def lib():
         L.orc_rt_primary_siddon.restype = i32
         L.orc_majorant.argtypes = [vp, vp]
         L.orc_majorant.restype = i32
+        L.orc_lm_cells.argtypes = [vp, vp]
+        L.orc_lm_cells.restype = i32
+        L.orc_lm_walk.argtypes = [vp, i32, vp, vp, ctypes.c_double, ctypes.c_double, vp]
+        L.orc_lm_walk.restype = i32
         L.orc_logf.argtypes = [ctypes.c_float]
         L.orc_logf.restype = ctypes.c_float
         L.orc_logf_many.argtypes = [vp, vp, i32]
@@ -113,7 +118,8 @@ def _ptr(a):
 class _Marshalled:
     """Keeps the contiguous arrays alive while C reads them."""
 
-    def __init__(self, prob, e_cut=1.0, max_steps=100000, nearest_voxel=0, scatter_filter=0, rayleigh_ff=0):
+    def __init__(self, prob, e_cut=1.0, max_steps=100000, nearest_voxel=0, scatter_filter=0, rayleigh_ff=0,
+                 local_majorant=0, cell_shift=0):
         self.material = np.ascontiguousarray(prob.material, np.uint8)
         self.density = np.ascontiguousarray(prob.density, np.float32)
         self.mu_hat = np.ascontiguousarray(prob.mu_hat, np.float32)
@@ -142,6 +148,7 @@ class _Marshalled:
         s.e_cut, s.max_steps = e_cut, max_steps
         s.nearest_voxel, s.scatter_filter = int(nearest_voxel), int(scatter_filter)
         s.rayleigh_ff = int(rayleigh_ff)
+        s.local_majorant, s.cell_shift = int(local_majorant), int(cell_shift)
         ff = getattr(prob, "form_factor", None)
         if rayleigh_ff and ff is None:
             raise ValueError("rayleigh_ff needs the problem's form_factor table")
@@ -153,13 +160,16 @@ class _Marshalled:
 
 def mc_run(prob, n_histories, seed=1, phi=0.0, angle_index=0, history_offset=0, precision=32,
            threads=1, records=False, e_cut=1.0, max_steps=100000, nearest_voxel=False, scatter_filter=0,
-           rayleigh_ff=False):
+           rayleigh_ff=False, local_majorant=False, cell_shift=1):
     """Monte Carlo projection (Section 2.4).  Returns (tally_p, tally_s, stats, records)
     with int64 fixed-point tallies shaped [nv, nu].  nearest_voxel: no density
     interpolation (the paper's speed variant); scatter_filter: 0 all scatter,
     1 single Compton, 2 single Rayleigh, 3 multiple scatter; rayleigh_ff: the
-    Rayleigh angle takes the problem's form factors (else Thomson)."""
-    m = _Marshalled(prob, e_cut, max_steps, nearest_voxel, scatter_filter, rayleigh_ff)
+    Rayleigh angle takes the problem's form factors (else Thomson);
+    local_majorant: delta tracking with one majorant per macro cell of
+    2^cell_shift voxels per edge instead of the global one."""
+    m = _Marshalled(prob, e_cut, max_steps, nearest_voxel, scatter_filter, rayleigh_ff, local_majorant,
+                    cell_shift)
     tp = np.zeros((prob.nv, prob.nu), np.int64)
     ts = np.zeros((prob.nv, prob.nu), np.int64)
     st = np.zeros(N_STATS, np.uint64)
@@ -170,6 +180,29 @@ def mc_run(prob, n_histories, seed=1, phi=0.0, angle_index=0, history_offset=0, 
     if rc:
         raise ValueError(f"oracle mc_run rejected the problem (rc={rc})")
     return tp, ts, dict(zip(STAT_NAMES, (int(x) for x in st))), rec
+
+
+def lm_cells(prob, cell_shift):
+    """The local-majorant cell table: [ncz, ncy, ncx, n_mat] largest densities."""
+    m = _Marshalled(prob, cell_shift=cell_shift)
+    nz, ny, nx = m.material.shape
+    nc = [((n - 1) >> cell_shift) + 1 for n in (nz, ny, nx)]
+    out = np.zeros(nc + [m.mu_hat.shape[0]], np.float32)
+    if lib().orc_lm_cells(ctypes.byref(m.struct), _ptr(out)):
+        raise ValueError("oracle lm_cells rejected the problem")
+    return out
+
+
+def lm_walk(prob, cell_shift, pos, direction, e, tau, precision=64):
+    """One local-majorant free flight: (hit, position, bound, crossings)."""
+    m = _Marshalled(prob, cell_shift=cell_shift)
+    p = np.ascontiguousarray(pos, np.float64)
+    d = np.ascontiguousarray(direction, np.float64)
+    out = np.zeros(5)
+    rc = lib().orc_lm_walk(ctypes.byref(m.struct), precision, _ptr(p), _ptr(d), float(e), float(tau), _ptr(out))
+    if rc < 0:
+        raise ValueError("oracle lm_walk rejected the problem")
+    return bool(rc), out[:3].copy(), float(out[3]), int(out[4])
 
 
 def rt_primary(prob, phi=0.0, pixels=None):

@@ -411,10 +411,13 @@ void set_defaults(gdrr_mc_options* o) {
 // edge with s = round(log2(4 mm / edge)) in 1..6.  On the torso, cells of 4 mm
 // ran faster than 2, 8 or 16 mm at 1 mm voxels and faster than 8 or 16 mm at
 // 2 mm (tighter bounds, fewer gathers, against a larger table that stays in
-// L2); the results do not depend on the choice.
-int default_cell_shift(const gdrr_ctx* c) {
+// L2); the results do not depend on the choice.  With local majorants the
+// cells are the flights' majorant and every cell a flight passes costs a
+// crossing: about 32 mm by default (on the 2 mm torso, 8, 16, 32 and 64 mm
+// cells gave 92.2, 71.8, 70.3 and 87.5 ms per 1e8 histories).
+int default_cell_shift(const gdrr_ctx* c, bool local_majorant) {
     const double v = std::min(c->vox[0], std::min(c->vox[1], c->vox[2]));
-    const int s = (int)std::lround(std::log2(4.0 / v));
+    const int s = (int)std::lround(std::log2((local_majorant ? 32.0 : 4.0) / v));
     return std::min(6, std::max(1, s));
 }
 
@@ -528,7 +531,7 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         c->bsz = 16 * nbx * nby;
         std::vector<double> rho_max;
         if ((rc = stage_phantom(c, ph, (size_t)16 * nbx * nby * nbz, rho_max))) break;
-        if (c->opt.cell_shift == 0) c->opt.cell_shift = default_cell_shift(c);
+        if (c->opt.cell_shift == 0) c->opt.cell_shift = default_cell_shift(c, false);
         if ((rc = build_cells(c, c->opt.cell_shift))) break;
         // Woodcock majorant nodes: max over materials of the largest density of
         // that material times its total coefficient, with a 1e-5 margin.
@@ -637,8 +640,10 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
     if (n.rayleigh_form_factor < 0 || n.rayleigh_form_factor > 1 || (n.rayleigh_form_factor && !ctx->n_ff))
         return GDRR_ERR_INVALID_ARG;
     if (n.photon_pool < -1 || n.photon_pool > 3) return GDRR_ERR_INVALID_ARG;
-    if (n.cell_shift == 0) n.cell_shift = default_cell_shift(ctx);
+    if (n.local_majorant < 0 || n.local_majorant > 1) return GDRR_ERR_INVALID_ARG;
+    if (n.cell_shift == 0) n.cell_shift = default_cell_shift(ctx, n.local_majorant != 0);
     if (n.cell_shift < -1 || n.cell_shift > 6) return GDRR_ERR_INVALID_ARG;
+    if (n.local_majorant && n.cell_shift < 0) return GDRR_ERR_INVALID_ARG;   // the cells are the majorant
     if (n.cell_shift != ctx->cell_shift) {
         if (ctx->n_scans > 0) return GDRR_ERR_INVALID_ARG;     // scans hold the old table pointer
         const int rc = build_cells(ctx, n.cell_shift);
@@ -762,7 +767,8 @@ GDRR_API int gdrr_raytrace_primary_siddon(gdrr_ctx* ctx, double angle_rad, doubl
 
 static int launch_grid(const gdrr_ctx* ctx, uint64_t total, bool rec) {
     const int block = ctx->opt.block_size;
-    const int per_sm = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : mc_occupancy_blocks(ctx->n_mat, block, rec);
+    const int per_sm = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm
+                                                  : mc_occupancy_blocks(ctx->n_mat, block, rec, ctx->opt.local_majorant != 0);
     int64_t grid = (int64_t)per_sm * ctx->n_sm;
     const int64_t useful = (int64_t)((total + 31) / 32 * 32 + block - 1) / block;
     if (grid > useful) grid = useful;
@@ -776,7 +782,7 @@ constexpr uint64_t SRC_MAX = 1ull << 27;
 // The source pass serves the lane form with default options and no records.
 static bool source_pass_applies(const gdrr_ctx* ctx, bool rec) {
     return !rec && ctx->opt.nearest_voxel == 0 && ctx->opt.scatter_filter == 0 && ctx->opt.rayleigh_form_factor == 0 &&
-           ctx->opt.photon_pool <= 0;
+           (ctx->opt.photon_pool <= 0 || ctx->opt.local_majorant);
 }
 
 // Grows a source-record buffer to min(total, SRC_MAX) histories.  When the
@@ -807,7 +813,7 @@ static void ensure_src(cudaStream_t s, float4** buf, uint64_t* cap, uint64_t tot
 static cudaError_t launch_transport(const gdrr_ctx* ctx, const McParams& p, uint64_t total, bool rec,
                                     cudaStream_t s, const float4* src = nullptr, uint64_t src_cap = 0) {
     const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0 || p.ray_ff != 0;
-    if (!rec && !gen && ctx->opt.photon_pool > 0) {
+    if (!rec && !gen && !p.lm && ctx->opt.photon_pool > 0) {
         int per_sm = mc_pool_occupancy_blocks(ctx->n_mat, ctx->opt.photon_pool);
         if (ctx->opt.blocks_per_sm > 0 && ctx->opt.blocks_per_sm < per_sm) per_sm = ctx->opt.blocks_per_sm;
         if (per_sm > 0) {
@@ -859,7 +865,9 @@ static McParams static_mc_params(const gdrr_ctx* ctx) {
     p.ff_s = ctx->d_ff_s; p.ff_a = ctx->d_ff_a; p.ff_g = ctx->d_ff_g;
     p.inv_hc = (float)(1.0 / 12.398419843320026);
     p.cells = ctx->d_cells;
-    p.cshift = ctx->cell_shift; p.ncx = ctx->ncx; p.ncy = ctx->ncy;
+    p.cshift = ctx->cell_shift; p.ncx = ctx->ncx; p.ncy = ctx->ncy; p.ncz = ctx->ncz;
+    p.lm = ctx->opt.local_majorant;
+    for (int k = 0; k < 3; ++k) p.vox_mm[k] = (float)ctx->vox[k];
     p.status = ctx->d_status;
     p.ff_idx = ctx->ff_idx;
     return p;
@@ -1072,6 +1080,7 @@ GDRR_API int gdrr_autotune(gdrr_ctx* ctx, double angle_rad, uint64_t n_probe, ui
             }
     for (int q : pools)
         for (int h : hpt) {
+            if (base.local_majorant) break;              // local majorants run the lane form only
             gdrr_mc_options o = base;
             o.hist_per_thread = h; o.blocks_per_sm = 0; o.photon_pool = q;
             grid.push_back(o);

@@ -106,7 +106,11 @@ struct McParams {
     // cell and the next voxel), [cell][NM] with NM the kernel's material
     // slots; NULL disables the early virtual-collision test
     const float* cells;
-    int cshift, ncx, ncy;
+    int cshift, ncx, ncy, ncz;
+    // local majorants (lm = 1): the cell bounds serve as the free flights'
+    // majorant; the cells' planes need the voxel edges
+    int lm;
+    float vox_mm[3];
     int* status;                   // NULL, or where a bounded loop that gave up records it
     int pool_tail, pool_park_min;  // pool form: tail width and parking minimum (0: defaults)
     // the launch covers flattened histories seg0 .. seg0 + total - 1; with src
@@ -178,7 +182,7 @@ cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cuda
 // p.total - 1 into p.src, and tallies and counts those that miss the box.
 cudaError_t launch_mc_source(const McParams& p, cudaStream_t s);
 constexpr size_t MC_SRC_BYTES = 32;    // bytes of one history's source record
-int mc_occupancy_blocks(int n_mat, int block, bool records);
+int mc_occupancy_blocks(int n_mat, int block, bool records, bool lm);
 // The photon-pool form of the transport (default options, no records):
 // blocks of pool_threads() threads, per_thread photons per thread in the
 // shared-memory pool; 0 blocks per SM when the pool does not fit.

@@ -30,6 +30,17 @@
 // events, for the warp's service batch, where its gathers run together with
 // those of the warp's other waiting lanes.
 //
+// Local majorants (an option, LM): the macro-cell bounds themselves serve as a
+// piecewise-constant majorant.  A flight draws its optical depth tau = -ln xi
+// and spends it cell by cell along the ray (a cell of bound b crossed whole
+// costs b times its chord); where it runs out, tau / b into the cell, lies the
+// tentative collision, real with probability mu / b (the same ordinate test,
+// t = xi' b against the mixture).  Cheap cell crossings replace most of the
+// flights (about 46 per history in the torso with the global majorant, 4 to 6
+// with 16 to 32 mm cells); the tentative collisions wait for the service
+// batch, where the gathers, the decision and the next flight's Philox block
+// run on the warp's waiting lanes together.
+//
 // Arithmetic contract.  This file is compiled with -fmad=false: every FP32
 // operation below is one IEEE-rounded operation, evaluated in the order
 // written (divide and square root are the correctly rounded ones).  The only
@@ -307,12 +318,18 @@ enum : uint32_t { OUT_PRIMARY = 0, OUT_SCATTER = 1, OUT_PHOTO = 2, OUT_CUTOFF = 
 // rare branches from running with one or two active lanes.
 enum : int { S_DEAD = 0, S_FLY = 1, S_RAY = 2, S_COMP = 3, S_ESC = 4, S_GATHER = 5 };
 
+// What a local-majorant lane needs before it flies on (LM): a new flight
+// (Philox block and optical depth), the reciprocal of a new direction, the
+// cell of a new history's entry point.
+enum : uint32_t { LM_DRAW = 1u, LM_DIR = 2u, LM_CELL = 4u, LM_ALL = 7u };
+
 // Block-shared counters (GDRR_NSTATS), flushed to the stats array at exit.
 __device__ __forceinline__ void count(unsigned long long* c, int k) { atomicAdd(c + k, 1ull); }
 
 // GEN: the general kernel, which honours the nearest-voxel and scatter-filter
-// options; the default kernel (GEN = false) carries neither.
-template <int NM, bool REC, bool GEN>
+// options; the default kernel (GEN = false) carries neither.  LM: free flights
+// with local majorants instead of the global one.
+template <int NM, bool REC, bool GEN, bool LM = false>
 struct Lane {
     float px, py, pz, dx, dy, dz, e;
     float mumax, inv_mumax;
@@ -329,7 +346,14 @@ struct Lane {
     bool defer_e;        // start / interact leave the energy tables to the caller
     bool need_e;         // ... which must then call set_energy(P, e) before the next flight
     float tg;            // t = xi mu_max of a flight waiting for its corner gathers
+                         // (LM: xi until the flight's cell is known, then xi b)
     uint32_t wz;         // that flight block's third word (GEN: form-factor material pick)
+    // LM: the flight's remaining optical depth, the direction's reciprocals,
+    // the cell of the position, what the lane needs next (LM_*) and the
+    // thread's count of cell crossings
+    float tau, idx, idy, idz;
+    int cx, cy, cz;
+    uint32_t lm_need, c_cross;
     Stream rs;
     // per-thread coefficient tables in shared memory: coef[k][m][tid],
     // k = 0 total, 1 Rayleigh, 2 Compton (photoelectric is the remainder)
@@ -394,6 +418,10 @@ struct Lane {
     // a history ended; esc: its last flight left the box
     __device__ __forceinline__ void end_counts(uint32_t esc) {
         if (GEN) return;
+        if (LM) {                    // no cell test: every virtual collision gathered
+            c_steps += nsteps;
+            return;
+        }
         const uint32_t skipped = nsteps - ngath - esc;
         c_steps += nsteps;
         c_skip += skipped;
@@ -544,6 +572,7 @@ struct Lane {
         py = py + tmin * dy;
         pz = pz + tmin * dz;
         if (defer_e) need_e = true; else set_energy(P, en);
+        if (LM) lm_need = LM_ALL;
         state = S_FLY;
     }
 
@@ -568,6 +597,7 @@ struct Lane {
         dx = a.w; dy = b.x; dz = b.y;
         e = b.z;
         if (defer_e) need_e = true; else set_energy(P, e);
+        if (LM) lm_need = LM_ALL;
         state = S_FLY;
     }
 
@@ -635,6 +665,95 @@ struct Lane {
         state = S_GATHER;
     }
 
+    // The boundary plane between cells j - 1 and j of axis a (n cells): the
+    // box faces for j = 0 and j = n, else where the lower trilinear corner
+    // index reaches j 2^s, i.e. (x - lo) / vox - 1/2 = j 2^s.
+    __device__ __forceinline__ static float lm_plane(const McParams& P, int a, int j, int n) {
+        if (j <= 0) return P.lo[a];
+        if (j >= n) return P.hi[a];
+        return P.lo[a] + ((float)(j << P.cshift) + 0.5f) * P.vox_mm[a];
+    }
+
+    // LM, in the service batch: the entry cell of a new history, the
+    // reciprocals of a new direction, and the next flight: its Philox block,
+    // its optical depth tau = -ln xi and the uniform of its ordinate test.
+    __device__ __forceinline__ void lm_prepare(const McParams& P, unsigned long long* cnt) {
+        if (lm_need & LM_CELL) {
+            const int gx = max((int)floorf((px - P.lo[0]) * P.ivox[0] - 0.5f), 0) >> P.cshift;
+            const int gy = max((int)floorf((py - P.lo[1]) * P.ivox[1] - 0.5f), 0) >> P.cshift;
+            const int gz = max((int)floorf((pz - P.lo[2]) * P.ivox[2] - 0.5f), 0) >> P.cshift;
+            cx = min(gx, P.ncx - 1);
+            cy = min(gy, P.ncy - 1);
+            cz = min(gz, P.ncz - 1);
+        }
+        if (lm_need & LM_DIR) {
+            idx = dx != 0.0f ? 1.0f / dx : 0.0f;
+            idy = dy != 0.0f ? 1.0f / dy : 0.0f;
+            idz = dz != 0.0f ? 1.0f / dz : 0.0f;
+        }
+        lm_need = 0u;
+        if ((int)nsteps >= P.max_steps) {
+            count(cnt, GDRR_ST_STEP_LIMIT);
+            record(P, OUT_STEP_LIMIT, -1, 0);
+            end_counts(0u);
+            state = S_DEAD;
+            return;
+        }
+        const uint4 wf = rs.block(P.rk);
+        ++nsteps;
+        if (GEN) ++c_steps;
+        tau = -gd_logf(uniform(wf.x));
+        tg = uniform(wf.y);
+        if (GEN) wz = wf.z;
+    }
+
+    // LM: one cell of a flight.  With b the cell's bound and tx the distance
+    // to its exit, the remaining depth either runs out inside (the tentative
+    // collision lies tau / b ahead and waits for the warp's service batch) or
+    // pays b tx, and the lane moves to the exit point and on to the next cell
+    // (one step along every axis whose exit plane is nearest, all of them on
+    // a tie).  Every crossing moves the cell along the direction of flight, so
+    // a flight crosses at most ncx + ncy + ncz cells; leaving the grid leaves
+    // the box, from the last position inside.
+    __device__ __forceinline__ void walk(const McParams& P) {
+        const float b = cell_bound(P, cx + P.ncx * (cy + P.ncy * cz));
+        float tx = (float)3.0e38, ty = tx, tz = tx;
+        if (dx > 0.0f) tx = (lm_plane(P, 0, cx + 1, P.ncx) - px) * idx;
+        else if (dx < 0.0f) tx = (lm_plane(P, 0, cx, P.ncx) - px) * idx;
+        if (dy > 0.0f) ty = (lm_plane(P, 1, cy + 1, P.ncy) - py) * idy;
+        else if (dy < 0.0f) ty = (lm_plane(P, 1, cy, P.ncy) - py) * idy;
+        if (dz > 0.0f) tz = (lm_plane(P, 2, cz + 1, P.ncz) - pz) * idz;
+        else if (dz < 0.0f) tz = (lm_plane(P, 2, cz, P.ncz) - pz) * idz;
+        if (dx != 0.0f && !(tx > 0.0f)) tx = 0.0f;       // already on the plane
+        if (dy != 0.0f && !(ty > 0.0f)) ty = 0.0f;
+        if (dz != 0.0f && !(tz > 0.0f)) tz = 0.0f;
+        const float t = fminf(tx, fminf(ty, tz));
+        const float bt = b * t;
+        if (tau < bt) {
+            const float s = tau / b;
+            px = px + s * dx;
+            py = py + s * dy;
+            pz = pz + s * dz;
+            tg = tg * b;
+            state = S_GATHER;
+            return;
+        }
+        tau = tau - bt;
+        const bool sx = dx != 0.0f && tx == t, sy = dy != 0.0f && ty == t, sz = dz != 0.0f && tz == t;
+        const int nx_ = sx ? cx + (dx > 0.0f ? 1 : -1) : cx;
+        const int ny_ = sy ? cy + (dy > 0.0f ? 1 : -1) : cy;
+        const int nz_ = sz ? cz + (dz > 0.0f ? 1 : -1) : cz;
+        if (!(sx || sy || sz) || nx_ < 0 || nx_ >= P.ncx || ny_ < 0 || ny_ >= P.ncy || nz_ < 0 || nz_ >= P.ncz) {
+            state = S_ESC;
+            return;
+        }
+        px = px + t * dx;
+        py = py + t * dy;
+        pz = pz + t * dz;
+        cx = nx_; cy = ny_; cz = nz_;
+        ++c_cross;
+    }
+
     // The deferred part of a free flight that passed the macro-cell test:
     // the eight-corner mixture at the lane's position and the real/virtual
     // decision for its t.  The warp serves its waiting lanes together, so the
@@ -643,6 +762,25 @@ struct Lane {
     __device__ __forceinline__ void gather(const McParams& P, unsigned long long* cnt) {
         if (!GEN) ++ngath;
         const float t = tg;
+        if (LM && GEN && P.nearest_voxel) {
+            // no density interpolation: the voxel containing the point
+            const int gx = min(max((int)floorf((px - P.lo[0]) * P.ivox[0]), 0), P.nx - 1);
+            const int gy = min(max((int)floorf((py - P.lo[1]) * P.ivox[1]), 0), P.ny - 1);
+            const int gz = min(max((int)floorf((pz - P.lo[2]) * P.ivox[2]), 0), P.nz - 1);
+            const uint2 vx = __ldg(P.vox + brick_x(gx) + brick_y(gy, P.bsy) + brick_z(gz, P.bsz));
+            const float a0 = __uint_as_float(vx.x);
+            const int m0 = (int)vx.y;
+            if (t > a0 * cf(0, m0)) {
+                ++c_virt;
+                if (REC) ++r_virt;
+                lm_need |= LM_DRAW;
+                state = S_FLY;
+                return;
+            }
+            m_ray = m0;
+            real_collision(P, t, a0 * cf(1, m0), a0 * cf(2, m0), cnt);
+            return;
+        }
         const float fx = (px - P.lo[0]) * P.ivox[0] - 0.5f;
         const float fy = (py - P.lo[1]) * P.ivox[1] - 0.5f;
         const float fz = (pz - P.lo[2]) * P.ivox[2] - 0.5f;
@@ -674,6 +812,7 @@ struct Lane {
         if (t > muT) {
             ++c_virt;
             if (REC) ++r_virt;
+            if (LM) lm_need |= LM_DRAW;
             state = S_FLY;
             return;
         }
@@ -735,6 +874,7 @@ struct Lane {
             if (GEN) n_int += 0x10000u;
             count(cnt, GDRR_ST_RAYLEIGH);
             if (REC) { ++r_ray; if (!r_first) r_first = 1; }
+            if (LM) lm_need |= LM_DRAW | LM_DIR;
             state = S_FLY;
             return;
         }
@@ -756,11 +896,12 @@ struct Lane {
         } else {
             set_energy(P, e2);
         }
+        if (LM) lm_need |= LM_DRAW | LM_DIR;
         state = S_FLY;
     }
 };
 
-template <int NM, bool REC, bool GEN>
+template <int NM, bool REC, bool GEN, bool LM>
 // Up to 512 threads per block, 64 registers per thread (the same cap at 2 x 512
 // or 4 x 256 resident threads): the autotuner's block sizes 64 ... 512.
 __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
@@ -770,13 +911,14 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    Lane<NM, REC, GEN> L;
+    Lane<NM, REC, GEN, LM> L;
     L.coef = smem + threadIdx.x;
     L.stride = blockDim.x;
     L.state = S_DEAD;
     L.defer_e = true;                 // new histories and Compton events share one table pass
     L.need_e = false;
     L.c_steps = 0; L.c_virt = 0; L.c_skip = 0;
+    L.lm_need = 0u; L.c_cross = 0u;
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
 
@@ -816,14 +958,19 @@ __global__ void __launch_bounds__(512, 2) mc_kernel(const McParams P) {
                 L.set_energy(P, L.e);
                 L.need_e = false;
             }
+            if (LM && L.lm_need) L.lm_prepare(P, cnt);
             if (exhausted && !__any_sync(FULL, L.state != S_DEAD)) break;
         }
-        if (L.state == S_FLY) L.step(P, cnt);
+        if (L.state == S_FLY) {
+            if constexpr (LM) L.walk(P);
+            else L.step(P, cnt);
+        }
     }
 
     atomicAdd(&cnt[GDRR_ST_STEPS], (unsigned long long)L.c_steps);
     atomicAdd(&cnt[GDRR_ST_VIRTUAL], (unsigned long long)L.c_virt);
     atomicAdd(&cnt[GDRR_ST_CELL_SKIPS], (unsigned long long)L.c_skip);
+    if (LM) atomicAdd(&cnt[GDRR_ST_CELL_CROSSINGS], (unsigned long long)L.c_cross);
     __syncthreads();
     for (int i = threadIdx.x; i < GDRR_NSTATS; i += blockDim.x)
         if (cnt[i]) atomicAdd(P.stats + i, cnt[i]);
@@ -1257,43 +1404,50 @@ constexpr size_t smem_bytes(int block) { return (size_t)3 * NM * block * sizeof(
 
 // Per-thread coefficient tables beyond 47 KB per block (8 materials at 512
 // threads) need the kernel's dynamic shared-memory cap raised first.
-template <int NM, bool REC, bool GEN>
+template <int NM, bool REC, bool GEN, bool LM>
 cudaError_t allow_smem(int block) {
     const size_t bytes = smem_bytes<NM>(block);
     if (bytes <= 47 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(mc_kernel<NM, REC, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaFuncSetAttribute(mc_kernel<NM, REC, GEN, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int NM, bool REC, bool GEN>
+template <int NM, bool REC, bool GEN, bool LM>
 cudaError_t launch_t(const McParams& p, int block, int grid, cudaStream_t s) {
-    const cudaError_t e = allow_smem<NM, REC, GEN>(block);
+    const cudaError_t e = allow_smem<NM, REC, GEN, LM>(block);
     if (e != cudaSuccess) return e;
-    mc_kernel<NM, REC, GEN><<<grid, block, smem_bytes<NM>(block), s>>>(p);
+    mc_kernel<NM, REC, GEN, LM><<<grid, block, smem_bytes<NM>(block), s>>>(p);
     return cudaGetLastError();
 }
 
-template <int NM, bool REC, bool GEN>
+template <int NM, bool REC, bool GEN, bool LM>
 int occupancy_t(int block) {
     int n = 0;
-    if (allow_smem<NM, REC, GEN>(block) != cudaSuccess
-        || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_kernel<NM, REC, GEN>, block, smem_bytes<NM>(block))
+    if (allow_smem<NM, REC, GEN, LM>(block) != cudaSuccess
+        || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mc_kernel<NM, REC, GEN, LM>, block, smem_bytes<NM>(block))
                != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
-template <bool REC, bool GEN>
+template <bool REC, bool GEN, bool LM>
 cudaError_t launch_nm(const McParams& p, int block, int grid, cudaStream_t s) {
-    if (p.n_mat <= 2) return launch_t<2, REC, GEN>(p, block, grid, s);
-    if (p.n_mat <= 4) return launch_t<4, REC, GEN>(p, block, grid, s);
-    return launch_t<8, REC, GEN>(p, block, grid, s);
+    if (p.n_mat <= 2) return launch_t<2, REC, GEN, LM>(p, block, grid, s);
+    if (p.n_mat <= 4) return launch_t<4, REC, GEN, LM>(p, block, grid, s);
+    return launch_t<8, REC, GEN, LM>(p, block, grid, s);
 }
 
-template <bool REC, bool GEN>
+template <bool REC, bool LM>
 int occupancy_nm(int n_mat, int block) {
-    if (n_mat <= 2) return occupancy_t<2, REC, GEN>(block);
-    if (n_mat <= 4) return occupancy_t<4, REC, GEN>(block);
-    return occupancy_t<8, REC, GEN>(block);
+    if (n_mat <= 2) return occupancy_t<2, REC, false, LM>(block);
+    if (n_mat <= 4) return occupancy_t<4, REC, false, LM>(block);
+    return occupancy_t<8, REC, false, LM>(block);
+}
+
+template <bool LM>
+cudaError_t launch_lm(const McParams& p, int block, int grid, bool records, cudaStream_t s) {
+    const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0 || p.ray_ff != 0;
+    if (records) return gen ? launch_nm<true, true, LM>(p, block, grid, s) : launch_nm<true, false, LM>(p, block, grid, s);
+    return gen ? launch_nm<false, true, LM>(p, block, grid, s) : launch_nm<false, false, LM>(p, block, grid, s);
 }
 
 template <int NM>
@@ -1357,12 +1511,15 @@ cudaError_t launch_mc_source(const McParams& p, cudaStream_t s) {
 }
 
 cudaError_t launch_mc(const McParams& p, int block, int grid, bool records, cudaStream_t s) {
-    const bool gen = p.nearest_voxel != 0 || p.scatter_filter != 0 || p.ray_ff != 0;
-    if (records) return gen ? launch_nm<true, true>(p, block, grid, s) : launch_nm<true, false>(p, block, grid, s);
-    return gen ? launch_nm<false, true>(p, block, grid, s) : launch_nm<false, false>(p, block, grid, s);
+    if (p.lm) {
+        if (!p.cells) return cudaErrorInvalidValue;       // the local majorants are the cell bounds
+        return launch_lm<true>(p, block, grid, records, s);
+    }
+    return launch_lm<false>(p, block, grid, records, s);
 }
 
-int mc_occupancy_blocks(int n_mat, int block, bool records) {
+int mc_occupancy_blocks(int n_mat, int block, bool records, bool lm) {
+    if (lm) return records ? occupancy_nm<true, true>(n_mat, block) : occupancy_nm<false, true>(n_mat, block);
     return records ? occupancy_nm<true, false>(n_mat, block) : occupancy_nm<false, false>(n_mat, block);
 }
 

@@ -18,12 +18,14 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgdrr.so")
 
-GDRR_NSTATS = 12
+GDRR_NSTATS = 13
 # the method's event counters; slot 11 (cell_skips) is the kernel's own count
-# of virtual collisions the macro-cell bound decided without corner gathers
+# of virtual collisions the macro-cell bound decided without corner gathers,
+# slot 12 the cell crossings of flights with local majorants
 STAT_NAMES = ("histories", "steps", "virtual", "rayleigh", "compton", "photo",
               "tally_primary", "tally_scatter", "miss", "cutoff", "step_limit")
 ST_CELL_SKIPS = 11
+ST_CELL_CROSSINGS = 12
 TALLY_BITS = 24
 RECORD_DTYPE = np.dtype([
     ("n_steps", "<u4"), ("n_virtual", "<u4"), ("n_rayleigh", "<u4"), ("n_compton", "<u4"),
@@ -74,7 +76,8 @@ class McOptions(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("hist_per_thread", ctypes.c_int32),
                 ("batch_min", ctypes.c_int32), ("nearest_voxel", ctypes.c_int32),
                 ("scatter_filter", ctypes.c_int32), ("rayleigh_form_factor", ctypes.c_int32),
-                ("cell_shift", ctypes.c_int32), ("photon_pool", ctypes.c_int32)]
+                ("cell_shift", ctypes.c_int32), ("photon_pool", ctypes.c_int32),
+                ("local_majorant", ctypes.c_int32)]
 
 
 class Projection(ctypes.Structure):
@@ -290,6 +293,8 @@ def gdrr_set_options(ctx: Context, **kw):
         if not hasattr(o, k):
             raise KeyError(k)
         setattr(o, k, v)
+    if "local_majorant" in kw and "cell_shift" not in kw:
+        o.cell_shift = 0                 # the default cell size of the chosen tracking
     _check("gdrr_set_options", lib().gdrr_set_options(ctx.handle, ctypes.byref(o)))
 
 
@@ -559,9 +564,12 @@ def gdrr_probe_fp32(stream=None) -> float:
 
 
 def stats_dict(stats) -> dict:
-    """The method's event counters (the oracle counts the same ones)."""
-    v = stats.cpu().numpy().view(np.uint64)
-    return dict(zip(STAT_NAMES, (int(x) for x in v)))
+    """The method's event counters and the cell crossings (the oracle counts
+    the same ones); stats a device tensor or a host array."""
+    v = (stats.cpu().numpy() if hasattr(stats, "cpu") else np.asarray(stats)).view(np.uint64)
+    d = dict(zip(STAT_NAMES, (int(x) for x in v)))
+    d["crossings"] = int(v[ST_CELL_CROSSINGS])
+    return d
 
 
 def cell_skips(stats) -> int:

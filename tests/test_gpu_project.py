@@ -68,7 +68,7 @@ def test_small_projection_against_the_oracle(gd, small, smoothing_px, beta):
     tp, ts, st, _ = oracle.mc_run(small, n, seed=seed, phi=phi, angle_index=3, threads=NTH)
     np.testing.assert_array_equal(g["prim"], tp)
     np.testing.assert_array_equal(g["scat"], ts)
-    assert dict(zip(gd.STAT_NAMES, (int(x) for x in g["stats"].view(np.uint64)))) == st
+    assert gd.stats_dict(g["stats"]) == st
     P_ref = oracle.rt_primary(small, phi)
     np.testing.assert_allclose(g["P"], P_ref, rtol=RT_RTOL, atol=1e-9 * P_ref.max())
     assert g["denoise_fused"] and g["step_limit"] == 0
@@ -84,7 +84,7 @@ def test_full_size_torso_projection(gd, torso):
         r = gd.project(ctx, n, seed, phi, bin_factor=4, beta=0.02, iters=300)
         g = _np(r)
     assert g["denoise_fused"] and g["step_limit"] == 0
-    st = dict(zip(gd.STAT_NAMES, (int(x) for x in g["stats"].view(np.uint64))))
+    st = gd.stats_dict(g["stats"])
     assert st["histories"] == n
     # the transport at this size is checked window by window elsewhere; here
     # the tallies themselves feed the oracle's image steps

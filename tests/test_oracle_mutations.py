@@ -111,6 +111,22 @@ MUTATIONS = [
      "count scale from the raw fixed-point tally", "test_oracle_project.py"),
     ("oracle.py", "return smoothing_px * smoothing_px / max(", "return smoothing_px / max(",
      "smoothing length not squared", "test_oracle_project.py"),
+    ("mc_history.inc", "return GEO(lo)[a] + ((REAL)(j << c->p->cell_shift) + RC(0.5)) * GEO(vox)[a];",
+     "return GEO(lo)[a] + ((REAL)(j << c->p->cell_shift) + RC(0)) * GEO(vox)[a];",
+     "local-majorant cell planes half a voxel off", "test_oracle_local_majorant.py"),
+    ("mc_history.inc", "tau = tau - bt;", "tau = tau - RC(0.5) * bt;",
+     "optical depth of a crossed cell half spent", "test_oracle_local_majorant.py"),
+    ("mc_history.inc", "REAL sc = tau / b;", "REAL sc = tau * b;",
+     "tentative collision distance inverted", "test_oracle_local_majorant.py"),
+    ("mc_history.inc", "nk[a] += d[a] > RC(0) ? 1 : -1;", "nk[a] += 1;",
+     "cells stepped forward along negative directions", "test_oracle_local_majorant.py"),
+    ("mc_history.inc", "REAL f = (x[a] - GEO(lo)[a]) * GEO(ivox)[a] - RC(0.5);",
+     "REAL f = (x[a] - GEO(lo)[a]) * GEO(ivox)[a];",
+     "entry cell by the containing voxel instead of the lower corner", "test_oracle_local_majorant.py"),
+    ("mc_history.inc", "REAL t = (REAL)uf[1] * maj;", "REAL t = (REAL)uf[1] * mumax;",
+     "local tentative collisions tested against the global majorant", "test_oracle_local_majorant.py"),
+    ("gdrr_oracle.c", "v1[a] = (k[a] + 1) << s;", "v1[a] = ((k[a] + 1) << s) - 1;",
+     "cell cover without the next voxel layer", "test_oracle_local_majorant.py"),
 ]
 
 
