@@ -10,7 +10,6 @@
 // These are element-wise or 5-point-stencil passes over at most a detector
 // image (196,608 pixels): launch- and latency-bound, not bandwidth-bound.
 #include <algorithm>
-#include <mutex>
 
 #include "gdrr_internal.cuh"
 
@@ -392,30 +391,18 @@ namespace gdrr {
 namespace {
 
 constexpr int STATIC_DENOISE_MAX_PIXELS = GDRR_STATIC_DENOISE_MAX_PIXELS;
-constexpr int MAX_DEVICES = 64;
-
 static __device__ __align__(256) double g_denoise_scratch[2 * (size_t)STATIC_DENOISE_MAX_PIXELS];
 
-std::mutex g_scratch_mutex;
-double* g_scratch_addr[MAX_DEVICES] = {nullptr};
-
-// The device address of g_denoise_scratch on the current device.  In host
-// code the array's name is only a host-side stand-in, so the address is
-// looked up with cudaGetSymbolAddress once per device, with that device
-// current, and cached.
+// The device address of g_denoise_scratch in the current context.  In host
+// code the array's name is only a host-side stand-in, so the address is looked
+// up on every call: it moves when the module is loaded again (a device reset,
+// a primary context released and created again), and the lookup allocates
+// nothing.
 cudaError_t static_scratch(double** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_denoise_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_denoise_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 

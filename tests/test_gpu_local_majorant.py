@@ -188,3 +188,37 @@ def test_full_size_2mm_torso_windows_and_global_majorant(gd):
         unit = (A.sum() + B.sum()) / (g[key] + l[key])
         sig = 1.5 * np.sqrt((A + B) / unit) * unit
         assert np.all(np.abs(A - B) <= 5.0 * sig + 3.0 * unit), np.abs(A - B).max() / unit
+
+
+def test_batched_scan_and_graph_carry_the_option(gd, small):
+    # one persistent launch over all angles, and its CUDA-graph replay, give
+    # each angle's per-angle local-majorant tallies; one angle against the oracle
+    angles = np.linspace(0, 2 * math.pi, 5, endpoint=False)
+    budgets = np.array([20_000, 7, 0, 55_555, 31_000], np.uint64)
+    with gd.Context(small) as ctx:
+        gd.gdrr_set_options(ctx, local_majorant=1, cell_shift=2)
+        bp, bs = gd.gdrr_mc_project_batched(ctx, angles, budgets, 23)
+        for a in range(angles.size):
+            p, s = gd.gdrr_mc_project(ctx, int(budgets[a]), 23, float(angles[a]), a)
+            assert torch.equal(bp[a], p) and torch.equal(bs[a], s), a
+        scan = gd.gdrr_scan_create(ctx, angles, budgets, 23, zero_tallies=True)
+        scan.launch()
+        scan.launch()
+        gd.gdrr_sync(ctx)
+        assert torch.equal(scan.prim, bp) and torch.equal(scan.scat, bs)
+        scan.close()
+    otp, ots, _, _ = oracle.mc_run(small, 55_555, seed=23, phi=float(angles[3]), angle_index=3, threads=NTH,
+                                   local_majorant=True, cell_shift=2)
+    np.testing.assert_array_equal(bp[3].cpu().numpy(), otp)
+    np.testing.assert_array_equal(bs[3].cpu().numpy(), ots)
+
+
+def test_autotune_keeps_the_option(gd, small):
+    # the autotuner times lane-form configurations only and keeps the option
+    with gd.Context(small) as ctx:
+        gd.gdrr_set_options(ctx, local_majorant=1, cell_shift=2)
+        ref = gd.gdrr_mc_project(ctx, 150_000, 8)
+        best = gd.gdrr_autotune(ctx, 0.0, 200_000, 3)
+        assert best["local_majorant"] == 1 and best["cell_shift"] == 2 and best["photon_pool"] == -1
+        got = gd.gdrr_mc_project(ctx, 150_000, 8)
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
