@@ -403,15 +403,20 @@ def run_ours(args):
         host_out = [torch.empty((prob.nv, prob.nu), dtype=torch.float64, pin_memory=True) for _ in range(5)]
         d2h = sum(h.numel() * h.element_size() for h in host_out)
         e2e_steps = max(1, min(args.steps, 3))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
+
+        def e2e_step():
             with gdrr.Context(hp, stream) as c2:
                 gdrr.gdrr_set_options(c2, **tuned)
                 o = gdrr.project(c2, n_hist, seed, angle, beta=0.02, iters=iters)
                 for h, key in zip(host_out, ("P", "P_hat", "S_hat", "S", "N")):
                     h.copy_(o[key], non_blocking=True)
                 torch.cuda.synchronize()
+
+        e2e_step()                                   # untimed: the library's memory pool grows once
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
         e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)   # the slowest rank's
         e2e = {"value": job_rate(n_hist, world, 1, 1e3 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "s_per_projection": e2e_s}

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <functional>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -32,6 +33,7 @@ struct ProjHost {
 
 struct gdrr_ctx {
     cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;    // the device's pool for the context's device memory
     int device = 0;
     int n_sm = 0;
     // inputs (host copies of the scalars)
@@ -116,6 +118,78 @@ int cuda_err(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? GDRR_ERR_OOM : GDRR_ERR_CUDA;
 }
 
+// Device memory of contexts.  Each device gets one stream-ordered pool, made
+// on first use, that keeps the blocks its contexts free (its release
+// threshold is the largest value): a context made after another one reuses
+// those blocks instead of mapping new memory (the transport's source records
+// alone take 3.2 GB at 1e8 histories), and destroying a context frees on its
+// stream instead of waiting for the device at every buffer.
+// gdrr_release_memory hands the unused blocks back.
+constexpr int MAX_POOL_DEVICES = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[MAX_POOL_DEVICES] = {};
+
+cudaError_t device_pool(int dev, cudaMemPool_t* out) {
+    if (dev < 0 || dev >= MAX_POOL_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pool[dev] = p;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+// A context buffer of the given size from its device's pool, ordered on the
+// context's stream; and its release, ordered after the work queued there.
+cudaError_t dalloc(const gdrr_ctx* c, void** p, size_t bytes) {
+    return cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 1), c->pool, c->stream);
+}
+template <typename T>
+cudaError_t dalloc(const gdrr_ctx* c, T** p, size_t bytes) {
+    return dalloc(c, reinterpret_cast<void**>(p), bytes);
+}
+void dfree(const gdrr_ctx* c, void* p) {
+    if (p) cudaFreeAsync(p, c->stream);
+}
+
+// Pinned host records of gdrr_project's scalars, kept for reuse: a page-locked
+// allocation costs far more than the record, and contexts come and go.
+std::mutex g_host_mutex;
+std::vector<ProjHost*> g_host_free;
+
+ProjHost* take_proj_host() {
+    {
+        std::lock_guard<std::mutex> lock(g_host_mutex);
+        if (!g_host_free.empty()) {
+            ProjHost* h = g_host_free.back();
+            g_host_free.pop_back();
+            return h;
+        }
+    }
+    ProjHost* h = nullptr;
+    return cudaMallocHost((void**)&h, sizeof(ProjHost)) == cudaSuccess ? h : nullptr;
+}
+
+void give_proj_host(ProjHost* h) {
+    if (!h) return;
+    std::lock_guard<std::mutex> lock(g_host_mutex);
+    g_host_free.push_back(h);
+}
+
 #define TRY_CUDA(x)                               \
     do {                                          \
         cudaError_t _e = (x);                     \
@@ -123,9 +197,9 @@ int cuda_err(cudaError_t e) {
     } while (0)
 
 template <typename T>
-int upload(T** dst, const T* src, size_t n, cudaStream_t s) {
-    TRY_CUDA(cudaMalloc((void**)dst, std::max<size_t>(n, 1) * sizeof(T)));
-    if (n) TRY_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+int upload(const gdrr_ctx* c, T** dst, const T* src, size_t n) {
+    TRY_CUDA(dalloc(c, dst, std::max<size_t>(n, 1) * sizeof(T)));
+    if (n) TRY_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
     return GDRR_OK;
 }
 
@@ -142,9 +216,9 @@ struct Arena {
         if (src && n) memcpy(host.data() + off, src, n * sizeof(T));
         bind.push_back([dst, off](char* base) { *dst = reinterpret_cast<T*>(base + off); });
     }
-    int commit(void** base, cudaStream_t s) {
-        TRY_CUDA(cudaMalloc(base, std::max<size_t>(host.size(), 1)));
-        TRY_CUDA(cudaMemcpyAsync(*base, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    int commit(const gdrr_ctx* c, void** base) {
+        TRY_CUDA(dalloc(c, base, host.size()));
+        TRY_CUDA(cudaMemcpyAsync(*base, host.data(), host.size(), cudaMemcpyHostToDevice, c->stream));
         for (auto& b : bind) b(static_cast<char*>(*base));
         return GDRR_OK;
     }
@@ -218,14 +292,14 @@ __global__ void build_cells_kernel(const uint2* __restrict__ vox, int nx, int ny
 int build_cells(gdrr_ctx* c, int shift) {
     cudaStream_t s = c->stream;
     if (cudaStreamSynchronize(s) != cudaSuccess) return GDRR_ERR_CUDA;
-    cudaFree(c->d_cells);
+    dfree(c, c->d_cells);
     c->d_cells = nullptr;
     c->cell_shift = -1;
     if (shift < 0) return GDRR_OK;
     const int ncx = ((c->nx - 1) >> shift) + 1, ncy = ((c->ny - 1) >> shift) + 1, ncz = ((c->nz - 1) >> shift) + 1;
     const int slots = material_slots(c->n_mat);
     const size_t bytes = (size_t)ncx * ncy * ncz * slots * sizeof(float);
-    if (cudaMalloc((void**)&c->d_cells, bytes) != cudaSuccess) {
+    if (dalloc(c, &c->d_cells, bytes) != cudaSuccess) {
         c->d_cells = nullptr;
         return GDRR_ERR_OOM;
     }
@@ -240,7 +314,7 @@ int build_cells(gdrr_ctx* c, int shift) {
     }
     if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
     if (rc) {
-        cudaFree(c->d_cells);
+        dfree(c, c->d_cells);
         c->d_cells = nullptr;
         return rc;
     }
@@ -267,9 +341,9 @@ int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, std::vector
     int rc = GDRR_OK;
     std::vector<unsigned int> aux(1 + c->n_mat, 0u);
     do {
-        if ((rc = cuda_err(cudaMalloc((void**)&c->d_vox, n_rec * sizeof(uint2))))) break;
+        if ((rc = cuda_err(dalloc(c, &c->d_vox, n_rec * sizeof(uint2))))) break;
         if ((rc = cuda_err(cudaMemsetAsync(c->d_vox, 0, n_rec * sizeof(uint2), s)))) break;
-        if ((rc = cuda_err(cudaMalloc((void**)&d_tmp, mat_off + (size_t)nvox)))) break;
+        if ((rc = cuda_err(dalloc(c, &d_tmp, mat_off + (size_t)nvox)))) break;
         d_den = reinterpret_cast<float*>(d_tmp);
         d_aux = reinterpret_cast<unsigned int*>(d_tmp + aux_off);
         d_mat = reinterpret_cast<uint8_t*>(d_tmp + mat_off);
@@ -284,7 +358,7 @@ int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, std::vector
                                            cudaMemcpyDeviceToHost, s)))) break;
         if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
     } while (0);
-    if (d_tmp) cudaFree(d_tmp);
+    dfree(c, d_tmp);
     if (rc) return rc;
     if (aux[0]) return GDRR_ERR_INVALID_ARG;
     rho_max.assign(c->n_mat, 0.0);
@@ -426,9 +500,9 @@ int free_ctx(gdrr_ctx* c) {
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->d_vox, c->d_arena, c->d_jobs, c->d_denoise, c->d_tune,
                     c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells, c->d_proj, c->d_src};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
-    if (c->h_proj) cudaFreeHost(c->h_proj);
+    if (c->pool)
+        for (void* b : bufs) dfree(c, b);
+    give_proj_host(c->h_proj);
     for (cudaEvent_t e : c->ev_proj)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -517,6 +591,7 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
     int rc = GDRR_OK;
     do {
         if (cudaGetDevice(&c->device) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
+        if ((rc = cuda_err(device_pool(c->device, &c->pool)))) break;
         if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
             rc = GDRR_ERR_CUDA;
             break;
@@ -616,7 +691,7 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         ar.add(&c->d_stats, (const unsigned long long*)nullptr, GDRR_NSTATS);
         ar.add(&c->d_flag, (const int*)nullptr, 1);
         ar.add(&c->d_status, (const int*)nullptr, 1);
-        if ((rc = ar.commit(&c->d_arena, s))) break;
+        if ((rc = ar.commit(c, &c->d_arena))) break;
         // the host vectors above die at return: finish the copies first
         if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
     } while (0);
@@ -626,6 +701,13 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
 }
 
 GDRR_API void gdrr_destroy(gdrr_ctx* ctx) { free_ctx(ctx); }
+
+GDRR_API int gdrr_release_memory(void) {
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    for (cudaMemPool_t p : g_pool)
+        if (p && cudaMemPoolTrimTo(p, 0) != cudaSuccess) return GDRR_ERR_CUDA;
+    return GDRR_OK;
+}
 
 GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
     if (!ctx || !o) return GDRR_ERR_INVALID_ARG;
@@ -661,8 +743,7 @@ GDRR_API int gdrr_set_form_factor(gdrr_ctx* ctx, const gdrr_form_factor* ff) {
     if (ctx->n_scans > 0) return GDRR_ERR_INVALID_ARG;     // scans hold the old table pointers
     if (!ff->form_factor) {
         if (ctx->opt.rayleigh_form_factor) return GDRR_ERR_INVALID_ARG;
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(ctx->d_ff_s); cudaFree(ctx->d_ff_a); cudaFree(ctx->d_ff_g);
+        dfree(ctx, ctx->d_ff_s); dfree(ctx, ctx->d_ff_a); dfree(ctx, ctx->d_ff_g);
         ctx->d_ff_s = ctx->d_ff_a = ctx->d_ff_g = nullptr;
         ctx->n_ff = 0;
         return GDRR_OK;
@@ -699,13 +780,13 @@ GDRR_API int gdrr_set_form_factor(gdrr_ctx* ctx, const gdrr_form_factor* ff) {
     float *ds = nullptr, *da = nullptr, *dg = nullptr;
     int rc = GDRR_OK;
     do {
-        if ((rc = upload(&ds, s.data(), s.size(), ctx->stream))) break;
-        if ((rc = upload(&da, A.data(), A.size(), ctx->stream))) break;
-        if ((rc = upload(&dg, G.data(), G.size(), ctx->stream))) break;
+        if ((rc = upload(ctx, &ds, s.data(), s.size()))) break;
+        if ((rc = upload(ctx, &da, A.data(), A.size()))) break;
+        if ((rc = upload(ctx, &dg, G.data(), G.size()))) break;
         if ((rc = cuda_err(cudaStreamSynchronize(ctx->stream)))) break;
     } while (0);
-    if (rc) { cudaFree(ds); cudaFree(da); cudaFree(dg); return rc; }
-    cudaFree(ctx->d_ff_s); cudaFree(ctx->d_ff_a); cudaFree(ctx->d_ff_g);
+    if (rc) { dfree(ctx, ds); dfree(ctx, da); dfree(ctx, dg); return rc; }
+    dfree(ctx, ctx->d_ff_s); dfree(ctx, ctx->d_ff_a); dfree(ctx, ctx->d_ff_g);
     ctx->d_ff_s = ds; ctx->d_ff_a = da; ctx->d_ff_g = dg;
     ctx->n_ff = n;
     ctx->ff_idx = (float)(1.0 / dx);
@@ -785,19 +866,27 @@ static bool source_pass_applies(const gdrr_ctx* ctx, bool rec) {
            (ctx->opt.photon_pool <= 0 || ctx->opt.local_majorant);
 }
 
-// Grows a source-record buffer to min(total, SRC_MAX) histories.  When the
-// memory is not there the buffer stays empty and the transport samples the
-// sources inline (the same arithmetic, so the same results).
-static void ensure_src(cudaStream_t s, float4** buf, uint64_t* cap, uint64_t total) {
+// Grows a source-record buffer to min(total, SRC_MAX) histories: the
+// context's from its device pool (owner given), a scan's with cudaMalloc
+// (owner NULL, on stream s).  When the memory is not there the buffer stays
+// empty and the transport samples the sources inline (the same arithmetic, so
+// the same results).
+static void ensure_src(const gdrr_ctx* owner, cudaStream_t s, float4** buf, uint64_t* cap, uint64_t total) {
     const uint64_t want = std::min(total, SRC_MAX);
     if (*cap >= want) return;
     if (*buf) {
-        cudaStreamSynchronize(s);
-        cudaFree(*buf);
+        if (owner) {
+            dfree(owner, *buf);
+        } else {
+            cudaStreamSynchronize(s);
+            cudaFree(*buf);
+        }
         *buf = nullptr;
         *cap = 0;
     }
-    if (cudaMalloc((void**)buf, want * MC_SRC_BYTES) == cudaSuccess) {
+    const cudaError_t e = owner ? dalloc(owner, buf, want * MC_SRC_BYTES)
+                                : cudaMalloc((void**)buf, want * MC_SRC_BYTES);
+    if (e == cudaSuccess) {
         *cap = want;
     } else {
         *buf = nullptr;
@@ -878,8 +967,10 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     if (total == 0) return GDRR_OK;
     const int nj = (int)jobs.size();
     if (nj > ctx->jobs_cap) {
-        if (ctx->d_jobs) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->d_jobs); ctx->d_jobs = nullptr; }
-        TRY_CUDA(cudaMalloc((void**)&ctx->d_jobs, sizeof(Job) * nj));
+        dfree(ctx, ctx->d_jobs);
+        ctx->d_jobs = nullptr;
+        ctx->jobs_cap = 0;
+        TRY_CUDA(dalloc(ctx, &ctx->d_jobs, sizeof(Job) * nj));
         ctx->jobs_cap = nj;
     }
     // pageable source: staged before the call returns, so the vector may die
@@ -903,7 +994,7 @@ static int mc_launch(gdrr_ctx* ctx, const std::vector<Job>& jobs, uint64_t total
     p.ray_ff = ctx->opt.rayleigh_form_factor;
     const bool rec = records_dev != nullptr;
     if (source_pass_applies(ctx, rec)) {
-        ensure_src(ctx->stream, &ctx->d_src, &ctx->src_cap, total);
+        ensure_src(ctx, ctx->stream, &ctx->d_src, &ctx->src_cap, total);
         return cuda_err(launch_transport(ctx, p, total, rec, ctx->stream, ctx->d_src, ctx->src_cap));
     }
     return cuda_err(launch_transport(ctx, p, total, rec, ctx->stream));
@@ -1000,7 +1091,7 @@ GDRR_API int gdrr_scan_create(gdrr_ctx* ctx, int32_t n_angles, const double* ang
         p.nearest_voxel = ctx->opt.nearest_voxel;
         p.scatter_filter = ctx->opt.scatter_filter;
         p.ray_ff = ctx->opt.rayleigh_form_factor;
-        if (source_pass_applies(ctx, false)) ensure_src(ctx->stream, &sc->d_src, &sc->src_cap, total);
+        if (source_pass_applies(ctx, false)) ensure_src(nullptr, ctx->stream, &sc->d_src, &sc->src_cap, total);
         if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
         const size_t tally_bytes = (size_t)n_angles * ctx->geo.nu * ctx->geo.nv * sizeof(int64_t);
@@ -1051,7 +1142,7 @@ GDRR_API int gdrr_autotune(gdrr_ctx* ctx, double angle_rad, uint64_t n_probe, ui
                            gdrr_mc_options* best_out) {
     if (!ctx || n_probe == 0 || !std::isfinite(angle_rad) || !geometry_ok(ctx, angle_rad)) return GDRR_ERR_INVALID_ARG;
     const size_t npix = (size_t)ctx->geo.nu * ctx->geo.nv;
-    if (!ctx->d_tune) TRY_CUDA(cudaMalloc((void**)&ctx->d_tune, 2 * npix * sizeof(int64_t)));
+    if (!ctx->d_tune) TRY_CUDA(dalloc(ctx, &ctx->d_tune, 2 * npix * sizeof(int64_t)));
     Job j;
     memset(&j, 0, sizeof j);
     j.f = make_frame(ctx->geo, angle_rad);
@@ -1136,9 +1227,10 @@ GDRR_API int gdrr_upsample(gdrr_ctx* ctx, const double* coarse_dev, int32_t cu, 
 static int denoise_scratch(gdrr_ctx* ctx, int nu, int nv) {
     const size_t need = std::max(denoise_scratch_doubles(nu, nv) * sizeof(double), denoise_fused_scratch_bytes(nu, nv));
     if (need > ctx->denoise_cap) {
-        if (ctx->d_denoise) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->d_denoise); ctx->d_denoise = nullptr; }
+        dfree(ctx, ctx->d_denoise);
+        ctx->d_denoise = nullptr;
         ctx->denoise_cap = 0;
-        TRY_CUDA(cudaMalloc((void**)&ctx->d_denoise, need));
+        TRY_CUDA(dalloc(ctx, &ctx->d_denoise, need));
         ctx->denoise_cap = need;
     }
     return GDRR_OK;
@@ -1188,8 +1280,8 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
     // scratch: prim, scat, coarse tally (int64 [npix] each), coarse S^ and S
     // (double [npix] each: enough for any bin factor), scalars, counters
     const size_t scratch = 5 * npix * 8 + 8 * sizeof(double) + GDRR_NSTATS * sizeof(unsigned long long) + 64;
-    if (!ctx->d_proj) TRY_CUDA(cudaMalloc(&ctx->d_proj, scratch));
-    if (!ctx->h_proj) TRY_CUDA(cudaMallocHost((void**)&ctx->h_proj, sizeof(ProjHost)));
+    if (!ctx->d_proj) TRY_CUDA(dalloc(ctx, &ctx->d_proj, scratch));
+    if (!ctx->h_proj && !(ctx->h_proj = take_proj_host())) return GDRR_ERR_OOM;
     for (cudaEvent_t& e : ctx->ev_proj)
         if (!e) TRY_CUDA(cudaEventCreate(&e));
     cudaEvent_t* ev = ctx->ev_proj;

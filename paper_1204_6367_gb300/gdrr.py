@@ -171,6 +171,7 @@ def lib():
             "gdrr_fdk_backproject": [vp, i32, vp, dbl, vp, vp, i32, vp],
             "gdrr_project": [vp, vp, vp, vp],
             "gdrr_probe_bounded_wait": [u64, vp],
+            "gdrr_release_memory": [],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -284,6 +285,11 @@ def gdrr_create(prob, stream=None) -> Context:
 
 def gdrr_destroy(ctx: Context):
     ctx.close()
+
+
+def gdrr_release_memory():
+    """Return the unused blocks of the contexts' device memory pools."""
+    _check("gdrr_release_memory", lib().gdrr_release_memory())
 
 
 def gdrr_set_options(ctx: Context, **kw):

@@ -133,3 +133,30 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(gd, small):
         r = gd.project(ctx, 10_000, 1, iters=20, smoothing_px=2.0)
         gd.gdrr_sync(ctx)
         assert int(r["stats"][0].item()) == 10_000
+
+
+def test_contexts_reuse_pool_memory_and_release_it(gd, small):
+    # contexts draw their device buffers from one pool per device that keeps
+    # the blocks of destroyed contexts: a run of create / project / destroy
+    # gives the same projection every time, and releasing the pool returns
+    # the memory to the driver
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    outs = []
+    for _ in range(3):
+        with gd.Context(small) as ctx:
+            o = gd.project(ctx, 300_000, 9, 0.3, beta=0.3, iters=50)
+            outs.append({k: o[k].cpu() for k in ("P_hat", "S_hat", "S", "N")})
+    for o in outs[1:]:
+        for k in o:
+            assert torch.equal(o[k], outs[0][k]), k
+    big = inputs.torso_problem(vox=4.0, nu=128, nv=96, det_px=0.776 * 4)
+    with gd.Context(big) as ctx:
+        gd.gdrr_mc_project(ctx, 2_000_000, 1)
+        gd.gdrr_sync(ctx)
+    torch.cuda.synchronize()
+    held = torch.cuda.mem_get_info()[0]
+    gd.gdrr_release_memory()
+    torch.cuda.synchronize()
+    freed = torch.cuda.mem_get_info()[0]
+    assert freed >= held and freed >= free0 - (256 << 20), (free0, held, freed)
