@@ -595,7 +595,7 @@ GDRR_API int gdrr_fit_zeta(const double* inv_sqrt_mAs, const double* ratio, int3
  * the same layout and index arithmetic as a Woodcock free flight, and nothing
  * else.  *seconds_out (host) receives the device time of those gathers; the
  * call synchronises the context stream.  Not part of the paper's method: it
- * measures the ceiling against which the transport's gather rate is judged. */
+ * measures the ceiling the transport's gather rate is compared with. */
 GDRR_API int gdrr_gather_roofline(gdrr_ctx* ctx, uint64_t n_cells, double* seconds_out);
 
 /* dst = (float)(src * scale) and dst = (double)src * scale over n device
