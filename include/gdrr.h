@@ -177,13 +177,13 @@ typedef struct {
                                   new histories each run on full warps (block_size and
                                   batch_min do not apply to it); -1: the lane form, one
                                   photon per lane with warp-batched services.  Runs
-                                  with records, nearest_voxel, scatter_filter or
-                                  rayleigh_form_factor always take the lane form.
-                                  Tallies, counters and records are the same for
-                                  every choice.  On the 2 mm torso the pool form ran
-                                  at 112 ms per 1e8 histories against 99 ms for the
-                                  lane form, so the lane form is the default and the
-                                  autotuner times both [-1]                            */
+                                  with records, nearest_voxel, scatter_filter,
+                                  rayleigh_form_factor or local_majorant always take
+                                  the lane form.  Tallies, counters and records are
+                                  the same for every choice.  On the 2 mm torso the
+                                  pool form ran at 125-158 ms per 1e8 histories
+                                  against 75 ms for the lane form, so the lane form is
+                                  the default and the autotuner times both [-1]       */
     int32_t local_majorant;    /* 1: delta tracking with local majorants, an option
                                   beside the paper's global Woodcock majorant: the
                                   macro-cell bounds (cell_shift, which must not be -1)
