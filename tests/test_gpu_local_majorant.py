@@ -222,3 +222,20 @@ def test_autotune_keeps_the_option(gd, small):
         assert best["local_majorant"] == 1 and best["cell_shift"] == 2 and best["photon_pool"] == -1
         got = gd.gdrr_mc_project(ctx, 150_000, 8)
         assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+
+
+def test_vacuum_cells_anisotropic_voxels_and_step_limit(gd, small):
+    # cells of bound zero (vacuum) are crossed without spending depth; the
+    # cell planes follow each axis's own voxel edge; a history that reaches
+    # max_steps at a flight draw ends as the oracle's does
+    import copy
+    prob = copy.deepcopy(small)
+    prob.density[prob.material == 0] = 0.0                  # air becomes vacuum
+    prob.voxel = (4.0, 3.0, 5.0)
+    n = 1500
+    for shift in (1, 2):
+        _same(_run(gd, prob, n, 41, phi=0.9, records=True, shift=shift), prob, n, 41, phi=0.9, records=True)
+    _same(_run(gd, prob, 200_000, 43, phi=2.3, shift=2), prob, 200_000, 43, phi=2.3)
+    st = _same(_run(gd, prob, 3000, 47, phi=0.2, records=True, shift=1, max_steps=2), prob, 3000, 47, phi=0.2,
+               records=True, max_steps=2)
+    assert st["step_limit"] > 0
