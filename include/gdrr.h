@@ -141,7 +141,9 @@ typedef struct {
     int32_t hist_per_thread;   /* histories a warp claims per lane at a time [8]    */
     int32_t batch_min;         /* lanes of a warp that must be waiting for an
                                   interaction, a tally or a new history before the
-                                  warp serves them together, 1..32 [16]            */
+                                  warp serves them together, 1..32 [16; 24 with
+                                  local_majorant, whose short flights bring the
+                                  services more often]                              */
     int32_t nearest_voxel;     /* 1: no density interpolation, each point takes its
                                   voxel's density and material (the speed variant of
                                   the paper's appendix); 0: trilinear [0]           */

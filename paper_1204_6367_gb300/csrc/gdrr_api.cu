@@ -477,7 +477,7 @@ void set_defaults(gdrr_mc_options* o) {
     if (o->max_steps <= 0) o->max_steps = 100000;
     if (o->block_size <= 0) o->block_size = 256;
     if (o->hist_per_thread <= 0) o->hist_per_thread = 8;
-    if (o->batch_min <= 0) o->batch_min = 16;
+    if (o->batch_min <= 0) o->batch_min = o->local_majorant ? 24 : 16;
     if (o->photon_pool == 0) o->photon_pool = -1;
 }
 

@@ -299,8 +299,11 @@ def gdrr_set_options(ctx: Context, **kw):
         if not hasattr(o, k):
             raise KeyError(k)
         setattr(o, k, v)
-    if "local_majorant" in kw and "cell_shift" not in kw:
-        o.cell_shift = 0                 # the default cell size of the chosen tracking
+    if "local_majorant" in kw:           # the defaults of the chosen tracking
+        if "cell_shift" not in kw:
+            o.cell_shift = 0
+        if "batch_min" not in kw:
+            o.batch_min = 0
     _check("gdrr_set_options", lib().gdrr_set_options(ctx.handle, ctypes.byref(o)))
 
 

@@ -146,6 +146,10 @@ def test_option_checks(gd, small):
             gd.gdrr_set_options(ctx, local_majorant=0)
             assert gd.gdrr_get_options(ctx)["cell_shift"] == max(1, round(math.log2(4.0 / vox)))
     with gd.Context(small) as ctx:
+        gd.gdrr_set_options(ctx, local_majorant=1)
+        assert gd.gdrr_get_options(ctx)["batch_min"] == 24          # the option's default
+        gd.gdrr_set_options(ctx, local_majorant=0)
+        assert gd.gdrr_get_options(ctx)["batch_min"] == 16
         for bad in (dict(local_majorant=2), dict(local_majorant=-1), dict(local_majorant=1, cell_shift=-1)):
             with pytest.raises(gd.GdrrError):
                 gd.gdrr_set_options(ctx, **bad)
