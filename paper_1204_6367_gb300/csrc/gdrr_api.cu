@@ -85,7 +85,8 @@ struct gdrr_ctx {
     // gdrr_project scratch: tallies, coarse tally and images, device scalars,
     // and the pinned host block the scalars come back through
     void* d_proj = nullptr;
-    ProjHost* h_proj = nullptr;
+    ProjHost* h_proj = nullptr;      // page-locked, from the reuse list
+    size_t h_proj_cap = 0;
     cudaEvent_t ev_proj[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // step / transport / denoise
     gdrr_mc_options opt{};
 };
@@ -166,28 +167,43 @@ void dfree(const gdrr_ctx* c, void* p) {
     if (p) cudaFreeAsync(p, c->stream);
 }
 
-// Pinned host records of gdrr_project's scalars, kept for reuse: a page-locked
-// allocation costs far more than the record, and contexts come and go.
+// Page-locked host blocks (staging of the context's tables, the staging
+// kernel's counters, gdrr_project's scalars), kept for reuse: a page-locked
+// allocation costs far more than the copies it serves, and contexts come and
+// go.  take_pinned hands out the smallest free block that is large enough.
+struct Pinned {
+    void* p = nullptr;
+    size_t cap = 0;
+};
 std::mutex g_host_mutex;
-std::vector<ProjHost*> g_host_free;
+std::vector<Pinned> g_host_free;
 
-ProjHost* take_proj_host() {
+Pinned take_pinned(size_t bytes) {
     {
         std::lock_guard<std::mutex> lock(g_host_mutex);
-        if (!g_host_free.empty()) {
-            ProjHost* h = g_host_free.back();
-            g_host_free.pop_back();
-            return h;
+        size_t best = g_host_free.size();
+        for (size_t i = 0; i < g_host_free.size(); ++i)
+            if (g_host_free[i].cap >= bytes && (best == g_host_free.size() || g_host_free[i].cap < g_host_free[best].cap))
+                best = i;
+        if (best < g_host_free.size()) {
+            const Pinned b = g_host_free[best];
+            g_host_free.erase(g_host_free.begin() + (std::ptrdiff_t)best);
+            return b;
         }
     }
-    ProjHost* h = nullptr;
-    return cudaMallocHost((void**)&h, sizeof(ProjHost)) == cudaSuccess ? h : nullptr;
+    Pinned b;
+    b.cap = std::max<size_t>(bytes, 4096);
+    if (cudaMallocHost(&b.p, b.cap) != cudaSuccess) {
+        cudaGetLastError();
+        return Pinned();
+    }
+    return b;
 }
 
-void give_proj_host(ProjHost* h) {
-    if (!h) return;
+void give_pinned(Pinned b) {
+    if (!b.p) return;
     std::lock_guard<std::mutex> lock(g_host_mutex);
-    g_host_free.push_back(h);
+    g_host_free.push_back(b);
 }
 
 #define TRY_CUDA(x)                               \
@@ -204,21 +220,41 @@ int upload(const gdrr_ctx* c, T** dst, const T* src, size_t n) {
 }
 
 // The context's small tables and counters in one device allocation, staged
-// in one host buffer and copied once: each piece starts on a 256-byte
-// boundary; pieces without source data are zero.
+// in one page-locked host block and copied once: each piece starts on a
+// 256-byte boundary; pieces without source data are zero.  The sources must
+// stay alive until commit, which waits for the copy.
 struct Arena {
-    std::vector<char> host;
+    struct Piece {
+        const void* src;
+        size_t off, bytes;
+    };
+    std::vector<Piece> pieces;
     std::vector<std::function<void(char*)>> bind;
+    size_t size = 0;
     template <typename T>
     void add(T** dst, const T* src, size_t n) {
-        const size_t off = (host.size() + 255) / 256 * 256;
-        host.resize(off + std::max<size_t>(n, 1) * sizeof(T), 0);
-        if (src && n) memcpy(host.data() + off, src, n * sizeof(T));
+        const size_t off = (size + 255) / 256 * 256;
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        pieces.push_back({n ? src : nullptr, off, bytes});
+        size = off + bytes;
         bind.push_back([dst, off](char* base) { *dst = reinterpret_cast<T*>(base + off); });
     }
     int commit(const gdrr_ctx* c, void** base) {
-        TRY_CUDA(dalloc(c, base, host.size()));
-        TRY_CUDA(cudaMemcpyAsync(*base, host.data(), host.size(), cudaMemcpyHostToDevice, c->stream));
+        Pinned st = take_pinned(size);
+        std::vector<char> pageable;                   // only when page-locked memory is short
+        char* h = static_cast<char*>(st.p);
+        if (!h) {
+            pageable.resize(size);
+            h = pageable.data();
+        }
+        memset(h, 0, size);
+        for (const Piece& q : pieces)
+            if (q.src) memcpy(h + q.off, q.src, q.bytes);
+        cudaError_t e = dalloc(c, base, size);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(*base, h, size, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        give_pinned(st);
+        TRY_CUDA(e);
         for (auto& b : bind) b(static_cast<char*>(*base));
         return GDRR_OK;
     }
@@ -289,9 +325,9 @@ __global__ void build_cells_kernel(const uint2* __restrict__ vox, int nx, int ny
 
 // (Re)build the macro-cell table for cells of 2^shift voxels per edge, or
 // drop it (shift < 0).  Synchronises the context stream.
-int build_cells(gdrr_ctx* c, int shift) {
+int build_cells(gdrr_ctx* c, int shift, bool sync) {
     cudaStream_t s = c->stream;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return GDRR_ERR_CUDA;
+    if (sync && cudaStreamSynchronize(s) != cudaSuccess) return GDRR_ERR_CUDA;
     dfree(c, c->d_cells);
     c->d_cells = nullptr;
     c->cell_shift = -1;
@@ -312,7 +348,7 @@ int build_cells(gdrr_ctx* c, int shift) {
             reinterpret_cast<unsigned int*>(c->d_cells));
         rc = cuda_err(cudaGetLastError());
     }
-    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+    if (!rc && sync) rc = cuda_err(cudaStreamSynchronize(s));
     if (rc) {
         dfree(c, c->d_cells);
         c->d_cells = nullptr;
@@ -326,7 +362,11 @@ int build_cells(gdrr_ctx* c, int shift) {
 // Copy the host phantom to the device and stage it into ctx->d_vox (n_rec
 // bricked records, padding zero).  Returns the per-material maximum density
 // in rho_max, or GDRR_ERR_INVALID_ARG when a voxel is invalid.  Synchronises.
-int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, std::vector<double>& rho_max) {
+// Queues the phantom's staging on the context stream: the copies, the staging
+// kernel and the read-back of its counters into aux (page-locked, 1 + n_mat
+// words), which are valid once the stream has been synchronised; then
+// stage_phantom_finish checks them.
+int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, unsigned int* aux) {
     const int64_t nvox = (int64_t)ph.nx * ph.ny * ph.nz;
     cudaStream_t s = c->stream;
     // the inputs staged in one temporary allocation: densities, counters,
@@ -339,7 +379,7 @@ int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, std::vector
     unsigned int* d_aux = nullptr;
     uint8_t* d_mat = nullptr;
     int rc = GDRR_OK;
-    std::vector<unsigned int> aux(1 + c->n_mat, 0u);
+    const size_t aux_bytes = sizeof(unsigned int) * (1 + (size_t)c->n_mat);
     do {
         if ((rc = cuda_err(dalloc(c, &c->d_vox, n_rec * sizeof(uint2))))) break;
         if ((rc = cuda_err(cudaMemsetAsync(c->d_vox, 0, n_rec * sizeof(uint2), s)))) break;
@@ -349,17 +389,20 @@ int stage_phantom(gdrr_ctx* c, const gdrr_phantom& ph, size_t n_rec, std::vector
         d_mat = reinterpret_cast<uint8_t*>(d_tmp + mat_off);
         if ((rc = cuda_err(cudaMemcpyAsync(d_den, ph.density, den_bytes, cudaMemcpyHostToDevice, s)))) break;
         if ((rc = cuda_err(cudaMemcpyAsync(d_mat, ph.material, (size_t)nvox, cudaMemcpyHostToDevice, s)))) break;
-        if ((rc = cuda_err(cudaMemsetAsync(d_aux, 0, aux.size() * sizeof(unsigned int), s)))) break;
+        if ((rc = cuda_err(cudaMemsetAsync(d_aux, 0, aux_bytes, s)))) break;
         const int block = 256;
         stage_voxels_kernel<<<(unsigned)((nvox + block - 1) / block), block, 0, s>>>(
             d_mat, d_den, ph.nx, ph.ny, ph.nz, c->n_mat, c->bsy, c->bsz, c->d_vox, d_aux);
         if ((rc = cuda_err(cudaGetLastError()))) break;
-        if ((rc = cuda_err(cudaMemcpyAsync(aux.data(), d_aux, aux.size() * sizeof(unsigned int),
-                                           cudaMemcpyDeviceToHost, s)))) break;
-        if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
+        if ((rc = cuda_err(cudaMemcpyAsync(aux, d_aux, aux_bytes, cudaMemcpyDeviceToHost, s)))) break;
     } while (0);
-    dfree(c, d_tmp);
-    if (rc) return rc;
+    dfree(c, d_tmp);                                  // after the read-back, in stream order
+    return rc;
+}
+
+// The staging's counters, read back by stage_phantom: any invalid voxel
+// rejects the phantom; else each material's largest density.
+int stage_phantom_finish(const gdrr_ctx* c, const unsigned int* aux, std::vector<double>& rho_max) {
     if (aux[0]) return GDRR_ERR_INVALID_ARG;
     rho_max.assign(c->n_mat, 0.0);
     for (int m = 0; m < c->n_mat; ++m) {
@@ -502,7 +545,10 @@ int free_ctx(gdrr_ctx* c) {
                     c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells, c->d_proj, c->d_src};
     if (c->pool)
         for (void* b : bufs) dfree(c, b);
-    give_proj_host(c->h_proj);
+    Pinned hp;
+    hp.p = c->h_proj;
+    hp.cap = c->h_proj_cap;
+    give_pinned(hp);
     for (cudaEvent_t e : c->ev_proj)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -589,6 +635,7 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
     if (!geometry_ok(c, 0.0)) { delete c; return GDRR_ERR_INVALID_ARG; }
 
     int rc = GDRR_OK;
+    Pinned aux_blk;                   // the staging kernel's counters, read back
     do {
         if (cudaGetDevice(&c->device) != cudaSuccess) { rc = GDRR_ERR_CUDA; break; }
         if ((rc = cuda_err(device_pool(c->device, &c->pool)))) break;
@@ -599,27 +646,18 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         // material coefficients in mm^-1 per g/cm^3 (mu_hat cm^2/g * 0.1)
         std::vector<float> tab(nt);
         for (int64_t i = 0; i < nt; ++i) tab[i] = (float)((double)mt.mu_hat[i] * 0.1);
-        // the phantom is validated, reduced and bricked on the device
+        // the phantom is validated, reduced and bricked on the device, and the
+        // macro-cell table built from it, while the host builds the tables below
         cudaStream_t s = c->stream;
         const int nbx = (ph.nx + 3) / 4, nby = (ph.ny + 1) / 2, nbz = (ph.nz + 1) / 2;
         c->bsy = 16 * nbx;
         c->bsz = 16 * nbx * nby;
-        std::vector<double> rho_max;
-        if ((rc = stage_phantom(c, ph, (size_t)16 * nbx * nby * nbz, rho_max))) break;
+        aux_blk = take_pinned(sizeof(unsigned int) * (1 + (size_t)mt.n_materials));
+        if (!aux_blk.p) { rc = GDRR_ERR_OOM; break; }
+        unsigned int* aux = static_cast<unsigned int*>(aux_blk.p);
+        if ((rc = stage_phantom(c, ph, (size_t)16 * nbx * nby * nbz, aux))) break;
         if (c->opt.cell_shift == 0) c->opt.cell_shift = default_cell_shift(c, false);
-        if ((rc = build_cells(c, c->opt.cell_shift))) break;
-        // Woodcock majorant nodes: max over materials of the largest density of
-        // that material times its total coefficient, with a 1e-5 margin.
-        std::vector<float> major(mt.n_energies);
-        for (int e = 0; e < mt.n_energies; ++e) {
-            double mx = 0.0;
-            for (int m = 0; m < mt.n_materials; ++m) {
-                const float* t = tab.data() + (size_t)m * 3 * mt.n_energies;
-                const double tot = ((double)t[e] + (double)t[mt.n_energies + e]) + (double)t[2 * mt.n_energies + e];
-                mx = std::max(mx, rho_max[m] * tot);
-            }
-            major[e] = (float)(mx * (1.0 + 1e-5));
-        }
+        if ((rc = build_cells(c, c->opt.cell_shift, false))) break;
         std::vector<float> bin_e(sp.n_bins);
         for (int b = 0; b < sp.n_bins; ++b) bin_e[b] = (float)sp.energy_kev[b];
         c->n_guide_pix = npix;
@@ -672,13 +710,30 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         for (int i = 0; i < npix; ++i) fsum += bowtie->fluence[i];
         std::vector<double> wnorm(npix);
         for (int i = 0; i < npix; ++i) wnorm[i] = bowtie->fluence[i] / fsum;
+        const std::vector<uint32_t> kcdf_pix = kcdf_of(cdf_pix);
+
+        // the staging's counters: valid phantom, each material's largest density
+        if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
+        std::vector<double> rho_max;
+        if ((rc = stage_phantom_finish(c, aux, rho_max))) break;
+        // Woodcock majorant nodes: max over materials of the largest density of
+        // that material times its total coefficient, with a 1e-5 margin.
+        std::vector<float> major(mt.n_energies);
+        for (int e = 0; e < mt.n_energies; ++e) {
+            double mx = 0.0;
+            for (int m = 0; m < mt.n_materials; ++m) {
+                const float* t = tab.data() + (size_t)m * 3 * mt.n_energies;
+                const double tot = ((double)t[e] + (double)t[mt.n_energies + e]) + (double)t[2 * mt.n_energies + e];
+                mx = std::max(mx, rho_max[m] * tot);
+            }
+            major[e] = (float)(mx * (1.0 + 1e-5));
+        }
 
         Arena ar;
         ar.add(&c->d_tab, tab.data(), tab.size());
         ar.add(&c->d_major, major.data(), major.size());
         ar.add(&c->d_resp, dt.response, (size_t)dt.n_energies);
         ar.add(&c->d_bin_e, bin_e.data(), bin_e.size());
-        const std::vector<uint32_t> kcdf_pix = kcdf_of(cdf_pix);
         ar.add(&c->d_kcdf_pix, kcdf_pix.data(), kcdf_pix.size());
         ar.add(&c->d_guide_pix, guide_pix.data(), guide_pix.size());
         ar.add(&c->d_kcdf_e, kcdf_e.data(), kcdf_e.size());
@@ -691,10 +746,11 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
         ar.add(&c->d_stats, (const unsigned long long*)nullptr, GDRR_NSTATS);
         ar.add(&c->d_flag, (const int*)nullptr, 1);
         ar.add(&c->d_status, (const int*)nullptr, 1);
-        if ((rc = ar.commit(c, &c->d_arena))) break;
-        // the host vectors above die at return: finish the copies first
-        if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
+        if ((rc = ar.commit(c, &c->d_arena))) break;       // waits for its copy
     } while (0);
+    // no copy may still target the counters' block when it goes back
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess && !rc) rc = GDRR_ERR_CUDA;
+    give_pinned(aux_blk);
     if (rc) { free_ctx(c); return rc; }
     *out = c;
     return GDRR_OK;
@@ -728,7 +784,7 @@ GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
     if (n.local_majorant && n.cell_shift < 0) return GDRR_ERR_INVALID_ARG;   // the cells are the majorant
     if (n.cell_shift != ctx->cell_shift) {
         if (ctx->n_scans > 0) return GDRR_ERR_INVALID_ARG;     // scans hold the old table pointer
-        const int rc = build_cells(ctx, n.cell_shift);
+        const int rc = build_cells(ctx, n.cell_shift, true);
         if (rc) {
             ctx->opt.cell_shift = ctx->cell_shift;              // -1: the table is gone
             return rc;
@@ -1281,7 +1337,12 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
     // (double [npix] each: enough for any bin factor), scalars, counters
     const size_t scratch = 5 * npix * 8 + 8 * sizeof(double) + GDRR_NSTATS * sizeof(unsigned long long) + 64;
     if (!ctx->d_proj) TRY_CUDA(dalloc(ctx, &ctx->d_proj, scratch));
-    if (!ctx->h_proj && !(ctx->h_proj = take_proj_host())) return GDRR_ERR_OOM;
+    if (!ctx->h_proj) {
+        const Pinned hp = take_pinned(sizeof(ProjHost));
+        if (!hp.p) return GDRR_ERR_OOM;
+        ctx->h_proj = static_cast<ProjHost*>(hp.p);
+        ctx->h_proj_cap = hp.cap;
+    }
     for (cudaEvent_t& e : ctx->ev_proj)
         if (!e) TRY_CUDA(cudaEventCreate(&e));
     cudaEvent_t* ev = ctx->ev_proj;
