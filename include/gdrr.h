@@ -558,7 +558,9 @@ typedef struct {
 } gdrr_projection_info;
 
 /* Steps 1-4 of Section 2.2 in one call, every step a kernel on the context
- * stream and every scalar computed on the device:
+ * stream (Step 1 on a side stream of the context, forked from and joined
+ * back to it, so that the ray trace fills the SMs the transport leaves at
+ * its end) and every scalar computed on the device:
  *   1  P = ray-traced primary (gdrr_raytrace_primary);
  *   2  fixed-point tallies of n_photons histories (gdrr_mc_project with
  *      history_offset 0, into zeroed tallies), P^ and S^ per source photon

@@ -88,6 +88,10 @@ struct gdrr_ctx {
     ProjHost* h_proj = nullptr;      // page-locked, from the reuse list
     size_t h_proj_cap = 0;
     cudaEvent_t ev_proj[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // step / transport / denoise
+    // gdrr_project's side stream (the ray trace, beside the transport) and
+    // its fork and join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     gdrr_mc_options opt{};
 };
 
@@ -551,6 +555,12 @@ int free_ctx(gdrr_ctx* c) {
     give_pinned(hp);
     for (cudaEvent_t e : c->ev_proj)
         if (e) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
     delete c;
     return GDRR_OK;
 }
@@ -876,7 +886,7 @@ GDRR_API int gdrr_air_scan(gdrr_ctx* ctx, double* I0_dev) {
     return cuda_err(launch_air(p, I0_dev, ctx->stream));
 }
 
-static int raytrace(gdrr_ctx* ctx, double angle_rad, double* P_dev, bool siddon) {
+static int raytrace(gdrr_ctx* ctx, double angle_rad, double* P_dev, bool siddon, cudaStream_t stream) {
     if (!ctx || !P_dev || !std::isfinite(angle_rad)) return GDRR_ERR_INVALID_ARG;
     if (!geometry_ok(ctx, angle_rad)) return GDRR_ERR_INVALID_ARG;
     RtParams p;
@@ -891,15 +901,15 @@ static int raytrace(gdrr_ctx* ctx, double angle_rad, double* P_dev, bool siddon)
     p.du = (float)ctx->geo.du_mm; p.dv = (float)ctx->geo.dv_mm;
     p.half_step = (float)(0.5 * std::min(ctx->vox[0], std::min(ctx->vox[1], ctx->vox[2])));
     p.f = make_frame(ctx->geo, angle_rad);
-    return cuda_err(siddon ? launch_rt_siddon(p, P_dev, ctx->stream) : launch_rt(p, P_dev, ctx->stream));
+    return cuda_err(siddon ? launch_rt_siddon(p, P_dev, stream) : launch_rt(p, P_dev, stream));
 }
 
 GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_dev) {
-    return raytrace(ctx, angle_rad, P_dev, false);
+    return raytrace(ctx, angle_rad, P_dev, false, ctx->stream);
 }
 
 GDRR_API int gdrr_raytrace_primary_siddon(gdrr_ctx* ctx, double angle_rad, double* P_dev) {
-    return raytrace(ctx, angle_rad, P_dev, true);
+    return raytrace(ctx, angle_rad, P_dev, true, ctx->stream);
 }
 
 static int launch_grid(const gdrr_ctx* ctx, uint64_t total, bool rec) {
@@ -1345,6 +1355,9 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
     }
     for (cudaEvent_t& e : ctx->ev_proj)
         if (!e) TRY_CUDA(cudaEventCreate(&e));
+    if (!ctx->side) TRY_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    if (!ctx->ev_fork) TRY_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    if (!ctx->ev_join) TRY_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     cudaEvent_t* ev = ctx->ev_proj;
     char* base = static_cast<char*>(ctx->d_proj);
     int64_t* prim = out->prim_tally ? out->prim_tally : reinterpret_cast<int64_t*>(base);
@@ -1362,8 +1375,7 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
     bool fused = false;
     int rc = GDRR_OK;
     TRY_CUDA(cudaEventRecord(ev[0], st));
-    // Step 1
-    if ((rc = gdrr_raytrace_primary(ctx, pr->angle_rad, out->P))) return rc;
+    TRY_CUDA(cudaEventRecord(ctx->ev_fork, st));
     // Step 2: zeroed tallies and counters, transport, signal per source photon
     TRY_CUDA(cudaMemsetAsync(prim, 0, npix * sizeof(int64_t), st));
     TRY_CUDA(cudaMemsetAsync(scat, 0, npix * sizeof(int64_t), st));
@@ -1374,6 +1386,12 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
                               reinterpret_cast<uint64_t*>(stats), nullptr)))
         return rc;
     TRY_CUDA(cudaEventRecord(ev[3], st));
+    // Step 1 on the side stream, queued behind the transport: the transport's
+    // grid holds every SM's registers, so the ray trace's blocks take the SMs
+    // its persistent blocks leave at the end of the launch; Step 4 joins it
+    TRY_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    if ((rc = raytrace(ctx, pr->angle_rad, out->P, false, ctx->side))) return rc;
+    TRY_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
     TRY_CUDA(launch_finalize(prim, (int64_t)npix, t2s, out->P_hat, ctx->d_flag, st));
     TRY_CUDA(launch_finalize(scat, (int64_t)npix, t2s, out->S_hat, ctx->d_flag, st));
     // Step 3: coarse grid, scalars on the device, Eq. 5, upsampling
@@ -1385,7 +1403,8 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
     if ((rc = denoise_on_ctx(ctx, shc, sc, cu, cv, 0.0, 0.0, scal, omega, pr->iters, &fused))) return rc;
     TRY_CUDA(cudaEventRecord(ev[5], st));
     TRY_CUDA(launch_upsample(sc, cu, cv, f, out->S, st));
-    // Step 4
+    // Step 4 (needs Step 1's primary)
+    TRY_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     const double alpha = sqrt((double)pr->n_photons / (pr->zeta * pr->mAs));
     TRY_CUDA(launch_noise(out->P_hat, out->P, out->S_hat, out->S, (int64_t)npix, alpha, out->N, st));
     TRY_CUDA(cudaEventRecord(ev[1], st));
