@@ -544,6 +544,7 @@ int default_cell_shift(const gdrr_ctx* c, bool local_majorant) {
 
 int free_ctx(gdrr_ctx* c) {
     if (!c) return GDRR_OK;
+    if (c->side) cudaStreamSynchronize(c->side);   // a projection's ray trace reads the tables
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->d_vox, c->d_arena, c->d_jobs, c->d_denoise, c->d_tune,
                     c->d_ff_s, c->d_ff_a, c->d_ff_g, c->d_cells, c->d_proj, c->d_src};
@@ -1329,6 +1330,16 @@ GDRR_API int gdrr_denoise_scatter(gdrr_ctx* ctx, const double* S_hat_dev, double
     return denoise_on_ctx(ctx, S_hat_dev, S_dev, nu, nv, count_scale, beta, nullptr, omega, iters, nullptr);
 }
 
+// Waits for a stream when it goes out of scope, once armed: a projection
+// that returns early never leaves its side stream's ray trace running.
+struct StreamGuard {
+    cudaStream_t s = nullptr;
+    bool armed = false;
+    ~StreamGuard() {
+        if (armed) cudaStreamSynchronize(s);
+    }
+};
+
 GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_projection_out* out,
                           gdrr_projection_info* info) {
     if (!ctx || !pr || !out) return GDRR_ERR_INVALID_ARG;
@@ -1390,6 +1401,9 @@ GDRR_API int gdrr_project(gdrr_ctx* ctx, const gdrr_projection* pr, const gdrr_p
     // grid holds every SM's registers, so the ray trace's blocks take the SMs
     // its persistent blocks leave at the end of the launch; Step 4 joins it
     TRY_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    StreamGuard side_done;
+    side_done.s = ctx->side;
+    side_done.armed = true;
     if ((rc = raytrace(ctx, pr->angle_rad, out->P, false, ctx->side))) return rc;
     TRY_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
     TRY_CUDA(launch_finalize(prim, (int64_t)npix, t2s, out->P_hat, ctx->d_flag, st));
