@@ -168,10 +168,13 @@ typedef struct {
                                   times the material's coefficient, raised by 2^-10
                                   against rounding); a tentative collision above it is
                                   virtual without the gathers.  The bound is never below
-                                  the mu the gathers would give, so tallies, counters and
-                                  records are the same for every cell_shift; only
-                                  GDRR_ST_CELL_SKIPS and the time change.  Changing it
-                                  rebuilds the cell table (not while a scan exists).   */
+                                  the mu the gathers would give, so with the global
+                                  majorant tallies, counters and records are the same
+                                  for every cell_shift; only GDRR_ST_CELL_SKIPS and the
+                                  time change.  With local_majorant the cells are the
+                                  majorant itself, and the draws depend on their size.
+                                  Changing it rebuilds the cell table (not while a scan
+                                  exists).                                              */
     int32_t photon_pool;       /* photons per thread, 1..3, in the shared-memory pool
                                   of the pool form of the transport: blocks of 256
                                   threads move photons between warps so that free
