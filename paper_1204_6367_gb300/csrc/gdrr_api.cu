@@ -906,10 +906,12 @@ static int raytrace(gdrr_ctx* ctx, double angle_rad, double* P_dev, bool siddon,
 }
 
 GDRR_API int gdrr_raytrace_primary(gdrr_ctx* ctx, double angle_rad, double* P_dev) {
+    if (!ctx) return GDRR_ERR_INVALID_ARG;
     return raytrace(ctx, angle_rad, P_dev, false, ctx->stream);
 }
 
 GDRR_API int gdrr_raytrace_primary_siddon(gdrr_ctx* ctx, double angle_rad, double* P_dev) {
+    if (!ctx) return GDRR_ERR_INVALID_ARG;
     return raytrace(ctx, angle_rad, P_dev, true, ctx->stream);
 }
 

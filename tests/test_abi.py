@@ -109,8 +109,59 @@ def test_projection_structs_match_the_header():
     from paper_1204_6367_gb300 import gdrr
     text = open(os.path.join(ROOT, "include", "gdrr.h")).read()
     for cname, cls in (("gdrr_projection", gdrr.Projection), ("gdrr_projection_out", gdrr.ProjectionOut),
-                       ("gdrr_projection_info", gdrr.ProjectionInfo)):
+                       ("gdrr_projection_info", gdrr.ProjectionInfo), ("gdrr_mc_options", gdrr.McOptions)):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + r";", text).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         fields = re.findall(r"\b(\w+)\s*;", body)
         assert fields == [f for f, _ in cls._fields_], cname
+
+
+def test_stats_layout_matches_the_header():
+    # the counters' enum of the header and the binding's slots: the method's
+    # eleven counters, then the cell-test skips and the cell crossings
+    import re
+    from paper_1204_6367_gb300 import gdrr
+    text = open(os.path.join(ROOT, "include", "gdrr.h")).read()
+    body = re.search(r"enum \{\s*(GDRR_ST_HISTORIES[^}]*)\}", text).group(1)
+    names = [n.split("=")[0].strip() for n in body.replace("\n", " ").split(",") if n.strip()]
+    assert names[-1] == "GDRR_NSTATS" and len(names) - 1 == gdrr.GDRR_NSTATS
+    assert names.index("GDRR_ST_CELL_SKIPS") == gdrr.ST_CELL_SKIPS
+    assert names.index("GDRR_ST_CELL_CROSSINGS") == gdrr.ST_CELL_CROSSINGS
+    v = np.arange(gdrr.GDRR_NSTATS, dtype=np.uint64) * 3 + 1
+    d = gdrr.stats_dict(v.view(np.int64))
+    assert [d[k] for k in gdrr.STAT_NAMES] == [int(x) for x in v[:len(gdrr.STAT_NAMES)]]
+    assert d["crossings"] == int(v[gdrr.ST_CELL_CROSSINGS]) and "cell_skips" not in d
+
+
+def test_option_helper_takes_the_tracking_defaults(monkeypatch):
+    # gdrr_set_options reads the context's options, applies the keywords and
+    # writes them back; switching the tracking resets cell_shift and batch_min
+    # to 0 (the library's defaults for that tracking) unless they are given
+    import ctypes as ct
+    from paper_1204_6367_gb300 import gdrr
+    written = []
+
+    class FakeLib:
+        def gdrr_get_options(self, handle, ref):
+            o = ct.cast(ref, ct.POINTER(gdrr.McOptions)).contents
+            o.cell_shift, o.batch_min, o.block_size, o.local_majorant = 1, 16, 512, 0
+            return 0
+
+        def gdrr_set_options(self, handle, ref):
+            o = ct.cast(ref, ct.POINTER(gdrr.McOptions)).contents
+            written.append({k: getattr(o, k) for k, _ in gdrr.McOptions._fields_})
+            return 0
+
+    monkeypatch.setattr(gdrr, "lib", lambda: FakeLib())
+
+    class Ctx:
+        handle = None
+
+    gdrr.gdrr_set_options(Ctx(), local_majorant=1)
+    gdrr.gdrr_set_options(Ctx(), local_majorant=1, cell_shift=3, batch_min=20)
+    gdrr.gdrr_set_options(Ctx(), block_size=256)
+    assert (written[0]["local_majorant"], written[0]["cell_shift"], written[0]["batch_min"]) == (1, 0, 0)
+    assert (written[1]["cell_shift"], written[1]["batch_min"]) == (3, 20)
+    assert (written[2]["cell_shift"], written[2]["batch_min"], written[2]["block_size"]) == (1, 16, 256)
+    with pytest.raises(KeyError):
+        gdrr.gdrr_set_options(Ctx(), no_such_option=1)
