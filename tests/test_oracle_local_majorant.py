@@ -317,3 +317,19 @@ def test_torso_fewer_flights_same_images():
         unit = (A.sum() + B.sum()) / (stw[key] + stl[key])
         sig = 1.5 * np.sqrt((A + B) / unit) * unit
         assert np.all(np.abs(A - B) <= 5.0 * sig + 3.0 * unit), np.abs(A - B).max() / unit
+
+
+def test_fp64_histories_follow_the_fp32_histories(small):
+    # The same streams in FP32 (the parity reference) and FP64 (the accuracy
+    # reference): rounding can flip a decision only where it sits within
+    # ~1e-7 of a threshold, so nearly every history ends the same way, and
+    # the per-history counts agree.
+    n = 20000
+    _, _, s32, r32 = oracle.mc_run(small, n, seed=13, records=True, local_majorant=True, cell_shift=2)
+    _, _, s64, r64 = oracle.mc_run(small, n, seed=13, records=True, local_majorant=True, cell_shift=2,
+                                   precision=64)
+    same = (r32["outcome"] == r64["outcome"]) & (r32["pixel"] == r64["pixel"]) & \
+           (r32["n_steps"] == r64["n_steps"]) & (r32["rng_blocks"] == r64["rng_blocks"])
+    assert same.mean() > 0.995, same.mean()
+    for k in ("steps", "virtual", "rayleigh", "compton", "photo", "crossings"):
+        assert abs(s32[k] - s64[k]) <= 0.005 * s32[k] + 5, (k, s32[k], s64[k])
