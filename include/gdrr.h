@@ -256,8 +256,9 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
 GDRR_API void gdrr_destroy(gdrr_ctx* ctx);
 
 /* Return the unused blocks of the contexts' device memory pools (on every
- * device) to the driver; memory of live contexts stays.  GDRR_ERR_CUDA if a
- * pool cannot be trimmed. */
+ * device), and the page-locked host staging blocks kept for reuse, to the
+ * driver; memory of live contexts stays.  GDRR_ERR_CUDA if a pool cannot be
+ * trimmed or a host block freed. */
 GDRR_API int gdrr_release_memory(void);
 
 /* Static description of an error code. */

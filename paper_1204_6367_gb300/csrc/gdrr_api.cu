@@ -770,10 +770,18 @@ GDRR_API int gdrr_create(const gdrr_geometry* geometry, const gdrr_phantom* phan
 GDRR_API void gdrr_destroy(gdrr_ctx* ctx) { free_ctx(ctx); }
 
 GDRR_API int gdrr_release_memory(void) {
-    std::lock_guard<std::mutex> lock(g_pool_mutex);
-    for (cudaMemPool_t p : g_pool)
-        if (p && cudaMemPoolTrimTo(p, 0) != cudaSuccess) return GDRR_ERR_CUDA;
-    return GDRR_OK;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        for (cudaMemPool_t p : g_pool)
+            if (p && cudaMemPoolTrimTo(p, 0) != cudaSuccess) return GDRR_ERR_CUDA;
+    }
+    // the page-locked host blocks on the reuse list (none of them in use)
+    std::lock_guard<std::mutex> lock(g_host_mutex);
+    int rc = GDRR_OK;
+    for (const Pinned& b : g_host_free)
+        if (cudaFreeHost(b.p) != cudaSuccess) rc = GDRR_ERR_CUDA;
+    g_host_free.clear();
+    return rc;
 }
 
 GDRR_API int gdrr_set_options(gdrr_ctx* ctx, const gdrr_mc_options* o) {
